@@ -1,0 +1,19 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device and the built library")
+    config.addinivalue_line("markers", "slow: statistical tests that take tens of seconds")
+
+
+@pytest.fixture(scope="session")
+def oracle():
+    from oracle import ipa_oracle
+    return ipa_oracle
