@@ -1,0 +1,209 @@
+/*
+ * ipanema.h -- C ABI of the GB300 unbinned-likelihood library.
+ *
+ * The library evaluates, on one GPU, the per-event normalised PDF of an
+ * unbinned maximum-likelihood fit (Ipanema-beta, arXiv:1706.01420), takes
+ * -w log P per event and reduces it deterministically in FP64 to the negative
+ * log-likelihood (NLL) and its gradient; it generates pseudo-experiments by
+ * accept-reject and fits many of them at once.
+ *
+ * Paper passages (section numbers of arXiv:1706.01420):
+ *   Sec. 3 (Example 1)  event-parallel PDF kernel, analytic normalisation,
+ *                       log of the signal/background mixture, sum of logs,
+ *                       FCN = -log L with errors at Delta FCN = 1/2, MIGRAD/HESSE;
+ *   Sec. 4 (Example 2)  decay-time x helicity-angle fit of Bs -> J/psi K K:
+ *                       P wave (3 polarisations) + S wave; Parameter/Free with
+ *                       limits, Cat (per-category event array);
+ *   Sec. 7 (Example 5)  toy generation by accept-reject with a counter-based
+ *                       generator, Poisson-fluctuated counts drawn on the host;
+ *   App. A-C            ParamBox, Parameter and Cat classes.
+ *
+ * Model (the paper prints no formula; this is the reading the library uses):
+ *   g(tau)  = 1/2 exp(-Gamma tau + Gamma^2 sigma^2 / 2) erfc((Gamma sigma^2 - tau)/(sqrt2 sigma)),
+ *             tau = t - mu: exp(-Gamma t) convolved with a Gaussian of width sigma;
+ *   I_T     = int_{t_lo}^{t_hi} g(t - mu) dt (closed form);
+ *   A(Omega)= sum_{k=1..10} h_k f_k(cos thK, cos thmu, phi)   (4D model only),
+ *             I_Omega = 16 pi / 9;
+ *   P       = (1 - f_b) g/I_T [A/I_Omega] + f_b / V,   V = volume of the box;
+ *   NLL     = -sum_e w_e log P_e   (w_e = 1 when no weight column is given).
+ *
+ * Conventions for every call:
+ *   - Event columns, theta and outputs are DEVICE pointers (cudaMalloc'd or torch
+ *     CUDA tensors) unless a parameter says "host".  The caller owns them; the
+ *     library never frees or keeps them after the call returns.
+ *   - Event columns are contiguous FP64 structure-of-arrays and must be 16-byte
+ *     aligned (vectorised loads); a misaligned column gives IPA_ERR_ARG.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream: results are valid once the stream reaches
+ *     them.  Calls on the same stream are ordered; calls that share library
+ *     scratch (see ipa_reserve) must not run concurrently on different streams.
+ *   - Errors are returned as a status and never abort the process; the text
+ *     of the last error of the calling thread is ipa_last_error().
+ *   - Non-physical parameters (sigma <= 0, Gamma <= 0, fractions outside [0,1])
+ *     are not rejected on the host (theta lives on the device); they produce
+ *     NaN results, which the fitter reports as IPA_FIT_BAD_PDF.
+ */
+#ifndef IPANEMA_H
+#define IPANEMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IPA_OK = 0,
+    IPA_ERR_ARG = -1,      /* invalid argument (null, size, alignment, model kind) */
+    IPA_ERR_OOM = -2,      /* a device allocation failed */
+    IPA_ERR_CUDA = -3,     /* a CUDA runtime call failed; see ipa_last_error() */
+    IPA_ERR_TIMEOUT = -4,  /* a bounded wait ran out */
+    IPA_ERR_BUSY = -5,     /* no free slot / budget (server admission) */
+    IPA_PENDING = 1        /* the request is still running (server poll) */
+} ipa_status;
+
+typedef enum {
+    IPA_MODEL_TIME1D = 1,     /* decay time only: P(t)                              */
+    IPA_MODEL_ANGTIME4D = 2   /* decay time x helicity angles: P(t, ck, cl, phi)    */
+} ipa_model_kind;
+
+/* Parameter indices (theta layout).  1D uses the first 4, 4D all 10. */
+enum {
+    IPA_GAMMA = 0,   /* decay width Gamma [1/ps]                   */
+    IPA_SIGMA = 1,   /* Gaussian time resolution sigma [ps]        */
+    IPA_MU = 2,      /* resolution offset mu [ps]                  */
+    IPA_FB = 3,      /* flat background fraction f_b               */
+    IPA_A0SQ = 4,    /* |A_0|^2 (P-wave fraction, before 1 - F_S)  */
+    IPA_APESQ = 5,   /* |A_perp|^2; |A_par|^2 = 1 - |A_0|^2 - |A_perp|^2 */
+    IPA_DPA = 6,     /* strong phase delta_par [rad]               */
+    IPA_DPE = 7,     /* strong phase delta_perp [rad]              */
+    IPA_FS = 8,      /* S-wave fraction F_S                        */
+    IPA_DS = 9,      /* S-wave phase delta_S [rad]; delta_0 = 0    */
+    IPA_NPAR_1D = 4,
+    IPA_NPAR_4D = 10,
+    IPA_MAX_PAR = 16
+};
+
+/* One fit parameter (Parameter / Free of App. B): start value, limits, step,
+ * and whether it is held constant (fixed != 0). */
+typedef struct {
+    double value, lo, hi, step;
+    int32_t fixed;
+    int32_t _pad;
+} ipa_param;
+
+/* An event set (Cat of App. C): n events as FP64 SoA device columns.
+ * t is required; ck, cl, phi are required for the 4D model and ignored for 1D;
+ * w may be NULL (unit weights). */
+typedef struct {
+    int64_t n;
+    const double *t, *ck, *cl, *phi, *w;
+} ipa_events;
+
+/* Writable event columns for the generator; `capacity` is the number of
+ * events each non-NULL column can hold. */
+typedef struct {
+    int64_t capacity;
+    double *t, *ck, *cl, *phi;
+} ipa_event_buffers;
+
+/* The model: its kind, number of parameters and the decay-time range. */
+typedef struct {
+    int32_t kind;      /* ipa_model_kind */
+    int32_t n_par;     /* IPA_NPAR_1D or IPA_NPAR_4D (set by ipa_model_init) */
+    double t_lo, t_hi; /* decay-time range [ps], t_lo < t_hi */
+} ipa_model;
+
+/* Per-fit status written by ipa_fit_batch. */
+enum {
+    IPA_FIT_CONVERGED = 0,  /* Newton decrement (step in sigma units) below tol  */
+    IPA_FIT_MAXITER = 1,    /* max_iter reached                                  */
+    IPA_FIT_AT_LIMIT = 2,   /* converged with a free parameter on a limit        */
+    IPA_FIT_BAD_PDF = 3,    /* NaN/inf NLL or gradient (non-physical parameters) */
+    IPA_FIT_EMPTY = 4       /* the fit has no events                             */
+};
+
+/* Fill *m for `kind` on [t_lo, t_hi].  IPA_ERR_ARG for an unknown kind or an
+ * empty range. */
+ipa_status ipa_model_init(ipa_model* m, int32_t kind, double t_lo, double t_hi);
+
+/* NLL = -sum_e w_e log P_e (Sec. 3: per-event PDF, log of the mixture, sum of
+ * logs; Sec. 4: the 4D model).  theta_dev: n_par doubles (device).
+ * out_dev: 1 double (device).  The sum is a fixed-order FP64 tree over
+ * 512-event tiles: the result does not depend on launch geometry.  n = 0
+ * gives 0.  Uses library scratch (ipa_reserve). */
+ipa_status ipa_nll(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
+                   double* out_dev, void* stream);
+
+/* NLL and its analytic gradient in one event pass (Sec. 3 / App. B: analytic
+ * gradients handed to the minimiser).  out_dev: 1 + n_par doubles (device):
+ * out[0] = NLL, out[1 + j] = dNLL/dtheta_j for every j (free or not). */
+ipa_status ipa_nll_grad(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
+                        double* out_dev, void* stream);
+
+/* Same as ipa_nll_grad for n_seg event segments packed back to back in one
+ * set of columns: segment s is events [seg_off[s], seg_off[s+1]) and uses
+ * theta_dev + s*n_par; out_dev receives (1 + n_par) doubles per segment.
+ * seg_off_dev: n_seg + 1 int64 (device), non-decreasing, seg_off[0] = 0,
+ * seg_off[n_seg] = ev->n (not checked on the host: the offsets live on the
+ * device).  Each segment's result is bitwise the result of ipa_nll_grad on
+ * that segment alone; an empty segment gives NLL = 0 and a zero gradient. */
+ipa_status ipa_nll_grad_segmented(const ipa_model* model, const ipa_events* ev,
+                                  const int64_t* seg_off_dev, int32_t n_seg,
+                                  const double* theta_dev, double* out_dev, void* stream);
+
+/* Accept-reject pseudo-experiments (Sec. 7).  Toy k holds n_sig[k] signal
+ * events then n_bkg[k] background events, written at event offset
+ * offsets[k] of each output column (offsets[k] + n_sig[k] + n_bkg[k] <=
+ * out->capacity).  Signal candidate j of toy k uses Philox-4x32-10 with key =
+ * (seed lo32, seed hi32) and counters (j lo32, j hi32, k, c) for c = 0,1,2;
+ * the toy keeps the first n_sig[k] accepted candidates in increasing j.
+ * Background event i uses counters (i lo32, i hi32, k, 4) and (.., 5).
+ * Candidates are built with IEEE-exact operations only, so a stream is
+ * reproducible bit for bit.  n_sig, n_bkg, offsets: n_toys int64 each
+ * (device).  For 1D only out->t is written.  A toy with a negative count or
+ * a range outside [0, capacity) is skipped (its slots are left untouched).
+ * Parameters for which nothing can be accepted (non-finite envelope), or a
+ * toy that exhausts its candidate budget (65536 n_sig + 2^22 candidates),
+ * leave NaN in the unfilled signal slots. */
+ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev, uint64_t seed,
+                      int32_t n_toys, const int64_t* n_sig_dev, const int64_t* n_bkg_dev,
+                      const int64_t* offsets_dev, const ipa_event_buffers* out, void* stream);
+
+/* Fit n_fits event segments at once (Sec. 3-4: MIGRAD minimisation and HESSE
+ * errors).  Segments as in ipa_nll_grad_segmented.  spec (host): n_par
+ * parameters (start value, limits, fixed flag), shared by all fits; the start
+ * values are read from theta_io_dev (n_fits x n_par, device) and the fitted
+ * values written back there.  Outputs (device): err_out_dev n_fits x n_par
+ * (sqrt of the inverse-Hessian diagonal, 0 for fixed parameters), nll_out_dev
+ * n_fits, fit_status_dev n_fits (IPA_FIT_*), iters_out_dev n_fits (may be
+ * NULL).  Stops each fit when its Newton decrement is below tol or after
+ * max_iter iterations.  Blocks the calling thread until all fits end. */
+ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                         int32_t n_fits, const ipa_param* spec, double* theta_io_dev,
+                         double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
+                         int32_t* iters_out_dev, int32_t max_iter, double tol, void* stream);
+
+/* Grow the library's device scratch on the current device to hold one call
+ * over `max_events` events in up to `max_segments` segments, so that later
+ * calls allocate nothing (needed before CUDA-graph capture).  Calls allocate
+ * on demand otherwise. */
+ipa_status ipa_reserve(int64_t max_events, int32_t max_segments);
+
+/* FP64 roofline calibration on the current device (blocking, ~1 s).
+ * results (host, 9 doubles): [0] DFMA per clock per SM, [1] DFMA per second
+ * for the whole GPU, [2..7] cost of one exp, erfc, log, sincos, sqrt and
+ * reciprocal in DFMA issue slots, [8] SM clock during the DFMA run [MHz]. */
+ipa_status ipa_calibrate_fp64(double* results, void* stream);
+
+/* Text of the calling thread's last error ("" if none). */
+const char* ipa_last_error(void);
+
+/* Library version string. */
+const char* ipa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPANEMA_H */

@@ -1,0 +1,78 @@
+"""ctypes view of the C ABI in include/ipanema.h (structs, enums, prototypes).
+
+Loading fails loudly when libipanema.so has not been built: there is no CPU
+fallback.  Build it with ``python -c "import __graft_entry__ as g; g.build()"``
+or ``python paper_1706_01420_gb300/build.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint64, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libipanema.so")
+
+IPA_OK, IPA_ERR_ARG, IPA_ERR_OOM, IPA_ERR_CUDA, IPA_ERR_TIMEOUT, IPA_ERR_BUSY, IPA_PENDING = 0, -1, -2, -3, -4, -5, 1
+IPA_MODEL_TIME1D, IPA_MODEL_ANGTIME4D = 1, 2
+IPA_GAMMA, IPA_SIGMA, IPA_MU, IPA_FB, IPA_A0SQ, IPA_APESQ, IPA_DPA, IPA_DPE, IPA_FS, IPA_DS = range(10)
+IPA_NPAR_1D, IPA_NPAR_4D, IPA_MAX_PAR = 4, 10, 16
+IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)
+STATUS_NAMES = {0: "IPA_OK", -1: "IPA_ERR_ARG", -2: "IPA_ERR_OOM", -3: "IPA_ERR_CUDA",
+                -4: "IPA_ERR_TIMEOUT", -5: "IPA_ERR_BUSY", 1: "IPA_PENDING"}
+
+
+class ipa_model(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("n_par", c_int32), ("t_lo", c_double), ("t_hi", c_double)]
+
+
+class ipa_events(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("t", c_void_p), ("ck", c_void_p), ("cl", c_void_p),
+                ("phi", c_void_p), ("w", c_void_p)]
+
+
+class ipa_event_buffers(ctypes.Structure):
+    _fields_ = [("capacity", c_int64), ("t", c_void_p), ("ck", c_void_p), ("cl", c_void_p),
+                ("phi", c_void_p)]
+
+
+class ipa_param(ctypes.Structure):
+    _fields_ = [("value", c_double), ("lo", c_double), ("hi", c_double), ("step", c_double),
+                ("fixed", c_int32), ("_pad", c_int32)]
+
+
+# name -> (restype, argtypes); every function declared in include/ipanema.h
+PROTOTYPES = {
+    "ipa_model_init": (c_int32, [POINTER(ipa_model), c_int32, c_double, c_double]),
+    "ipa_nll": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
+    "ipa_nll_grad": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
+    "ipa_nll_grad_segmented": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
+                                         c_void_p, c_void_p, c_void_p]),
+    "ipa_toygen": (c_int32, [POINTER(ipa_model), c_void_p, c_uint64, c_int32, c_void_p, c_void_p,
+                             c_void_p, POINTER(ipa_event_buffers), c_void_p]),
+    "ipa_fit_batch": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
+                                POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_int32, c_double, c_void_p]),
+    "ipa_reserve": (c_int32, [c_int64, c_int32]),
+    "ipa_calibrate_fp64": (c_int32, [POINTER(c_double), c_void_p]),
+    "ipa_last_error": (c_char_p, []),
+    "ipa_version": (c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libipanema.so and attach the prototypes (cached)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(paper_1706_01420_gb300/build.py); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,175 @@
+"""Thin Python binding of the C ABI: the same names as include/ipanema.h.
+
+Argument marshalling only: torch CUDA tensors in, device pointers and the
+current torch stream out to libipanema.so.  Every step of the likelihood,
+generator and fitter runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _capi as C
+
+
+class IpaError(RuntimeError):
+    pass
+
+
+def _lib():
+    return C.load()
+
+
+def _check(status: int, what: str):
+    if status != C.IPA_OK:
+        msg = _lib().ipa_last_error().decode(errors="replace")
+        raise IpaError(f"{what}: {C.STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _ptr(x: torch.Tensor | None, dtype=torch.float64, name="tensor") -> int | None:
+    if x is None:
+        return None
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise IpaError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise IpaError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise IpaError(f"{name} must be contiguous")
+    return x.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def ipa_model_init(kind: int, t_lo: float, t_hi: float) -> C.ipa_model:
+    m = C.ipa_model()
+    _check(_lib().ipa_model_init(ctypes.byref(m), kind, t_lo, t_hi), "ipa_model_init")
+    return m
+
+
+def model_1d(t_lo: float = 0.3, t_hi: float = 15.0) -> C.ipa_model:
+    return ipa_model_init(C.IPA_MODEL_TIME1D, t_lo, t_hi)
+
+
+def model_4d(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
+    return ipa_model_init(C.IPA_MODEL_ANGTIME4D, t_lo, t_hi)
+
+
+def ipa_events(ev: dict) -> C.ipa_events:
+    """dict of CUDA float64 columns (t[, ck, cl, phi][, w]) -> ipa_events."""
+    t = ev["t"]
+    e = C.ipa_events()
+    e.n = int(t.numel())
+    e.t = _ptr(t, name="t")
+    for k in ("ck", "cl", "phi", "w"):
+        v = ev.get(k)
+        setattr(e, k, _ptr(v, name=k) if v is not None else None)
+    return e
+
+
+def ipa_nll(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    out = torch.empty(1, dtype=torch.float64, device=theta.device) if out is None else out
+    e = ipa_events(ev)
+    _check(_lib().ipa_nll(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
+                          _ptr(out, name="out"), _stream(stream)), "ipa_nll")
+    return out
+
+
+def ipa_nll_grad(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    out = torch.empty(1 + model.n_par, dtype=torch.float64, device=theta.device) if out is None else out
+    e = ipa_events(ev)
+    _check(_lib().ipa_nll_grad(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
+                               _ptr(out, name="out"), _stream(stream)), "ipa_nll_grad")
+    return out
+
+
+def ipa_nll_grad_segmented(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, theta: torch.Tensor,
+                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    n_seg = int(seg_off.numel()) - 1
+    if out is None:
+        out = torch.empty(n_seg, 1 + model.n_par, dtype=torch.float64, device=theta.device)
+    e = ipa_events(ev)
+    _check(_lib().ipa_nll_grad_segmented(ctypes.byref(model), ctypes.byref(e),
+                                         _ptr(seg_off, torch.int64, "seg_off"), n_seg,
+                                         _ptr(theta, name="theta"), _ptr(out, name="out"),
+                                         _stream(stream)), "ipa_nll_grad_segmented")
+    return out
+
+
+def ipa_toygen(model: C.ipa_model, theta: torch.Tensor, seed: int, n_sig: torch.Tensor,
+               n_bkg: torch.Tensor, offsets: torch.Tensor, out: dict, stream=None) -> dict:
+    """Fill the columns of `out` (dict of CUDA float64 tensors of equal length)."""
+    b = C.ipa_event_buffers()
+    b.capacity = int(out["t"].numel())
+    for k in ("t", "ck", "cl", "phi"):
+        v = out.get(k)
+        setattr(b, k, _ptr(v, name=k) if v is not None else None)
+    _check(_lib().ipa_toygen(ctypes.byref(model), _ptr(theta, name="theta"), ctypes.c_uint64(seed),
+                             int(n_sig.numel()), _ptr(n_sig, torch.int64, "n_sig"),
+                             _ptr(n_bkg, torch.int64, "n_bkg"), _ptr(offsets, torch.int64, "offsets"),
+                             ctypes.byref(b), _stream(stream)), "ipa_toygen")
+    return out
+
+
+@dataclass
+class Param:
+    """Parameter / Free (App. B): start value, limits, step and the fixed flag."""
+    value: float
+    lo: float = -1e300
+    hi: float = 1e300
+    step: float = 0.0
+    fixed: bool = False
+
+
+def _spec(params: list[Param]):
+    arr = (C.ipa_param * len(params))()
+    for i, p in enumerate(params):
+        arr[i].value, arr[i].lo, arr[i].hi = p.value, p.lo, p.hi
+        arr[i].step = p.step if p.step > 0 else (
+            (p.hi - p.lo) / 10 if p.hi < 1e299 and p.lo > -1e299 else 0.0)
+        arr[i].fixed = 1 if p.fixed else 0
+    return arr
+
+
+def ipa_fit_batch(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[Param],
+                  theta: torch.Tensor, max_iter: int = 100, tol: float = 1e-9, stream=None) -> dict:
+    """Fit every segment; theta (n_fits x n_par) holds the start values and receives the result."""
+    n_fits = int(seg_off.numel()) - 1
+    dev = theta.device
+    err = torch.zeros(n_fits, model.n_par, dtype=torch.float64, device=dev)
+    nll = torch.zeros(n_fits, dtype=torch.float64, device=dev)
+    status = torch.zeros(n_fits, dtype=torch.int32, device=dev)
+    iters = torch.zeros(n_fits, dtype=torch.int32, device=dev)
+    e = ipa_events(ev)
+    spec = _spec(params)
+    _check(_lib().ipa_fit_batch(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
+                                n_fits, spec, _ptr(theta, name="theta"), _ptr(err, name="err"),
+                                _ptr(nll, name="nll"), _ptr(status, torch.int32, "status"),
+                                _ptr(iters, torch.int32, "iters"), max_iter, tol, _stream(stream)),
+           "ipa_fit_batch")
+    return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters}
+
+
+def ipa_reserve(max_events: int, max_segments: int = 1):
+    _check(_lib().ipa_reserve(max_events, max_segments), "ipa_reserve")
+
+
+def ipa_calibrate_fp64(stream=None) -> dict:
+    """DFMA rate and FP64 math-function costs of the current GPU (see the header)."""
+    r = (ctypes.c_double * 9)()
+    _check(_lib().ipa_calibrate_fp64(r, _stream(stream)), "ipa_calibrate_fp64")
+    names = ["dfma_per_clk_per_sm", "dfma_per_s", "exp", "erfc", "log", "sincos", "sqrt", "rcp", "sm_mhz"]
+    return dict(zip(names, list(r)))
+
+
+def ipa_version() -> str:
+    return _lib().ipa_version().decode()

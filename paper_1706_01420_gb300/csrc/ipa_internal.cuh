@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipanema.h"
+
+namespace ipa {
+
+// Events per reduction tile and threads per block of the likelihood kernels.
+// Each of the 256 slots of a tile handles two consecutive events (one 16-byte
+// load per column); the in-tile and cross-tile trees are fixed, so results do
+// not depend on grid size or scheduling.
+constexpr int kTile = 512;
+constexpr int kSlots = 256;
+constexpr int kBlock = 256;
+
+// Number of FP64 accumulators per tile.
+//   NLL only:   L = sum w log P
+//   1D + grad:  L, Q = sum w/P, S = sum (w/P) T, D_Gamma, D_sigma, D_mu
+//   4D + grad:  L, Q, S_1..S_10 = sum (w/P) T f_k, D_Gamma, D_sigma, D_mu
+__host__ __device__ constexpr int n_acc(int kind, bool grad) {
+    return !grad ? 1 : (kind == IPA_MODEL_TIME1D ? 6 : 15);
+}
+
+// Parameter-derived constants of one fit (step a1 of the hot path), computed
+// once per call on the device from theta and read by every event tile.
+struct Consts {
+    double Gamma, sigma, mu, fb;
+    double c_exp;     // Gamma^2 sigma^2 / 2
+    double Gs2;       // Gamma sigma^2
+    double k_z;       // 1 / (sqrt2 sigma)   (erfc argument scale)
+    double k_g;       // 1 / (2 sigma^2)     (Gaussian exponent scale)
+    double cG;        // 1 / (sqrt(2 pi) sigma)
+    double s2;        // sigma^2
+    double G2s;       // Gamma^2 sigma
+    double Gsig;      // Gamma sigma
+    double inv_s;     // 1 / sigma
+    double cs;        // (1 - f_b) / (I_T I_Omega)
+    double cb;        // f_b / V
+    double inv_ITIO;  // 1 / (I_T I_Omega)
+    double inv_V;     // 1 / V
+    double dlnIT[3];  // (dI_T / dtheta_j) / I_T for Gamma, sigma, mu
+    double h[10];     // amplitude coefficients h_k (4D), h[0] = 1 for 1D
+    double dh[10][6]; // dh_k / d(A0sq, Apesq, delta_pa, delta_pe, F_S, delta_S)
+    double MT;        // time envelope: max of g(t - mu) on [t_lo, t_hi] (upper bound)
+    double MO;        // angular envelope: sum |h_k| max|f_k|
+    double IT;        // I_T
+    double pad_;
+};
+constexpr int kConstsDoubles = sizeof(Consts) / sizeof(double);
+static_assert(sizeof(Consts) % 16 == 0, "Consts must be a multiple of 16 bytes");
+
+// Model description passed by value to kernels.
+struct ModelDev {
+    int kind;
+    int n_par;
+    double t_lo, t_hi;
+};
+
+struct Cols {
+    const double *t, *ck, *cl, *phi, *w;
+};
+
+// ---- host-side helpers (runtime.cu) ----
+void set_error(const char* fmt, ...);
+ipa_status cuda_fail(cudaError_t e, const char* what);
+ipa_status check_model(const ipa_model* m);
+ipa_status check_events(const ipa_model* m, const ipa_events* ev);
+
+// Per-device scratch shared by the likelihood, generator and fitter kernels.
+struct Scratch {
+    double* partials = nullptr;     // tiles * n_acc doubles
+    size_t partials_cap = 0;        // doubles
+    unsigned* counters = nullptr;   // one per segment, zero between calls
+    int64_t* seg_tiles = nullptr;   // n_seg + 1 prefix of tiles per segment
+    Consts* consts = nullptr;       // one per segment
+    size_t seg_cap = 0;             // segments
+};
+// Ensure the current device's scratch holds `tiles` tiles of 15 accumulators
+// and `segs` segments.  May synchronise the device when it grows.
+ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out);
+
+// ---- kernels launched across translation units ----
+// consts.cu: theta (n_seg x n_par) -> Consts[n_seg]
+ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
+                         cudaStream_t s);
+// compute_consts (consts.cuh): device function theta -> Consts, shared by the kernels.
+
+// nll.cu: segmented NLL(+grad) over precomputed consts; out: (1 + n_par) per segment
+// With seg_off == nullptr there is one segment [0, n).  Otherwise seg_tiles must
+// hold the device prefix of tiles per segment (launch_seg_tiles).
+ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
+                      const int64_t* seg_off, const int64_t* seg_tiles, int n_seg,
+                      const Consts* consts, Scratch* sc, double* out, cudaStream_t s);
+// nll.cu: seg_tiles[s] = sum_{r<s} ceil(size_r / kTile), s = 0..n_seg, with the
+// offsets clamped to [0, n] and made non-decreasing
+ipa_status launch_seg_tiles(const int64_t* seg_off, int n_seg, int64_t n, int64_t* seg_tiles,
+                            cudaStream_t s);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+}  // namespace ipa

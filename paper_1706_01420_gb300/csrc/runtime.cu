@@ -1,0 +1,186 @@
+// Host runtime: argument checks, thread-local error text, per-device scratch.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "ipa_internal.cuh"
+
+namespace ipa {
+
+namespace {
+thread_local char g_err[512] = "";
+std::mutex g_mu;
+std::vector<Scratch> g_scratch;   // indexed by device ordinal
+std::vector<int> g_sms;
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+ipa_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return IPA_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? IPA_ERR_OOM : IPA_ERR_CUDA;
+}
+
+ipa_status check_model(const ipa_model* m) {
+    if (!m) {
+        set_error("model is NULL");
+        return IPA_ERR_ARG;
+    }
+    if (m->kind != IPA_MODEL_TIME1D && m->kind != IPA_MODEL_ANGTIME4D) {
+        set_error("unknown model kind %d", m->kind);
+        return IPA_ERR_ARG;
+    }
+    const int want = m->kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D : IPA_NPAR_4D;
+    if (m->n_par != want) {
+        set_error("model n_par %d, expected %d (use ipa_model_init)", m->n_par, want);
+        return IPA_ERR_ARG;
+    }
+    if (!(m->t_lo < m->t_hi)) {
+        set_error("empty decay-time range [%g, %g]", m->t_lo, m->t_hi);
+        return IPA_ERR_ARG;
+    }
+    return IPA_OK;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+ipa_status check_events(const ipa_model* m, const ipa_events* ev) {
+    if (!ev) {
+        set_error("events are NULL");
+        return IPA_ERR_ARG;
+    }
+    if (ev->n < 0) {
+        set_error("negative event count %lld", (long long)ev->n);
+        return IPA_ERR_ARG;
+    }
+    if (ev->n == 0) return IPA_OK;
+    const double* need[4] = {ev->t, ev->ck, ev->cl, ev->phi};
+    const int n_need = m->kind == IPA_MODEL_TIME1D ? 1 : 4;
+    const char* names[4] = {"t", "ck", "cl", "phi"};
+    for (int i = 0; i < n_need; ++i) {
+        if (!need[i]) {
+            set_error("event column %s is NULL", names[i]);
+            return IPA_ERR_ARG;
+        }
+        if (!aligned16(need[i])) {
+            set_error("event column %s is not 16-byte aligned", names[i]);
+            return IPA_ERR_ARG;
+        }
+    }
+    if (ev->w && !aligned16(ev->w)) {
+        set_error("weight column is not 16-byte aligned");
+        return IPA_ERR_ARG;
+    }
+    return IPA_OK;
+}
+
+int sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_sms.size() <= dev) g_sms.resize(dev + 1, 0);
+    if (g_sms[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = v > 0 ? v : 1;
+    }
+    return g_sms[dev];
+}
+
+// Grow-only scratch.  Growing frees the old buffers after a device
+// synchronisation (a kernel of an earlier call may still read them).
+ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
+    int dev = 0;
+    ipa_status st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != IPA_OK) return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_scratch.size() <= dev) g_scratch.resize(dev + 1);
+    Scratch& s = g_scratch[dev];
+    const size_t need_p = (size_t)(tiles < 1 ? 1 : tiles) * 15;
+    const size_t need_s = (size_t)(segs < 2 ? 2 : segs);
+    if (need_p > s.partials_cap) {
+        size_t cap = s.partials_cap ? s.partials_cap : (size_t)1 << 16;
+        while (cap < need_p) cap *= 2;
+        if (s.partials) {
+            cudaDeviceSynchronize();
+            cudaFree(s.partials);
+            s.partials = nullptr;
+            s.partials_cap = 0;
+        }
+        if ((st = cuda_fail(cudaMalloc(&s.partials, cap * sizeof(double)), "scratch partials")) != IPA_OK)
+            return st;
+        s.partials_cap = cap;
+    }
+    if (need_s > s.seg_cap) {
+        size_t cap = s.seg_cap ? s.seg_cap : 64;
+        while (cap < need_s) cap *= 2;
+        if (s.counters) {
+            cudaDeviceSynchronize();
+            cudaFree(s.counters);
+            cudaFree(s.seg_tiles);
+            cudaFree(s.consts);
+            s.counters = nullptr;
+            s.seg_tiles = nullptr;
+            s.consts = nullptr;
+            s.seg_cap = 0;
+        }
+        if ((st = cuda_fail(cudaMalloc(&s.counters, cap * sizeof(unsigned)), "scratch counters")) != IPA_OK)
+            return st;
+        if ((st = cuda_fail(cudaMalloc(&s.seg_tiles, (cap + 1) * sizeof(int64_t)), "scratch tiles")) != IPA_OK)
+            return st;
+        if ((st = cuda_fail(cudaMalloc(&s.consts, cap * sizeof(Consts)), "scratch consts")) != IPA_OK)
+            return st;
+        // counters must be zero between calls; kernels reset what they use
+        if ((st = cuda_fail(cudaMemset(s.counters, 0, cap * sizeof(unsigned)), "scratch memset")) != IPA_OK)
+            return st;
+        if ((st = cuda_fail(cudaDeviceSynchronize(), "scratch init")) != IPA_OK) return st;
+        s.seg_cap = cap;
+    }
+    *out = &s;
+    return IPA_OK;
+}
+
+}  // namespace ipa
+
+extern "C" ipa_status ipa_model_init(ipa_model* m, int32_t kind, double t_lo, double t_hi) {
+    if (!m) {
+        ipa::set_error("model is NULL");
+        return IPA_ERR_ARG;
+    }
+    if (kind != IPA_MODEL_TIME1D && kind != IPA_MODEL_ANGTIME4D) {
+        ipa::set_error("unknown model kind %d", kind);
+        return IPA_ERR_ARG;
+    }
+    if (!(t_lo < t_hi)) {
+        ipa::set_error("empty decay-time range [%g, %g]", t_lo, t_hi);
+        return IPA_ERR_ARG;
+    }
+    m->kind = kind;
+    m->n_par = kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D : IPA_NPAR_4D;
+    m->t_lo = t_lo;
+    m->t_hi = t_hi;
+    return IPA_OK;
+}
+
+extern "C" ipa_status ipa_reserve(int64_t max_events, int32_t max_segments) {
+    if (max_events < 0 || max_segments < 1) {
+        ipa::set_error("ipa_reserve: bad sizes");
+        return IPA_ERR_ARG;
+    }
+    ipa::Scratch* sc = nullptr;
+    return ipa::scratch_get((max_events + ipa::kTile - 1) / ipa::kTile + max_segments,
+                            (int64_t)max_segments + 1, &sc);
+}
+
+extern "C" const char* ipa_last_error(void) { return ipa::g_err; }
+
+extern "C" const char* ipa_version(void) { return "ipanema-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,156 @@
+"""GPU parity of ipa_nll / ipa_nll_grad / ipa_nll_grad_segmented against the oracle.
+
+Tolerances (BASELINE the benchmark spec): NLL to 1e-12 relative (to sum |w log P|);
+gradient to 1e-9 relative to max(|g_j|, condition scale of g_j) -- see
+gpu_common.grad_scale -- and, against central finite differences of the GPU
+NLL itself, to 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1706_01420_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TH1 = np.array([0.66, 0.045, 0.0, 0.1])
+TH4 = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3])
+
+
+@pytest.fixture(scope="module")
+def env(oracle):
+    from tests import gpu_common as G
+    G.need_gpu()
+    import torch
+    from paper_1706_01420_gb300 import api
+    return oracle, G, torch, api
+
+
+def _parity(env, kind, n, seed, weighted, th, t_lo=None):
+    O, G, torch, api = env
+    if kind == "1d":
+        t_lo = 0.3 if t_lo is None else t_lo
+        m_o, m_g = O.Model("1d", t_lo, 15.0), api.model_1d(t_lo, 15.0)
+        cols = {"t": synth.events_1d(n, seed, t_lo=t_lo)}
+        if weighted:
+            cols["w"] = synth.weights(n, seed + 1)
+    else:
+        t_lo = 0.0 if t_lo is None else t_lo
+        m_o, m_g = O.Model("4d", t_lo, 15.0), api.model_4d(t_lo, 15.0)
+        cols = synth.events_4d(n, seed, t_lo=t_lo, weighted=weighted)
+    ev = G.to_dev(cols)
+    theta = torch.tensor(th, device="cuda")
+    got = api.ipa_nll_grad(m_g, ev, theta).cpu().numpy()
+    nll_only = float(api.ipa_nll(m_g, ev, theta).cpu()[0])
+    f_ref, g_ref = O.nll_grad(m_o, cols, th)
+    logl, _ = O.nll_grad_terms(m_o, cols, th)
+    labs = math.fsum(np.abs(logl)) if n else 1.0
+    scale = G.grad_scale(O, m_o, cols, th) if n else np.zeros(th.size)
+    G.assert_nll_grad_close(got, f_ref, g_ref, scale, labs)
+    assert abs(nll_only - f_ref) <= 1e-12 * labs
+    return got
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 511, 512, 513, 1025, 4097, 100000])
+@pytest.mark.parametrize("kind", ["1d", "4d"])
+def test_parity_sizes(env, kind, n):
+    _parity(env, kind, n, seed=n + 3, weighted=False, th=TH1 if kind == "1d" else TH4)
+
+
+@pytest.mark.parametrize("kind", ["1d", "4d"])
+def test_parity_weighted_and_off_truth(env, kind):
+    th = (TH1 if kind == "1d" else TH4).copy()
+    th[0], th[1], th[2] = 0.8, 0.06, 0.01
+    if kind == "4d":
+        th[4:10] = [0.45, 0.3, 2.5, -0.4, 0.15, 1.1]
+    _parity(env, kind, 20000, seed=5, weighted=True, th=th, t_lo=0.0)
+
+
+def test_parity_config2_full_size(env):
+    """4D, 1e6 events (the headline workload), unweighted."""
+    _parity(env, "4d", 1_000_000, seed=0, weighted=False, th=TH4)
+
+
+def test_parity_config1_full_size(env):
+    """1D, 1e5 events on [0.3, 15] ps."""
+    _parity(env, "1d", 100_000, seed=0, weighted=False, th=TH1)
+
+
+def test_gradient_vs_gpu_finite_differences(env):
+    O, G, torch, api = env
+    cols = synth.events_4d(50000, 11, weighted=True)
+    ev = G.to_dev(cols)
+    m = api.model_4d()
+    th = TH4.copy()
+    th[2] = 0.003
+    g = api.ipa_nll_grad(m, ev, torch.tensor(th, device="cuda")).cpu().numpy()[1:]
+    f0 = float(api.ipa_nll(m, ev, torch.tensor(th, device="cuda")).cpu()[0])
+    for j in range(th.size):
+        h = 1e-5 * max(abs(th[j]), 0.05)
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        fp = float(api.ipa_nll(m, ev, torch.tensor(tp, device="cuda")).cpu()[0])
+        fm = float(api.ipa_nll(m, ev, torch.tensor(tm, device="cuda")).cpu()[0])
+        fd = (fp - fm) / (2 * h)
+        noise = abs(f0) * 4e-16 / h
+        assert abs(g[j] - fd) <= 1e-6 * max(abs(g[j]), abs(fd)) + noise + 1e-6, (j, g[j], fd)
+
+
+def test_deterministic_and_segment_equals_solo(env):
+    """Bitwise: repeated calls agree; each segment of a packed call equals the solo call."""
+    O, G, torch, api = env
+    m = api.model_4d()
+    sizes = [0, 1, 700, 513, 20000, 3, 4096, 0, 12345]
+    cols = synth.events_4d(sum(sizes), 21, weighted=True)
+    ev = G.to_dev(cols)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    rng = np.random.default_rng(2)
+    thetas = np.tile(TH4, (len(sizes), 1))
+    thetas[:, 0] += rng.normal(0, 0.02, len(sizes))
+    seg = api.ipa_nll_grad_segmented(m, ev, torch.tensor(off, device="cuda"),
+                                     torch.tensor(thetas, device="cuda")).cpu().numpy()
+    seg2 = api.ipa_nll_grad_segmented(m, ev, torch.tensor(off, device="cuda"),
+                                      torch.tensor(thetas, device="cuda")).cpu().numpy()
+    assert np.array_equal(seg, seg2)
+    for s, (a, b) in enumerate(zip(off[:-1], off[1:])):
+        sub = {k: v[a:b].clone() for k, v in ev.items()}   # fresh, 16-byte aligned
+        solo = api.ipa_nll_grad(m, sub, torch.tensor(thetas[s], device="cuda")).cpu().numpy()
+        assert np.array_equal(solo, seg[s]), s
+        if b == a:
+            assert np.all(seg[s] == 0.0)
+
+
+def test_misaligned_column_rejected(env):
+    O, G, torch, api = env
+    t = torch.zeros(101, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.IpaError, match="aligned"):
+        api.ipa_nll(api.model_1d(), {"t": t[1:]}, torch.tensor(TH1, device="cuda"))
+
+
+def test_large_weighted_sampled(env):
+    """5e7 weighted 4D events (the large single-fit workload, ~2 GB): the full NLL+grad
+    equals the sum over 50 segments of 1e6 (a property at any size), and three of
+    those segments match the oracle."""
+    O, G, torch, api = env
+    n, k = 50_000_000, 50
+    ev = G.to_dev(synth.events_4d(n, 5, weighted=True))
+    m = api.model_4d()
+    th = torch.tensor(TH4, device="cuda")
+    full = api.ipa_nll_grad(m, ev, th).cpu().numpy()
+    off = torch.arange(0, n + 1, n // k, dtype=torch.int64, device="cuda")
+    seg = api.ipa_nll_grad_segmented(m, ev, off, th.repeat(k, 1)).cpu().numpy()
+    tot = seg.sum(axis=0)
+    assert abs(full[0] - tot[0]) <= 1e-12 * abs(full[0])
+    np.testing.assert_allclose(full[1:], tot[1:], rtol=1e-9, atol=1e-9 * np.abs(seg[:, 1:]).sum(axis=0).max())
+    mo = O.Model("4d", 0.0, 15.0)
+    for s in (0, 17, 49):
+        a, b = s * (n // k), (s + 1) * (n // k)
+        cols = {key: v[a:b].cpu().numpy() for key, v in ev.items()}
+        f_ref, g_ref = O.nll_grad(mo, cols, TH4)
+        logl, _ = O.nll_grad_terms(mo, cols, TH4)
+        G.assert_nll_grad_close(seg[s], f_ref, g_ref, G.grad_scale(O, mo, cols, TH4),
+                                math.fsum(np.abs(logl)))
+    del ev
+    torch.cuda.empty_cache()
