@@ -339,8 +339,8 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
     bumped by the Weyl constants (W0, W1) between rounds.
     """
     c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & _M32 for c in (c0, c1, c2, c3))
-    k0 = np.uint64(k0) & _M32
-    k1 = np.uint64(k1) & _M32
+    k0 = np.asarray(k0, dtype=np.uint64) & _M32
+    k1 = np.asarray(k1, dtype=np.uint64) & _M32
     m0, m1 = np.uint64(PHILOX_M0), np.uint64(PHILOX_M1)
     for r in range(10):
         if r:
