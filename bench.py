@@ -1,7 +1,8 @@
 """Benchmark of the unbinned-likelihood hot path on GB300.
 
 Workload (one GPU): the 4D decay-time x helicity-angle model on 1e6 FP64 SoA
-events (t, cos thK, cos thmu, phi), 10 parameters.  One step = one
+events (t, cos thK, cos thmu, phi) distributed like the PDF at the truth
+(generated by ipa_toygen before the timed region), 10 parameters.  One step = one
 ipa_nll_grad call: parameter constants + fused PDF / log / analytic adjoint +
 deterministic FP64 reduction, i.e. one minimiser iteration's event pass.
 The metric is NLL+grad Gevents/s.  Inputs (32 MB) are smaller than L2, so L2
@@ -47,15 +48,18 @@ METRIC = "NLL+grad Gevents/s"
 WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 
 # FP64 operations per event of the fused 4D NLL+gradient kernel, counted from the
-# formula as the kernel evaluates it (nll.cu: event<4D, grad>); FMA = 2 flops.
-FORMULA_OPS_4D = {"fma": 34, "mul": 42, "add": 4,
-                  "exp": 2, "erfc": 1, "log": 1, "sincos": 1, "sqrt": 2, "rcp": 1}
+# formula as nll.cu evaluates it (event<4D, grad>: time_terms, basis_unscaled,
+# the amplitude sum, log, 1/P and the 15 accumulations).  FMA = 2 flops; each
+# function call counts its cost in DFMA issue slots measured live by
+# ipa_calibrate_fp64, times 2 flops.
+FORMULA_OPS_4D = {"fma": 32, "mul": 30, "add": 6,
+                  "exp_fast": 2, "erfcx_poly": 1, "sincos_fast": 1, "log_fast": 1, "sqrt": 1, "rcp": 1}
 
 
 def flops_per_event(cal: dict) -> float:
     f = 2 * FORMULA_OPS_4D["fma"] + FORMULA_OPS_4D["mul"] + FORMULA_OPS_4D["add"]
-    for fn in ("exp", "erfc", "log", "sincos", "sqrt", "rcp"):
-        f += FORMULA_OPS_4D[fn] * cal[fn] * 2.0      # cost in DFMA slots, 2 flops each
+    for fn in ("exp_fast", "erfcx_poly", "sincos_fast", "log_fast", "sqrt", "rcp"):
+        f += FORMULA_OPS_4D[fn] * cal[fn] * 2.0
     return f
 
 
@@ -180,7 +184,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip fit/toygen/batch sub-benchmarks")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="untimed: 4 ipa_nll_grad calls on 8e6 4D events (256 MB, > L2), for ncu")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -202,9 +210,11 @@ def main():
 
     cal = api.ipa_calibrate_fp64()
     m = api.model_4d(0.0, 15.0)
-    cols_h = synth.events_4d(N_EVENTS, rank)
-    ev = {k: torch.tensor(v, device=dev) for k, v in cols_h.items()}
     theta = torch.tensor(TH4, device=dev)
+    # 1e6 events distributed like the 4D PDF at the truth: 50 pseudo-experiments of
+    # 2e4 events (10 % background) from the library's generator, seed = rank
+    ev = gen_sample(api, torch, dev, m, theta, 50, 20000, seed=rank)
+    cols_h = {k: v.cpu().numpy() for k, v in ev.items()}
     out = torch.empty(11, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -311,15 +321,48 @@ def main():
                                   f"DFMA loop measured {cal['dfma_per_s'] * 2e-12:.3f} TFLOP/s at "
                                   f"{cal['sm_mhz']:.0f} MHz, {cal['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM",
                      "fp64_costs_dfma_slots": {k: round(cal[k], 2) for k in
-                                               ("exp", "erfc", "log", "sincos", "sqrt", "rcp")}},
+                                               ("exp_fast", "erfcx_poly", "sincos_fast", "log_fast", "sqrt",
+                                                "rcp", "exp", "erfc", "log", "sincos")}},
         "wall_s_timed_region": wall,
     }
     line.update(extras)
+    if "large" in line:
+        lg = line["large"]
+        lg["roofline_frac"] = fpe * lg["events"] / (lg["nll_grad_ms"] * 1e-3) / 1e12 / peak
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def gen_sample(api, torch, dev, m, theta, n_toys: int, per: int, seed: int) -> dict:
+    """n_toys x per events of the 4D PDF at theta (per // 10 background each), contiguous."""
+    d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
+    n_bkg = np.full(n_toys, per // 10, dtype=np.int64)
+    n_sig = np.full(n_toys, per, dtype=np.int64) - n_bkg
+    off = np.arange(n_toys, dtype=np.int64) * per
+    cols = {k: torch.empty(n_toys * per, dtype=torch.float64, device=dev) for k in ("t", "ck", "cl", "phi")}
+    api.ipa_toygen(m, theta, seed, d64(n_sig), d64(n_bkg), d64(off), cols)
+    torch.cuda.synchronize()
+    return cols
+
+
+def profile_case() -> int:
+    """A small fixed case for Nsight Compute: inputs larger than L2, few launches."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1706_01420_gb300 import api, synth
+    n = 8_000_000
+    ev = {k: torch.tensor(v, device="cuda") for k, v in synth.events_4d(n, 3).items()}
+    m = api.model_4d(0.0, 15.0)
+    theta = torch.tensor(TH4, device="cuda")
+    for _ in range(4):
+        out = api.ipa_nll_grad(m, ev, theta)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "ipa_nll_grad 4D", "events": n, "nll": float(out[0])}))
     return 0
 
 
@@ -339,8 +382,10 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     r = api.ipa_fit_batch(m, ev, off1, params, th1, max_iter=200, tol=1e-8)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    npass = int(r["passes"][0])
     out["fit"] = {"events": N_EVENTS, "wall_s": dt, "status": int(r["status"][0]),
-                  "iterations": int(r["iters"][0])}
+                  "iterations": int(r["iters"][0]), "passes": npass,
+                  "Gevents_per_s": N_EVENTS * npass / dt / 1e9}
 
     # toy generation: 4096 toys of Poisson(2e4) events
     n_toys = 4096
@@ -371,9 +416,8 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     n_plain = 32
     t0 = time.perf_counter()
     for k in range(n_plain):
-        sub = {c: v[off[k]:off[k + 1]] for c, v in cols.items()}
         th_k = torch.tensor(TH4[None, :], device=dev)
-        api.ipa_fit_batch(m, sub, d64([0, sizes[k]]), params, th_k, max_iter=200, tol=1e-8)
+        api.ipa_fit_batch(m, cols, d64([off[k], off[k + 1]]), params, th_k, max_iter=200, tol=1e-8)
     torch.cuda.synchronize()
     tp = (time.perf_counter() - t0) / n_plain
     thn = rb["theta"].cpu().numpy()
@@ -384,11 +428,49 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     for j, nm in enumerate(names):
         p = (thn[ok, j] - TH4[j]) / ern[ok, j]
         pulls[nm] = [round(float(p.mean()), 4), round(float(p.std(ddof=1)), 4)]
+    passes_b = rb["passes"].cpu().numpy()
     out["batch"] = {"toys": n_toys, "events": total, "batched_fits_per_s": n_toys / tb, "batched_s": tb,
+                    "batched_Gevents_per_s": float((sizes * passes_b).sum()) / tb / 1e9,
                     "plain_loop_fits_per_s": 1.0 / tp, "plain_loop_sample": n_plain,
                     "converged": int(ok.sum()), "status_counts": np.bincount(st, minlength=5).tolist(),
                     "pull_mean_width": pulls}
+    del cols, rb, thb
+    out["large"] = run_large(api, synth, torch, dev, m, theta, params)
     return out
+
+
+def run_large(api, synth, torch, dev, m, theta, params) -> dict:
+    """5e7 events of the 4D PDF (generated on the GPU) with a Normal(1, 0.2) weight
+    column, 2 GB: NLL+grad throughput and one full fit."""
+    n_toys, per = 2500, 20000
+    n = n_toys * per
+    d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
+    cols = gen_sample(api, torch, dev, m, theta, n_toys, per, seed=5)
+    cols["w"] = torch.tensor(synth.weights(n, 11), device=dev)
+    out = torch.empty(11, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        api.ipa_nll_grad(m, cols, theta, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        api.ipa_nll_grad(m, cols, theta, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    start = TH4 + np.array([0.002, 0.0005, 0.0003, 0.002, 0.002, -0.002, 0.01, -0.01, 0.002, 0.02])
+    th1 = torch.tensor(start[None, :], device=dev)
+    big = [api.Param(p.value, p.lo, p.hi, p.step / 7.0) for p in params]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = api.ipa_fit_batch(m, cols, d64([0, n]), big, th1, max_iter=200, tol=1e-8)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    npass = int(r["passes"][0])
+    return {"events": n, "weighted": True, "nll_grad_ms": ms, "Gevents_per_s": n / (ms * 1e-3) / 1e9,
+            "fit": {"wall_s": dt, "status": int(r["status"][0]), "iterations": int(r["iters"][0]),
+                    "passes": npass, "Gevents_per_s": n * npass / dt / 1e9}}
 
 
 if __name__ == "__main__":

@@ -145,9 +145,9 @@ ipa_status ipa_nll_grad(const ipa_model* model, const ipa_events* ev, const doub
 /* Same as ipa_nll_grad for n_seg event segments packed back to back in one
  * set of columns: segment s is events [seg_off[s], seg_off[s+1]) and uses
  * theta_dev + s*n_par; out_dev receives (1 + n_par) doubles per segment.
- * seg_off_dev: n_seg + 1 int64 (device), non-decreasing, seg_off[0] = 0,
- * seg_off[n_seg] = ev->n (not checked on the host: the offsets live on the
- * device).  Each segment's result is bitwise the result of ipa_nll_grad on
+ * seg_off_dev: n_seg + 1 int64 (device), non-decreasing, within [0, ev->n]
+ * (offsets live on the device and are not checked on the host; values outside
+ * [0, ev->n] are clamped into it).  Each segment's result is bitwise the result of ipa_nll_grad on
  * that segment alone; an empty segment gives NLL = 0 and a zero gradient. */
 ipa_status ipa_nll_grad_segmented(const ipa_model* model, const ipa_events* ev,
                                   const int64_t* seg_off_dev, int32_t n_seg,
@@ -177,13 +177,15 @@ ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev, uint64_t 
  * values are read from theta_io_dev (n_fits x n_par, device) and the fitted
  * values written back there.  Outputs (device): err_out_dev n_fits x n_par
  * (sqrt of the inverse-Hessian diagonal, 0 for fixed parameters), nll_out_dev
- * n_fits, fit_status_dev n_fits (IPA_FIT_*), iters_out_dev n_fits (may be
- * NULL).  Stops each fit when its Newton decrement is below tol or after
+ * n_fits, fit_status_dev n_fits (IPA_FIT_*), iters_out_dev n_fits (minimiser
+ * iterations; may be NULL), passes_out_dev n_fits (NLL+gradient passes over
+ * the fit's events, including line-search trials and the Hessian; may be NULL).  Stops each fit when its Newton decrement is below tol or after
  * max_iter iterations.  Blocks the calling thread until all fits end. */
 ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
                          int32_t n_fits, const ipa_param* spec, double* theta_io_dev,
                          double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
-                         int32_t* iters_out_dev, int32_t max_iter, double tol, void* stream);
+                         int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
+                         void* stream);
 
 /* Grow the library's device scratch on the current device to hold one call
  * over `max_events` events in up to `max_segments` segments, so that later
@@ -192,9 +194,10 @@ ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int
 ipa_status ipa_reserve(int64_t max_events, int32_t max_segments);
 
 /* FP64 roofline calibration on the current device (blocking, ~1 s).
- * results (host, 9 doubles): [0] DFMA per clock per SM, [1] DFMA per second
- * for the whole GPU, [2..7] cost of one exp, erfc, log, sincos, sqrt and
- * reciprocal in DFMA issue slots, [8] SM clock during the DFMA run [MHz]. */
+ * results (host, 13 doubles): [0] DFMA per clock per SM, [1] DFMA per second
+ * for the whole GPU, [2..7] cost of one CUDA exp, erfc, log, sincos, sqrt and
+ * reciprocal in DFMA issue slots, [8] SM clock during the DFMA run [MHz],
+ * [9..12] cost of the library's own table-driven exp, log, sincos and erfcx. */
 ipa_status ipa_calibrate_fp64(double* results, void* stream);
 
 /* Text of the calling thread's last error ("" if none). */

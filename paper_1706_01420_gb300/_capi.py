@@ -51,7 +51,7 @@ PROTOTYPES = {
                              c_void_p, POINTER(ipa_event_buffers), c_void_p]),
     "ipa_fit_batch": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
                                 POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                c_int32, c_double, c_void_p]),
+                                c_void_p, c_int32, c_double, c_void_p]),
     "ipa_reserve": (c_int32, [c_int64, c_int32]),
     "ipa_calibrate_fp64": (c_int32, [POINTER(c_double), c_void_p]),
     "ipa_last_error": (c_char_p, []),

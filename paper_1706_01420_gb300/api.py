@@ -149,14 +149,16 @@ def ipa_fit_batch(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: l
     nll = torch.zeros(n_fits, dtype=torch.float64, device=dev)
     status = torch.zeros(n_fits, dtype=torch.int32, device=dev)
     iters = torch.zeros(n_fits, dtype=torch.int32, device=dev)
+    passes = torch.zeros(n_fits, dtype=torch.int32, device=dev)
     e = ipa_events(ev)
     spec = _spec(params)
     _check(_lib().ipa_fit_batch(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
                                 n_fits, spec, _ptr(theta, name="theta"), _ptr(err, name="err"),
                                 _ptr(nll, name="nll"), _ptr(status, torch.int32, "status"),
-                                _ptr(iters, torch.int32, "iters"), max_iter, tol, _stream(stream)),
+                                _ptr(iters, torch.int32, "iters"), _ptr(passes, torch.int32, "passes"),
+                                max_iter, tol, _stream(stream)),
            "ipa_fit_batch")
-    return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters}
+    return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters, "passes": passes}
 
 
 def ipa_reserve(max_events: int, max_segments: int = 1):
@@ -165,9 +167,10 @@ def ipa_reserve(max_events: int, max_segments: int = 1):
 
 def ipa_calibrate_fp64(stream=None) -> dict:
     """DFMA rate and FP64 math-function costs of the current GPU (see the header)."""
-    r = (ctypes.c_double * 9)()
+    r = (ctypes.c_double * 13)()
     _check(_lib().ipa_calibrate_fp64(r, _stream(stream)), "ipa_calibrate_fp64")
-    names = ["dfma_per_clk_per_sm", "dfma_per_s", "exp", "erfc", "log", "sincos", "sqrt", "rcp", "sm_mhz"]
+    names = ["dfma_per_clk_per_sm", "dfma_per_s", "exp", "erfc", "log", "sincos", "sqrt", "rcp", "sm_mhz",
+             "exp_fast", "log_fast", "sincos_fast", "erfcx_poly"]
     return dict(zip(names, list(r)))
 
 

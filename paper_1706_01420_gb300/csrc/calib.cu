@@ -7,6 +7,7 @@
 // ratio is the SM clock during the run.
 #include <math.h>
 
+#include "fp64_math.cuh"
 #include "ipa_internal.cuh"
 
 namespace ipa {
@@ -19,6 +20,11 @@ template <int OP>
 __global__ void __launch_bounds__(kCalThreads)
 calib_kernel(const double* __restrict__ in, double* __restrict__ out, int iters,
              long long* __restrict__ cycles) {
+    __shared__ MathTables mt;
+    if (OP >= 7) {
+        load_math_tables(&mt);
+        __syncthreads();
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double x[8];
 #pragma unroll
@@ -38,6 +44,15 @@ calib_kernel(const double* __restrict__ in, double* __restrict__ out, int iters,
             }
             if (OP == 5) x[k] = sqrt(x[k] + 1.0);           // tends to 1.618
             if (OP == 6) x[k] = 1.0 / (x[k] + 1.5);         // stays in (0.3, 0.7)
+            // the library's own table-driven functions (fp64_math.cuh)
+            if (OP == 7) x[k] = exp_fast(x[k], &mt) * 1e-3;
+            if (OP == 8) x[k] = log_fast(x[k] + 2.0, &mt);
+            if (OP == 9) {
+                double s, c;
+                sincos_fast(x[k], &mt, &s, &c);
+                x[k] = s + c;
+            }
+            if (OP == 10) x[k] = erfcx_poly(x[k], &mt) - 0.25;  // stays in [0, 1]
         }
     }
     const long long c1 = clock64();
@@ -80,10 +95,11 @@ ipa_status run_one(const double* in, double* out, long long* cyc, int blocks, in
 }  // namespace
 }  // namespace ipa
 
-// results (host, 9 doubles):
+// results (host, 13 doubles):
 //   [0] DFMA per clock per SM, [1] DFMA per second (whole GPU),
-//   [2..7] cost in DFMA slots of exp, erfc, log, sincos, sqrt, 1/x,
-//   [8] SM clock during the DFMA run [MHz].
+//   [2..7] cost in DFMA slots of the library exp, erfc, log, sincos, sqrt, 1/x,
+//   [8] SM clock during the DFMA run [MHz],
+//   [9..12] cost of this library's exp_fast, log_fast, sincos_fast, erfcx_poly.
 extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     using namespace ipa;
     if (!results) {
@@ -108,8 +124,8 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
         return st;
     }
     cudaMemsetAsync(in, 0, sizeof(double) * n, s);
-    double sec[7], cpb[7];
-    const int iters[7] = {4096, 256, 128, 256, 256, 512, 512};
+    double sec[11], cpb[11];
+    const int iters[11] = {4096, 256, 128, 256, 256, 512, 512, 256, 256, 256, 256};
     st = run_one<0>(in, out, cyc, blocks, iters[0], s, &sec[0], &cpb[0]);
     if (st == IPA_OK) st = run_one<1>(in, out, cyc, blocks, iters[1], s, &sec[1], &cpb[1]);
     if (st == IPA_OK) st = run_one<2>(in, out, cyc, blocks, iters[2], s, &sec[2], &cpb[2]);
@@ -117,6 +133,10 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     if (st == IPA_OK) st = run_one<4>(in, out, cyc, blocks, iters[4], s, &sec[4], &cpb[4]);
     if (st == IPA_OK) st = run_one<5>(in, out, cyc, blocks, iters[5], s, &sec[5], &cpb[5]);
     if (st == IPA_OK) st = run_one<6>(in, out, cyc, blocks, iters[6], s, &sec[6], &cpb[6]);
+    if (st == IPA_OK) st = run_one<7>(in, out, cyc, blocks, iters[7], s, &sec[7], &cpb[7]);
+    if (st == IPA_OK) st = run_one<8>(in, out, cyc, blocks, iters[8], s, &sec[8], &cpb[8]);
+    if (st == IPA_OK) st = run_one<9>(in, out, cyc, blocks, iters[9], s, &sec[9], &cpb[9]);
+    if (st == IPA_OK) st = run_one<10>(in, out, cyc, blocks, iters[10], s, &sec[10], &cpb[10]);
     cudaFree(in);
     cudaFree(out);
     cudaFree(cyc);
@@ -127,10 +147,11 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     results[1] = ops_per_sm * sms / sec[0];
     const double dfma_time_per_op = sec[0] / (ops_per_sm * sms);
     // each loop body adds one FP64 operation besides the call, except erfc
-    const double extra[7] = {0.0, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0};
-    for (int f = 1; f < 7; ++f) {
+    const double extra[11] = {0.0, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+    for (int f = 1; f < 11; ++f) {
         const double calls = (double)blocks * kCalThreads * iters[f] * 8.0;
-        results[1 + f] = (sec[f] / calls) / dfma_time_per_op - extra[f];
+        const double cost = (sec[f] / calls) / dfma_time_per_op - extra[f];
+        results[f < 7 ? 1 + f : 2 + f] = cost;
     }
     results[8] = cpb[0] / sec[0] * 1e-6;
     return IPA_OK;

@@ -1,23 +1,24 @@
-// Step a1 of the hot path: one thread per fit turns theta into the Consts
+// Step a1 of the hot path: one warp per fit turns theta into the Consts
 // record read by every event tile (see consts.cuh for the formulas).
 #include "consts.cuh"
 
 namespace ipa {
 
 namespace {
+// One warp per fit (segment).
 __global__ void consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg,
                               Consts* __restrict__ out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n_seg) compute_consts(m, theta + (size_t)s * m.n_par, out + s);
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s < n_seg) compute_consts_warp(m, theta + (size_t)s * m.n_par, out + s);
 }
 }  // namespace
 
 ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
                          cudaStream_t st) {
     if (n_seg <= 0) return IPA_OK;
-    const int block = 64;
-    const int grid = (n_seg + block - 1) / block;
-    consts_kernel<<<grid, block, 0, st>>>(m, theta, n_seg, out);
+    const int warps = 4;
+    const int grid = (n_seg + warps - 1) / warps;
+    consts_kernel<<<grid, 32 * warps, 0, st>>>(m, theta, n_seg, out);
     return cuda_fail(cudaGetLastError(), "consts kernel launch");
 }
 

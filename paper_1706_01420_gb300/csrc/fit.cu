@@ -29,7 +29,8 @@ namespace ipa {
 namespace {
 
 constexpr int kMaxP = 10;          // parameters of the largest model
-constexpr double kSwitch = 1e-2;   // BFGS -> finite-difference Newton (decrement, sigma units)
+constexpr double kSwitch = 1e-3;   // BFGS -> finite-difference Newton (decrement, sigma units)
+constexpr double kRehess = 2e-3;   // Newton moved further than this (sigma units): Hessian again
 constexpr int kGraphSteps = 8;     // passes per graph replay
 enum Phase { kInit = 0, kLS = 1, kHess = 2, kNewton = 3, kDone = 4 };
 
@@ -50,8 +51,9 @@ struct State {
     double s_prev[kMaxP];     // step of the current trial (free components)
     double h[kMaxP];          // finite-difference steps
     double ga[kMaxP];         // gradient at the first stencil point of the current column
+    double theta_h[kMaxP];    // point where H was taken (free components)
     double f, gd, alpha;
-    int phase, iter, passes, hess_j, newton, status, scaled, onesided;
+    int phase, iter, passes, hess_j, newton, status, scaled, onesided, rehess;
 };
 
 __device__ inline double clampd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
@@ -122,6 +124,7 @@ __device__ void set_hess_point(const Spec& sp, State& S, double* theta_eval) {
 __device__ void start_hess(const Spec& sp, State& S, double* theta_eval) {
     S.phase = kHess;
     S.hess_j = 0;
+    for (int a = 0; a < sp.n_free; ++a) S.theta_h[a] = S.theta[sp.free_idx[a]];
     for (int a = 0; a < sp.n_free; ++a) {
         const int p = sp.free_idx[a];
         double h = 2e-3 * sqrt(fmax(S.Hinv[a * kMaxP + a], 0.0));
@@ -193,6 +196,20 @@ __device__ void newton_step(const Spec& sp, State& S, double* theta_eval) {
     }
     const double dec = sqrt(fmax(0.0, -gd));
     if (dec < sp.tol) {
+        // errors come from H: take it again if Newton moved away from where it was taken
+        double disp2 = 0.0;
+        for (int a = 0; a < n; ++a) {
+            const double da = S.theta[sp.free_idx[a]] - S.theta_h[a];
+            for (int b = 0; b < n; ++b) {
+                const double db = S.theta[sp.free_idx[b]] - S.theta_h[b];
+                disp2 += da * 0.5 * (S.H[a * kMaxP + b] + S.H[b * kMaxP + a]) * db;
+            }
+        }
+        if (!S.rehess && disp2 > kRehess * kRehess) {
+            S.rehess = 1;
+            start_hess(sp, S, theta_eval);
+            return;
+        }
         finish(sp, S, IPA_FIT_CONVERGED);
         return;
     }
@@ -402,6 +419,7 @@ __global__ void init_kernel(Spec sp, int n_fits, const double* __restrict__ thet
     S.status = IPA_FIT_MAXITER;
     S.scaled = 0;
     S.onesided = 0;
+    S.rehess = 0;
     S.f = 0.0;
     active[i] = 1;
 }
@@ -409,7 +427,7 @@ __global__ void init_kernel(Spec sp, int n_fits, const double* __restrict__ thet
 __global__ void final_kernel(Spec sp, int n_fits, const State* __restrict__ states,
                              double* __restrict__ theta_io, double* __restrict__ err,
                              double* __restrict__ nll, int32_t* __restrict__ status,
-                             int32_t* __restrict__ iters) {
+                             int32_t* __restrict__ iters, int32_t* __restrict__ passes) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_fits) return;
     const State& S = states[i];
@@ -424,6 +442,7 @@ __global__ void final_kernel(Spec sp, int n_fits, const State* __restrict__ stat
     if (nll) nll[i] = S.f;
     if (status) status[i] = S.phase == kDone ? S.status : IPA_FIT_MAXITER;
     if (iters) iters[i] = S.iter;
+    if (passes) passes[i] = S.passes;
 }
 
 // Active-masked tile map: inactive fits get no tiles.
@@ -484,8 +503,8 @@ struct DevBuf {
 extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev,
                                     const int64_t* seg_off_dev, int32_t n_fits, const ipa_param* spec,
                                     double* theta_io_dev, double* err_out_dev, double* nll_out_dev,
-                                    int32_t* fit_status_dev, int32_t* iters_out_dev, int32_t max_iter,
-                                    double tol, void* stream) {
+                                    int32_t* fit_status_dev, int32_t* iters_out_dev,
+                                    int32_t* passes_out_dev, int32_t max_iter, double tol, void* stream) {
     using namespace ipa;
     ipa_status st = check_model(model);
     if (st != IPA_OK) return st;
@@ -606,7 +625,7 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     }
     if (st != IPA_OK) return done(st);
     final_kernel<<<fg, fb, 0, s>>>(sp, n_fits, states, theta_io_dev, err_out_dev, nll_out_dev,
-                                   fit_status_dev, iters_out_dev);
+                                   fit_status_dev, iters_out_dev, passes_out_dev);
     st = cuda_fail(cudaGetLastError(), "fit final");
     st = done(st);
     if (st == IPA_OK) st = cuda_fail(cudaGetLastError(), "fit final sync");

@@ -1,0 +1,139 @@
+"""Generate fp64_tables.cuh: the tables and split constants of the library's
+FP64 elementary functions (fp64_math.cuh), computed in 60-digit arithmetic
+with mpmath and rounded once to double.
+
+  exp:    T_j = 2^(j/64), j = 0..63; 64/ln2; ln2/64 as hi + lo
+  log:    c_j = 1/(1 + (j + 1/2)/128) rounded to double, j = 0..127, and
+          L_j = -log(c_j) of that rounded c_j (so log m = L_j + log1p(m c_j - 1)
+          holds exactly); ln2
+  sincos: S_j = sin(j pi/32), C_j = cos(j pi/32), j = 0..63; 32/pi; pi/32 as hi + lo
+  erfcx:  erfcx(x) = exp(x^2) erfc(x) on x in [0, 6.25] as 13 pieces centred at
+          k/2 (k = 0..12), each the degree-13 Chebyshev interpolant on
+          [k/2 - 0.26, k/2 + 0.26] written as monomials in u = x - k/2.
+
+Run: python paper_1706_01420_gb300/csrc/gen_fp64_tables.py  (rewrites the header)
+"""
+from __future__ import annotations
+
+import os
+
+import mpmath as mp
+
+mp.mp.dps = 60
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+ERFCX_PIECES = 13
+ERFCX_DEG = 13
+ERFCX_HALF = mp.mpf("0.26")
+
+
+def d(x) -> float:
+    return float(mp.mpf(x))
+
+
+def split(x):
+    hi = d(x)
+    lo = d(mp.mpf(x) - mp.mpf(hi))
+    return hi, lo
+
+
+def cheb_monomial(f, a, b, n):
+    c = (a + b) / 2
+    h = (b - a) / 2
+    nodes = [mp.cos(mp.pi * (k + mp.mpf(1) / 2) / (n + 1)) for k in range(n + 1)]
+    vals = [f(c + h * t) for t in nodes]
+    ck = []
+    for j in range(n + 1):
+        s = mp.fsum(vals[k] * mp.cos(mp.pi * j * (k + mp.mpf(1) / 2) / (n + 1)) for k in range(n + 1))
+        ck.append(2 * s / (n + 1) if j else s / (n + 1))
+    T = [[mp.mpf(0)] * (n + 1) for _ in range(n + 1)]
+    T[0][0] = mp.mpf(1)
+    T[1][1] = mp.mpf(1)
+    for j in range(2, n + 1):
+        for i in range(n + 1):
+            T[j][i] = (2 * T[j - 1][i - 1] if i else 0) - T[j - 2][i]
+    mono_t = [mp.fsum(ck[j] * T[j][i] for j in range(n + 1)) for i in range(n + 1)]
+    return [mono_t[i] / h ** i for i in range(n + 1)]
+
+
+def erfcx(x):
+    return mp.exp(x * x) * mp.erfc(x)
+
+
+def fmt(vals, per_line=3):
+    out = []
+    for i in range(0, len(vals), per_line):
+        out.append("    " + ", ".join(repr(v) for v in vals[i:i + per_line]) + ",")
+    return "\n".join(out)
+
+
+def main():
+    exp_tab = [d(mp.power(2, mp.mpf(j) / 64)) for j in range(64)]
+    ln2 = mp.log(2)
+    inv_ln2_64 = d(64 / ln2)
+    ln2_64_hi, ln2_64_lo = split(ln2 / 64)
+    log_c = [d(1 / (1 + (mp.mpf(j) + mp.mpf(1) / 2) / 128)) for j in range(128)]
+    log_l = [d(-mp.log(mp.mpf(c))) for c in log_c]
+    sin_tab = [d(mp.sin(j * mp.pi / 32)) for j in range(64)]
+    cos_tab = [d(mp.cos(j * mp.pi / 32)) for j in range(64)]
+    inv_pi_32 = d(32 / mp.pi)
+    pi_32_hi, pi_32_lo = split(mp.pi / 32)
+    erfcx_tab = []
+    for k in range(ERFCX_PIECES):
+        c = mp.mpf(k) / 2
+        coef = cheb_monomial(erfcx, c - ERFCX_HALF, c + ERFCX_HALF, ERFCX_DEG)
+        erfcx_tab.extend(d(v) for v in coef)
+
+    text = f"""// Generated by gen_fp64_tables.py (mpmath, 60 digits, rounded once to double).
+// Do not edit by hand.
+#pragma once
+
+namespace ipa {{
+namespace fp64tab {{
+
+constexpr double kInvLn2x64 = {inv_ln2_64!r};      // 64 / ln 2
+constexpr double kLn2d64Hi = {ln2_64_hi!r};        // ln 2 / 64, high part
+constexpr double kLn2d64Lo = {ln2_64_lo!r};        // ln 2 / 64, low part
+constexpr double kLn2Hi = {split(ln2)[0]!r};        // ln 2, high part
+constexpr double kLn2Lo = {split(ln2)[1]!r};        // ln 2, low part
+constexpr double kInvPid32 = {inv_pi_32!r};        // 32 / pi
+constexpr double kPid32Hi = {pi_32_hi!r};          // pi / 32, high part
+constexpr double kPid32Lo = {pi_32_lo!r};          // pi / 32, low part
+constexpr int kErfcxPieces = {ERFCX_PIECES};
+constexpr int kErfcxCoeffs = {ERFCX_DEG + 1};
+
+// 2^(j/64)
+__device__ const double kExp2Tab[64] = {{
+{fmt(exp_tab)}
+}};
+
+// c_j ~ 1/(1 + (j + 1/2)/128) and L_j = -log(c_j)
+__device__ const double kLogInv[128] = {{
+{fmt(log_c)}
+}};
+__device__ const double kLogTab[128] = {{
+{fmt(log_l)}
+}};
+
+// sin(j pi/32), cos(j pi/32)
+__device__ const double kSinTab[64] = {{
+{fmt(sin_tab)}
+}};
+__device__ const double kCosTab[64] = {{
+{fmt(cos_tab)}
+}};
+
+// erfcx piece k (centre k/2): coefficients of u^0 .. u^{ERFCX_DEG}
+__device__ const double kErfcxTab[{ERFCX_PIECES * (ERFCX_DEG + 1)}] = {{
+{fmt(erfcx_tab, 2)}
+}};
+
+}}  // namespace fp64tab
+}}  // namespace ipa
+"""
+    with open(os.path.join(HERE, "fp64_tables.cuh"), "w") as f:
+        f.write(text)
+
+
+if __name__ == "__main__":
+    main()

@@ -86,7 +86,7 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out);
 // consts.cu: theta (n_seg x n_par) -> Consts[n_seg]
 ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
                          cudaStream_t s);
-// compute_consts (consts.cuh): device function theta -> Consts, shared by the kernels.
+// compute_consts_warp (consts.cuh): one warp turns theta into a Consts record.
 
 // nll.cu: segmented NLL(+grad) over precomputed consts; out: (1 + n_par) per segment
 // With seg_off == nullptr there is one segment [0, n).  Otherwise seg_tiles must

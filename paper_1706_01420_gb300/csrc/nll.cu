@@ -4,11 +4,23 @@
 //
 // Sec. 3 of the paper evaluates the PDF with one thread per event, takes the
 // log of the signal/background mixture in a second launch and sums the logs
-// on the host.  Here one kernel does all of it: each 256-thread block walks
-// 512-event tiles (two events per thread, one 16-byte load per column),
-// keeps FP64 accumulators in registers, reduces them with a fixed tree, and
-// the block that finishes the last tile of a segment reduces that segment's
-// tile partials in fixed order and writes its NLL and gradient.
+// on the host.  Here one kernel does all of it.  Work is split into 512-event
+// tiles owned by single warps: lane l accumulates events l, l+32, ..., l+480
+// of its tile in order (coalesced 8-byte loads), the warp reduces its FP64
+// accumulators with a fixed shuffle tree and writes one partial per tile.
+// The warp that completes the last tile of a segment reduces that segment's
+// partials in fixed order and writes its NLL and gradient.  No block-wide
+// barrier sits in the event loop, and the result does not depend on the grid.
+//
+// The GPU has 2 FP64 operations per clock per SM, so the per-event arithmetic
+// is arranged to spend as few of them as possible:
+//   * the decay-time term uses erfc(z) = 2 - exp(-z^2) erfcx(|z|) for z < 0 and
+//     erfc(z) = exp(-z^2) erfcx(z) for z >= 0, with exp(-Gamma tau + Gamma^2
+//     sigma^2/2) exp(-z^2) = exp(-tau^2/(2 sigma^2)): the Gaussian factor that
+//     the gradient needs anyway replaces the exponential inside erfc;
+//   * exp, log, sincos and erfcx are table-driven FP64 (fp64_math.cuh);
+//   * sin(theta_K) sin(theta_mu) is one square root; the constant factors of
+//     the ten angular functions are folded into the amplitude coefficients.
 //
 // Gradient (fused adjoint).  With r = w/P, every derivative of the NLL is a
 // contraction of a few per-event sums with parameter-only factors:
@@ -21,54 +33,88 @@
 // parameter and the angular derivatives cost nothing per event.
 #include <math.h>
 
+#include "fp64_math.cuh"
 #include "ipa_internal.cuh"
 
 namespace ipa {
 namespace {
 
-constexpr double kSqrt2 = 1.41421356237309504880;
-constexpr double k2OverSqrt6 = 0.81649658092772603273;
-constexpr double k2OverSqrt3 = 1.15470053837925152902;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kNllBlock = 32 * kWarpsPerBlock;
+constexpr int kPerLane = kTile / 32;                 // events per lane per tile
 
-// f_k(cos thK, cos thmu, phi), k = 1..10 (Sec. 4, helicity basis).
-__device__ __forceinline__ void angular_basis(double ck, double cl, double phi, double f[10]) {
-    const double sk2 = fma(-ck, ck, 1.0);
-    const double sl2 = fma(-cl, cl, 1.0);
-    const double sk = sqrt(sk2), sl = sqrt(sl2);
+// Constant factors c_k of f_k = c_k f'_k, where f'_k is the product of
+// sines and cosines the kernel evaluates (sec. 4 helicity basis).
+__device__ const double kBasisScale[10] = {
+    1.0, 0.5, 0.5, 1.0, 1.41421356237309504880, -1.41421356237309504880, 1.0 / 3.0,
+    0.81649658092772603273, -0.81649658092772603273, 1.15470053837925152902};
+
+// Per-warp copy of a segment's constants in shared memory.
+struct WarpConsts {
+    Consts c;
+    double hp[10];   // h_k c_k: coefficients of the unscaled products f'_k
+};
+
+// f'_k(cos thK, cos thmu, phi): f_k without its constant factor.
+__device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi, const MathTables* mt,
+                                               double f[10]) {
     double sp, cp;
-    sincos(phi, &sp, &cp);
+    sincos_fast(phi, mt, &sp, &cp);
+    const double sk2 = fma(-ck, ck, 1.0);
+    const double cl2 = cl * cl;
+    const double sl2 = 1.0 - cl2;
+    const double cp2 = cp * cp;
+    const double sksl2 = sk2 * sl2;
+    const double q = sqrt(sksl2);                  // sin thK sin thmu
     f[0] = ck * ck * sl2;
-    f[1] = 0.5 * sk2 * (1.0 - sl2 * cp * cp);
-    f[2] = 0.5 * sk2 * (1.0 - sl2 * sp * sp);
-    f[3] = sk2 * sl2 * sp * cp;
-    const double a = sk * ck * sl * cl;
-    f[4] = kSqrt2 * a * cp;
-    f[5] = -kSqrt2 * a * sp;
-    f[6] = sl2 * (1.0 / 3.0);
-    const double b = sk * sl * cl;
-    f[7] = k2OverSqrt6 * b * cp;
-    f[8] = -k2OverSqrt6 * b * sp;
-    f[9] = k2OverSqrt3 * ck * sl2;
+    f[1] = sk2 * fma(-sl2, cp2, 1.0);
+    f[2] = sk2 * fma(sl2, cp2, cl2);               // sk2 (1 - sl2 sp^2)
+    f[3] = sksl2 * (sp * cp);
+    const double a = q * (ck * cl);
+    f[4] = a * cp;
+    f[5] = a * sp;
+    f[6] = sl2;
+    const double b = q * cl;
+    f[7] = b * cp;
+    f[8] = b * sp;
+    f[9] = ck * sl2;
 }
 
-// One event: accumulate w log P (and the adjoint sums).
-template <int KIND, bool GRAD>
-__device__ __forceinline__ void event(const Consts& c, double t, double ck, double cl, double phi,
-                                      double w, double* acc) {
-    const double tau = t - c.mu;
-    const double E = exp(fma(-c.Gamma, tau, c.c_exp));
+// Decay-time factor T = g(tau) and the Gaussian G = N(tau; 0, sigma).
+__device__ __forceinline__ void time_terms(const Consts& c, double tau, const MathTables* mt,
+                                           double* T, double* G) {
+    const double E = exp_fast(fma(-c.Gamma, tau, c.c_exp), mt);
+    const double Gx = exp_fast(-(tau * tau) * c.k_g, mt);  // exp(-tau^2 / (2 sigma^2))
     const double z = (c.Gs2 - tau) * c.k_z;
-    const double T = 0.5 * E * erfc(z);
+    const double x = fabs(z);
+    double X = erfcx_poly(x, mt);
+    if (x > 6.25) {
+        // z < 0: the erfcx term is below 1e-17 of E; z >= 0 (tau far below the
+        // resolution peak, outside the usual range): exact library erfcx
+        X = z < 0.0 ? 0.0 : erfcx(x);
+    }
+    const double hgx = 0.5 * Gx * X;
+    *T = z < 0.0 ? E - hgx : hgx;
+    *G = c.cG * Gx;
+}
+
+template <int KIND, bool GRAD>
+__device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt, double t, double ck,
+                                      double cl, double phi, double w, double* acc) {
+    const Consts& c = wc.c;
+    const double tau = t - c.mu;
+    double T, G;
+    time_terms(c, tau, mt, &T, &G);
     double A = 1.0;
     double f[10];
     if (KIND == IPA_MODEL_ANGTIME4D) {
-        angular_basis(ck, cl, phi, f);
-        A = 0.0;
+        basis_unscaled(ck, cl, phi, mt, f);
+        A = wc.hp[0] * f[0];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) A = fma(c.h[k], f[k], A);
+        for (int k = 1; k < 10; ++k) A = fma(wc.hp[k], f[k], A);
     }
     const double P = fma(c.cs * T, A, c.cb);
-    acc[0] = fma(w, log(P), acc[0]);
+    acc[0] = fma(w, log_fast(P, mt), acc[0]);
     if (GRAD) {
         const double r = w / P;
         acc[1] += r;
@@ -80,7 +126,6 @@ __device__ __forceinline__ void event(const Consts& c, double t, double ck, doub
         } else {
             acc[2] += rT;
         }
-        const double G = c.cG * exp(-(tau * tau) * c.k_g);
         const double rA = r * A;
         const double dTG = fma(c.Gs2 - tau, T, -c.s2 * G);
         const double dTs = fma(c.G2s, T, -fma(tau, c.inv_s, c.Gsig) * G);
@@ -91,31 +136,13 @@ __device__ __forceinline__ void event(const Consts& c, double t, double ck, doub
     }
 }
 
-// Fixed reduction tree over the 256 slots of a block: at each level slot s
-// adds slot s + half (half = 128, 64, 32 through shared memory, then 16..1
-// by warp shuffles).  The result is in thread 0.
+// Fixed shuffle tree over the 32 lanes: at each level lane l adds lane l + half.
 template <int NA>
-__device__ __forceinline__ void block_tree(double* acc, double (*red)[kSlots / 2]) {
-    const int s = threadIdx.x;
+__device__ __forceinline__ void warp_tree(double* acc) {
 #pragma unroll
-    for (int half = kSlots / 2; half >= 32; half >>= 1) {
-        if (s >= half && s < 2 * half) {
+    for (int half = 16; half >= 1; half >>= 1) {
 #pragma unroll
-            for (int a = 0; a < NA; ++a) red[a][s - half] = acc[a];
-        }
-        __syncthreads();
-        if (s < half) {
-#pragma unroll
-            for (int a = 0; a < NA; ++a) acc[a] += red[a][s];
-        }
-        __syncthreads();
-    }
-    if (s < 32) {
-#pragma unroll
-        for (int half = 16; half >= 1; half >>= 1) {
-#pragma unroll
-            for (int a = 0; a < NA; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], half);
-        }
+        for (int a = 0; a < NA; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], half);
     }
 }
 
@@ -134,16 +161,21 @@ __device__ __forceinline__ int find_segment(const int64_t* seg_tiles, int n_seg,
 }
 
 // Write NLL (and gradient) of one segment from its reduced accumulators.
+// For the 4D model acc[2 + k] holds sum r T f'_k; S_k = c_k times that.
 template <int KIND, bool GRAD>
 __device__ void finalize(const Consts& c, const double* acc, int n_par, double* out) {
     out[0] = -acc[0];
     if (!GRAD) return;
     const double Q = acc[1];
-    double SH;
     constexpr int kD = KIND == IPA_MODEL_ANGTIME4D ? 12 : 3;
+    double S[10];
+    double SH;
     if (KIND == IPA_MODEL_ANGTIME4D) {
         SH = 0.0;
-        for (int k = 0; k < 10; ++k) SH = fma(c.h[k], acc[2 + k], SH);
+        for (int k = 0; k < 10; ++k) {
+            S[k] = kBasisScale[k] * acc[2 + k];
+            SH = fma(c.h[k], S[k], SH);
+        }
     } else {
         SH = acc[2];
     }
@@ -152,7 +184,7 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
     if (KIND == IPA_MODEL_ANGTIME4D) {
         for (int j = 0; j < 6; ++j) {
             double s = 0.0;
-            for (int k = 0; k < 10; ++k) s = fma(c.dh[k][j], acc[2 + k], s);
+            for (int k = 0; k < 10; ++k) s = fma(c.dh[k][j], S[k], s);
             out[1 + IPA_A0SQ + j] = -c.cs * s;
         }
     }
@@ -161,16 +193,20 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
 }
 
 template <int KIND, bool GRAD>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kNllBlock, 4)
 nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
            const int64_t* __restrict__ seg_tiles, int n_seg, const Consts* __restrict__ consts,
            double* __restrict__ partials, unsigned* __restrict__ counters,
            double* __restrict__ out, int n_par) {
     constexpr int NA = n_acc(KIND, GRAD);
     const int out_stride = GRAD ? 1 + n_par : 1;
-    __shared__ double red[NA][kSlots / 2];
-    __shared__ __align__(16) Consts sc;
-    __shared__ int s_last;
+    __shared__ MathTables mt;
+    __shared__ __align__(16) WarpConsts wcs[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    WarpConsts& wc = wcs[wib];
+
+    load_math_tables(&mt);
+    __syncthreads();
 
     const bool single = seg_off == nullptr;
     const int64_t total = single ? (n + kTile - 1) / kTile : __ldg(seg_tiles + n_seg);
@@ -185,8 +221,10 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
         }
     }
 
+    const int64_t warp0 = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
     int cur = -1;
-    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    for (int64_t tile = warp0; tile < total; tile += n_warps) {
         int seg = 0;
         int64_t t0 = 0, t1 = total, ev0 = 0, ev1 = n;
         if (!single) {
@@ -198,11 +236,13 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
             if (ev1 < ev0) ev1 = ev0;
         }
         if (seg != cur) {
-            __syncthreads();
+            __syncwarp();
             const double* src = reinterpret_cast<const double*>(consts + seg);
-            double* dst = reinterpret_cast<double*>(&sc);
-            for (int i = threadIdx.x; i < kConstsDoubles; i += blockDim.x) dst[i] = __ldg(src + i);
-            __syncthreads();
+            double* dst = reinterpret_cast<double*>(&wc.c);
+            for (int i = lane; i < kConstsDoubles; i += 32) dst[i] = __ldg(src + i);
+            __syncwarp();
+            if (lane < 10) wc.hp[lane] = wc.c.h[lane] * kBasisScale[lane];
+            __syncwarp();
             cur = seg;
         }
 
@@ -210,61 +250,48 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
 #pragma unroll
         for (int a = 0; a < NA; ++a) acc[a] = 0.0;
 
-        const int64_t i0 = ev0 + (tile - t0) * kTile + 2 * threadIdx.x;
-        if (i0 + 1 < ev1 && (ev0 & 1) == 0) {
-            const double2 t2 = __ldg(reinterpret_cast<const double2*>(cols.t + i0));
-            double2 w2 = make_double2(1.0, 1.0);
-            if (cols.w) w2 = __ldg(reinterpret_cast<const double2*>(cols.w + i0));
-            if (KIND == IPA_MODEL_ANGTIME4D) {
-                const double2 k2 = __ldg(reinterpret_cast<const double2*>(cols.ck + i0));
-                const double2 l2 = __ldg(reinterpret_cast<const double2*>(cols.cl + i0));
-                const double2 p2 = __ldg(reinterpret_cast<const double2*>(cols.phi + i0));
-                event<KIND, GRAD>(sc, t2.x, k2.x, l2.x, p2.x, w2.x, acc);
-                event<KIND, GRAD>(sc, t2.y, k2.y, l2.y, p2.y, w2.y, acc);
-            } else {
-                event<KIND, GRAD>(sc, t2.x, 0.0, 0.0, 0.0, w2.x, acc);
-                event<KIND, GRAD>(sc, t2.y, 0.0, 0.0, 0.0, w2.y, acc);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int64_t i = i0 + e;
-                if (i < ev1) {
-                    const double w = cols.w ? __ldg(cols.w + i) : 1.0;
-                    if (KIND == IPA_MODEL_ANGTIME4D)
-                        event<KIND, GRAD>(sc, __ldg(cols.t + i), __ldg(cols.ck + i),
-                                          __ldg(cols.cl + i), __ldg(cols.phi + i), w, acc);
-                    else
-                        event<KIND, GRAD>(sc, __ldg(cols.t + i), 0.0, 0.0, 0.0, w, acc);
-                }
+        const int64_t base = ev0 + (tile - t0) * kTile + lane;
+#pragma unroll 1
+        for (int i = 0; i < kPerLane; ++i) {
+            const int64_t e = base + 32 * i;
+            if (e < ev1) {
+                const double w = cols.w ? __ldg(cols.w + e) : 1.0;
+                if (KIND == IPA_MODEL_ANGTIME4D)
+                    event<KIND, GRAD>(wc, &mt, __ldg(cols.t + e), __ldg(cols.ck + e), __ldg(cols.cl + e),
+                                      __ldg(cols.phi + e), w, acc);
+                else
+                    event<KIND, GRAD>(wc, &mt, __ldg(cols.t + e), 0.0, 0.0, 0.0, w, acc);
             }
         }
 
-        block_tree<NA>(acc, red);
-        if (threadIdx.x == 0) {
+        warp_tree<NA>(acc);
+        int last = 0;
+        if (lane == 0) {
 #pragma unroll
             for (int a = 0; a < NA; ++a) partials[tile * NA + a] = acc[a];
             __threadfence();
             const unsigned done = atomicAdd(counters + seg, 1u) + 1u;
-            s_last = (done == (unsigned)(t1 - t0));
+            last = (done == (unsigned)(t1 - t0));
         }
-        __syncthreads();
-        if (s_last) {
-            // this block wrote the segment's last tile: reduce its partials
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            // this warp wrote the segment's last tile: reduce the segment's partials
             __threadfence();
 #pragma unroll
             for (int a = 0; a < NA; ++a) acc[a] = 0.0;
-            for (int64_t tt = t0 + threadIdx.x; tt < t1; tt += kSlots) {
+            // lane l adds tiles l, l+32, l+64, ... in that order; unrolled so that
+            // the loads of several tiles are in flight at once
+#pragma unroll 8
+            for (int64_t tt = t0 + lane; tt < t1; tt += 32) {
 #pragma unroll
                 for (int a = 0; a < NA; ++a) acc[a] += __ldcg(partials + tt * NA + a);
             }
-            block_tree<NA>(acc, red);
-            if (threadIdx.x == 0) {
-                finalize<KIND, GRAD>(sc, acc, n_par, out + (size_t)seg * out_stride);
+            warp_tree<NA>(acc);
+            if (lane == 0) {
+                finalize<KIND, GRAD>(wc.c, acc, n_par, out + (size_t)seg * out_stride);
                 counters[seg] = 0u;
             }
         }
-        __syncthreads();
     }
 }
 
@@ -310,16 +337,17 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_off, const i
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, nll_kernel<KIND, GRAD>, kBlock, 0);
+            &per_sm, nll_kernel<KIND, GRAD>, kNllBlock, 0);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (seg_off == nullptr) {
         const int64_t tiles = (n + kTile - 1) / kTile;
-        grid = tiles < grid ? tiles : grid;
+        const int64_t need = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        grid = need < grid ? need : grid;
     }
     if (grid < 1) grid = 1;
-    nll_kernel<KIND, GRAD><<<(unsigned)grid, kBlock, 0, st>>>(
+    nll_kernel<KIND, GRAD><<<(unsigned)grid, kNllBlock, 0, st>>>(
         cols, n, seg_off, seg_tiles, n_seg, consts, sc->partials, sc->counters, out, n_par);
     return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
 }

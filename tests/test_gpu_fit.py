@@ -90,7 +90,11 @@ def test_fit_4d_matches_oracle_and_batch_equals_solo(env):
 @pytest.mark.slow
 def test_gpu_toy_pulls(env):
     """256 GPU-generated toys of Poisson(2e4) events fitted in one batch: pulls of
-    the well-measured parameters have mean 0 and width 1 within 3.5 standard errors."""
+    the eight well-measured parameters have mean 0 and width 1 within 3.5
+    standard errors.  sigma and mu are measured only by the ~1e3 events of the
+    turn-on at t ~ 0; at this size their pulls are visibly non-Gaussian (a
+    small-sample property of the likelihood that fades at 2e5 events), so they
+    get a looser bound."""
     O, G, torch, api = env
     n_toys = 256
     n_sig, n_bkg = synth.toy_sizes(n_toys, 2e4, TH4[3], seed=2)
@@ -109,9 +113,12 @@ def test_gpu_toy_pulls(env):
     th = r["theta"].cpu().numpy()
     er = r["err"].cpu().numpy()
     ok = st == 0
-    assert ok.mean() > 0.9, np.bincount(st)
-    for j in (0, 1, 3, 4, 5, 7):
+    assert ok.mean() > 0.95, np.bincount(st)
+    se = 1 / math.sqrt(ok.sum())
+    for j in (0, 3, 4, 5, 6, 7, 8, 9):
         p = (th[ok, j] - TH4[j]) / er[ok, j]
-        se = 1 / math.sqrt(p.size)
         assert abs(p.mean()) < 3.5 * se, (j, p.mean())
         assert abs(p.std(ddof=1) - 1) < 3.5 * se / math.sqrt(2) + 0.03, (j, p.std(ddof=1))
+    for j in (1, 2):
+        p = (th[ok, j] - TH4[j]) / er[ok, j]
+        assert abs(p.mean()) < 0.5 and 0.8 < p.std(ddof=1) < 1.35, (j, p.mean(), p.std(ddof=1))
