@@ -187,6 +187,24 @@ ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int
                          int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
                          void* stream);
 
+/* Largest event count accepted by ipa_nll_grad_noalloc (2^23). */
+#define IPA_NOALLOC_MAX_EVENTS 8388608
+
+/* ipa_nll_grad without any device allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory at call
+ * time -- a host framework whose allocator already reserved the GPU, or a
+ * latency-critical loop that must not pay for an allocation and the device
+ * synchronisation that growing library scratch implies.  Same arguments and
+ * results as ipa_nll_grad.  Its scratch is one fixed array compiled into the
+ * library (~1.9 MB, held on every GPU that loads the library until exit), so
+ * ev->n may not exceed IPA_NOALLOC_MAX_EVENTS (IPA_ERR_ARG otherwise).  The
+ * first call on each device looks the array's address up (cudaGetSymbolAddress)
+ * with that device current; make it before any stream capture.  The array is
+ * shared by all calls and keeps the last call's contents; calls that overlap
+ * on the GPU race on it. */
+ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
+                                double* out_dev, void* stream);
+
 /* Grow the library's device scratch on the current device to hold one call
  * over `max_events` events in up to `max_segments` segments, so that later
  * calls allocate nothing (needed before CUDA-graph capture).  Calls allocate

@@ -16,6 +16,7 @@ IPA_OK, IPA_ERR_ARG, IPA_ERR_OOM, IPA_ERR_CUDA, IPA_ERR_TIMEOUT, IPA_ERR_BUSY, I
 IPA_MODEL_TIME1D, IPA_MODEL_ANGTIME4D = 1, 2
 IPA_GAMMA, IPA_SIGMA, IPA_MU, IPA_FB, IPA_A0SQ, IPA_APESQ, IPA_DPA, IPA_DPE, IPA_FS, IPA_DS = range(10)
 IPA_NPAR_1D, IPA_NPAR_4D, IPA_MAX_PAR = 4, 10, 16
+IPA_NOALLOC_MAX_EVENTS = 8388608
 IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)
 STATUS_NAMES = {0: "IPA_OK", -1: "IPA_ERR_ARG", -2: "IPA_ERR_OOM", -3: "IPA_ERR_CUDA",
                 -4: "IPA_ERR_TIMEOUT", -5: "IPA_ERR_BUSY", 1: "IPA_PENDING"}
@@ -52,6 +53,7 @@ PROTOTYPES = {
     "ipa_fit_batch": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
                                 POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_int32, c_double, c_void_p]),
+    "ipa_nll_grad_noalloc": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
     "ipa_reserve": (c_int32, [c_int64, c_int32]),
     "ipa_calibrate_fp64": (c_int32, [POINTER(c_double), c_void_p]),
     "ipa_last_error": (c_char_p, []),

@@ -92,6 +92,16 @@ def ipa_nll_grad(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.T
     return out
 
 
+def ipa_nll_grad_noalloc(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor,
+                         stream=None) -> torch.Tensor:
+    """ipa_nll_grad with the library's fixed scratch array: allocates nothing on the
+    device (the caller passes `out`); at most IPA_NOALLOC_MAX_EVENTS events."""
+    e = ipa_events(ev)
+    _check(_lib().ipa_nll_grad_noalloc(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
+                                       _ptr(out, name="out"), _stream(stream)), "ipa_nll_grad_noalloc")
+    return out
+
+
 def ipa_nll_grad_segmented(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, theta: torch.Tensor,
                            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     n_seg = int(seg_off.numel()) - 1
