@@ -63,6 +63,24 @@ def flops_per_event(cal: dict) -> float:
     return f
 
 
+def kernel_traffic(n_events: int):
+    """DRAM bytes per launch of the fused kernel from the committed ncu capture
+    (profiles/traffic.json), scaled by events; None if the kernel sources changed
+    since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, "paper_1706_01420_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["bytes_per_event"] * n_events
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -265,14 +283,7 @@ def main():
     peak_dfma_derived = 2.0 * 152 * 2070e6          # DFMA/s: 2 per clock per SM x 152 SMs x 2070 MHz
     achieved = fpe * N_EVENTS / (kernel_ms * 1e-3) / 1e12
     peak = 2.0 * peak_dfma_derived / 1e12
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            tr = json.load(open(tr_path))
-            traffic = tr.get("nll_kernel_4d_grad_bytes_per_launch_1e6")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = kernel_traffic(N_EVENTS)
 
     # e2e: pinned host columns -> device, call, result -> host, every step
     pinned = {k: torch.tensor(v).pin_memory() for k, v in cols_h.items()}
