@@ -447,6 +447,75 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
                     "pull_mean_width": pulls}
     del cols, rb, thb
     out["large"] = run_large(api, synth, torch, dev, m, theta, params)
+    out["serve"] = run_serve(api, synth, torch, dev, m, theta, params)
+    return out
+
+
+def run_serve(api, synth, torch, dev, m, theta, params, n_req: int = 60,
+              rates=(25.0, 50.0, 100.0, 200.0)) -> dict:
+    """Fit requests arriving Poisson at each rate, sizes log-uniform on [1e3, 1e7],
+    weights Normal(1, 0.2), events of the 4D PDF: latency (arrival -> result) and
+    throughput of the continuous-batching server vs plain sequential fits (one
+    ipa_fit_batch call per request, first come first served)."""
+    pool_n = 20_000_000
+    cols = gen_sample(api, torch, dev, m, theta, pool_n // 20000, 20000, seed=9)
+    pool = {k: v.cpu().numpy() for k, v in cols.items()}
+    del cols
+    pool["w"] = synth.weights(pool_n, 13)
+    d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
+    out = {"requests_per_rate": n_req, "sizes": "log-uniform [1e3, 1e7]", "weights": "Normal(1, 0.2)"}
+
+    def slices(rate):
+        reqs = synth.request_stream(n_req, rate, seed=int(rate))
+        rng = np.random.default_rng(int(rate) + 1)
+        return [(r.arrival_s, int(rng.integers(0, pool_n - r.n_events)), r.n_events) for r in reqs]
+
+    for rate in rates:
+        plan = slices(rate)
+        srv = api.ipa_server_create(m, 16 << 30, max_slots=64, max_iter=200, tol=1e-8)
+        lat, done_t = {}, {}
+        try:
+            pending = {}
+            t0 = time.perf_counter()
+            i = 0
+            while len(lat) < len(plan):
+                now = time.perf_counter() - t0
+                while i < len(plan) and plan[i][0] <= now:
+                    arr, a, n = plan[i]
+                    ev = {k: v[a:a + n] for k, v in pool.items()}
+                    pending[api.ipa_serve_submit(srv, ev, params)] = (i, arr)
+                    i += 1
+                for tk in list(pending):
+                    r = api.ipa_serve_poll(srv, tk, 10)
+                    if r is not None:
+                        k, arr = pending.pop(tk)
+                        tnow = time.perf_counter() - t0
+                        lat[k] = tnow - arr
+                        done_t[k] = tnow
+                time.sleep(0.0005)
+        finally:
+            api.ipa_server_destroy(srv)
+        ls = np.array([lat[k] for k in range(len(plan))])
+        span = max(done_t.values()) - plan[0][0]
+        # plain sequential: one fit call per request, first come first served
+        plat = []
+        t0 = time.perf_counter()
+        for arr, a, n in plan:
+            now = time.perf_counter() - t0
+            if now < arr:
+                time.sleep(arr - now)
+            ev = {k: torch.tensor(v[a:a + n], device=dev) for k, v in pool.items()}
+            th = torch.tensor(TH4[None, :], device=dev)
+            api.ipa_fit_batch(m, ev, d64([0, n]), params, th, max_iter=200, tol=1e-8)
+            torch.cuda.synchronize()
+            plat.append(time.perf_counter() - t0 - arr)
+        pspan = time.perf_counter() - t0 - plan[0][0]
+        pl = np.array(plat)
+        out[f"rate_{int(rate)}"] = {
+            "served": {"p50_s": float(np.percentile(ls, 50)), "p99_s": float(np.percentile(ls, 99)),
+                       "fits_per_s": len(plan) / span},
+            "plain_sequential": {"p50_s": float(np.percentile(pl, 50)), "p99_s": float(np.percentile(pl, 99)),
+                                 "fits_per_s": len(plan) / pspan}}
     return out
 
 

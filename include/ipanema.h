@@ -187,6 +187,39 @@ ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int
                          int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
                          void* stream);
 
+/* Fit server (continuous batching).  Fits of different sizes are submitted
+ * as they arrive; each is admitted into a device slot when a slot and a
+ * contiguous range of the event arena (the HBM budget, 40 bytes per event) are
+ * free, in submission order; all admitted fits advance together, four passes
+ * per tick, with the state machine of ipa_fit_batch, so a fit's result is
+ * bitwise the one ipa_fit_batch gives for it alone.  The paper fits one data
+ * set at a time (Sec. 3-4); this is the serving form of the same path. */
+typedef struct ipa_server ipa_server;
+
+/* Create a server on the current device: event arena of hbm_budget_bytes,
+ * max_slots concurrent fits, minimiser budget and tolerance as in
+ * ipa_fit_batch.  Starts one host worker thread.  *out owns device memory
+ * until ipa_server_destroy. */
+ipa_status ipa_server_create(const ipa_model* model, size_t hbm_budget_bytes, int32_t max_slots,
+                             int32_t max_iter, double tol, ipa_server** out);
+
+/* Submit one fit: ev (columns in host or device memory, any alignment; w may
+ * be NULL) and spec (host, n_par parameters: start value, limits, step, fixed).
+ * The events are copied before the call returns, so the caller may free them.
+ * *ticket identifies the fit.  IPA_ERR_ARG if ev->n exceeds the arena. */
+ipa_status ipa_serve_submit(ipa_server* server, const ipa_events* ev, const ipa_param* spec,
+                            uint64_t* ticket);
+
+/* Poll a fit: IPA_PENDING while it waits or runs; IPA_OK once finished, with
+ * theta_out and err_out (host, n_par each), *nll and *fit_status (IPA_FIT_*)
+ * written (NULL outputs are skipped) and the ticket released; IPA_ERR_ARG for
+ * an unknown ticket; the server's error status if it stopped on a CUDA error. */
+ipa_status ipa_serve_poll(ipa_server* server, uint64_t ticket, double* theta_out, double* err_out,
+                          double* nll, int32_t* fit_status);
+
+/* Stop the worker, drop unfinished fits and free the server's memory. */
+ipa_status ipa_server_destroy(ipa_server* server);
+
 /* Largest event count accepted by ipa_nll_grad_noalloc (2^23). */
 #define IPA_NOALLOC_MAX_EVENTS 8388608
 

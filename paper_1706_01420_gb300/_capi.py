@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint64, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_uint64, c_void_p
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libipanema.so")
 
@@ -54,6 +54,12 @@ PROTOTYPES = {
                                 POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_int32, c_double, c_void_p]),
     "ipa_nll_grad_noalloc": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
+    "ipa_server_create": (c_int32, [POINTER(ipa_model), c_size_t, c_int32, c_int32, c_double,
+                                    POINTER(c_void_p)]),
+    "ipa_serve_submit": (c_int32, [c_void_p, POINTER(ipa_events), POINTER(ipa_param), POINTER(c_uint64)]),
+    "ipa_serve_poll": (c_int32, [c_void_p, c_uint64, POINTER(c_double), POINTER(c_double), POINTER(c_double),
+                                 POINTER(c_int32)]),
+    "ipa_server_destroy": (c_int32, [c_void_p]),
     "ipa_reserve": (c_int32, [c_int64, c_int32]),
     "ipa_calibrate_fp64": (c_int32, [POINTER(c_double), c_void_p]),
     "ipa_last_error": (c_char_p, []),

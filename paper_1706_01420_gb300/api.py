@@ -171,6 +171,62 @@ def ipa_fit_batch(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: l
     return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters, "passes": passes}
 
 
+def _host_or_dev_ptr(x, name):
+    """Pointer of a C-contiguous float64 numpy array (host) or CUDA tensor (device)."""
+    import numpy as np
+    if isinstance(x, torch.Tensor):
+        return _ptr(x, name=name), int(x.numel())
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+        raise IpaError(f"{name} must be a contiguous float64 numpy array or CUDA tensor")
+    return x.ctypes.data, int(x.size)
+
+
+def ipa_server_create(model: C.ipa_model, hbm_budget_bytes: int, max_slots: int = 256,
+                      max_iter: int = 200, tol: float = 1e-8) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib().ipa_server_create(ctypes.byref(model), hbm_budget_bytes, max_slots, max_iter, tol,
+                                    ctypes.byref(h)), "ipa_server_create")
+    return h
+
+
+def ipa_serve_submit(server, ev: dict, params: list[Param]) -> int:
+    """Submit one fit; ev holds host numpy arrays or CUDA tensors (copied before return)."""
+    e = C.ipa_events()
+    keep = []
+    for k in ("t", "ck", "cl", "phi", "w"):
+        v = ev.get(k)
+        if v is None:
+            setattr(e, k, None)
+            continue
+        ptr, n = _host_or_dev_ptr(v, k)
+        keep.append(v)
+        setattr(e, k, ptr)
+        if k == "t":
+            e.n = n
+    ticket = ctypes.c_uint64()
+    _check(_lib().ipa_serve_submit(server, ctypes.byref(e), _spec(params), ctypes.byref(ticket)),
+           "ipa_serve_submit")
+    return ticket.value
+
+
+def ipa_serve_poll(server, ticket: int, n_par: int):
+    """None while the fit is pending; else dict(theta, err, nll, status)."""
+    import numpy as np
+    th = (ctypes.c_double * n_par)()
+    er = (ctypes.c_double * n_par)()
+    nll = ctypes.c_double()
+    st = ctypes.c_int32()
+    r = _lib().ipa_serve_poll(server, ctypes.c_uint64(ticket), th, er, ctypes.byref(nll), ctypes.byref(st))
+    if r == C.IPA_PENDING:
+        return None
+    _check(r, "ipa_serve_poll")
+    return {"theta": np.array(th[:]), "err": np.array(er[:]), "nll": nll.value, "status": st.value}
+
+
+def ipa_server_destroy(server):
+    _check(_lib().ipa_server_destroy(server), "ipa_server_destroy")
+
+
 def ipa_reserve(max_events: int, max_segments: int = 1):
     _check(_lib().ipa_reserve(max_events, max_segments), "ipa_reserve")
 

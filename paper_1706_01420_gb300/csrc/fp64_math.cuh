@@ -56,6 +56,19 @@ __device__ __forceinline__ void load_math_tables(MathTables* t) {
 // in the low bits of the sum's bit pattern.
 constexpr double kRoundShift = 6755399441055744.0;
 
+// Range tests on bit patterns (integer pipe; the FP64 pipe is the scarce one).
+// For doubles of one sign the bit patterns are ordered like the values.
+__device__ __forceinline__ bool above(double x, double c) {          // x > c, c >= 0
+    return __double_as_longlong(x) > __double_as_longlong(c);
+}
+__device__ __forceinline__ bool below_neg(double x, double c) {      // x < c, c < 0
+    return (unsigned long long)__double_as_longlong(x) > (unsigned long long)__double_as_longlong(c);
+}
+__device__ __forceinline__ bool abs_below(double x, double c) {      // |x| < c, c > 0
+    return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) < __double_as_longlong(c);
+}
+__device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
+
 __device__ __forceinline__ double exp_fast(double x, const MathTables* t) {
     using namespace fp64tab;
     const double kd = fma(x, kInvLn2x64, kRoundShift);
@@ -71,14 +84,15 @@ __device__ __forceinline__ double exp_fast(double x, const MathTables* t) {
     const double tj = t->exp2[k & 63];
     const double v = fma(tj, p, tj);
     const long long scaled = __double_as_longlong(v) + (long long)(k >> 6) * (1ll << 52);
-    if (x > 709.0) return exp(x);                 // overflow range: library exp
-    return x < -707.0 ? 0.0 : __longlong_as_double(scaled);
+    if (above(x, 709.0)) return exp(x);           // overflow range: library exp
+    return below_neg(x, -707.0) ? 0.0 : __longlong_as_double(scaled);
 }
 
 __device__ __forceinline__ double log_fast(double x, const MathTables* t) {
     using namespace fp64tab;
-    if (!(x >= 2.2250738585072014e-308 && x < 1.7976931348623157e308)) return log(x);
     const long long b = __double_as_longlong(x);
+    // positive, normal and finite: 0x0010... <= b < 0x7FF0... (one unsigned compare)
+    if ((unsigned long long)(b - 0x0010000000000000ll) >= 0x7FE0000000000000ull) return log(x);
     const int e = (int)(b >> 52) - 1023;
     const int j = (int)((b >> 45) & 127);
     const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
@@ -97,7 +111,7 @@ __device__ __forceinline__ double log_fast(double x, const MathTables* t) {
 
 __device__ __forceinline__ void sincos_fast(double p, const MathTables* t, double* s, double* c) {
     using namespace fp64tab;
-    if (!(fabs(p) < 1e5)) {
+    if (!abs_below(p, 1e5)) {
         sincos(p, s, c);
         return;
     }
@@ -137,7 +151,7 @@ __device__ __forceinline__ double erfcx_poly(double x, const MathTables* t) {
 }
 
 __device__ __forceinline__ double erfcx_fast(double x, const MathTables* t) {
-    return x > 6.25 ? erfcx(x) : erfcx_poly(x, t);
+    return above(x, 6.25) ? erfcx(x) : erfcx_poly(x, t);
 }
 
 }  // namespace ipa

@@ -88,16 +88,18 @@ ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Cons
                          cudaStream_t s);
 // compute_consts_warp (consts.cuh): one warp turns theta into a Consts record.
 
-// nll.cu: segmented NLL(+grad) over precomputed consts; out: (1 + n_par) per segment
-// With seg_off == nullptr there is one segment [0, n).  Otherwise seg_tiles must
-// hold the device prefix of tiles per segment (launch_seg_tiles).
+// nll.cu: NLL(+grad) over precomputed consts; out: (1 + n_par) per segment (1 without
+// the gradient).  With seg_begin == nullptr there is one segment [0, n).  Otherwise
+// segment s is events [seg_begin[s], seg_end[s]) and seg_tiles must hold the device
+// prefix of its tiles (launch_seg_tiles).
 ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
-                      const int64_t* seg_off, const int64_t* seg_tiles, int n_seg,
+                      const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t s);
 // nll.cu: seg_tiles[s] = sum_{r<s} ceil(size_r / kTile), s = 0..n_seg, with the
-// offsets clamped to [0, n] and made non-decreasing
-ipa_status launch_seg_tiles(const int64_t* seg_off, int n_seg, int64_t n, int64_t* seg_tiles,
-                            cudaStream_t s);
+// ranges clamped to [0, n]; segments with active[r] == 0 get no tiles (active may
+// be NULL).
+ipa_status launch_seg_tiles(const int64_t* seg_begin, const int64_t* seg_end, const int* active, int n_seg,
+                            int64_t n, int64_t* seg_tiles, cudaStream_t s);
 
 // Number of SMs of the current device (cached).
 int sm_count();

@@ -87,14 +87,15 @@ __device__ __forceinline__ void time_terms(const Consts& c, double tau, const Ma
     const double Gx = exp_fast(-(tau * tau) * c.k_g, mt);  // exp(-tau^2 / (2 sigma^2))
     const double z = (c.Gs2 - tau) * c.k_z;
     const double x = fabs(z);
+    const bool zneg = negative(z);
     double X = erfcx_poly(x, mt);
-    if (x > 6.25) {
+    if (above(x, 6.25)) {
         // z < 0: the erfcx term is below 1e-17 of E; z >= 0 (tau far below the
         // resolution peak, outside the usual range): exact library erfcx
-        X = z < 0.0 ? 0.0 : erfcx(x);
+        X = zneg ? 0.0 : erfcx(x);
     }
     const double hgx = 0.5 * Gx * X;
-    *T = z < 0.0 ? E - hgx : hgx;
+    *T = zneg ? E - hgx : hgx;
     *G = c.cG * Gx;
 }
 
@@ -194,8 +195,9 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
 
 template <int KIND, bool GRAD>
 __global__ void __launch_bounds__(kNllBlock, 4)
-nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
-           const int64_t* __restrict__ seg_tiles, int n_seg, const Consts* __restrict__ consts,
+nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
+           const int64_t* __restrict__ seg_end, const int64_t* __restrict__ seg_tiles, int n_seg,
+           const Consts* __restrict__ consts,
            double* __restrict__ partials, unsigned* __restrict__ counters,
            double* __restrict__ out, int n_par) {
     constexpr int NA = n_acc(KIND, GRAD);
@@ -208,7 +210,7 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
     load_math_tables(&mt);
     __syncthreads();
 
-    const bool single = seg_off == nullptr;
+    const bool single = seg_begin == nullptr;
     const int64_t total = single ? (n + kTile - 1) / kTile : __ldg(seg_tiles + n_seg);
 
     // empty segments have no tile to finalise them: block 0 writes their zeros
@@ -231,8 +233,8 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
             seg = find_segment(seg_tiles, n_seg, tile);
             t0 = __ldg(seg_tiles + seg);
             t1 = __ldg(seg_tiles + seg + 1);
-            ev0 = clamp_off(__ldg(seg_off + seg), n);
-            ev1 = clamp_off(__ldg(seg_off + seg + 1), n);
+            ev0 = clamp_off(__ldg(seg_begin + seg), n);
+            ev1 = clamp_off(__ldg(seg_end + seg), n);
             if (ev1 < ev0) ev1 = ev0;
         }
         if (seg != cur) {
@@ -295,22 +297,26 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_off,
     }
 }
 
-// seg_tiles[s] = sum_{r<s} ceil(size_r / kTile), one block, sequential per thread
-// over a contiguous run of segments, then a block scan of the run totals.
-__global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_off, int n_seg, int64_t n,
+// seg_tiles[s] = sum_{r<s} tiles(r), tiles(r) = ceil(size_r / kTile) for an active
+// segment (0 when active[r] == 0), one block: sequential per thread over a
+// contiguous run of segments, then a block scan of the run totals.
+__global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_begin, const int64_t* __restrict__ seg_end,
+                                 const int* __restrict__ active, int n_seg, int64_t n,
                                  int64_t* __restrict__ seg_tiles) {
     __shared__ int64_t run[1024];
     const int nt = blockDim.x;
     const int per = (n_seg + nt - 1) / nt;
     const int b = threadIdx.x * per;
     const int e = min(n_seg, b + per);
-    int64_t sum = 0;
-    for (int s = b; s < e; ++s) {
-        const int64_t lo = clamp_off(seg_off[s], n);
-        int64_t hi = clamp_off(seg_off[s + 1], n);
+    auto tiles = [&](int s) -> int64_t {
+        if (active && !active[s]) return 0;
+        const int64_t lo = clamp_off(seg_begin[s], n);
+        int64_t hi = clamp_off(seg_end[s], n);
         if (hi < lo) hi = lo;
-        sum += (hi - lo + kTile - 1) / kTile;
-    }
+        return (hi - lo + kTile - 1) / kTile;
+    };
+    int64_t sum = 0;
+    for (int s = b; s < e; ++s) sum += tiles(s);
     run[threadIdx.x] = sum;
     __syncthreads();
     for (int d = 1; d < nt; d <<= 1) {
@@ -322,18 +328,15 @@ __global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_off, int n_seg,
     int64_t acc = threadIdx.x ? run[threadIdx.x - 1] : 0;
     for (int s = b; s < e; ++s) {
         seg_tiles[s] = acc;
-        const int64_t lo = clamp_off(seg_off[s], n);
-        int64_t hi = clamp_off(seg_off[s + 1], n);
-        if (hi < lo) hi = lo;
-        acc += (hi - lo + kTile - 1) / kTile;
+        acc += tiles(s);
     }
     if (threadIdx.x == nt - 1) seg_tiles[n_seg] = run[nt - 1];
 }
 
 template <int KIND, bool GRAD>
-ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_off, const int64_t* seg_tiles,
-                    int n_seg, const Consts* consts, Scratch* sc, double* out, int n_par,
-                    cudaStream_t st) {
+ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const int64_t* seg_end,
+                    const int64_t* seg_tiles, int n_seg, const Consts* consts, Scratch* sc, double* out,
+                    int n_par, cudaStream_t st) {
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -341,33 +344,34 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_off, const i
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     int64_t grid = (int64_t)sm_count() * per_sm;
-    if (seg_off == nullptr) {
+    if (seg_begin == nullptr) {
         const int64_t tiles = (n + kTile - 1) / kTile;
         const int64_t need = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
         grid = need < grid ? need : grid;
     }
     if (grid < 1) grid = 1;
     nll_kernel<KIND, GRAD><<<(unsigned)grid, kNllBlock, 0, st>>>(
-        cols, n, seg_off, seg_tiles, n_seg, consts, sc->partials, sc->counters, out, n_par);
+        cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, out, n_par);
     return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
 }
 
 }  // namespace
 
-ipa_status launch_seg_tiles(const int64_t* seg_off, int n_seg, int64_t n, int64_t* seg_tiles,
-                            cudaStream_t st) {
-    seg_tiles_kernel<<<1, 1024, 0, st>>>(seg_off, n_seg, n, seg_tiles);
+ipa_status launch_seg_tiles(const int64_t* seg_begin, const int64_t* seg_end, const int* active, int n_seg,
+                            int64_t n, int64_t* seg_tiles, cudaStream_t st) {
+    seg_tiles_kernel<<<1, 1024, 0, st>>>(seg_begin, seg_end, active, n_seg, n, seg_tiles);
     return cuda_fail(cudaGetLastError(), "segment tiling kernel launch");
 }
 
 ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
-                      const int64_t* seg_off, const int64_t* seg_tiles, int n_seg,
+                      const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t st) {
+    const int P = m.n_par;
     if (m.kind == IPA_MODEL_TIME1D)
-        return grad ? launch_t<IPA_MODEL_TIME1D, true>(cols, n, seg_off, seg_tiles, n_seg, consts, sc, out, m.n_par, st)
-                    : launch_t<IPA_MODEL_TIME1D, false>(cols, n, seg_off, seg_tiles, n_seg, consts, sc, out, m.n_par, st);
-    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true>(cols, n, seg_off, seg_tiles, n_seg, consts, sc, out, m.n_par, st)
-                : launch_t<IPA_MODEL_ANGTIME4D, false>(cols, n, seg_off, seg_tiles, n_seg, consts, sc, out, m.n_par, st);
+        return grad ? launch_t<IPA_MODEL_TIME1D, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
+                    : launch_t<IPA_MODEL_TIME1D, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
+    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
+                : launch_t<IPA_MODEL_ANGTIME4D, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
 }
 
 namespace {
@@ -396,11 +400,12 @@ ipa_status run(const ipa_model* model, const ipa_events* ev, const int64_t* seg_
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     if ((st = launch_consts(m, theta, n_seg, sc->consts, s)) != IPA_OK) return st;
     if (seg_off) {
-        if ((st = launch_seg_tiles(seg_off, n_seg, ev->n, sc->seg_tiles, s)) != IPA_OK) return st;
+        if ((st = launch_seg_tiles(seg_off, seg_off + 1, nullptr, n_seg, ev->n, sc->seg_tiles, s)) != IPA_OK)
+            return st;
     }
     const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w};
-    return launch_nll(m, grad, cols, ev->n, seg_off, seg_off ? sc->seg_tiles : nullptr, n_seg,
-                      sc->consts, sc, out, s);
+    return launch_nll(m, grad, cols, ev->n, seg_off, seg_off ? seg_off + 1 : nullptr,
+                      seg_off ? sc->seg_tiles : nullptr, n_seg, sc->consts, sc, out, s);
 }
 
 }  // namespace
