@@ -23,6 +23,10 @@ LIB = os.path.join(HERE, "libipanema.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]
+# Per-file flags.  The parameter constants are computed by a per-thread and a
+# per-warp kernel that share every arithmetic step; without contraction into
+# FMA both give the same bits, so a fit gives the same result alone or batched.
+FILE_FLAGS = {"consts.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
@@ -53,7 +57,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         if _stale(obj, [src, __file__] + hdrs):
-            cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
+            cmd = [cc, *ARCH, *flags, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             r = subprocess.run(cmd, capture_output=True, text=True)

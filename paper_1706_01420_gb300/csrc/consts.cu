@@ -1,21 +1,33 @@
-// Step a1 of the hot path: one warp per fit turns theta into the Consts
-// record read by every event tile (see consts.cuh for the formulas).
+// Step a1 of the hot path: theta -> the Consts record read by every event
+// tile (see consts.cuh for the formulas): one warp per fit for a few fits,
+// one thread per fit for many.
 #include "consts.cuh"
 
 namespace ipa {
 
 namespace {
-// One warp per fit (segment).
+// One warp per fit (few fits: latency).
 __global__ void consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg,
                               Consts* __restrict__ out) {
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s < n_seg) compute_consts_warp(m, theta + (size_t)s * m.n_par, out + s);
+}
+
+// One thread per fit (many fits: throughput).
+__global__ void consts_thread_kernel(ModelDev m, const double* __restrict__ theta, int n_seg,
+                                     Consts* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n_seg) compute_consts_thread(m, theta + (size_t)s * m.n_par, out + s);
 }
 }  // namespace
 
 ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
                          cudaStream_t st) {
     if (n_seg <= 0) return IPA_OK;
+    if (n_seg >= 64) {
+        consts_thread_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
+        return cuda_fail(cudaGetLastError(), "consts kernel launch");
+    }
     const int warps = 4;
     const int grid = (n_seg + warps - 1) / warps;
     consts_kernel<<<grid, 32 * warps, 0, st>>>(m, theta, n_seg, out);

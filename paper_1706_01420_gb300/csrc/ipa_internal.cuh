@@ -12,7 +12,10 @@ namespace ipa {
 // Each of the 256 slots of a tile handles two consecutive events (one 16-byte
 // load per column); the in-tile and cross-tile trees are fixed, so results do
 // not depend on grid size or scheduling.
-constexpr int kTile = 512;
+#ifndef IPA_TILE_EVENTS
+#define IPA_TILE_EVENTS 512
+#endif
+constexpr int kTile = IPA_TILE_EVENTS;
 constexpr int kSlots = 256;
 constexpr int kBlock = 256;
 
@@ -74,6 +77,7 @@ struct Scratch {
     double* partials = nullptr;     // tiles * n_acc doubles
     size_t partials_cap = 0;        // doubles
     unsigned* counters = nullptr;   // one per segment, zero between calls
+    unsigned* work = nullptr;       // [tiles taken, warps finished], zero between calls
     int64_t* seg_tiles = nullptr;   // n_seg + 1 prefix of tiles per segment
     Consts* consts = nullptr;       // one per segment
     size_t seg_cap = 0;             // segments

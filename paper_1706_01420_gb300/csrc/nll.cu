@@ -199,7 +199,7 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
            const int64_t* __restrict__ seg_end, const int64_t* __restrict__ seg_tiles, int n_seg,
            const Consts* __restrict__ consts,
            double* __restrict__ partials, unsigned* __restrict__ counters,
-           double* __restrict__ out, int n_par) {
+           unsigned* __restrict__ work, double* __restrict__ out, int n_par) {
     constexpr int NA = n_acc(KIND, GRAD);
     const int out_stride = GRAD ? 1 + n_par : 1;
     __shared__ MathTables mt;
@@ -223,10 +223,15 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
         }
     }
 
-    const int64_t warp0 = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    // Tiles are handed out dynamically (work[0] counts the tiles taken), so SMs
+    // whose warps finish early take more; a tile's partial does not depend on
+    // which warp computes it.  The last warp to leave resets both counters.
     int cur = -1;
-    for (int64_t tile = warp0; tile < total; tile += n_warps) {
+    while (true) {
+        unsigned taken = 0;
+        if (lane == 0) taken = atomicAdd(work, 1u);
+        const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, taken, 0);
+        if (tile >= total) break;
         int seg = 0;
         int64_t t0 = 0, t1 = total, ev0 = 0, ev1 = n;
         if (!single) {
@@ -295,6 +300,13 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             }
         }
     }
+    if (lane == 0) {
+        const unsigned n_warps = gridDim.x * kWarpsPerBlock;
+        if (atomicAdd(work + 1, 1u) == n_warps - 1u) {
+            work[0] = 0u;
+            work[1] = 0u;
+        }
+    }
 }
 
 // seg_tiles[s] = sum_{r<s} tiles(r), tiles(r) = ceil(size_r / kTile) for an active
@@ -351,7 +363,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
     }
     if (grid < 1) grid = 1;
     nll_kernel<KIND, GRAD><<<(unsigned)grid, kNllBlock, 0, st>>>(
-        cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, out, n_par);
+        cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->work, out, n_par);
     return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
 }
 

@@ -13,8 +13,8 @@
 // the address up with cudaGetSymbolAddress while that device is current, and
 // later calls reuse it.  That first call should therefore come before any
 // stream capture.  All calls share the one array and it keeps the previous
-// call's contents: the completion counter is cleared on the stream before
-// every launch, and calls that overlap on the GPU (different streams, or
+// call's contents: the completion and work counters are cleared on the stream
+// before every launch, and calls that overlap on the GPU (different streams, or
 // different host threads without ordering) race on the array.
 #include <mutex>
 
@@ -26,7 +26,7 @@ namespace {
 constexpr int64_t kNoAllocMaxEvents = IPA_NOALLOC_MAX_EVENTS;
 constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxEvents / kTile + 1;
 constexpr size_t kConstsBytes = 1024;     // one Consts record, padded
-constexpr size_t kCounterBytes = 256;     // one completion counter, padded
+constexpr size_t kCounterBytes = 256;     // completion counter and the two work counters, padded
 constexpr size_t kPartialsBytes = (size_t)kNoAllocMaxTiles * 15 * sizeof(double);
 static_assert(sizeof(Consts) <= kConstsBytes, "Consts must fit its slot");
 
@@ -79,11 +79,12 @@ extern "C" ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_eve
     Scratch sc;
     sc.consts = reinterpret_cast<Consts*>(base);
     sc.counters = reinterpret_cast<unsigned*>(base + kConstsBytes);
+    sc.work = sc.counters + 1;
     sc.partials = reinterpret_cast<double*>(base + kConstsBytes + kCounterBytes);
     sc.partials_cap = (size_t)kNoAllocMaxTiles * 15;
     sc.seg_cap = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((st = cuda_fail(cudaMemsetAsync(sc.counters, 0, sizeof(unsigned), s), "counter clear")) != IPA_OK)
+    if ((st = cuda_fail(cudaMemsetAsync(sc.counters, 0, 3 * sizeof(unsigned), s), "counter clear")) != IPA_OK)
         return st;
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     if ((st = launch_consts(m, theta_dev, 1, sc.consts, s)) != IPA_OK) return st;

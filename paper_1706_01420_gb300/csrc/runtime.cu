@@ -120,6 +120,11 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
             return st;
         s.partials_cap = cap;
     }
+    if (!s.work) {
+        if ((st = cuda_fail(cudaMalloc(&s.work, 2 * sizeof(unsigned)), "scratch work counters")) != IPA_OK) return st;
+        if ((st = cuda_fail(cudaMemset(s.work, 0, 2 * sizeof(unsigned)), "scratch memset")) != IPA_OK) return st;
+        if ((st = cuda_fail(cudaDeviceSynchronize(), "scratch init")) != IPA_OK) return st;
+    }
     if (need_s > s.seg_cap) {
         size_t cap = s.seg_cap ? s.seg_cap : 64;
         while (cap < need_s) cap *= 2;

@@ -122,6 +122,28 @@ def test_deterministic_and_segment_equals_solo(env):
             assert np.all(seg[s] == 0.0)
 
 
+def test_many_segments_equal_solo(env):
+    """80 segments (the constants are then computed one thread per fit) against
+    solo calls (one warp per fit): bitwise equal."""
+    O, G, torch, api = env
+    m = api.model_4d()
+    rng = np.random.default_rng(8)
+    sizes = rng.integers(0, 3000, 80)
+    cols = synth.events_4d(int(sizes.sum()), 22, weighted=True)
+    ev = G.to_dev(cols)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    thetas = np.tile(TH4, (80, 1))
+    thetas[:, 0] += rng.normal(0, 0.02, 80)
+    thetas[:, 4] += rng.normal(0, 0.02, 80)
+    seg = api.ipa_nll_grad_segmented(m, ev, torch.tensor(off, device="cuda"),
+                                     torch.tensor(thetas, device="cuda")).cpu().numpy()
+    for s in (0, 1, 41, 79):
+        a, b = off[s], off[s + 1]
+        sub = {k: v[a:b].clone() for k, v in ev.items()}
+        solo = api.ipa_nll_grad(m, sub, torch.tensor(thetas[s], device="cuda")).cpu().numpy()
+        assert np.array_equal(solo, seg[s]), s
+
+
 def test_misaligned_column_rejected(env):
     O, G, torch, api = env
     t = torch.zeros(101, dtype=torch.float64, device="cuda")
