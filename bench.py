@@ -390,13 +390,15 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     th1 = torch.tensor(start[None, :], device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    r = api.ipa_fit_batch(m, ev, off1, params, th1, max_iter=200, tol=1e-8)
+    evc = dict(ev, fk=api.ipa_angular_basis(m, ev))        # cached angular basis, inside the timing
+    r = api.ipa_fit_batch(m, evc, off1, params, th1, max_iter=200, tol=1e-8)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     npass = int(r["passes"][0])
     out["fit"] = {"events": N_EVENTS, "wall_s": dt, "status": int(r["status"][0]),
                   "iterations": int(r["iters"][0]), "passes": npass,
-                  "Gevents_per_s": N_EVENTS * npass / dt / 1e9}
+                  "Gevents_per_s": N_EVENTS * npass / dt / 1e9, "angular_basis": "cached"}
+    del evc
 
     # toy generation: 4096 toys of Poisson(2e4) events
     n_toys = 4096
@@ -416,7 +418,13 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     tg = e0.elapsed_time(e1) * 1e-3
     out["toygen"] = {"toys": n_toys, "events": total, "s": tg, "Mevents_per_s": total / tg / 1e6}
 
-    # batched fits of all toys vs the plain loop (one fit per call) on a subset
+    # batched fits of all toys vs the plain loop (one fit per call) on a subset; both
+    # read the cached angular basis, computed once for all toys
+    e0.record()
+    cols["fk"] = api.ipa_angular_basis(m, cols)
+    e1.record()
+    torch.cuda.synchronize()
+    t_basis = e0.elapsed_time(e1) * 1e-3
     thb = torch.tensor(np.tile(TH4, (n_toys, 1)), device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -443,6 +451,7 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     out["batch"] = {"toys": n_toys, "events": total, "batched_fits_per_s": n_toys / tb, "batched_s": tb,
                     "batched_Gevents_per_s": float((sizes * passes_b).sum()) / tb / 1e9,
                     "plain_loop_fits_per_s": 1.0 / tp, "plain_loop_sample": n_plain,
+                    "angular_basis_s": t_basis,
                     "converged": int(ok.sum()), "status_counts": np.bincount(st, minlength=5).tolist(),
                     "pull_mean_width": pulls}
     del cols, rb, thb
@@ -544,11 +553,19 @@ def run_large(api, synth, torch, dev, m, theta, params) -> dict:
     big = [api.Param(p.value, p.lo, p.hi, p.step / 7.0) for p in params]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    cols["fk"] = api.ipa_angular_basis(m, cols)              # inside the fit timing
     r = api.ipa_fit_batch(m, cols, d64([0, n]), big, th1, max_iter=200, tol=1e-8)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     npass = int(r["passes"][0])
+    e0.record()
+    for _ in range(reps):
+        api.ipa_nll_grad(m, cols, theta, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_c = e0.elapsed_time(e1) / reps
     return {"events": n, "weighted": True, "nll_grad_ms": ms, "Gevents_per_s": n / (ms * 1e-3) / 1e9,
+            "nll_grad_ms_cached_basis": ms_c, "Gevents_per_s_cached_basis": n / (ms_c * 1e-3) / 1e9,
             "fit": {"wall_s": dt, "status": int(r["status"][0]), "iterations": int(r["iters"][0]),
                     "passes": npass, "Gevents_per_s": n * npass / dt / 1e9}}
 

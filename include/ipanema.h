@@ -95,10 +95,15 @@ typedef struct {
 
 /* An event set (Cat of App. C): n events as FP64 SoA device columns.
  * t is required; ck, cl, phi are required for the 4D model and ignored for 1D;
- * w may be NULL (unit weights). */
+ * w may be NULL (unit weights).  fk may be NULL, or hold the angular basis of
+ * these events written by ipa_angular_basis (10 columns of fk_stride doubles);
+ * 4D likelihood and fit calls then read it instead of evaluating the angular
+ * functions. */
 typedef struct {
     int64_t n;
     const double *t, *ck, *cl, *phi, *w;
+    const double* fk;
+    int64_t fk_stride;
 } ipa_events;
 
 /* Writable event columns for the generator; `capacity` is the number of
@@ -152,6 +157,15 @@ ipa_status ipa_nll_grad(const ipa_model* model, const ipa_events* ev, const doub
 ipa_status ipa_nll_grad_segmented(const ipa_model* model, const ipa_events* ev,
                                   const int64_t* seg_off_dev, int32_t n_seg,
                                   const double* theta_dev, double* out_dev, void* stream);
+
+/* Angular basis of an event set (hot-path step a3, data-only; Sec. 4 and the
+ * symbolic-programming section): fk_dev[k * stride + e] = f_{k+1}(ck[e], cl[e],
+ * phi[e]) for k = 0..9, e < ev->n.  stride >= ev->n and even; fk_dev 16-byte
+ * aligned (device, 10 * stride doubles, caller-owned).  Computed once per event
+ * set, it replaces the sine, cosine, square root and ten products of every
+ * later likelihood pass by 80 bytes of reads.  4D model only. */
+ipa_status ipa_angular_basis(const ipa_model* model, const ipa_events* ev, double* fk_dev, int64_t stride,
+                             void* stream);
 
 /* Accept-reject pseudo-experiments (Sec. 7).  Toy k holds n_sig[k] signal
  * events then n_bkg[k] background events, written at event offset

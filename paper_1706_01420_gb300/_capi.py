@@ -28,7 +28,7 @@ class ipa_model(ctypes.Structure):
 
 class ipa_events(ctypes.Structure):
     _fields_ = [("n", c_int64), ("t", c_void_p), ("ck", c_void_p), ("cl", c_void_p),
-                ("phi", c_void_p), ("w", c_void_p)]
+                ("phi", c_void_p), ("w", c_void_p), ("fk", c_void_p), ("fk_stride", c_int64)]
 
 
 class ipa_event_buffers(ctypes.Structure):
@@ -48,6 +48,7 @@ PROTOTYPES = {
     "ipa_nll_grad": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
     "ipa_nll_grad_segmented": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
                                          c_void_p, c_void_p, c_void_p]),
+    "ipa_angular_basis": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int64, c_void_p]),
     "ipa_toygen": (c_int32, [POINTER(ipa_model), c_void_p, c_uint64, c_int32, c_void_p, c_void_p,
                              c_void_p, POINTER(ipa_event_buffers), c_void_p]),
     "ipa_fit_batch": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,

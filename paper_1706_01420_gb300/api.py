@@ -63,7 +63,9 @@ def model_4d(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
 
 
 def ipa_events(ev: dict) -> C.ipa_events:
-    """dict of CUDA float64 columns (t[, ck, cl, phi][, w]) -> ipa_events."""
+    """dict of CUDA float64 columns (t[, ck, cl, phi][, w][, fk]) -> ipa_events.
+
+    fk, if present, is the (10, stride) tensor written by ipa_angular_basis."""
     t = ev["t"]
     e = C.ipa_events()
     e.n = int(t.numel())
@@ -71,7 +73,24 @@ def ipa_events(ev: dict) -> C.ipa_events:
     for k in ("ck", "cl", "phi", "w"):
         v = ev.get(k)
         setattr(e, k, _ptr(v, name=k) if v is not None else None)
+    fk = ev.get("fk")
+    if fk is not None:
+        if fk.dim() != 2 or fk.shape[0] != 10:
+            raise IpaError("fk must be the (10, stride) angular basis")
+        e.fk = _ptr(fk, name="fk")
+        e.fk_stride = int(fk.shape[1])
     return e
+
+
+def ipa_angular_basis(model: C.ipa_model, ev: dict, stream=None) -> torch.Tensor:
+    """The 10 angular functions of every event, as a (10, stride) tensor (stride = n rounded
+    up to even); put it in the event dict as "fk" to let later calls read it."""
+    n = int(ev["t"].numel())
+    fk = torch.empty(10, n + (n & 1), dtype=torch.float64, device=ev["t"].device)
+    e = ipa_events({k: v for k, v in ev.items() if k != "fk"})
+    _check(_lib().ipa_angular_basis(ctypes.byref(model), ctypes.byref(e), _ptr(fk, name="fk"),
+                                    int(fk.shape[1]), _stream(stream)), "ipa_angular_basis")
+    return fk
 
 
 def ipa_nll(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor | None = None,

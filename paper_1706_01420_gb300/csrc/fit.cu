@@ -104,7 +104,7 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     init_kernel<<<fg, fb, 0, s>>>(d_spec, 0, n_fits, theta_io_dev, states, theta_eval, active);
     if ((st = cuda_fail(cudaGetLastError(), "fit init")) != IPA_OK) return done(st);
 
-    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w};
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
     // one pass = tile map, constants, segmented NLL+grad, state update
     auto pass = [&](int k) -> ipa_status {
         ipa_status q;

@@ -64,6 +64,8 @@ struct ModelDev {
 
 struct Cols {
     const double *t, *ck, *cl, *phi, *w;
+    const double* fk = nullptr;   // cached angular basis (10 columns) or nullptr
+    int64_t fk_stride = 0;
 };
 
 // ---- host-side helpers (runtime.cu) ----

@@ -99,20 +99,22 @@ __device__ __forceinline__ void time_terms(const Consts& c, double tau, const Ma
     *G = c.cG * Gx;
 }
 
-template <int KIND, bool GRAD>
-__device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt, double t, double ck,
-                                      double cl, double phi, double w, double* acc) {
+// One event: accumulate w log P (and the adjoint sums).  For the 4D model f
+// holds either the unscaled products f'_k (CACHED = false, coefficients h_k c_k)
+// or the cached basis f_k itself (CACHED = true, coefficients h_k).
+template <int KIND, bool GRAD, bool CACHED>
+__device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt, double t, const double* f,
+                                      double w, double* acc) {
     const Consts& c = wc.c;
     const double tau = t - c.mu;
     double T, G;
     time_terms(c, tau, mt, &T, &G);
     double A = 1.0;
-    double f[10];
     if (KIND == IPA_MODEL_ANGTIME4D) {
-        basis_unscaled(ck, cl, phi, mt, f);
-        A = wc.hp[0] * f[0];
+        const double* hk = CACHED ? c.h : wc.hp;
+        A = hk[0] * f[0];
 #pragma unroll
-        for (int k = 1; k < 10; ++k) A = fma(wc.hp[k], f[k], A);
+        for (int k = 1; k < 10; ++k) A = fma(hk[k], f[k], A);
     }
     const double P = fma(c.cs * T, A, c.cb);
     acc[0] = fma(w, log_fast(P, mt), acc[0]);
@@ -162,8 +164,9 @@ __device__ __forceinline__ int find_segment(const int64_t* seg_tiles, int n_seg,
 }
 
 // Write NLL (and gradient) of one segment from its reduced accumulators.
-// For the 4D model acc[2 + k] holds sum r T f'_k; S_k = c_k times that.
-template <int KIND, bool GRAD>
+// For the 4D model acc[2 + k] holds sum r T f'_k (S_k = c_k times that) or,
+// with a cached basis, S_k itself.
+template <int KIND, bool GRAD, bool CACHED>
 __device__ void finalize(const Consts& c, const double* acc, int n_par, double* out) {
     out[0] = -acc[0];
     if (!GRAD) return;
@@ -174,7 +177,7 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
     if (KIND == IPA_MODEL_ANGTIME4D) {
         SH = 0.0;
         for (int k = 0; k < 10; ++k) {
-            S[k] = kBasisScale[k] * acc[2 + k];
+            S[k] = CACHED ? acc[2 + k] : kBasisScale[k] * acc[2 + k];
             SH = fma(c.h[k], S[k], SH);
         }
     } else {
@@ -193,7 +196,7 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
         out[1 + j] = 0.0;
 }
 
-template <int KIND, bool GRAD>
+template <int KIND, bool GRAD, bool CACHED>
 __global__ void __launch_bounds__(kNllBlock, 4)
 nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
            const int64_t* __restrict__ seg_end, const int64_t* __restrict__ seg_tiles, int n_seg,
@@ -263,11 +266,16 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             const int64_t e = base + 32 * i;
             if (e < ev1) {
                 const double w = cols.w ? __ldg(cols.w + e) : 1.0;
-                if (KIND == IPA_MODEL_ANGTIME4D)
-                    event<KIND, GRAD>(wc, &mt, __ldg(cols.t + e), __ldg(cols.ck + e), __ldg(cols.cl + e),
-                                      __ldg(cols.phi + e), w, acc);
-                else
-                    event<KIND, GRAD>(wc, &mt, __ldg(cols.t + e), 0.0, 0.0, 0.0, w, acc);
+                double f[10];
+                if (KIND == IPA_MODEL_ANGTIME4D) {
+                    if (CACHED) {
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
+                    } else {
+                        basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
+                    }
+                }
+                event<KIND, GRAD, CACHED>(wc, &mt, __ldg(cols.t + e), f, w, acc);
             }
         }
 
@@ -295,7 +303,7 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             }
             warp_tree<NA>(acc);
             if (lane == 0) {
-                finalize<KIND, GRAD>(wc.c, acc, n_par, out + (size_t)seg * out_stride);
+                finalize<KIND, GRAD, CACHED>(wc.c, acc, n_par, out + (size_t)seg * out_stride);
                 counters[seg] = 0u;
             }
         }
@@ -345,14 +353,14 @@ __global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_begin, const in
     if (threadIdx.x == nt - 1) seg_tiles[n_seg] = run[nt - 1];
 }
 
-template <int KIND, bool GRAD>
+template <int KIND, bool GRAD, bool CACHED>
 ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const int64_t* seg_end,
                     const int64_t* seg_tiles, int n_seg, const Consts* consts, Scratch* sc, double* out,
                     int n_par, cudaStream_t st) {
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, nll_kernel<KIND, GRAD>, kNllBlock, 0);
+            &per_sm, nll_kernel<KIND, GRAD, CACHED>, kNllBlock, 0);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     int64_t grid = (int64_t)sm_count() * per_sm;
@@ -362,7 +370,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
         grid = need < grid ? need : grid;
     }
     if (grid < 1) grid = 1;
-    nll_kernel<KIND, GRAD><<<(unsigned)grid, kNllBlock, 0, st>>>(
+    nll_kernel<KIND, GRAD, CACHED><<<(unsigned)grid, kNllBlock, 0, st>>>(
         cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->work, out, n_par);
     return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
 }
@@ -380,11 +388,57 @@ ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t st) {
     const int P = m.n_par;
     if (m.kind == IPA_MODEL_TIME1D)
-        return grad ? launch_t<IPA_MODEL_TIME1D, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
-                    : launch_t<IPA_MODEL_TIME1D, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
-    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
-                : launch_t<IPA_MODEL_ANGTIME4D, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
+        return grad ? launch_t<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
+                    : launch_t<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
+    if (cols.fk)
+        return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
+                    : launch_t<IPA_MODEL_ANGTIME4D, false, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
+    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
+                : launch_t<IPA_MODEL_ANGTIME4D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
 }
+
+// f_k = c_k f'_k for every event (the cached angular basis).
+__global__ void __launch_bounds__(kNllBlock)
+basis_kernel(const double* __restrict__ ck, const double* __restrict__ cl, const double* __restrict__ phi,
+             int64_t n, double* __restrict__ fk, int64_t stride) {
+    __shared__ MathTables mt;
+    load_math_tables(&mt);
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double f[10];
+        basis_unscaled(__ldg(ck + e), __ldg(cl + e), __ldg(phi + e), &mt, f);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) fk[k * stride + e] = kBasisScale[k] * f[k];
+    }
+}
+
+}  // namespace ipa
+
+extern "C" ipa_status ipa_angular_basis(const ipa_model* model, const ipa_events* ev, double* fk_dev,
+                                        int64_t stride, void* stream) {
+    using namespace ipa;
+    ipa_status st = check_model(model);
+    if (st != IPA_OK) return st;
+    if (model->kind != IPA_MODEL_ANGTIME4D) {
+        set_error("ipa_angular_basis: the model has no angles");
+        return IPA_ERR_ARG;
+    }
+    ipa_events plain = *ev;
+    plain.fk = nullptr;
+    if ((st = check_events(model, &plain)) != IPA_OK) return st;
+    if (!fk_dev || (reinterpret_cast<uintptr_t>(fk_dev) & 15u) || stride < ev->n || (stride & 1)) {
+        set_error("ipa_angular_basis: 16-byte aligned output with an even stride >= n required");
+        return IPA_ERR_ARG;
+    }
+    if (ev->n == 0) return IPA_OK;
+    const int64_t blocks = (ev->n + kNllBlock - 1) / kNllBlock;
+    const int grid = (int)(blocks < 4 * sm_count() * 4 ? blocks : 4 * sm_count() * 4);
+    basis_kernel<<<grid, kNllBlock, 0, static_cast<cudaStream_t>(stream)>>>(ev->ck, ev->cl, ev->phi, ev->n, fk_dev,
+                                                                            stride);
+    return cuda_fail(cudaGetLastError(), "angular basis kernel launch");
+}
+
+namespace ipa {
 
 namespace {
 
@@ -415,7 +469,7 @@ ipa_status run(const ipa_model* model, const ipa_events* ev, const int64_t* seg_
         if ((st = launch_seg_tiles(seg_off, seg_off + 1, nullptr, n_seg, ev->n, sc->seg_tiles, s)) != IPA_OK)
             return st;
     }
-    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w};
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
     return launch_nll(m, grad, cols, ev->n, seg_off, seg_off ? seg_off + 1 : nullptr,
                       seg_off ? sc->seg_tiles : nullptr, n_seg, sc->consts, sc, out, s);
 }

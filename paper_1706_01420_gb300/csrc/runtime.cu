@@ -80,6 +80,16 @@ ipa_status check_events(const ipa_model* m, const ipa_events* ev) {
         set_error("weight column is not 16-byte aligned");
         return IPA_ERR_ARG;
     }
+    if (ev->fk) {
+        if (m->kind != IPA_MODEL_ANGTIME4D) {
+            set_error("an angular basis was given for a model without angles");
+            return IPA_ERR_ARG;
+        }
+        if (!aligned16(ev->fk) || ev->fk_stride < ev->n || (ev->fk_stride & 1)) {
+            set_error("angular basis: 16-byte aligned, even stride >= n required");
+            return IPA_ERR_ARG;
+        }
+    }
     return IPA_OK;
 }
 
