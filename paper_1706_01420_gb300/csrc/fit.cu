@@ -1,11 +1,13 @@
 // ipa_fit_batch: many fits advanced together on the device (the per-fit
-// state machine is in fitcore.cuh).  The host replays a CUDA graph of K passes
-// [tile map -> constants -> NLL+grad -> state update] until every fit is DONE;
-// fits that are done drop out of the tile map, so stragglers do not pay for
-// the whole batch.
+// state machine is in fitcore.cuh).  One CUDA graph launch runs the whole
+// minimisation: a conditional WHILE node repeats K passes [tile map ->
+// constants -> NLL+grad -> state update] until every fit is DONE, decided on
+// the device; fits that are done drop out of the tile map, so stragglers do not
+// pay for the whole batch.
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "fitcore.cuh"
@@ -28,12 +30,103 @@ cudaStream_t fit_stream() {
     return streams[dev];
 }
 
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() {
-        if (p) cudaFree(p);
+// Last kernel of the loop body: run the body again while any fit is active and
+// fewer than max_rounds bodies have run.
+__global__ void continue_kernel(cudaGraphConditionalHandle handle, const int* n_active, int* rounds,
+                                int max_rounds) {
+    const int r = ++(*rounds);
+    cudaGraphSetConditional(handle, (*n_active > 0 && r < max_rounds) ? 1u : 0u);
+}
+
+// Per-device fit workspace, kept between calls (grow-only), with the graph of
+// the last call: a graph reads only workspace and scratch buffers and the event
+// columns, so consecutive fits of the same event set (one toy after another)
+// reuse it without capturing again.
+struct GraphKey {
+    int kind = 0, n_par = 0, n_fits = 0, max_rounds = 0;
+    double t_lo = 0.0, t_hi = 0.0;
+    int64_t n = 0, fk_stride = 0;
+    const void* ptr[14] = {};
+    bool operator==(const GraphKey& o) const {
+        if (kind != o.kind || n_par != o.n_par || n_fits != o.n_fits || max_rounds != o.max_rounds ||
+            t_lo != o.t_lo || t_hi != o.t_hi || n != o.n || fk_stride != o.fk_stride)
+            return false;
+        for (int i = 0; i < 14; ++i)
+            if (ptr[i] != o.ptr[i]) return false;
+        return true;
     }
 };
+
+struct FitContext {
+    std::mutex mu;
+    int cap = 0;                   // fits the buffers hold
+    Spec* spec = nullptr;
+    State* states = nullptr;
+    double* theta_eval = nullptr;
+    double* res = nullptr;
+    int* active = nullptr;
+    int64_t* seg_off = nullptr;
+    int* nact = nullptr;           // kGraphSteps pass counts + the loop-body counter
+    int* h_nact = nullptr;         // pinned copy of the pass counts (host-loop fallback)
+    cudaEvent_t order = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool one_launch = false;
+    bool have_key = false;
+    GraphKey key;
+};
+
+FitContext* fit_context() {
+    static FitContext ctx[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    return &ctx[dev];
+}
+
+void drop_graph(FitContext& c) {
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c.exec = nullptr;
+    c.graph = nullptr;
+    c.have_key = false;
+}
+
+ipa_status ensure_capacity(FitContext& c, int n_fits, int P) {
+    if (!c.order) {
+        ipa_status st = cuda_fail(cudaEventCreateWithFlags(&c.order, cudaEventDisableTiming), "fit event");
+        if (st != IPA_OK) return st;
+    }
+    if (!c.nact) {
+        ipa_status st = cuda_fail(cudaMalloc(&c.nact, sizeof(int) * (kGraphSteps + 1)), "fit count");
+        if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.spec, sizeof(Spec)), "fit spec");
+        if (st == IPA_OK) st = cuda_fail(cudaMallocHost(&c.h_nact, sizeof(int) * kGraphSteps), "pinned count");
+        if (st != IPA_OK) return st;
+    }
+    if (n_fits <= c.cap) return IPA_OK;
+    int cap = c.cap ? c.cap : 64;
+    while (cap < n_fits) cap *= 2;
+    cudaDeviceSynchronize();
+    drop_graph(c);
+    cudaFree(c.states);
+    cudaFree(c.theta_eval);
+    cudaFree(c.res);
+    cudaFree(c.active);
+    cudaFree(c.seg_off);
+    c.states = nullptr;
+    c.theta_eval = c.res = nullptr;
+    c.active = nullptr;
+    c.seg_off = nullptr;
+    c.cap = 0;
+    const size_t n = (size_t)cap;
+    ipa_status st = cuda_fail(cudaMalloc(&c.states, sizeof(State) * n), "fit state");
+    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.theta_eval, sizeof(double) * n * kMaxP), "fit theta");
+    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.res, sizeof(double) * n * (1 + kMaxP)), "fit results");
+    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.active, sizeof(int) * n), "fit mask");
+    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.seg_off, sizeof(int64_t) * (n + 1)), "fit offsets");
+    if (st == IPA_OK) c.cap = cap;
+    (void)P;
+    return st;
+}
 
 }  // namespace
 }  // namespace ipa
@@ -58,100 +151,143 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     // legacy default stream), ordered after the caller's stream by an event.
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     cudaStream_t s = fit_stream();
-    if (!s) return IPA_ERR_CUDA;
-    cudaEvent_t ev_in = nullptr;
-    if ((st = cuda_fail(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming), "fit event")) != IPA_OK)
-        return st;
-    cudaEventRecord(ev_in, user);
-    cudaStreamWaitEvent(s, ev_in, 0);
-    cudaEventDestroy(ev_in);
+    FitContext* cp = fit_context();
+    if (!s || !cp) return IPA_ERR_CUDA;
+    FitContext& c = *cp;
+    std::lock_guard<std::mutex> lk(c.mu);      // one fit call per device at a time
+    if ((st = ensure_capacity(c, n_fits, model->n_par)) != IPA_OK) return st;
+    cudaEventRecord(c.order, user);
+    cudaStreamWaitEvent(s, c.order, 0);
 
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
-    const int P = model->n_par;
     Scratch* sc = nullptr;
     if ((st = scratch_get((ev->n + kTile - 1) / kTile + n_fits, n_fits + 1, &sc)) != IPA_OK) return st;
-
-    DevBuf b_spec, b_state, b_eval, b_res, b_active, b_nact;
-    if ((st = cuda_fail(cudaMalloc(&b_spec.p, sizeof(Spec)), "fit spec")) != IPA_OK) return st;
-    if ((st = cuda_fail(cudaMalloc(&b_state.p, sizeof(State) * (size_t)n_fits), "fit state")) != IPA_OK) return st;
-    if ((st = cuda_fail(cudaMalloc(&b_eval.p, sizeof(double) * (size_t)n_fits * P), "fit theta")) != IPA_OK) return st;
-    if ((st = cuda_fail(cudaMalloc(&b_res.p, sizeof(double) * (size_t)n_fits * (1 + P)), "fit results")) != IPA_OK) return st;
-    if ((st = cuda_fail(cudaMalloc(&b_active.p, sizeof(int) * (size_t)n_fits), "fit mask")) != IPA_OK) return st;
-    if ((st = cuda_fail(cudaMalloc(&b_nact.p, sizeof(int) * kGraphSteps), "fit count")) != IPA_OK) return st;
-    Spec* d_spec = static_cast<Spec*>(b_spec.p);
-    State* states = static_cast<State*>(b_state.p);
-    double* theta_eval = static_cast<double*>(b_eval.p);
-    double* res = static_cast<double*>(b_res.p);
-    int* active = static_cast<int*>(b_active.p);
-    int* n_active = static_cast<int*>(b_nact.p);
-    int* h_nact = nullptr;
-    if ((st = cuda_fail(cudaMallocHost(&h_nact, sizeof(int) * kGraphSteps), "pinned count")) != IPA_OK) return st;
-
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    // every exit waits for the library stream before the buffers are freed
+    int* n_active = c.nact;
+    int* d_rounds = c.nact + kGraphSteps;
+    const int max_rounds = (sp.max_passes + kGraphSteps - 1) / kGraphSteps + 2;
     auto done = [&](ipa_status r) -> ipa_status {
         cudaStreamSynchronize(s);
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        cudaFreeHost(h_nact);
         return r;
     };
 
     const int fb = 128, fg = (n_fits + fb - 1) / fb;
-    if ((st = cuda_fail(cudaMemcpyAsync(d_spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s), "fit spec copy")) != IPA_OK)
+    if ((st = cuda_fail(cudaMemcpyAsync(c.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s), "fit spec copy")) != IPA_OK)
         return done(st);
-    init_kernel<<<fg, fb, 0, s>>>(d_spec, 0, n_fits, theta_io_dev, states, theta_eval, active);
+    if ((st = cuda_fail(cudaMemcpyAsync(c.seg_off, seg_off_dev, sizeof(int64_t) * (n_fits + 1),
+                                        cudaMemcpyDeviceToDevice, s), "fit offsets copy")) != IPA_OK)
+        return done(st);
+    init_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, theta_io_dev, c.states, c.theta_eval, c.active);
     if ((st = cuda_fail(cudaGetLastError(), "fit init")) != IPA_OK) return done(st);
 
     const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
     // one pass = tile map, constants, segmented NLL+grad, state update
     auto pass = [&](int k) -> ipa_status {
         ipa_status q;
-        if ((q = launch_seg_tiles(seg_off_dev, seg_off_dev + 1, active, n_fits, ev->n, sc->seg_tiles, s)) != IPA_OK)
+        if ((q = launch_seg_tiles(c.seg_off, c.seg_off + 1, c.active, n_fits, ev->n, sc->seg_tiles, s)) != IPA_OK)
             return q;
-        if ((q = launch_consts(m, theta_eval, n_fits, sc->consts, s)) != IPA_OK) return q;
-        if ((q = launch_nll(m, true, cols, ev->n, seg_off_dev, seg_off_dev + 1, sc->seg_tiles, n_fits,
-                            sc->consts, sc, res, s)) != IPA_OK)
+        if ((q = launch_consts(m, c.theta_eval, n_fits, sc->consts, s)) != IPA_OK) return q;
+        if ((q = launch_nll(m, true, cols, ev->n, c.seg_off, c.seg_off + 1, sc->seg_tiles, n_fits,
+                            sc->consts, sc, c.res, s)) != IPA_OK)
             return q;
         if ((q = cuda_fail(cudaMemsetAsync(n_active + k, 0, sizeof(int), s), "fit count reset")) != IPA_OK)
             return q;
-        qn_kernel<<<fg, fb, 0, s>>>(d_spec, 0, n_fits, seg_off_dev, seg_off_dev + 1, res, states, theta_eval,
-                                    active, n_active + k);
+        qn_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, c.seg_off, c.seg_off + 1, c.res, c.states, c.theta_eval,
+                                    c.active, n_active + k);
         return cuda_fail(cudaGetLastError(), "fit step");
     };
 
-    // capture kGraphSteps passes once, replay until every fit is done
-    bool use_graph = false;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        ipa_status q = IPA_OK;
-        for (int k = 0; k < kGraphSteps && q == IPA_OK; ++k) q = pass(k);
-        const cudaError_t e = cudaStreamEndCapture(s, &graph);
-        use_graph = q == IPA_OK && e == cudaSuccess &&
-                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
-        if (!use_graph) cudaGetLastError();
-    } else {
-        cudaGetLastError();
-    }
-    const int max_rounds = (sp.max_passes + kGraphSteps - 1) / kGraphSteps + 2;
-    for (int round = 0; round < max_rounds && st == IPA_OK; ++round) {
-        if (use_graph) {
-            st = cuda_fail(cudaGraphLaunch(exec, s), "fit graph launch");
-        } else {
-            for (int k = 0; k < kGraphSteps && st == IPA_OK; ++k) st = pass(k);
+    GraphKey key;
+    key.kind = m.kind;
+    key.n_par = m.n_par;
+    key.n_fits = n_fits;
+    key.max_rounds = max_rounds;
+    key.t_lo = m.t_lo;
+    key.t_hi = m.t_hi;
+    key.n = ev->n;
+    key.fk_stride = ev->fk_stride;
+    const void* ptrs[14] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, sc->partials, sc->counters, sc->work,
+                            sc->seg_tiles, sc->consts, c.states, c.seg_off, (const void*)s};
+    for (int i = 0; i < 14; ++i) key.ptr[i] = ptrs[i];
+
+    if (!(c.have_key && c.key == key)) {
+        // Preferred: the whole minimisation as ONE graph launch.  A conditional
+        // WHILE node repeats a body of kGraphSteps passes; the last kernel of the
+        // body keeps the loop going while any fit is active and fewer than
+        // max_rounds bodies have run (so the loop always ends).
+        drop_graph(c);
+        cudaGraphConditionalHandle handle;
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t cnode;
+        bool ok = cudaGraphCreate(&c.graph, 0) == cudaSuccess &&
+                  cudaGraphConditionalHandleCreate(&handle, c.graph, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+        if (ok) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = handle;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            ok = cudaGraphAddNode(&cnode, c.graph, nullptr, nullptr, 0, &np) == cudaSuccess;
         }
-        if (st != IPA_OK) break;
-        st = cuda_fail(cudaMemcpyAsync(h_nact, n_active, sizeof(int) * kGraphSteps, cudaMemcpyDeviceToHost, s),
-                       "fit count copy");
-        if (st == IPA_OK) st = cuda_fail(cudaStreamSynchronize(s), "fit sync");
-        if (st == IPA_OK && h_nact[kGraphSteps - 1] == 0) break;
+        if (ok && cudaStreamBeginCaptureToGraph(s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            ipa_status q = IPA_OK;
+            for (int k = 0; k < kGraphSteps && q == IPA_OK; ++k) q = pass(k);
+            if (q == IPA_OK) {
+                continue_kernel<<<1, 1, 0, s>>>(handle, n_active + kGraphSteps - 1, d_rounds, max_rounds);
+                q = cuda_fail(cudaGetLastError(), "fit loop condition");
+            }
+            cudaGraph_t body = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &body);
+            ok = q == IPA_OK && e == cudaSuccess && cudaGraphInstantiate(&c.exec, c.graph, 0) == cudaSuccess;
+        } else {
+            ok = false;
+        }
+        c.one_launch = ok;
+        if (!ok) {
+            // Fallback: a graph of kGraphSteps passes replayed from the host
+            cudaGetLastError();
+            drop_graph(c);
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                ipa_status q = IPA_OK;
+                for (int k = 0; k < kGraphSteps && q == IPA_OK; ++k) q = pass(k);
+                const cudaError_t e = cudaStreamEndCapture(s, &c.graph);
+                if (!(q == IPA_OK && e == cudaSuccess && cudaGraphInstantiate(&c.exec, c.graph, 0) == cudaSuccess)) {
+                    cudaGetLastError();
+                    drop_graph(c);
+                }
+            } else {
+                cudaGetLastError();
+            }
+        }
+        if (c.exec) {
+            c.key = key;
+            c.have_key = true;
+        }
+    }
+    if (c.one_launch && c.exec) {
+        st = cuda_fail(cudaMemsetAsync(d_rounds, 0, sizeof(int), s), "fit loop counter");
+        if (st == IPA_OK) st = cuda_fail(cudaGraphLaunch(c.exec, s), "fit graph launch");
+    } else {
+        for (int round = 0; round < max_rounds && st == IPA_OK; ++round) {
+            if (c.exec) {
+                st = cuda_fail(cudaGraphLaunch(c.exec, s), "fit graph launch");
+            } else {
+                for (int k = 0; k < kGraphSteps && st == IPA_OK; ++k) st = pass(k);
+            }
+            if (st != IPA_OK) break;
+            st = cuda_fail(cudaMemcpyAsync(c.h_nact, n_active, sizeof(int) * kGraphSteps, cudaMemcpyDeviceToHost, s),
+                           "fit count copy");
+            if (st == IPA_OK) st = cuda_fail(cudaStreamSynchronize(s), "fit sync");
+            if (st == IPA_OK && c.h_nact[kGraphSteps - 1] == 0) break;
+        }
     }
     if (st != IPA_OK) return done(st);
-    final_kernel<<<fg, fb, 0, s>>>(d_spec, 0, n_fits, states, theta_io_dev, err_out_dev, nll_out_dev,
+    final_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, c.states, theta_io_dev, err_out_dev, nll_out_dev,
                                    fit_status_dev, iters_out_dev, passes_out_dev);
     st = cuda_fail(cudaGetLastError(), "fit final");
     st = done(st);
     if (st == IPA_OK) st = cuda_fail(cudaGetLastError(), "fit final sync");
+    trace("{\"call\": \"ipa_fit_batch\", \"n_fits\": %d, \"events\": %lld, \"loop\": \"%s\"}", n_fits,
+          (long long)ev->n, c.one_launch && c.exec ? "device" : "host");
     // later work on the caller's stream sees the results: the call is blocking
     return st;
 }

@@ -70,6 +70,8 @@ struct Cols {
 
 // ---- host-side helpers (runtime.cu) ----
 void set_error(const char* fmt, ...);
+// Append one line to the IPA_TRACE file (if the variable is set).
+void trace(const char* fmt, ...);
 ipa_status cuda_fail(cudaError_t e, const char* what);
 ipa_status check_model(const ipa_model* m);
 ipa_status check_events(const ipa_model* m, const ipa_events* ev);

@@ -1,6 +1,7 @@
 // Host runtime: argument checks, thread-local error text, per-device scratch.
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -16,6 +17,29 @@ std::mutex g_mu;
 std::vector<Scratch> g_scratch;   // indexed by device ordinal
 std::vector<int> g_sms;
 }  // namespace
+
+// IPA_TRACE=<path>: one JSON line per traced call, appended to <path> (the
+// variable is read at every call, so it can be set or changed at run time).
+void trace(const char* fmt, ...) {
+    static std::mutex mu;
+    static FILE* f = nullptr;
+    static char open_path[1024] = "";
+    const char* path = getenv("IPA_TRACE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!f || strncmp(path, open_path, sizeof(open_path)) != 0) {
+        if (f) fclose(f);
+        f = fopen(path, "a");
+        snprintf(open_path, sizeof(open_path), "%s", path);
+    }
+    if (!f) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vfprintf(f, fmt, ap);
+    va_end(ap);
+    fputc('\n', f);
+    fflush(f);
+}
 
 void set_error(const char* fmt, ...) {
     va_list ap;

@@ -87,6 +87,30 @@ def test_fit_4d_matches_oracle_and_batch_equals_solo(env):
         assert batch["nll"][k] == pytest.approx(ref.nll, rel=1e-12)
 
 
+def test_fit_runs_as_one_device_loop_and_reuses_its_graph(env, tmp_path, monkeypatch):
+    """With IPA_TRACE set, ipa_fit_batch reports that the minimisation ran as one
+    graph launch with a device-side loop; consecutive fits of toys of the same
+    event set give the same results as a fresh call."""
+    O, G, torch, api = env
+    trace = tmp_path / "trace.jsonl"
+    monkeypatch.setenv("IPA_TRACE", str(trace))
+    m_o = O.Model("4d", 0.0, 15.0)
+    toys = [O.toy_one(m_o, TH4, 9, k, 4500, 500) for k in range(3)]
+    cols = {k: np.concatenate([t[k] for t in toys]) for k in toys[0]}
+    ev = G.to_dev(cols)
+    m = api.model_4d(0.0, 15.0)
+    params = _params(api, TH4, LO4, HI4, STEP4, list(range(10)))
+    res = []
+    for k in (0, 1, 2, 1):
+        off = torch.tensor([5000 * k, 5000 * (k + 1)], dtype=torch.int64, device="cuda")
+        r = api.ipa_fit_batch(m, ev, off, params, torch.tensor(TH4[None, :], device="cuda"), tol=1e-8)
+        res.append(r["theta"][0].cpu().numpy())
+    assert np.array_equal(res[1], res[3])
+    import json
+    lines = [json.loads(x) for x in trace.read_text().splitlines()]
+    assert len(lines) == 4 and all(x["loop"] == "device" for x in lines)
+
+
 @pytest.mark.slow
 def test_gpu_toy_pulls(env):
     """256 GPU-generated toys of Poisson(2e4) events fitted in one batch: pulls of
