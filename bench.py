@@ -81,6 +81,17 @@ def kernel_traffic(n_events: int):
         return None
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Max of a per-rank number over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -238,6 +249,21 @@ def main():
     stream = torch.cuda.current_stream()
     api.ipa_reserve(N_EVENTS, 4096)
 
+    # launch geometry: time the built-in default, then let the autotuner pick
+    def mean_ms(reps=30):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        api.ipa_nll_grad(m, ev, theta, out)
+        a.record(stream)
+        for _ in range(reps):
+            api.ipa_nll_grad(m, ev, theta, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    default_ms = mean_ms()
+    picked = api.ipa_autotune(m, ev, theta, grad=True, stream=stream)
+    launch = {"picked": picked, "default": api.ipa_launch_config_get(m, 0), "default_step_ms": default_ms,
+              "tuned_step_ms": mean_ms()}
+
     for _ in range(args.warmup):
         api.ipa_nll_grad(m, ev, theta, out)
     torch.cuda.synchronize()
@@ -260,10 +286,7 @@ def main():
         torch.distributed.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dev)
     value = N_EVENTS * ws / (ms_max * 1e-3) / 1e9
 
     # kernel-only time of the dominant kernel, measured with events on its stream:
@@ -319,7 +342,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "events": N_EVENTS, "step": "ipa_nll_grad (a1-a6)",
-                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas",
+                   "launch": launch},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "Gevents/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 88,
@@ -388,6 +412,7 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     start = TH4 + np.array([0.01, 0.002, 0.001, 0.01, 0.01, -0.01, 0.05, -0.05, 0.01, 0.1])
     off1 = torch.tensor([0, N_EVENTS], dtype=torch.int64, device=dev)
     th1 = torch.tensor(start[None, :], device=dev)
+    tune = {"fit_1e6": api.ipa_autotune(m, dict(ev, fk=api.ipa_angular_basis(m, ev)), th1, seg_off=off1)}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     evc = dict(ev, fk=api.ipa_angular_basis(m, ev))        # cached angular basis, inside the timing
@@ -426,6 +451,8 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     torch.cuda.synchronize()
     t_basis = e0.elapsed_time(e1) * 1e-3
     thb = torch.tensor(np.tile(TH4, (n_toys, 1)), device=dev)
+    tune["batch"] = api.ipa_autotune(m, cols, thb, seg_off=d64(off))
+    tune["plain_loop"] = api.ipa_autotune(m, cols, thb[:1], seg_off=d64(off[:2]))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rb = api.ipa_fit_batch(m, cols, d64(off), params, thb, max_iter=200, tol=1e-8)
@@ -454,6 +481,7 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
                     "angular_basis_s": t_basis,
                     "converged": int(ok.sum()), "status_counts": np.bincount(st, minlength=5).tolist(),
                     "pull_mean_width": pulls}
+    out["autotuned"] = tune
     del cols, rb, thb
     out["large"] = run_large(api, synth, torch, dev, m, theta, params)
     out["serve"] = run_serve(api, synth, torch, dev, m, theta, params)
@@ -537,6 +565,7 @@ def run_large(api, synth, torch, dev, m, theta, params) -> dict:
     cols = gen_sample(api, torch, dev, m, theta, n_toys, per, seed=5)
     cols["w"] = torch.tensor(synth.weights(n, 11), device=dev)
     out = torch.empty(11, dtype=torch.float64, device=dev)
+    tuned = {"raw": api.ipa_autotune(m, cols, theta)}
     for _ in range(2):
         api.ipa_nll_grad(m, cols, theta, out)
     torch.cuda.synchronize()
@@ -551,6 +580,7 @@ def run_large(api, synth, torch, dev, m, theta, params) -> dict:
     start = TH4 + np.array([0.002, 0.0005, 0.0003, 0.002, 0.002, -0.002, 0.01, -0.01, 0.002, 0.02])
     th1 = torch.tensor(start[None, :], device=dev)
     big = [api.Param(p.value, p.lo, p.hi, p.step / 7.0) for p in params]
+    tuned["cached_basis"] = api.ipa_autotune(m, dict(cols, fk=api.ipa_angular_basis(m, cols)), theta)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     cols["fk"] = api.ipa_angular_basis(m, cols)              # inside the fit timing
@@ -567,7 +597,8 @@ def run_large(api, synth, torch, dev, m, theta, params) -> dict:
     return {"events": n, "weighted": True, "nll_grad_ms": ms, "Gevents_per_s": n / (ms * 1e-3) / 1e9,
             "nll_grad_ms_cached_basis": ms_c, "Gevents_per_s_cached_basis": n / (ms_c * 1e-3) / 1e9,
             "fit": {"wall_s": dt, "status": int(r["status"][0]), "iterations": int(r["iters"][0]),
-                    "passes": npass, "Gevents_per_s": n * npass / dt / 1e9}}
+                    "passes": npass, "Gevents_per_s": n * npass / dt / 1e9},
+            "autotuned": tuned}
 
 
 if __name__ == "__main__":

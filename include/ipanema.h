@@ -243,7 +243,7 @@ ipa_status ipa_server_destroy(ipa_server* server);
  * latency-critical loop that must not pay for an allocation and the device
  * synchronisation that growing library scratch implies.  Same arguments and
  * results as ipa_nll_grad.  Its scratch is one fixed array compiled into the
- * library (~1.9 MB, held on every GPU that loads the library until exit), so
+ * library (~2 MB, held on every GPU that loads the library until exit), so
  * ev->n may not exceed IPA_NOALLOC_MAX_EVENTS (IPA_ERR_ARG otherwise).  The
  * first call on each device looks the array's address up (cudaGetSymbolAddress)
  * with that device current; make it before any stream capture.  The array is
@@ -257,6 +257,45 @@ ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_events* ev, co
  * calls allocate nothing (needed before CUDA-graph capture).  Calls allocate
  * on demand otherwise. */
 ipa_status ipa_reserve(int64_t max_events, int32_t max_segments);
+
+/* ---- launch geometry and its autotuner (the paper has no counterpart: its
+ * kernels use one thread per event and a host-side sum, Sec. 3) ----
+ *
+ * The likelihood kernel adds each segment's events in an order fixed by
+ * 512-event tiles and groups of 32 tiles, so the geometry below changes the
+ * speed of ipa_nll, ipa_nll_grad, ipa_nll_grad_segmented, ipa_fit_batch and the
+ * server, never a result (bit for bit).  A geometry is kept per device, kernel
+ * variant (model kind, gradient or not, cached angular basis or not, one
+ * segment or several) and size class (tile count rounded down to a power of
+ * two).  Untuned classes use single-warp blocks with ceil(tiles / SMs)
+ * resident warps per SM. */
+typedef struct {
+    int32_t warps_per_block;   /* 1, 2, 4 or 8 */
+    int32_t warps_per_sm;      /* resident warps wanted per SM (capped by occupancy);
+                                  0 = one per tile-take per SM, ceil(takes / SMs) */
+    int32_t tiles_per_take;    /* 512-event tiles a warp takes from the work counter at once: 1, 2 or 4 */
+    float ms;                  /* ipa_autotune: measured time per launch of the pick; 0 otherwise */
+} ipa_launch_config;
+
+/* Time every geometry (block size 1/2/4/8 warps x {ceil(takes/SMs), occupancy}
+ * warps per SM x 1/2/4 tiles per take) on these events and parameters and
+ * keep the fastest for their variant and size class.  seg_off_dev (device,
+ * n_seg + 1 offsets) may be NULL for one segment; theta_dev holds n_seg x
+ * n_par parameters; grad selects the NLL+gradient (1) or NLL-only (0) kernel;
+ * a cached basis in ev->fk selects the cached variant.  Blocking (synchronises
+ * the stream; about 24 x 5 ms); IPA_ERR_BUSY if the stream is being captured,
+ * IPA_ERR_ARG for no events.  `picked` (host, may be NULL) receives the pick
+ * with its time.  Graphs the fitter cached before the call are re-captured. */
+ipa_status ipa_autotune(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev, int32_t n_seg,
+                        const double* theta_dev, int32_t grad, ipa_launch_config* picked, void* stream);
+
+/* Geometry that a launch over n_events events in n_seg segments would use
+ * (host output), and explicit setting of a class's geometry (IPA_ERR_ARG for
+ * values outside the ranges above). */
+ipa_status ipa_launch_config_get(const ipa_model* model, int64_t n_events, int32_t n_seg, int32_t grad,
+                                 int32_t cached, ipa_launch_config* cfg);
+ipa_status ipa_launch_config_set(const ipa_model* model, int64_t n_events, int32_t n_seg, int32_t grad,
+                                 int32_t cached, const ipa_launch_config* cfg);
 
 /* FP64 roofline calibration on the current device (blocking, ~1 s).
  * results (host, 13 doubles): [0] DFMA per clock per SM, [1] DFMA per second

@@ -41,6 +41,11 @@ class ipa_param(ctypes.Structure):
                 ("fixed", c_int32), ("_pad", c_int32)]
 
 
+class ipa_launch_config(ctypes.Structure):
+    _fields_ = [("warps_per_block", c_int32), ("warps_per_sm", c_int32), ("tiles_per_take", c_int32),
+                ("ms", ctypes.c_float)]
+
+
 # name -> (restype, argtypes); every function declared in include/ipanema.h
 PROTOTYPES = {
     "ipa_model_init": (c_int32, [POINTER(ipa_model), c_int32, c_double, c_double]),
@@ -62,6 +67,12 @@ PROTOTYPES = {
                                  POINTER(c_int32)]),
     "ipa_server_destroy": (c_int32, [c_void_p]),
     "ipa_reserve": (c_int32, [c_int64, c_int32]),
+    "ipa_autotune": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, c_void_p, c_int32,
+                               POINTER(ipa_launch_config), c_void_p]),
+    "ipa_launch_config_get": (c_int32, [POINTER(ipa_model), c_int64, c_int32, c_int32, c_int32,
+                                        POINTER(ipa_launch_config)]),
+    "ipa_launch_config_set": (c_int32, [POINTER(ipa_model), c_int64, c_int32, c_int32, c_int32,
+                                        POINTER(ipa_launch_config)]),
     "ipa_calibrate_fp64": (c_int32, [POINTER(c_double), c_void_p]),
     "ipa_last_error": (c_char_p, []),
     "ipa_version": (c_char_p, []),

@@ -250,6 +250,41 @@ def ipa_reserve(max_events: int, max_segments: int = 1):
     _check(_lib().ipa_reserve(max_events, max_segments), "ipa_reserve")
 
 
+def _cfg_dict(c: C.ipa_launch_config) -> dict:
+    return {"warps_per_block": c.warps_per_block, "warps_per_sm": c.warps_per_sm,
+            "tiles_per_take": c.tiles_per_take, "ms": float(c.ms)}
+
+
+def ipa_autotune(model: C.ipa_model, ev: dict, theta: torch.Tensor, grad: bool = True,
+                 seg_off: torch.Tensor | None = None, stream=None) -> dict:
+    """Time every launch geometry of the likelihood kernel on these events and keep
+    the fastest for their size class (results never depend on the geometry)."""
+    n_seg = 1 if seg_off is None else int(seg_off.numel()) - 1
+    picked = C.ipa_launch_config()
+    e = ipa_events(ev)
+    _check(_lib().ipa_autotune(ctypes.byref(model), ctypes.byref(e),
+                               None if seg_off is None else _ptr(seg_off, torch.int64, "seg_off"), n_seg,
+                               _ptr(theta, name="theta"), int(bool(grad)), ctypes.byref(picked),
+                               _stream(stream)), "ipa_autotune")
+    return _cfg_dict(picked)
+
+
+def ipa_launch_config_get(model: C.ipa_model, n_events: int, n_seg: int = 1, grad: bool = True,
+                          cached: bool = False) -> dict:
+    c = C.ipa_launch_config()
+    _check(_lib().ipa_launch_config_get(ctypes.byref(model), n_events, n_seg, int(bool(grad)), int(bool(cached)),
+                                        ctypes.byref(c)), "ipa_launch_config_get")
+    return _cfg_dict(c)
+
+
+def ipa_launch_config_set(model: C.ipa_model, n_events: int, cfg: dict, n_seg: int = 1, grad: bool = True,
+                          cached: bool = False):
+    c = C.ipa_launch_config(int(cfg["warps_per_block"]), int(cfg["warps_per_sm"]), int(cfg["tiles_per_take"]),
+                            0.0)
+    _check(_lib().ipa_launch_config_set(ctypes.byref(model), n_events, n_seg, int(bool(grad)), int(bool(cached)),
+                                        ctypes.byref(c)), "ipa_launch_config_set")
+
+
 def ipa_calibrate_fp64(stream=None) -> dict:
     """DFMA rate and FP64 math-function costs of the current GPU (see the header)."""
     r = (ctypes.c_double * 13)()

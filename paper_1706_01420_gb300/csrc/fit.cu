@@ -44,14 +44,15 @@ __global__ void continue_kernel(cudaGraphConditionalHandle handle, const int* n_
 // reuse it without capturing again.
 struct GraphKey {
     int kind = 0, n_par = 0, n_fits = 0, max_rounds = 0;
+    unsigned tune = 0;             // launch-geometry table version the graph was captured with
     double t_lo = 0.0, t_hi = 0.0;
     int64_t n = 0, fk_stride = 0;
-    const void* ptr[14] = {};
+    const void* ptr[15] = {};
     bool operator==(const GraphKey& o) const {
         if (kind != o.kind || n_par != o.n_par || n_fits != o.n_fits || max_rounds != o.max_rounds ||
-            t_lo != o.t_lo || t_hi != o.t_hi || n != o.n || fk_stride != o.fk_stride)
+            tune != o.tune || t_lo != o.t_lo || t_hi != o.t_hi || n != o.n || fk_stride != o.fk_stride)
             return false;
-        for (int i = 0; i < 14; ++i)
+        for (int i = 0; i < 15; ++i)
             if (ptr[i] != o.ptr[i]) return false;
         return true;
     }
@@ -205,9 +206,10 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     key.t_hi = m.t_hi;
     key.n = ev->n;
     key.fk_stride = ev->fk_stride;
-    const void* ptrs[14] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, sc->partials, sc->counters, sc->work,
-                            sc->seg_tiles, sc->consts, c.states, c.seg_off, (const void*)s};
-    for (int i = 0; i < 14; ++i) key.ptr[i] = ptrs[i];
+    key.tune = tune_epoch();
+    const void* ptrs[15] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, sc->partials, sc->counters, sc->gcount,
+                            sc->work, sc->seg_tiles, sc->consts, c.states, c.seg_off, (const void*)s};
+    for (int i = 0; i < 15; ++i) key.ptr[i] = ptrs[i];
 
     if (!(c.have_key && c.key == key)) {
         // Preferred: the whole minimisation as ONE graph launch.  A conditional

@@ -8,16 +8,19 @@
 
 namespace ipa {
 
-// Events per reduction tile and threads per block of the likelihood kernels.
-// Each of the 256 slots of a tile handles two consecutive events (one 16-byte
-// load per column); the in-tile and cross-tile trees are fixed, so results do
-// not depend on grid size or scheduling.
+// Events per reduction tile.  Lane l of the warp that owns a tile adds events
+// l, l+32, ... of the tile in order; the warp reduces its lanes with a fixed
+// shuffle tree into one partial per tile, each group of kGroupTiles tiles is
+// reduced (lane l holding tile l of the group) into one group partial, and a
+// segment's group partials are added in a fixed order.  This order depends
+// only on the segment's events, not on the launch geometry (block size, grid,
+// tiles taken at once), so tuning the geometry never changes a result.
 #ifndef IPA_TILE_EVENTS
 #define IPA_TILE_EVENTS 512
 #endif
 constexpr int kTile = IPA_TILE_EVENTS;
-constexpr int kSlots = 256;
-constexpr int kBlock = 256;
+constexpr int kGroupTiles = 32;
+constexpr int kBlock = 256;   // threads per block of the generator and helper kernels
 
 // Number of FP64 accumulators per tile.
 //   NLL only:   L = sum w log P
@@ -81,13 +84,15 @@ struct Scratch {
     double* partials = nullptr;     // tiles * n_acc doubles
     size_t partials_cap = 0;        // doubles
     unsigned* counters = nullptr;   // one per segment, zero between calls
+    unsigned* gcount = nullptr;     // one per tile (used at a group's first tile), zero between calls
     unsigned* work = nullptr;       // [tiles taken, warps finished], zero between calls
     int64_t* seg_tiles = nullptr;   // n_seg + 1 prefix of tiles per segment
     Consts* consts = nullptr;       // one per segment
     size_t seg_cap = 0;             // segments
 };
 // Ensure the current device's scratch holds `tiles` tiles of 15 accumulators
-// and `segs` segments.  May synchronise the device when it grows.
+// (and their group counters) and `segs` segments.  May synchronise the device
+// when it grows.
 ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out);
 
 // ---- kernels launched across translation units ----
@@ -96,13 +101,34 @@ ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Cons
                          cudaStream_t s);
 // compute_consts_warp (consts.cuh): one warp turns theta into a Consts record.
 
+// Launch geometry of the likelihood kernel (tune.cu picks it; no result
+// depends on it).
+struct LaunchCfg {
+    int warps_per_block;   // 1, 2, 4 or 8
+    int warps_per_sm;      // resident warps wanted per SM; 0 = ceil(work units / SMs)
+    int tiles_per_take;    // tiles a warp takes from the work counter at once: 1, 2 or 4
+};
+// Host estimate of a launch's tile count (selects the size class only): exact
+// for one segment, ceil(n / kTile) + n_seg / 2 for several.
+inline int64_t tile_estimate(int64_t n, int n_seg) {
+    return (n + kTile - 1) / kTile + (n_seg > 1 ? n_seg / 2 : 0);
+}
+// Configuration for a launch over about `tiles` tiles (table entry of the
+// autotuner for this kernel variant and size, else the built-in default).
+LaunchCfg launch_cfg(int kind, bool grad, bool cached, bool segmented, int64_t tiles);
+// Incremented whenever a table entry changes (cached CUDA graphs that hold a
+// likelihood launch compare it to know when to re-capture).
+unsigned tune_epoch();
+
 // nll.cu: NLL(+grad) over precomputed consts; out: (1 + n_par) per segment (1 without
 // the gradient).  With seg_begin == nullptr there is one segment [0, n).  Otherwise
 // segment s is events [seg_begin[s], seg_end[s]) and seg_tiles must hold the device
-// prefix of its tiles (launch_seg_tiles).
+// prefix of its tiles (launch_seg_tiles).  The geometry is launch_cfg's for
+// tile_estimate(n, n_seg) tiles and n_seg > 1, unless `cfg` forces one.
 ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
-                      const Consts* consts, Scratch* sc, double* out, cudaStream_t s);
+                      const Consts* consts, Scratch* sc, double* out, cudaStream_t s,
+                      const LaunchCfg* cfg = nullptr);
 // nll.cu: seg_tiles[s] = sum_{r<s} ceil(size_r / kTile), s = 0..n_seg, with the
 // ranges clamped to [0, n]; segments with active[r] == 0 get no tiles (active may
 // be NULL).

@@ -8,9 +8,11 @@
 // tiles owned by single warps: lane l accumulates events l, l+32, ..., l+480
 // of its tile in order (coalesced 8-byte loads), the warp reduces its FP64
 // accumulators with a fixed shuffle tree and writes one partial per tile.
-// The warp that completes the last tile of a segment reduces that segment's
-// partials in fixed order and writes its NLL and gradient.  No block-wide
-// barrier sits in the event loop, and the result does not depend on the grid.
+// The warp that completes the last tile of a group of 32 tiles reduces the
+// group, and the warp that completes a segment's last group adds its group
+// partials in fixed order and writes the NLL and gradient.  No block-wide
+// barrier sits in the event loop, and the result does not depend on the
+// launch geometry (block size, grid, tiles taken at once).
 //
 // The GPU has 2 FP64 operations per clock per SM, so the per-event arithmetic
 // is arranged to spend as few of them as possible:
@@ -39,8 +41,7 @@
 namespace ipa {
 namespace {
 
-constexpr int kWarpsPerBlock = 4;
-constexpr int kNllBlock = 32 * kWarpsPerBlock;
+constexpr int kNllBlock = 128;                       // threads per block of the basis kernel
 constexpr int kPerLane = kTile / 32;                 // events per lane per tile
 
 // Constant factors c_k of f_k = c_k f'_k, where f'_k is the product of
@@ -196,19 +197,40 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
         out[1 + j] = 0.0;
 }
 
+// Reduce the tile partials of one group (lane l holds tile g0 + l) or, with
+// `stride` = kGroupTiles, the group partials of one segment (lane l adds groups
+// l, l+32, ... in that order), then the fixed shuffle tree.
+template <int NA>
+__device__ __forceinline__ void reduce_partials(const double* partials, int64_t first, int64_t count,
+                                                int64_t stride, int lane, double* acc) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = 0.0;
+#pragma unroll 4
+    for (int64_t i = lane; i < count; i += 32) {
+        const double* p = partials + (first + i * stride) * NA;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] += __ldcg(p + a);
+    }
+    warp_tree<NA>(acc);
+}
+
+// Blocks of any whole number of warps (1..kMaxWarps); each warp keeps a copy of
+// its current segment's constants in dynamic shared memory.
+constexpr int kMaxWarps = 8;
+
 template <int KIND, bool GRAD, bool CACHED>
-__global__ void __launch_bounds__(kNllBlock, 4)
+__global__ void __launch_bounds__(32 * kMaxWarps, 2)
 nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
            const int64_t* __restrict__ seg_end, const int64_t* __restrict__ seg_tiles, int n_seg,
            const Consts* __restrict__ consts,
-           double* __restrict__ partials, unsigned* __restrict__ counters,
-           unsigned* __restrict__ work, double* __restrict__ out, int n_par) {
+           double* __restrict__ partials, unsigned* __restrict__ counters, unsigned* __restrict__ gcount,
+           unsigned* __restrict__ work, double* __restrict__ out, int n_par, int per_take) {
     constexpr int NA = n_acc(KIND, GRAD);
     const int out_stride = GRAD ? 1 + n_par : 1;
     __shared__ MathTables mt;
-    __shared__ __align__(16) WarpConsts wcs[kWarpsPerBlock];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    WarpConsts& wc = wcs[wib];
+    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem)[wib];
 
     load_math_tables(&mt);
     __syncthreads();
@@ -226,82 +248,90 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
         }
     }
 
-    // Tiles are handed out dynamically (work[0] counts the tiles taken), so SMs
-    // whose warps finish early take more; a tile's partial does not depend on
-    // which warp computes it.  The last warp to leave resets both counters.
+    // Tiles are handed out dynamically, `per_take` consecutive tiles at a time
+    // (work[0] counts the takes), so SMs whose warps finish early take more; a
+    // tile's partial does not depend on which warp computes it.  The last warp
+    // to leave resets both work counters.
     int cur = -1;
     while (true) {
         unsigned taken = 0;
         if (lane == 0) taken = atomicAdd(work, 1u);
-        const int64_t tile = (int64_t)__shfl_sync(0xffffffffu, taken, 0);
-        if (tile >= total) break;
-        int seg = 0;
-        int64_t t0 = 0, t1 = total, ev0 = 0, ev1 = n;
-        if (!single) {
-            seg = find_segment(seg_tiles, n_seg, tile);
-            t0 = __ldg(seg_tiles + seg);
-            t1 = __ldg(seg_tiles + seg + 1);
-            ev0 = clamp_off(__ldg(seg_begin + seg), n);
-            ev1 = clamp_off(__ldg(seg_end + seg), n);
-            if (ev1 < ev0) ev1 = ev0;
-        }
-        if (seg != cur) {
-            __syncwarp();
-            const double* src = reinterpret_cast<const double*>(consts + seg);
-            double* dst = reinterpret_cast<double*>(&wc.c);
-            for (int i = lane; i < kConstsDoubles; i += 32) dst[i] = __ldg(src + i);
-            __syncwarp();
-            if (lane < 10) wc.hp[lane] = wc.c.h[lane] * kBasisScale[lane];
-            __syncwarp();
-            cur = seg;
-        }
-
-        double acc[NA];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) acc[a] = 0.0;
-
-        const int64_t base = ev0 + (tile - t0) * kTile + lane;
-#pragma unroll 1
-        for (int i = 0; i < kPerLane; ++i) {
-            const int64_t e = base + 32 * i;
-            if (e < ev1) {
-                const double w = cols.w ? __ldg(cols.w + e) : 1.0;
-                double f[10];
-                if (KIND == IPA_MODEL_ANGTIME4D) {
-                    if (CACHED) {
-#pragma unroll
-                        for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
-                    } else {
-                        basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
-                    }
-                }
-                event<KIND, GRAD, CACHED>(wc, &mt, __ldg(cols.t + e), f, w, acc);
+        const int64_t first = (int64_t)__shfl_sync(0xffffffffu, taken, 0) * per_take;
+        if (first >= total) break;
+        const int64_t stop = first + per_take < total ? first + per_take : total;
+        for (int64_t tile = first; tile < stop; ++tile) {
+            int seg = 0;
+            int64_t t0 = 0, t1 = total, ev0 = 0, ev1 = n;
+            if (!single) {
+                seg = find_segment(seg_tiles, n_seg, tile);
+                t0 = __ldg(seg_tiles + seg);
+                t1 = __ldg(seg_tiles + seg + 1);
+                ev0 = clamp_off(__ldg(seg_begin + seg), n);
+                ev1 = clamp_off(__ldg(seg_end + seg), n);
+                if (ev1 < ev0) ev1 = ev0;
             }
-        }
+            if (seg != cur) {
+                __syncwarp();
+                const double* src = reinterpret_cast<const double*>(consts + seg);
+                double* dst = reinterpret_cast<double*>(&wc.c);
+                for (int i = lane; i < kConstsDoubles; i += 32) dst[i] = __ldg(src + i);
+                __syncwarp();
+                if (lane < 10) wc.hp[lane] = wc.c.h[lane] * kBasisScale[lane];
+                __syncwarp();
+                cur = seg;
+            }
 
-        warp_tree<NA>(acc);
-        int last = 0;
-        if (lane == 0) {
-#pragma unroll
-            for (int a = 0; a < NA; ++a) partials[tile * NA + a] = acc[a];
-            __threadfence();
-            const unsigned done = atomicAdd(counters + seg, 1u) + 1u;
-            last = (done == (unsigned)(t1 - t0));
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-            // this warp wrote the segment's last tile: reduce the segment's partials
-            __threadfence();
+            double acc[NA];
 #pragma unroll
             for (int a = 0; a < NA; ++a) acc[a] = 0.0;
-            // lane l adds tiles l, l+32, l+64, ... in that order; unrolled so that
-            // the loads of several tiles are in flight at once
-#pragma unroll 8
-            for (int64_t tt = t0 + lane; tt < t1; tt += 32) {
+
+            const int64_t base = ev0 + (tile - t0) * kTile + lane;
+#pragma unroll 1
+            for (int i = 0; i < kPerLane; ++i) {
+                const int64_t e = base + 32 * i;
+                if (e < ev1) {
+                    const double w = cols.w ? __ldg(cols.w + e) : 1.0;
+                    double f[10];
+                    if (KIND == IPA_MODEL_ANGTIME4D) {
+                        if (CACHED) {
 #pragma unroll
-                for (int a = 0; a < NA; ++a) acc[a] += __ldcg(partials + tt * NA + a);
+                            for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
+                        } else {
+                            basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
+                        }
+                    }
+                    event<KIND, GRAD, CACHED>(wc, &mt, __ldg(cols.t + e), f, w, acc);
+                }
             }
             warp_tree<NA>(acc);
+
+            // level 1: the warp that completes a group of kGroupTiles tiles
+            // reduces it into the partial slot of the group's first tile
+            const int64_t g0 = t0 + ((tile - t0) / kGroupTiles) * kGroupTiles;
+            const int64_t g1 = g0 + kGroupTiles < t1 ? g0 + kGroupTiles : t1;
+            int last = 0;
+            if (lane == 0) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) partials[tile * NA + a] = acc[a];
+                __threadfence();
+                last = atomicAdd(gcount + g0, 1u) + 1u == (unsigned)(g1 - g0);
+            }
+            if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+            __threadfence();
+            reduce_partials<NA>(partials, g0, g1 - g0, 1, lane, acc);
+            // level 2: the warp that completes a segment's last group adds the
+            // segment's group partials and writes its NLL and gradient
+            const int64_t n_groups = (t1 - t0 + kGroupTiles - 1) / kGroupTiles;
+            if (lane == 0) {
+                gcount[g0] = 0u;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) partials[g0 * NA + a] = acc[a];
+                __threadfence();
+                last = atomicAdd(counters + seg, 1u) + 1u == (unsigned)n_groups;
+            }
+            if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+            __threadfence();
+            reduce_partials<NA>(partials, t0, n_groups, kGroupTiles, lane, acc);
             if (lane == 0) {
                 finalize<KIND, GRAD, CACHED>(wc.c, acc, n_par, out + (size_t)seg * out_stride);
                 counters[seg] = 0u;
@@ -309,7 +339,7 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
         }
     }
     if (lane == 0) {
-        const unsigned n_warps = gridDim.x * kWarpsPerBlock;
+        const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
         if (atomicAdd(work + 1, 1u) == n_warps - 1u) {
             work[0] = 0u;
             work[1] = 0u;
@@ -356,22 +386,38 @@ __global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_begin, const in
 template <int KIND, bool GRAD, bool CACHED>
 ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const int64_t* seg_end,
                     const int64_t* seg_tiles, int n_seg, const Consts* consts, Scratch* sc, double* out,
-                    int n_par, cudaStream_t st) {
-    static int per_sm = 0;
+                    int n_par, cudaStream_t st, const LaunchCfg* force) {
+    const bool single = seg_begin == nullptr;
+    const int64_t tiles = tile_estimate(n, n_seg);
+    const LaunchCfg cfg = force ? *force : launch_cfg(KIND, GRAD, CACHED, n_seg > 1, tiles);
+    const int W = cfg.warps_per_block >= 1 && cfg.warps_per_block <= kMaxWarps ? cfg.warps_per_block : 1;
+    const int K = cfg.tiles_per_take >= 1 ? cfg.tiles_per_take : 1;
+    const size_t smem = (size_t)W * sizeof(WarpConsts);
+    // resident blocks per SM for each block size (cached per device and variant)
+    static int occ[64][kMaxWarps + 1] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& per_sm = occ[dev & 63][W];
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, nll_kernel<KIND, GRAD, CACHED>, kNllBlock, 0);
-        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        int v = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, nll_kernel<KIND, GRAD, CACHED>,
+                                                                      32 * W, smem);
+        per_sm = e == cudaSuccess && v >= 1 ? v : 1;
     }
-    int64_t grid = (int64_t)sm_count() * per_sm;
-    if (seg_begin == nullptr) {
-        const int64_t tiles = (n + kTile - 1) / kTile;
-        const int64_t need = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t sms = sm_count();
+    const int64_t units = (tiles + K - 1) / K;
+    int64_t want = cfg.warps_per_sm > 0 ? cfg.warps_per_sm : (units + sms - 1) / sms;
+    if (want > (int64_t)per_sm * W) want = (int64_t)per_sm * W;
+    if (want < 1) want = 1;
+    int64_t grid = sms * ((want + W - 1) / W);
+    if (single) {
+        const int64_t need = (units + W - 1) / W;   // blocks beyond this find no tile
         grid = need < grid ? need : grid;
     }
     if (grid < 1) grid = 1;
-    nll_kernel<KIND, GRAD, CACHED><<<(unsigned)grid, kNllBlock, 0, st>>>(
-        cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->work, out, n_par);
+    nll_kernel<KIND, GRAD, CACHED><<<(unsigned)grid, 32 * W, smem, st>>>(
+        cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->gcount, sc->work,
+        out, n_par, K);
     return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
 }
 
@@ -385,16 +431,16 @@ ipa_status launch_seg_tiles(const int64_t* seg_begin, const int64_t* seg_end, co
 
 ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
-                      const Consts* consts, Scratch* sc, double* out, cudaStream_t st) {
+                      const Consts* consts, Scratch* sc, double* out, cudaStream_t st, const LaunchCfg* cfg) {
     const int P = m.n_par;
     if (m.kind == IPA_MODEL_TIME1D)
-        return grad ? launch_t<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
-                    : launch_t<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
+        return grad ? launch_t<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
+                    : launch_t<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
     if (cols.fk)
-        return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
-                    : launch_t<IPA_MODEL_ANGTIME4D, false, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
-    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st)
-                : launch_t<IPA_MODEL_ANGTIME4D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st);
+        return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
+                    : launch_t<IPA_MODEL_ANGTIME4D, false, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
+    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
+                : launch_t<IPA_MODEL_ANGTIME4D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
 }
 
 // f_k = c_k f'_k for every event (the cached angular basis).

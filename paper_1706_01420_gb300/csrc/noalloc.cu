@@ -1,5 +1,5 @@
 // ipa_nll_grad_noalloc: the NLL + gradient pass of ipa_nll_grad with its
-// scratch (tile partials, the completion counter and the parameter constants)
+// scratch (tile partials, completion and group counters and the parameter constants)
 // in a fixed array compiled into this library instead of memory the library
 // allocates.  It exists for callers that cannot allocate device memory when
 // they call: code that must not trigger an allocation (and the device
@@ -8,12 +8,12 @@
 // reserved the GPU's memory so that a cudaMalloc from a plugin fails.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (about 1.9 MB) until the process exits.  Host code may not
+// library holds it (about 2 MB) until the process exits.  Host code may not
 // use its name as a device address, so the first call on each device looks
 // the address up with cudaGetSymbolAddress while that device is current, and
 // later calls reuse it.  That first call should therefore come before any
 // stream capture.  All calls share the one array and it keeps the previous
-// call's contents: the completion and work counters are cleared on the stream
+// call's contents: the completion, group and work counters are cleared on the stream
 // before every launch, and calls that overlap on the GPU (different streams, or
 // different host threads without ordering) race on the array.
 #include <mutex>
@@ -27,10 +27,11 @@ constexpr int64_t kNoAllocMaxEvents = IPA_NOALLOC_MAX_EVENTS;
 constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxEvents / kTile + 1;
 constexpr size_t kConstsBytes = 1024;     // one Consts record, padded
 constexpr size_t kCounterBytes = 256;     // completion counter and the two work counters, padded
+constexpr size_t kGroupBytes = ((size_t)kNoAllocMaxTiles * sizeof(unsigned) + 255) / 256 * 256;  // group counters
 constexpr size_t kPartialsBytes = (size_t)kNoAllocMaxTiles * 15 * sizeof(double);
 static_assert(sizeof(Consts) <= kConstsBytes, "Consts must fit its slot");
 
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kConstsBytes + kCounterBytes + kPartialsBytes];
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kConstsBytes + kCounterBytes + kGroupBytes + kPartialsBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -80,11 +81,17 @@ extern "C" ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_eve
     sc.consts = reinterpret_cast<Consts*>(base);
     sc.counters = reinterpret_cast<unsigned*>(base + kConstsBytes);
     sc.work = sc.counters + 1;
-    sc.partials = reinterpret_cast<double*>(base + kConstsBytes + kCounterBytes);
+    sc.gcount = reinterpret_cast<unsigned*>(base + kConstsBytes + kCounterBytes);
+    sc.partials = reinterpret_cast<double*>(base + kConstsBytes + kCounterBytes + kGroupBytes);
     sc.partials_cap = (size_t)kNoAllocMaxTiles * 15;
     sc.seg_cap = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = cuda_fail(cudaMemsetAsync(sc.counters, 0, 3 * sizeof(unsigned), s), "counter clear")) != IPA_OK)
+        return st;
+    // group counters sit at each group's first tile: tiles 0, 32, 64, ...
+    const int64_t used = (ev->n + kTile - 1) / kTile;
+    if (used > 0 &&
+        (st = cuda_fail(cudaMemsetAsync(sc.gcount, 0, (size_t)used * sizeof(unsigned), s), "counter clear")) != IPA_OK)
         return st;
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     if ((st = launch_consts(m, theta_dev, 1, sc.consts, s)) != IPA_OK) return st;

@@ -147,11 +147,20 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
         if (s.partials) {
             cudaDeviceSynchronize();
             cudaFree(s.partials);
+            cudaFree(s.gcount);
             s.partials = nullptr;
+            s.gcount = nullptr;
             s.partials_cap = 0;
         }
         if ((st = cuda_fail(cudaMalloc(&s.partials, cap * sizeof(double)), "scratch partials")) != IPA_OK)
             return st;
+        // one group counter per tile; zero between calls (kernels reset what they use)
+        const size_t n_tiles = cap / 15 + 1;
+        if ((st = cuda_fail(cudaMalloc(&s.gcount, n_tiles * sizeof(unsigned)), "scratch group counters")) != IPA_OK)
+            return st;
+        if ((st = cuda_fail(cudaMemset(s.gcount, 0, n_tiles * sizeof(unsigned)), "scratch memset")) != IPA_OK)
+            return st;
+        if ((st = cuda_fail(cudaDeviceSynchronize(), "scratch init")) != IPA_OK) return st;
         s.partials_cap = cap;
     }
     if (!s.work) {

@@ -316,7 +316,8 @@ void server_free(ipa_server* s) {
     for (double* a : s->arena) cudaFree(a);
     void* dev[] = {s->d_specs, s->d_states, s->d_theta_eval, s->d_res, s->d_active, s->d_begin, s->d_end,
                    s->d_nact, s->d_out_theta, s->d_out_err, s->d_out_nll, s->d_out_status, s->d_out_iters,
-                   s->d_out_passes, s->sc.partials, s->sc.counters, s->sc.work, s->sc.seg_tiles, s->sc.consts};
+                   s->d_out_passes, s->sc.partials, s->sc.counters, s->sc.gcount, s->sc.work, s->sc.seg_tiles,
+                   s->sc.consts};
     for (void* p : dev) cudaFree(p);
     void* host[] = {s->h_begin, s->h_end, s->h_active, s->h_out_theta, s->h_out_err, s->h_out_nll,
                     s->h_out_status, s->h_out_iters, s->h_out_passes};
@@ -374,6 +375,7 @@ extern "C" ipa_status ipa_server_create(const ipa_model* model, size_t hbm_budge
     const size_t tiles = (size_t)(cap / kTile + max_slots + 1);
     if (st == IPA_OK) st = dalloc(&s->sc.partials, tiles * 15, "server partials");
     if (st == IPA_OK) st = dalloc(&s->sc.counters, S + 1, "server counters");
+    if (st == IPA_OK) st = dalloc(&s->sc.gcount, tiles, "server group counters");
     if (st == IPA_OK) st = dalloc(&s->sc.work, 2, "server work counters");
     if (st == IPA_OK) st = dalloc(&s->sc.seg_tiles, S + 1, "server tiles");
     if (st == IPA_OK) st = dalloc(&s->sc.consts, S, "server consts");
@@ -395,6 +397,7 @@ extern "C" ipa_status ipa_server_create(const ipa_model* model, size_t hbm_budge
     if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->d_res, 0, sizeof(double) * S * (1 + P), s->stream), "server init");
     if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->d_active, 0, sizeof(int) * S, s->stream), "server init");
     if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->sc.counters, 0, sizeof(unsigned) * (S + 1), s->stream), "server init");
+    if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->sc.gcount, 0, sizeof(unsigned) * tiles, s->stream), "server init");
     if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->sc.work, 0, 2 * sizeof(unsigned), s->stream), "server init");
     if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->d_begin, 0, sizeof(int64_t) * S, s->stream), "server init");
     if (st == IPA_OK) st = cuda_fail(cudaMemsetAsync(s->d_end, 0, sizeof(int64_t) * S, s->stream), "server init");

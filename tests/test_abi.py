@@ -80,3 +80,32 @@ def test_product_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "ipa_oracle" not in text, f
+
+
+def test_launch_config_table_host_logic(lib):
+    """Setting and reading back a launch geometry is host-only bookkeeping:
+    the value set for a size class is returned for every size of that class,
+    classes are kept apart, and out-of-range geometries are refused."""
+    from paper_1706_01420_gb300 import _capi as C
+    m = C.ipa_model()
+    lib.ipa_model_init(ctypes.byref(m), C.IPA_MODEL_ANGTIME4D, 0.0, 15.0)
+    default = C.ipa_launch_config()
+    assert lib.ipa_launch_config_get(ctypes.byref(m), 123_456_789, 1, 1, 0, ctypes.byref(default)) == C.IPA_OK
+    assert (default.warps_per_block, default.warps_per_sm, default.tiles_per_take) == (1, 0, 1)
+    cfg = C.ipa_launch_config(4, 12, 2, 0.0)
+    # 3e6 events = 5860 tiles: class [4096, 8192) tiles
+    assert lib.ipa_launch_config_set(ctypes.byref(m), 3_000_000, 1, 1, 0, ctypes.byref(cfg)) == C.IPA_OK
+    for n in (4096 * 512, 3_000_000, 8191 * 512):
+        got = C.ipa_launch_config()
+        assert lib.ipa_launch_config_get(ctypes.byref(m), n, 1, 1, 0, ctypes.byref(got)) == C.IPA_OK
+        assert (got.warps_per_block, got.warps_per_sm, got.tiles_per_take) == (4, 12, 2), n
+    for other in ((8192 * 512, 1, 1, 0), (3_000_000, 1, 0, 0), (3_000_000, 1, 1, 1), (3_000_000, 64, 1, 0)):
+        got = C.ipa_launch_config()
+        lib.ipa_launch_config_get(ctypes.byref(m), other[0], other[1], other[2], other[3], ctypes.byref(got))
+        assert (got.warps_per_block, got.warps_per_sm, got.tiles_per_take) == (1, 0, 1), other
+    for bad in ((3, 0, 1), (0, 0, 1), (16, 0, 1), (1, -1, 1), (1, 65, 1), (1, 0, 3), (1, 0, 0)):
+        c = C.ipa_launch_config(*bad, 0.0)
+        assert lib.ipa_launch_config_set(ctypes.byref(m), 1000, 1, 1, 0, ctypes.byref(c)) == C.IPA_ERR_ARG
+    assert lib.ipa_launch_config_get(ctypes.byref(m), -1, 1, 1, 0, ctypes.byref(cfg)) == C.IPA_ERR_ARG
+    assert lib.ipa_launch_config_get(ctypes.byref(m), 10, 0, 1, 0, ctypes.byref(cfg)) == C.IPA_ERR_ARG
+    lib.ipa_launch_config_set(ctypes.byref(m), 3_000_000, 1, 1, 0, ctypes.byref(default))   # leave the default
