@@ -5,7 +5,11 @@
 * ipa_toygen output equals the oracle's toys bit for bit (1D and 4D, small
   toys, ragged counts, empty toys);
 * the 4096-toy batch of Poisson(2e4) sizes: sampled toys bit-exact, every toy
-  fully written, per-toy background counts exact.
+  fully written, per-toy background counts exact;
+* parameter regimes where the generator's FP32 decision filter hands many
+  candidates to the FP64 test (decay times below the resolution offset, where
+  the erfc argument is large and positive; narrow and wide resolutions; large
+  exponents) still give the oracle's toys bit for bit.
 """
 import ctypes
 import os
@@ -32,14 +36,16 @@ def env(oracle):
     return oracle, G, torch, api
 
 
-def _gen(env, kind, th, seed, n_sig, n_bkg, pad=0):
+def _gen(env, kind, th, seed, n_sig, n_bkg, pad=0, t_range=None):
     O, G, torch, api = env
     n_sig = np.asarray(n_sig, dtype=np.int64)
     n_bkg = np.asarray(n_bkg, dtype=np.int64)
     sizes = n_sig + n_bkg + pad
     off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
     total = int(sizes.sum())
-    m = api.model_1d(0.3, 15.0) if kind == "1d" else api.model_4d(0.0, 15.0)
+    if t_range is None:
+        t_range = (0.3, 15.0) if kind == "1d" else (0.0, 15.0)
+    m = api.model_1d(*t_range) if kind == "1d" else api.model_4d(*t_range)
     keys = ("t",) if kind == "1d" else ("t", "ck", "cl", "phi")
     out = {k: torch.full((max(total, 1),), -7.0, dtype=torch.float64, device="cuda") for k in keys}
     d = lambda a: torch.tensor(a, dtype=torch.int64, device="cuda")
@@ -125,3 +131,22 @@ def test_non_physical_theta_terminates_with_nan(env):
     got, off = _gen(env, "1d", th, 1, [50], [4])
     assert np.all(np.isnan(got["t"][:50]))
     assert np.all(np.isfinite(got["t"][50:54]))
+
+
+@pytest.mark.parametrize("kind,t_range,th", [
+    ("1d", (-1.0, 15.0), [2.0, 0.01, 0.05, 0.2]),            # tau < 0: erfc argument up to ~75
+    ("1d", (0.0, 40.0), [0.3, 0.005, 0.0, 0.05]),            # narrow resolution, exponent up to 12
+    ("1d", (-0.2, 3.0), [4.0, 0.3, 0.1, 0.0]),               # wide resolution, steep decay
+    ("4d", (-0.5, 8.0), [1.5, 0.2, -0.1, 0.3, 0.45, 0.3, 2.5, -1.0, 0.2, 1.5]),
+])
+def test_toys_bit_exact_in_filter_edge_regimes(env, kind, t_range, th):
+    O = env[0]
+    th = np.asarray(th, dtype=np.float64)
+    n_sig, n_bkg = [2500, 700], [3, 0]
+    got, off = _gen(env, kind, th, 4242, n_sig, n_bkg, t_range=t_range)
+    m = O.Model(kind, *t_range)
+    for k in range(2):
+        ref = O.toy_one(m, th, 4242, k, n_sig[k], n_bkg[k])
+        n = n_sig[k] + n_bkg[k]
+        for col, v in ref.items():
+            np.testing.assert_array_equal(got[col][off[k]:off[k] + n], v, err_msg=f"toy {k} {col}")
