@@ -50,10 +50,17 @@ __device__ const double kBasisScale[10] = {
     1.0, 0.5, 0.5, 1.0, 1.41421356237309504880, -1.41421356237309504880, 1.0 / 3.0,
     0.81649658092772603273, -0.81649658092772603273, 1.15470053837925152902};
 
-// Per-warp copy of a segment's constants in shared memory.
+// Per-warp copy of a segment's constants in shared memory, with the factors
+// the event loop multiplies by folded in:
+//   A' = sum_k hq_k f_k = (cs / 2) A, so that P = T2 A' + cb with T2 = 2 T,
+//   hq_k = h_k c_k cs / 2 for the unscaled products f'_k (h_k cs / 2 for a
+//   cached basis), aq = cs / 2 (the 1D model's A' for A = 1),
+//   c2 = Gamma^2 sigma^2 / 2 + ln 2, so that exp(-Gamma tau + c2) = 2 E.
 struct WarpConsts {
     Consts c;
-    double hp[10];   // h_k c_k: coefficients of the unscaled products f'_k
+    double hq[10];
+    double aq;
+    double c2;
 };
 
 // f'_k(cos thK, cos thmu, phi): f_k without its constant factor.
@@ -81,11 +88,13 @@ __device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi,
     f[9] = ck * sl2;
 }
 
-// Decay-time factor T = g(tau) and the Gaussian G = N(tau; 0, sigma).
-__device__ __forceinline__ void time_terms(const Consts& c, double tau, const MathTables* mt,
-                                           double* T, double* G) {
-    const double E = exp_fast(fma(-c.Gamma, tau, c.c_exp), mt);
-    const double Gx = exp_fast(-(tau * tau) * c.k_g, mt);  // exp(-tau^2 / (2 sigma^2))
+// Twice the decay-time factor, T2 = 2 g(tau), and Gx = exp(-tau^2 / (2 sigma^2))
+// (the Gaussian density is cG Gx).
+__device__ __forceinline__ void time_terms(const WarpConsts& wc, double tau, const MathTables* mt,
+                                           double* T2, double* Gx) {
+    const Consts& c = wc.c;
+    const double E2 = exp_fast(fma(-c.Gamma, tau, wc.c2), mt);
+    const double g = exp_fast(-(tau * tau) * c.k_g, mt);
     const double z = (c.Gs2 - tau) * c.k_z;
     const double x = fabs(z);
     const bool zneg = negative(z);
@@ -95,34 +104,70 @@ __device__ __forceinline__ void time_terms(const Consts& c, double tau, const Ma
         // resolution peak, outside the usual range): exact library erfcx
         X = zneg ? 0.0 : erfcx(x);
     }
-    const double hgx = 0.5 * Gx * X;
-    *T = zneg ? E - hgx : hgx;
-    *G = c.cG * Gx;
+    const double gx = g * X;
+    *T2 = zneg ? E2 - gx : gx;
+    *Gx = g;
 }
 
-// One event: accumulate w log P (and the adjoint sums).  For the 4D model f
-// holds either the unscaled products f'_k (CACHED = false, coefficients h_k c_k)
-// or the cached basis f_k itself (CACHED = true, coefficients h_k).
-template <int KIND, bool GRAD, bool CACHED>
+// P = m 2^e with m in [1, 2): *prod *= m and *esum += e, so that the log of the
+// product of a lane's P values is log(*prod) + *esum ln 2 (bit operations on
+// the integer pipe and one FP64 multiply per event instead of a log).  Zero,
+// subnormal, negative, infinite and NaN P give what the sum of logs gives:
+// -inf for +-0, the exact value for subnormals, +inf for +inf, NaN otherwise.
+__device__ __forceinline__ void log_mul(double P, double* prod, int* esum) {
+    const long long b = __double_as_longlong(P);
+    long long mb = (b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;
+    int e = (int)(b >> 52) - 1023;
+    if ((unsigned long long)(b - 0x0010000000000000ll) >= 0x7FE0000000000000ull) {
+        if (b > 0 && b < 0x0010000000000000ll) {
+            const int sh = __clzll(b) - 11;
+            mb = ((b << sh) & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;
+            e = -1022 - sh;
+        } else {
+            mb = (b << 1) == 0 ? 0ll : (b == 0x7FF0000000000000ll ? b : 0x7FF8000000000000ll);
+            e = 0;
+        }
+    }
+    *prod *= __longlong_as_double(mb);
+    *esum += e;
+}
+
+// log(prod) + esum ln 2
+__device__ __forceinline__ double log_of(double prod, int esum, const MathTables* mt) {
+    const double ed = (double)esum;
+    return fma(ed, fp64tab::kLn2Hi, fma(ed, fp64tab::kLn2Lo, log_fast(prod, mt)));
+}
+
+// One event: the log term (weighted: w log P added to acc[0]; unweighted: P
+// folded into the lane's product) and the adjoint sums.  For the 4D model f
+// holds either the unscaled products f'_k (CACHED = false) or the cached basis
+// f_k (CACHED = true); wc.hq carries the matching coefficients.
+// Accumulators (kD = 12 for 4D, 3 for 1D), with r = w / P and A' = (cs/2) A:
+//   acc[1] = sum r,  acc[2 + k] = sum r T2 f_k (4D) or acc[2] = sum r T2 (1D),
+//   acc[kD] = sum r A' tau T2,  acc[kD + 1] = sum r A' Gx,  acc[kD + 2] = sum r A' tau Gx;
+// the derivatives in Gamma, sigma and mu are linear in these (finalize).
+template <int KIND, bool GRAD, bool CACHED, bool WEIGHTED>
 __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt, double t, const double* f,
-                                      double w, double* acc) {
+                                      double w, double* acc, double* prod, int* esum) {
     const Consts& c = wc.c;
     const double tau = t - c.mu;
-    double T, G;
-    time_terms(c, tau, mt, &T, &G);
-    double A = 1.0;
+    double T2, Gx;
+    time_terms(wc, tau, mt, &T2, &Gx);
+    double Ap = wc.aq;
     if (KIND == IPA_MODEL_ANGTIME4D) {
-        const double* hk = CACHED ? c.h : wc.hp;
-        A = hk[0] * f[0];
+        Ap = wc.hq[0] * f[0];
 #pragma unroll
-        for (int k = 1; k < 10; ++k) A = fma(hk[k], f[k], A);
+        for (int k = 1; k < 10; ++k) Ap = fma(wc.hq[k], f[k], Ap);
     }
-    const double P = fma(c.cs * T, A, c.cb);
-    acc[0] = fma(w, log_fast(P, mt), acc[0]);
+    const double P = fma(T2, Ap, c.cb);
+    if (WEIGHTED)
+        acc[0] = fma(w, log_fast(P, mt), acc[0]);
+    else
+        log_mul(P, prod, esum);
     if (GRAD) {
-        const double r = w / P;
+        const double r = WEIGHTED ? w / P : 1.0 / P;
         acc[1] += r;
-        const double rT = r * T;
+        const double rT = r * T2;
         constexpr int kD = KIND == IPA_MODEL_ANGTIME4D ? 12 : 3;
         if (KIND == IPA_MODEL_ANGTIME4D) {
 #pragma unroll
@@ -130,13 +175,11 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
         } else {
             acc[2] += rT;
         }
-        const double rA = r * A;
-        const double dTG = fma(c.Gs2 - tau, T, -c.s2 * G);
-        const double dTs = fma(c.G2s, T, -fma(tau, c.inv_s, c.Gsig) * G);
-        const double dTm = fma(c.Gamma, T, -G);
-        acc[kD + 0] = fma(rA, dTG, acc[kD + 0]);
-        acc[kD + 1] = fma(rA, dTs, acc[kD + 1]);
-        acc[kD + 2] = fma(rA, dTm, acc[kD + 2]);
+        const double rA = r * Ap;
+        const double u = rA * tau;
+        acc[kD + 0] = fma(u, T2, acc[kD + 0]);
+        acc[kD + 1] = fma(rA, Gx, acc[kD + 1]);
+        acc[kD + 2] = fma(u, Gx, acc[kD + 2]);
     }
 }
 
@@ -165,8 +208,14 @@ __device__ __forceinline__ int find_segment(const int64_t* seg_tiles, int n_seg,
 }
 
 // Write NLL (and gradient) of one segment from its reduced accumulators.
-// For the 4D model acc[2 + k] holds sum r T f'_k (S_k = c_k times that) or,
-// with a cached basis, S_k itself.
+// With S_k = sum r T f_k and SH = sum_k h_k S_k = sum r T A (A = 1 in 1D), and
+// D_j = sum r A dT/dtheta_j where
+//   dT/dGamma = (Gamma sigma^2 - tau) T - sigma^2 G,
+//   dT/dsigma = Gamma^2 sigma T - (tau / sigma + Gamma sigma) G,
+//   dT/dmu    = Gamma T - G,   G = cG Gx,
+// the accumulators give cs D_Gamma = cs Gamma sigma^2 SH - Y1 - 2 sigma^2 cG Y2,
+// cs D_sigma = cs Gamma^2 sigma SH - 2 cG (Y3 / sigma + Gamma sigma Y2) and
+// cs D_mu = cs Gamma SH - 2 cG Y2 (Y1..Y3 = acc[kD..kD+2]).
 template <int KIND, bool GRAD, bool CACHED>
 __device__ void finalize(const Consts& c, const double* acc, int n_par, double* out) {
     out[0] = -acc[0];
@@ -178,13 +227,20 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
     if (KIND == IPA_MODEL_ANGTIME4D) {
         SH = 0.0;
         for (int k = 0; k < 10; ++k) {
-            S[k] = CACHED ? acc[2 + k] : kBasisScale[k] * acc[2 + k];
+            S[k] = (CACHED ? 0.5 : 0.5 * kBasisScale[k]) * acc[2 + k];
             SH = fma(c.h[k], S[k], SH);
         }
     } else {
-        SH = acc[2];
+        SH = 0.5 * acc[2];
     }
-    for (int j = 0; j < 3; ++j) out[1 + j] = c.cs * fma(c.dlnIT[j], SH, -acc[kD + j]);
+    const double csSH = c.cs * SH;
+    const double Y1 = acc[kD], Y2 = acc[kD + 1], Y3 = acc[kD + 2];
+    const double tcG = 2.0 * c.cG;
+    double csD[3];
+    csD[0] = fma(c.Gs2, csSH, -fma(tcG * c.s2, Y2, Y1));
+    csD[1] = fma(c.G2s, csSH, -tcG * fma(c.inv_s, Y3, c.Gsig * Y2));
+    csD[2] = fma(c.Gamma, csSH, -tcG * Y2);
+    for (int j = 0; j < 3; ++j) out[1 + j] = fma(c.dlnIT[j], csSH, -csD[j]);
     out[1 + IPA_FB] = fma(SH, c.inv_ITIO, -Q * c.inv_V);
     if (KIND == IPA_MODEL_ANGTIME4D) {
         for (int j = 0; j < 6; ++j) {
@@ -218,7 +274,7 @@ __device__ __forceinline__ void reduce_partials(const double* partials, int64_t 
 // its current segment's constants in dynamic shared memory.
 constexpr int kMaxWarps = 8;
 
-template <int KIND, bool GRAD, bool CACHED>
+template <int KIND, bool GRAD, bool CACHED, bool WEIGHTED>
 __global__ void __launch_bounds__(32 * kMaxWarps, 2)
 nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
            const int64_t* __restrict__ seg_end, const int64_t* __restrict__ seg_tiles, int n_seg,
@@ -276,7 +332,10 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                 double* dst = reinterpret_cast<double*>(&wc.c);
                 for (int i = lane; i < kConstsDoubles; i += 32) dst[i] = __ldg(src + i);
                 __syncwarp();
-                if (lane < 10) wc.hp[lane] = wc.c.h[lane] * kBasisScale[lane];
+                const double half_cs = 0.5 * wc.c.cs;
+                if (lane < 10) wc.hq[lane] = (CACHED ? wc.c.h[lane] : wc.c.h[lane] * kBasisScale[lane]) * half_cs;
+                if (lane == 10) wc.aq = half_cs;
+                if (lane == 11) wc.c2 = wc.c.c_exp + fp64tab::kLn2Hi;
                 __syncwarp();
                 cur = seg;
             }
@@ -284,13 +343,15 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             double acc[NA];
 #pragma unroll
             for (int a = 0; a < NA; ++a) acc[a] = 0.0;
+            double prod = 1.0;   // unweighted: product of mantissas of P ...
+            int esum = 0;        // ... and sum of exponents (log_mul)
 
             const int64_t base = ev0 + (tile - t0) * kTile + lane;
 #pragma unroll 1
             for (int i = 0; i < kPerLane; ++i) {
                 const int64_t e = base + 32 * i;
                 if (e < ev1) {
-                    const double w = cols.w ? __ldg(cols.w + e) : 1.0;
+                    const double w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
                     double f[10];
                     if (KIND == IPA_MODEL_ANGTIME4D) {
                         if (CACHED) {
@@ -300,9 +361,10 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                             basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
                         }
                     }
-                    event<KIND, GRAD, CACHED>(wc, &mt, __ldg(cols.t + e), f, w, acc);
+                    event<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, __ldg(cols.t + e), f, w, acc, &prod, &esum);
                 }
             }
+            if (!WEIGHTED) acc[0] = log_of(prod, esum, &mt);
             warp_tree<NA>(acc);
 
             // level 1: the warp that completes a group of kGroupTiles tiles
@@ -383,7 +445,7 @@ __global__ void seg_tiles_kernel(const int64_t* __restrict__ seg_begin, const in
     if (threadIdx.x == nt - 1) seg_tiles[n_seg] = run[nt - 1];
 }
 
-template <int KIND, bool GRAD, bool CACHED>
+template <int KIND, bool GRAD, bool CACHED, bool WEIGHTED>
 ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const int64_t* seg_end,
                     const int64_t* seg_tiles, int n_seg, const Consts* consts, Scratch* sc, double* out,
                     int n_par, cudaStream_t st, const LaunchCfg* force) {
@@ -400,8 +462,8 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
     int& per_sm = occ[dev & 63][W];
     if (per_sm == 0) {
         int v = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, nll_kernel<KIND, GRAD, CACHED>,
-                                                                      32 * W, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &v, nll_kernel<KIND, GRAD, CACHED, WEIGHTED>, 32 * W, smem);
         per_sm = e == cudaSuccess && v >= 1 ? v : 1;
     }
     const int64_t sms = sm_count();
@@ -415,7 +477,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
         grid = need < grid ? need : grid;
     }
     if (grid < 1) grid = 1;
-    nll_kernel<KIND, GRAD, CACHED><<<(unsigned)grid, 32 * W, smem, st>>>(
+    nll_kernel<KIND, GRAD, CACHED, WEIGHTED><<<(unsigned)grid, 32 * W, smem, st>>>(
         cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->gcount, sc->work,
         out, n_par, K);
     return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
@@ -429,18 +491,30 @@ ipa_status launch_seg_tiles(const int64_t* seg_begin, const int64_t* seg_end, co
     return cuda_fail(cudaGetLastError(), "segment tiling kernel launch");
 }
 
+// Kernel variant for a launch: model, gradient, cached basis, weights.
+template <int KIND, bool GRAD, bool CACHED>
+ipa_status launch_w(const Cols& cols, int64_t n, const int64_t* seg_begin, const int64_t* seg_end,
+                    const int64_t* seg_tiles, int n_seg, const Consts* consts, Scratch* sc, double* out,
+                    int n_par, cudaStream_t st, const LaunchCfg* cfg) {
+    if (cols.w)
+        return launch_t<KIND, GRAD, CACHED, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out,
+                                                  n_par, st, cfg);
+    return launch_t<KIND, GRAD, CACHED, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out,
+                                               n_par, st, cfg);
+}
+
 ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t st, const LaunchCfg* cfg) {
     const int P = m.n_par;
     if (m.kind == IPA_MODEL_TIME1D)
-        return grad ? launch_t<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
-                    : launch_t<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
+        return grad ? launch_w<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
+                    : launch_w<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
     if (cols.fk)
-        return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
-                    : launch_t<IPA_MODEL_ANGTIME4D, false, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
-    return grad ? launch_t<IPA_MODEL_ANGTIME4D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
-                : launch_t<IPA_MODEL_ANGTIME4D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
+        return grad ? launch_w<IPA_MODEL_ANGTIME4D, true, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
+                    : launch_w<IPA_MODEL_ANGTIME4D, false, true>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
+    return grad ? launch_w<IPA_MODEL_ANGTIME4D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
+                : launch_w<IPA_MODEL_ANGTIME4D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
 }
 
 // f_k = c_k f'_k for every event (the cached angular basis).
