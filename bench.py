@@ -47,20 +47,42 @@ TH4 = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3])
 METRIC = "NLL+grad Gevents/s"
 WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 
-# FP64 operations per event of the fused 4D NLL+gradient kernel, counted from the
-# formula as nll.cu evaluates it (event<4D, grad>: time_terms, basis_unscaled,
-# the amplitude sum, log, 1/P and the 15 accumulations).  FMA = 2 flops; each
-# function call counts its cost in DFMA issue slots measured live by
-# ipa_calibrate_fp64, times 2 flops.
-FORMULA_OPS_4D = {"fma": 32, "mul": 30, "add": 6,
-                  "exp_fast": 2, "erfcx_poly": 1, "sincos_fast": 1, "log_fast": 1, "sqrt": 1, "rcp": 1}
+# FP64 operations of the fused 4D NLL+gradient kernel, counted from the formula
+# as nll.cu evaluates it (FMA = 2 flops; each function call counts its cost in
+# DFMA issue slots measured live by ipa_calibrate_fp64, times 2 flops):
+#   every event: tau, 2E (exp), T2, the angular products f'_k (sincos, one
+#     sqrt), A' (10 terms), P, 1/P, sum r, r T2, S_k (10), r A', u, Y1..Y3;
+#     unweighted: one multiply into the lane's log product; weighted: w log P;
+#   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma):
+#     the Gaussian (exp), the erfcx argument and erfcx, g X;
+#   unweighted, once per lane and 512-event tile (16 events): the log of the
+#     product and its exponent term.
+OPS_EVENT_4D = {"fma": 27, "mul": 21, "add": 4, "exp_fast": 1, "sincos_fast": 1, "sqrt": 1, "rcp": 1}
+OPS_UNWEIGHTED = {"mul": 1}
+OPS_WEIGHTED = {"fma": 1, "mul": 1, "log_fast": 1}
+OPS_NEAR_PEAK = {"mul": 4, "add": 2, "exp_fast": 1, "erfcx_poly": 1}
+OPS_LANE_TILE = {"fma": 2, "log_fast": 1}
 
 
-def flops_per_event(cal: dict) -> float:
-    f = 2 * FORMULA_OPS_4D["fma"] + FORMULA_OPS_4D["mul"] + FORMULA_OPS_4D["add"]
-    for fn in ("exp_fast", "erfcx_poly", "sincos_fast", "log_fast", "sqrt", "rcp"):
-        f += FORMULA_OPS_4D[fn] * cal[fn] * 2.0
+def _flops(ops: dict, cal: dict) -> float:
+    f = 0.0
+    for k, v in ops.items():
+        f += v * (2.0 if k == "fma" else 1.0 if k in ("mul", "add") else 2.0 * cal[k])
     return f
+
+
+def near_peak_fraction(t, theta) -> float:
+    """Fraction of events whose decay time needs the Gaussian and erfcx."""
+    Gamma, sigma, mu = float(theta[0]), float(theta[1]), float(theta[2])
+    cut = mu + Gamma * sigma * sigma + 6.25 * math.sqrt(2.0) * sigma
+    return float(np.mean(np.asarray(t) <= cut))
+
+
+def flops_per_event(cal: dict, near: float, weighted: bool = False) -> float:
+    f = _flops(OPS_EVENT_4D, cal) + near * _flops(OPS_NEAR_PEAK, cal)
+    if weighted:
+        return f + _flops(OPS_WEIGHTED, cal)
+    return f + _flops(OPS_UNWEIGHTED, cal) + _flops(OPS_LANE_TILE, cal) / 16.0
 
 
 def kernel_traffic(n_events: int):
@@ -302,7 +324,8 @@ def main():
         torch.cuda.synchronize()
         cons.append(k_ev0.elapsed_time(k_ev1))
     kernel_ms = max(ms - statistics.median(cons), 1e-6)
-    fpe = flops_per_event(cal)
+    near = near_peak_fraction(cols_h["t"], TH4)
+    fpe = flops_per_event(cal, near)
     peak_dfma_derived = 2.0 * 152 * 2070e6          # DFMA/s: 2 per clock per SM x 152 SMs x 2070 MHz
     achieved = fpe * N_EVENTS / (kernel_ms * 1e-3) / 1e12
     peak = 2.0 * peak_dfma_derived / 1e12
@@ -351,7 +374,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "nll_kernel<4D, grad>", "kernel_ms": kernel_ms,
-                     "flops_per_event": fpe,
+                     "flops_per_event": fpe, "near_peak_fraction": near,
                      "peak_note": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops (derived); "
                                   f"DFMA loop measured {cal['dfma_per_s'] * 2e-12:.3f} TFLOP/s at "
                                   f"{cal['sm_mhz']:.0f} MHz, {cal['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM",
@@ -363,7 +386,9 @@ def main():
     line.update(extras)
     if "large" in line:
         lg = line["large"]
-        lg["roofline_frac"] = fpe * lg["events"] / (lg["nll_grad_ms"] * 1e-3) / 1e12 / peak
+        fpe_w = flops_per_event(cal, lg.pop("near_peak_fraction"), weighted=True)
+        lg["flops_per_event"] = fpe_w
+        lg["roofline_frac"] = fpe_w * lg["events"] / (lg["nll_grad_ms"] * 1e-3) / 1e12 / peak
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
         print(json.dumps(line))
@@ -594,7 +619,8 @@ def run_large(api, synth, torch, dev, m, theta, params) -> dict:
     e1.record()
     torch.cuda.synchronize()
     ms_c = e0.elapsed_time(e1) / reps
-    return {"events": n, "weighted": True, "nll_grad_ms": ms, "Gevents_per_s": n / (ms * 1e-3) / 1e9,
+    return {"events": n, "weighted": True, "near_peak_fraction": near_peak_fraction(cols["t"].cpu().numpy(), TH4),
+            "nll_grad_ms": ms, "Gevents_per_s": n / (ms * 1e-3) / 1e9,
             "nll_grad_ms_cached_basis": ms_c, "Gevents_per_s_cached_basis": n / (ms_c * 1e-3) / 1e9,
             "fit": {"wall_s": dt, "status": int(r["status"][0]), "iterations": int(r["iters"][0]),
                     "passes": npass, "Gevents_per_s": n * npass / dt / 1e9},

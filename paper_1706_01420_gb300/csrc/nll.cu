@@ -61,7 +61,13 @@ struct WarpConsts {
     double hq[10];
     double aq;
     double c2;
+    double tcut;     // t above it: z < -6.25, the Gaussian-erfcx term is below 1e-17 of T
 };
+
+// Decay-time events per compaction round of one lane (see nll_kernel).
+constexpr int kSub = 4;
+static_assert(kSub == 4, "a compaction round keeps four ballot masks");
+static_assert((IPA_TILE_EVENTS / 32) % kSub == 0, "events per lane must be a multiple of kSub");
 
 // f'_k(cos thK, cos thmu, phi): f_k without its constant factor.
 __device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi, const MathTables* mt,
@@ -88,12 +94,13 @@ __device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi,
     f[9] = ck * sl2;
 }
 
-// Twice the decay-time factor, T2 = 2 g(tau), and Gx = exp(-tau^2 / (2 sigma^2))
-// (the Gaussian density is cG Gx).
-__device__ __forceinline__ void time_terms(const WarpConsts& wc, double tau, const MathTables* mt,
-                                           double* T2, double* Gx) {
-    const Consts& c = wc.c;
-    const double E2 = exp_fast(fma(-c.Gamma, tau, wc.c2), mt);
+// The part of the decay-time factor that needs the Gaussian and erfcx, for an
+// event with t <= tcut (z >= -6.25 up to rounding): with g = exp(-tau^2 /
+// (2 sigma^2)) and X = erfcx(|z|), returns g X in .x and g in .y, the sign of
+// .y carrying z >= 0 (negative) or z < 0 (positive).  Then 2 g(tau) = 2E - gX
+// (z < 0) or gX (z >= 0).  Events with t > tcut have 2 g(tau) = 2E to 1e-17
+// relative and a Gaussian below 1e-17; they are given (0, +0).
+__device__ __forceinline__ double2 gauss_erfcx(const Consts& c, double tau, const MathTables* mt) {
     const double g = exp_fast(-(tau * tau) * c.k_g, mt);
     const double z = (c.Gs2 - tau) * c.k_z;
     const double x = fabs(z);
@@ -104,9 +111,33 @@ __device__ __forceinline__ void time_terms(const WarpConsts& wc, double tau, con
         // resolution peak, outside the usual range): exact library erfcx
         X = zneg ? 0.0 : erfcx(x);
     }
-    const double gx = g * X;
-    *T2 = zneg ? E2 - gx : gx;
-    *Gx = g;
+    return make_double2(g * X, zneg ? g : -g);
+}
+
+// t > c for any doubles with c not NaN (integer compare of order-preserving keys).
+__device__ __forceinline__ bool greater(double t, double c) {
+    const long long a = __double_as_longlong(t), b = __double_as_longlong(c);
+    const long long ka = a >= 0 ? a : (long long)(0x8000000000000000ull - (unsigned long long)a);
+    const long long kb = b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b);
+    return ka > kb;
+}
+
+// Position of the n-th (from 0) set bit of m; n < popc(m).
+__device__ __forceinline__ int nth_set(unsigned m, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const unsigned low = m & ((1u << w) - 1u);
+        const int cnt = __popc(low);
+        if (n >= cnt) {
+            n -= cnt;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
 }
 
 // P = m 2^e with m in [1, 2): *prod *= m and *esum += e, so that the log of the
@@ -138,21 +169,24 @@ __device__ __forceinline__ double log_of(double prod, int esum, const MathTables
     return fma(ed, fp64tab::kLn2Hi, fma(ed, fp64tab::kLn2Lo, log_fast(prod, mt)));
 }
 
-// One event: the log term (weighted: w log P added to acc[0]; unweighted: P
+// One event: the log term (w log P added to acc[0], or for w = 1 exactly, P
 // folded into the lane's product) and the adjoint sums.  For the 4D model f
 // holds either the unscaled products f'_k (CACHED = false) or the cached basis
-// f_k (CACHED = true); wc.hq carries the matching coefficients.
+// f_k (CACHED = true); wc.hq carries the matching coefficients; ge is the
+// event's gauss_erfcx value or (0, +0).
 // Accumulators (kD = 12 for 4D, 3 for 1D), with r = w / P and A' = (cs/2) A:
 //   acc[1] = sum r,  acc[2 + k] = sum r T2 f_k (4D) or acc[2] = sum r T2 (1D),
 //   acc[kD] = sum r A' tau T2,  acc[kD + 1] = sum r A' Gx,  acc[kD + 2] = sum r A' tau Gx;
 // the derivatives in Gamma, sigma and mu are linear in these (finalize).
 template <int KIND, bool GRAD, bool CACHED, bool WEIGHTED>
 __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt, double t, const double* f,
-                                      double w, double* acc, double* prod, int* esum) {
+                                      double w, double2 ge, double* acc, double* prod, int* esum) {
     const Consts& c = wc.c;
     const double tau = t - c.mu;
-    double T2, Gx;
-    time_terms(wc, tau, mt, &T2, &Gx);
+    const double E2 = exp_fast(fma(-c.Gamma, tau, wc.c2), mt);
+    const long long gb = __double_as_longlong(ge.y);
+    const double T2 = gb >= 0 ? E2 - ge.x : ge.x;
+    const double Gx = __longlong_as_double(gb & 0x7FFFFFFFFFFFFFFFll);
     double Ap = wc.aq;
     if (KIND == IPA_MODEL_ANGTIME4D) {
         Ap = wc.hq[0] * f[0];
@@ -160,7 +194,9 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
         for (int k = 1; k < 10; ++k) Ap = fma(wc.hq[k], f[k], Ap);
     }
     const double P = fma(T2, Ap, c.cb);
-    if (WEIGHTED)
+    // events of weight exactly 1 (all events without a weight column) join the
+    // lane's log product, so a column of ones gives the same bits as no column
+    if (WEIGHTED && __double_as_longlong(w) != 0x3FF0000000000000ll)
         acc[0] = fma(w, log_fast(P, mt), acc[0]);
     else
         log_mul(P, prod, esum);
@@ -286,7 +322,9 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
     __shared__ MathTables mt;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem)[wib];
+    const int n_wib = blockDim.x >> 5;
+    double2* const sbuf = reinterpret_cast<double2*>(dyn_smem) + wib * (kSub * 32);
+    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem + (size_t)n_wib * kSub * 32 * sizeof(double2))[wib];
 
     load_math_tables(&mt);
     __syncthreads();
@@ -336,6 +374,10 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                 if (lane < 10) wc.hq[lane] = (CACHED ? wc.c.h[lane] : wc.c.h[lane] * kBasisScale[lane]) * half_cs;
                 if (lane == 10) wc.aq = half_cs;
                 if (lane == 11) wc.c2 = wc.c.c_exp + fp64tab::kLn2Hi;
+                if (lane == 12) {
+                    const double tc = wc.c.mu + (wc.c.Gs2 + 6.25 / wc.c.k_z);
+                    wc.tcut = tc == tc ? tc : INFINITY;    // NaN constants: every event takes the full path
+                }
                 __syncwarp();
                 cur = seg;
             }
@@ -346,25 +388,63 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             double prod = 1.0;   // unweighted: product of mantissas of P ...
             int esum = 0;        // ... and sum of exponents (log_mul)
 
-            const int64_t base = ev0 + (tile - t0) * kTile + lane;
+            // Events are taken kSub per lane at a time (lane l: l + 32 i).  Those
+            // with t <= tcut need the Gaussian and erfcx (about a fifth of them);
+            // they are listed in a ballot per i and evaluated packed, 32 per pass,
+            // into the warp's buffer, so the FP64 pipe does not spend a full warp
+            // instruction on lanes that would discard the result.
+            const int64_t tbase = ev0 + (tile - t0) * kTile;
+            const unsigned below = (1u << lane) - 1u;
 #pragma unroll 1
-            for (int i = 0; i < kPerLane; ++i) {
-                const int64_t e = base + 32 * i;
-                if (e < ev1) {
-                    const double w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
-                    double f[10];
-                    if (KIND == IPA_MODEL_ANGTIME4D) {
-                        if (CACHED) {
+            for (int i0 = 0; i0 < kPerLane; i0 += kSub) {
+                unsigned m0, m1, m2, m3;
+                {
+                    unsigned mk[kSub];
 #pragma unroll
-                            for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
-                        } else {
-                            basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
-                        }
+                    for (int q = 0; q < kSub; ++q) {
+                        const int64_t e = tbase + lane + 32 * (i0 + q);
+                        const bool slow = e < ev1 && !greater(__ldg(cols.t + e), wc.tcut);
+                        mk[q] = __ballot_sync(0xffffffffu, slow);
                     }
-                    event<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, __ldg(cols.t + e), f, w, acc, &prod, &esum);
+                    m0 = mk[0];
+                    m1 = mk[1];
+                    m2 = mk[2];
+                    m3 = mk[3];
                 }
+                const int p1 = __popc(m0), p2 = p1 + __popc(m1), p3 = p2 + __popc(m2);
+                const int n_slow = p3 + __popc(m3);
+                for (int j = lane; j < n_slow; j += 32) {
+                    const int q = (j >= p1) + (j >= p2) + (j >= p3);
+                    const unsigned m = q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
+                    const int before = q == 0 ? 0 : (q == 1 ? p1 : (q == 2 ? p2 : p3));
+                    const int64_t e = tbase + nth_set(m, j - before) + 32 * (i0 + q);
+                    sbuf[j] = gauss_erfcx(wc.c, __ldg(cols.t + e) - wc.c.mu, &mt);
+                }
+                __syncwarp();
+#pragma unroll 1
+                for (int q = 0; q < kSub; ++q) {
+                    const int64_t e = tbase + lane + 32 * (i0 + q);
+                    if (e < ev1) {
+                        const unsigned m = q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
+                        const int before = q == 0 ? 0 : (q == 1 ? p1 : (q == 2 ? p2 : p3));
+                        const double2 ge = (m >> lane) & 1u ? sbuf[before + __popc(m & below)]
+                                                            : make_double2(0.0, 0.0);
+                        const double w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
+                        double f[10];
+                        if (KIND == IPA_MODEL_ANGTIME4D) {
+                            if (CACHED) {
+#pragma unroll
+                                for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
+                            } else {
+                                basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
+                            }
+                        }
+                        event<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, __ldg(cols.t + e), f, w, ge, acc, &prod, &esum);
+                    }
+                }
+                __syncwarp();
             }
-            if (!WEIGHTED) acc[0] = log_of(prod, esum, &mt);
+            acc[0] += log_of(prod, esum, &mt);
             warp_tree<NA>(acc);
 
             // level 1: the warp that completes a group of kGroupTiles tiles
@@ -454,7 +534,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
     const LaunchCfg cfg = force ? *force : launch_cfg(KIND, GRAD, CACHED, n_seg > 1, tiles);
     const int W = cfg.warps_per_block >= 1 && cfg.warps_per_block <= kMaxWarps ? cfg.warps_per_block : 1;
     const int K = cfg.tiles_per_take >= 1 ? cfg.tiles_per_take : 1;
-    const size_t smem = (size_t)W * sizeof(WarpConsts);
+    const size_t smem = (size_t)W * (sizeof(WarpConsts) + kSub * 32 * sizeof(double2));
     // resident blocks per SM for each block size (cached per device and variant)
     static int occ[64][kMaxWarps + 1] = {};
     int dev = 0;

@@ -176,3 +176,31 @@ def test_large_weighted_sampled(env):
                                 math.fsum(np.abs(logl)))
     del ev
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kind", ["1d", "4d"])
+def test_weight_column_of_ones_equals_no_column(env, kind):
+    """Events of weight exactly 1 take the unweighted path's log product, so a
+    weight column of ones gives the NLL and gradient of no column bit for bit
+    (the server stores ones for unweighted requests); other weights keep
+    w log P and still match the oracle."""
+    O, G, torch, api = env
+    n = 30001
+    if kind == "1d":
+        m, th, cols = api.model_1d(0.3, 15.0), TH1, {"t": synth.events_1d(n, 8)}
+    else:
+        m, th, cols = api.model_4d(0.0, 15.0), TH4, synth.events_4d(n, 8)
+    ev = G.to_dev(cols)
+    theta = torch.tensor(th, device="cuda")
+    plain = api.ipa_nll_grad(m, ev, theta).cpu().numpy()
+    ones = api.ipa_nll_grad(m, dict(ev, w=torch.ones(n, dtype=torch.float64, device="cuda")), theta).cpu().numpy()
+    assert np.array_equal(plain, ones)
+    # mixed: a third of the weights exactly 1, the rest Normal(1, 0.2)
+    w = synth.weights(n, 9)
+    w[::3] = 1.0
+    got = api.ipa_nll_grad(m, dict(ev, w=torch.tensor(w, device="cuda")), theta).cpu().numpy()
+    wc = dict(cols, w=w)
+    m_o = O.Model(kind, 0.3 if kind == "1d" else 0.0, 15.0)
+    f_ref, g_ref = O.nll_grad(m_o, wc, th)
+    logl, _ = O.nll_grad_terms(m_o, wc, th)
+    G.assert_nll_grad_close(got, f_ref, g_ref, G.grad_scale(O, m_o, wc, th), math.fsum(np.abs(logl)))
