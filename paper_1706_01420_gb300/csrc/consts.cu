@@ -1,16 +1,17 @@
 // Step a1 of the hot path: theta -> the Consts record read by every event
-// tile (see consts.cuh for the formulas): one warp per fit for a few fits,
-// one thread per fit for many.
+// tile (see consts.cuh for the formulas): one four-warp block per fit for a
+// few fits, one thread per fit for many.
 #include "consts.cuh"
 
 namespace ipa {
 
 namespace {
-// One warp per fit (few fits: latency).
-__global__ void consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg,
-                              Consts* __restrict__ out) {
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (s < n_seg) compute_consts_warp(m, theta + (size_t)s * m.n_par, out + s);
+// One block of four warps per fit (few fits: latency).
+__global__ void __launch_bounds__(128) consts_block_kernel(ModelDev m, const double* __restrict__ theta,
+                                                           Consts* __restrict__ out) {
+    __shared__ ConstsBlockScratch S;
+    const int s = blockIdx.x;
+    compute_consts_block(m, theta + (size_t)s * m.n_par, out + s, &S);
 }
 
 // One thread per fit (many fits: throughput).
@@ -28,9 +29,7 @@ ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Cons
         consts_thread_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
         return cuda_fail(cudaGetLastError(), "consts kernel launch");
     }
-    const int warps = 4;
-    const int grid = (n_seg + warps - 1) / warps;
-    consts_kernel<<<grid, 32 * warps, 0, st>>>(m, theta, n_seg, out);
+    consts_block_kernel<<<n_seg, 128, 0, st>>>(m, theta, out);
     return cuda_fail(cudaGetLastError(), "consts kernel launch");
 }
 

@@ -2,7 +2,7 @@
 // from theta once per call, so that theta can stay in device memory and calls
 // can be captured in CUDA graphs.  Two layouts share every arithmetic step
 // (so they give bit-identical records): one thread per fit when many fits are
-// evaluated at once, one warp per fit when latency matters.
+// evaluated at once, one four-warp block per fit when latency matters.
 //
 // Time part (Sec. 3, analytic normalisation): with F(tau) = [Phi(tau/sigma) -
 // g(tau)] / Gamma, dF/dtau = g, the normalisation is I_T = F(t_hi - mu) -
@@ -39,17 +39,26 @@ __device__ inline double gauss(double tau, double sigma) {
     return kInvSqrt2Pi / sigma * exp(-0.5 * x * x);
 }
 
-// F(tau) and its derivatives (Gamma, sigma, mu) at one edge of the range.
-__device__ inline void edge(double tau, double Gamma, double sigma, double* F, double* dF) {
-    const double g = conv_g(tau, Gamma, sigma);
-    const double G = gauss(tau, sigma);
-    const double Phi = 0.5 * erfc(-tau / (kSqrt2 * sigma));
+// Normal CDF Phi(tau / sigma).
+__device__ inline double edge_phi(double tau, double sigma) {
+    return 0.5 * erfc(-tau / (kSqrt2 * sigma));
+}
+
+// F(tau) and its derivatives (Gamma, sigma, mu) at one edge of the range from
+// g(tau), the Gaussian G(tau) and Phi(tau / sigma).
+__device__ inline void edge_combine(double tau, double Gamma, double sigma, double g, double G, double Phi,
+                                    double* F, double* dF) {
     const double dg_dG = (Gamma * sigma * sigma - tau) * g - sigma * sigma * G;
     const double dg_ds = Gamma * Gamma * sigma * g - (Gamma * sigma + tau / sigma) * G;
     *F = (Phi - g) / Gamma;
     dF[0] = -(*F + dg_dG) / Gamma;
     dF[1] = (-(tau / sigma) * G - dg_ds) / Gamma;
     dF[2] = -g;
+}
+
+// F(tau) and its derivatives (Gamma, sigma, mu) at one edge of the range.
+__device__ inline void edge(double tau, double Gamma, double sigma, double* F, double* dF) {
+    edge_combine(tau, Gamma, sigma, conv_g(tau, Gamma, sigma), gauss(tau, sigma), edge_phi(tau, sigma), F, dF);
 }
 
 
@@ -156,37 +165,84 @@ __device__ inline double time_envelope(const ModelDev& m, double Gamma, double s
     return fmin(1.0, exp(-Gamma * (m.t_lo - mu) + 0.5 * Gamma * Gamma * sigma * sigma));
 }
 
-// Scalars of the record from I_T pieces and the envelopes.
-__device__ inline void write_scalars(const ModelDev& m, const double* th, double Fh, double Fl,
-                                     const double* dIT, double MT, double MO, Consts* c) {
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
+// The divisions of the record that need only theta and the model:
+// k_z, k_g, cG, inv_s, cb, inv_V (numerator and denominator of item i).
+__device__ inline void scalar_quotient(int i, const ModelDev& m, const double* th, double* num, double* den) {
+    const double sigma = th[IPA_SIGMA], fb = th[IPA_FB];
     const bool four = m.kind == IPA_MODEL_ANGTIME4D;
-    const double IT = Fh - Fl;
     const double span = m.t_hi - m.t_lo;
-    const double IO = four ? 16.0 * kPi / 9.0 : 1.0;
     const double V = four ? span * 8.0 * kPi : span;
+    switch (i) {
+    case 0: *num = 1.0; *den = kSqrt2 * sigma; break;
+    case 1: *num = 1.0; *den = 2.0 * sigma * sigma; break;
+    case 2: *num = kInvSqrt2Pi; *den = sigma; break;
+    case 3: *num = 1.0; *den = sigma; break;
+    case 4: *num = fb; *den = V; break;
+    default: *num = 1.0; *den = V; break;
+    }
+}
+constexpr int kScalarQuotients = 6;
+
+// The divisions by I_T: dlnIT[0..2], cs, inv_ITIO (numerator, denominator).
+__device__ inline void it_quotient(int i, const ModelDev& m, const double* th, double IT, const double* dIT,
+                                   double* num, double* den) {
+    const double fb = th[IPA_FB];
+    const double IO = m.kind == IPA_MODEL_ANGTIME4D ? 16.0 * kPi / 9.0 : 1.0;
+    if (i < 3) {
+        *num = dIT[i];
+        *den = IT;
+    } else {
+        *num = i == 3 ? 1.0 - fb : 1.0;
+        *den = IT * IO;
+    }
+}
+constexpr int kItQuotients = 5;
+
+// Scalars of the record without a division, and the quotients q[] of
+// scalar_quotient (q[0..5]) and it_quotient (q[6..10]).
+__device__ inline void write_plain_scalars(const double* th, double IT, double MT, double MO, bool four,
+                                           const double* q, Consts* c) {
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
     c->Gamma = Gamma;
     c->sigma = sigma;
     c->mu = mu;
     c->fb = fb;
     c->c_exp = 0.5 * Gamma * Gamma * sigma * sigma;
     c->Gs2 = Gamma * sigma * sigma;
-    c->k_z = 1.0 / (kSqrt2 * sigma);
-    c->k_g = 1.0 / (2.0 * sigma * sigma);
-    c->cG = kInvSqrt2Pi / sigma;
+    c->k_z = q[0];
+    c->k_g = q[1];
+    c->cG = q[2];
     c->s2 = sigma * sigma;
     c->G2s = Gamma * Gamma * sigma;
     c->Gsig = Gamma * sigma;
-    c->inv_s = 1.0 / sigma;
+    c->inv_s = q[3];
     c->IT = IT;
-    for (int j = 0; j < 3; ++j) c->dlnIT[j] = dIT[j] / IT;
+    for (int j = 0; j < 3; ++j) c->dlnIT[j] = q[6 + j];
     c->MT = MT;
     c->MO = four ? MO : 1.0;
-    c->cs = (1.0 - fb) / (IT * IO);
-    c->cb = fb / V;
-    c->inv_ITIO = 1.0 / (IT * IO);
-    c->inv_V = 1.0 / V;
+    c->cs = q[9];
+    c->cb = q[4];
+    c->inv_ITIO = q[10];
+    c->inv_V = q[5];
     c->pad_ = 0.0;
+}
+
+// Scalars of the record from I_T pieces and the envelopes.
+__device__ inline void write_scalars(const ModelDev& m, const double* th, double Fh, double Fl,
+                                     const double* dIT, double MT, double MO, Consts* c) {
+    const double IT = Fh - Fl;
+    double q[kScalarQuotients + kItQuotients];
+    for (int i = 0; i < kScalarQuotients; ++i) {
+        double a, b;
+        scalar_quotient(i, m, th, &a, &b);
+        q[i] = a / b;
+    }
+    for (int i = 0; i < kItQuotients; ++i) {
+        double a, b;
+        it_quotient(i, m, th, IT, dIT, &a, &b);
+        q[kScalarQuotients + i] = a / b;
+    }
+    write_plain_scalars(th, IT, MT, MO, m.kind == IPA_MODEL_ANGTIME4D, q, c);
 }
 
 struct AmpParams {
@@ -244,58 +300,93 @@ __device__ inline void compute_consts_thread(const ModelDev& m, const double* th
     write_scalars(m, th, Fh, Fl, dIT, MT, MO, c);
 }
 
-// One warp computes one Consts record (a single fit, where latency matters):
-// the transcendental pieces (both range edges of I_T, the envelope, six
-// sine/cosine pairs, five square roots) go to different lanes and are shared
-// by shuffles; lane k < 10 then builds h_k and row k of dh.  Every lane of
-// the warp must call this.
-__device__ inline void compute_consts_warp(const ModelDev& m, const double* th, Consts* c) {
+// Exchange buffer of compute_consts_block.
+struct ConstsBlockScratch {
+    double g[2], G[2], Phi[2];     // edge 0: t_hi, edge 1: t_lo
+    double F[2], dF[2][3];
+    double MT, MO;
+    cdetail::AngPieces a;
+    double q[cdetail::kScalarQuotients + cdetail::kItQuotients];
+    double h[10], d[10][6];
+};
+
+// One block of 128 threads (four warps, one per SM sub-partition) computes one
+// Consts record: a single fit, where latency matters.  On this GPU a warp's
+// FP64 instruction occupies its sub-partition's FP64 unit for tens of cycles
+// whatever the active lanes, so the record's independent pieces go to
+// different warps and, within a warp, to lanes running the same code:
+//   phase 1  warp 0: g at both edges (exp, erfc); warp 1: Phi at both edges
+//            (erfc); warp 2: the Gaussian at both edges and the envelope M_T;
+//            warp 3: six sine/cosine pairs, five square roots and the six
+//            divisions that need theta only;
+//   phase 2  warp 0: F and its derivatives at both edges; warps 1-3: the ten
+//            rows of h and dh (at most two rows with divisions per warp);
+//   phase 3  warp 0: the five divisions by I_T; warp 1: M_Omega.
+// Every value comes from the same expression as in compute_consts_thread, so
+// both give the same bits (this file is compiled without FMA contraction).
+__device__ inline void compute_consts_block(const ModelDev& m, const double* th, Consts* c,
+                                            ConstsBlockScratch* S) {
     using namespace cdetail;
-    const int lane = threadIdx.x & 31;
-    const unsigned all = 0xffffffffu;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU];
     const bool four = m.kind == IPA_MODEL_ANGTIME4D;
     const AmpParams p = amp_params(m, th);
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-    if (lane < 2) {
-        double dF[3];
-        edge((lane == 0 ? m.t_hi : m.t_lo) - mu, Gamma, sigma, &v0, dF);
-        v1 = dF[0];
-        v2 = dF[1];
-        v3 = dF[2];
-    } else if (lane == 2) {
-        v0 = time_envelope(m, Gamma, sigma, mu);
-    } else if (four && lane >= 3 && lane <= 8) {
-        sincos(ang_arg(lane - 3, p.dpa, p.dpe, p.dS), &v0, &v1);
-    } else if (four && lane >= 9 && lane <= 13) {
-        v0 = sqrt(sqrt_arg(lane - 9, p.x0, p.xa, p.xe, p.F, p.s));
+    const double tau_e = (lane == 0 ? m.t_hi : m.t_lo) - mu;
+    if (w == 0) {
+        if (lane < 2) S->g[lane] = conv_g(tau_e, Gamma, sigma);
+    } else if (w == 1) {
+        if (lane < 2) S->Phi[lane] = edge_phi(tau_e, sigma);
+    } else if (w == 2) {
+        if (lane < 2) S->G[lane] = gauss(tau_e, sigma);
+        else if (lane == 2) S->MT = time_envelope(m, Gamma, sigma, mu);
+    } else if (w == 3) {
+        if (lane < 6) {
+            if (four) sincos(ang_arg(lane, p.dpa, p.dpe, p.dS), &S->a.sn[lane], &S->a.cs[lane]);
+        } else if (lane < 11) {
+            if (four) S->a.rt[lane - 6] = sqrt(sqrt_arg(lane - 6, p.x0, p.xa, p.xe, p.F, p.s));
+        } else if (lane < 11 + kScalarQuotients) {
+            double num, den;
+            scalar_quotient(lane - 11, m, th, &num, &den);
+            S->q[lane - 11] = num / den;
+        }
     }
-    const double Fh = __shfl_sync(all, v0, 0), Fl = __shfl_sync(all, v0, 1);
-    double dIT[3];
-    dIT[0] = __shfl_sync(all, v1, 0) - __shfl_sync(all, v1, 1);
-    dIT[1] = __shfl_sync(all, v2, 0) - __shfl_sync(all, v2, 1);
-    dIT[2] = __shfl_sync(all, v3, 0) - __shfl_sync(all, v3, 1);
-    const double MT = __shfl_sync(all, v0, 2);
-    AngPieces a;
-    for (int i = 0; i < 6; ++i) {
-        a.sn[i] = __shfl_sync(all, v0, 3 + i);
-        a.cs[i] = __shfl_sync(all, v1, 3 + i);
+    __syncthreads();
+    // rows of h: warp 1 -> 0, 3, 4; warp 2 -> 1, 5, 7; warp 3 -> 2, 6, 8, 9
+    int k = -1;
+    if (w == 0) {
+        if (lane < 2) edge_combine(tau_e, Gamma, sigma, S->g[lane], S->G[lane], S->Phi[lane], &S->F[lane], S->dF[lane]);
+    } else if (w == 1) {
+        k = lane == 0 ? 0 : (lane == 1 ? 3 : (lane == 2 ? 4 : -1));
+    } else if (w == 2) {
+        k = lane == 0 ? 1 : (lane == 1 ? 5 : (lane == 2 ? 7 : -1));
+    } else if (w == 3) {
+        k = lane == 0 ? 2 : (lane == 1 ? 6 : (lane == 2 ? 8 : (lane == 3 ? 9 : -1)));
     }
-    for (int i = 0; i < 5; ++i) a.rt[i] = __shfl_sync(all, v0, 9 + i);
-    double h = 0.0, d[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (four && lane < 10) h_row(lane, a, p.x0, p.xe, p.xa, p.s, p.F, &h, d);
-    if (!four) h = lane == 0 ? 1.0 : 0.0;
-    // M_Omega = sum_k |h_k| max|f_k| in k order (lane 0 ends with the total)
-    double mo = lane < 10 ? fabs(h) * basis_max(lane) : 0.0;
-    for (int k = 1; k < 10; ++k) {
-        const double v = __shfl_sync(all, mo, k);
-        if (lane == 0) mo += v;
+    if (k >= 0) {
+        double h = k == 0 ? 1.0 : 0.0, d[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (four) h_row(k, S->a, p.x0, p.xe, p.xa, p.s, p.F, &h, d);
+        S->h[k] = h;
+        for (int j = 0; j < 6; ++j) S->d[k][j] = d[j];
     }
-    if (lane < 10) {
-        c->h[lane] = h;
-        for (int j = 0; j < 6; ++j) c->dh[lane][j] = d[j];
+    __syncthreads();
+    const double IT = S->F[0] - S->F[1];
+    if (w == 0 && lane < kItQuotients) {
+        double dIT[3];
+        for (int j = 0; j < 3; ++j) dIT[j] = S->dF[0][j] - S->dF[1][j];
+        double num, den;
+        it_quotient(lane, m, th, IT, dIT, &num, &den);
+        S->q[kScalarQuotients + lane] = num / den;
+    } else if (w == 1 && lane == 0) {
+        double MO = 0.0;
+        if (four)
+            for (int r = 0; r < 10; ++r)
+                MO = r ? MO + fabs(S->h[r]) * basis_max(r) : fabs(S->h[r]) * basis_max(r);
+        S->MO = MO;
     }
-    if (lane == 0) write_scalars(m, th, Fh, Fl, dIT, MT, mo, c);
+    __syncthreads();
+    if (threadIdx.x == 0) write_plain_scalars(th, IT, S->MT, S->MO, four, S->q, c);
+    if (threadIdx.x < 60) c->dh[threadIdx.x / 6][threadIdx.x % 6] = S->d[threadIdx.x / 6][threadIdx.x % 6];
+    if (threadIdx.x >= 64 && threadIdx.x < 74) c->h[threadIdx.x - 64] = S->h[threadIdx.x - 64];
 }
 
 }  // namespace ipa

@@ -99,7 +99,6 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out);
 // consts.cu: theta (n_seg x n_par) -> Consts[n_seg]
 ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
                          cudaStream_t s);
-// compute_consts_warp (consts.cuh): one warp turns theta into a Consts record.
 
 // Launch geometry of the likelihood kernel (tune.cu picks it; no result
 // depends on it).

@@ -124,7 +124,8 @@ def test_deterministic_and_segment_equals_solo(env):
 
 def test_many_segments_equal_solo(env):
     """80 segments (the constants are then computed one thread per fit) against
-    solo calls (one warp per fit): bitwise equal."""
+    solo calls (one four-warp block per fit): bitwise equal, with every
+    parameter moved so that every row of the constants is exercised."""
     O, G, torch, api = env
     m = api.model_4d()
     rng = np.random.default_rng(8)
@@ -135,9 +136,16 @@ def test_many_segments_equal_solo(env):
     thetas = np.tile(TH4, (80, 1))
     thetas[:, 0] += rng.normal(0, 0.02, 80)
     thetas[:, 4] += rng.normal(0, 0.02, 80)
+    thetas[:, 1] += rng.normal(0, 0.003, 80)
+    thetas[:, 2] += rng.normal(0, 0.005, 80)
+    thetas[:, 3] += rng.normal(0, 0.01, 80)
+    thetas[:, 5] += rng.normal(0, 0.02, 80)
+    thetas[:, 6:8] += rng.normal(0, 0.3, (80, 2))
+    thetas[:, 8] += rng.normal(0, 0.01, 80)
+    thetas[:, 9] += rng.normal(0, 0.3, 80)
     seg = api.ipa_nll_grad_segmented(m, ev, torch.tensor(off, device="cuda"),
                                      torch.tensor(thetas, device="cuda")).cpu().numpy()
-    for s in (0, 1, 41, 79):
+    for s in (0, 1, 17, 41, 63, 79):
         a, b = off[s], off[s + 1]
         sub = {k: v[a:b].clone() for k, v in ev.items()}
         solo = api.ipa_nll_grad(m, sub, torch.tensor(thetas[s], device="cuda")).cpu().numpy()
