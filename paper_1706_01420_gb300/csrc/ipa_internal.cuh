@@ -10,7 +10,7 @@ namespace ipa {
 
 // Events per reduction tile.  Lane l of the warp that owns a tile adds events
 // l, l+32, ... of the tile in order; the warp reduces its lanes with a fixed
-// shuffle tree into one partial per tile, each group of kGroupTiles tiles is
+// butterfly into one partial per tile, each group of kGroupTiles tiles is
 // reduced (lane l holding tile l of the group) into one group partial, and a
 // segment's group partials are added in a fixed order.  This order depends
 // only on the segment's events, not on the launch geometry (block size, grid,

@@ -7,7 +7,7 @@
 // on the host.  Here one kernel does all of it.  Work is split into 512-event
 // tiles owned by single warps: lane l accumulates events l, l+32, ..., l+480
 // of its tile in order (coalesced 8-byte loads), the warp reduces its FP64
-// accumulators with a fixed shuffle tree and writes one partial per tile.
+// accumulators with a fixed butterfly and writes one partial per tile.
 // The warp that completes the last tile of a group of 32 tiles reduces the
 // group, and the warp that completes a segment's last group adds its group
 // partials in fixed order and writes the NLL and gradient.  No block-wide
@@ -219,14 +219,57 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
     }
 }
 
-// Fixed shuffle tree over the 32 lanes: at each level lane l adds lane l + half.
+// Butterfly reduction of NA accumulators over the 32 lanes of a warp (NA padded
+// to the power of two NP).  The first log2(NP) levels halve the values each
+// lane holds: at the level of lane bit j the lane keeps the half of its
+// values selected by that bit and adds the partner's copy of that half, so
+// every level costs NP / 2^(level+1) FP64 adds instead of NA.  The remaining
+// levels add the partner's value of the same accumulator.  Afterwards lane l
+// holds the full sum of accumulator acc_index<NA>(l) (two or more lanes hold
+// each, with identical bits: addition is commutative), in an order fixed by
+// the lane pairing.  NA = 15: 16 adds and 16 shuffles per warp instead of 75.
 template <int NA>
-__device__ __forceinline__ void warp_tree(double* acc) {
+struct Butterfly {
+    static constexpr int NP = NA <= 1 ? 1 : NA <= 2 ? 2 : NA <= 4 ? 4 : NA <= 8 ? 8 : 16;
+    static constexpr int SPLITS = NP == 1 ? 0 : NP == 2 ? 1 : NP == 4 ? 2 : NP == 8 ? 3 : 4;
+};
+
+template <int NA>
+__device__ __forceinline__ int acc_index(int lane) {
+    constexpr int S = Butterfly<NA>::SPLITS;
+    return (lane >> (5 - S)) & ((1 << S) - 1);
+}
+
+template <int NA>
+__device__ __forceinline__ double warp_butterfly(const double* acc, int lane) {
+    constexpr int NP = Butterfly<NA>::NP;
+    constexpr int S = Butterfly<NA>::SPLITS;
+    double v[NP];
 #pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
+    for (int a = 0; a < NP; ++a) v[a] = a < NA ? acc[a] : 0.0;
 #pragma unroll
-        for (int a = 0; a < NA; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], half);
+    for (int lev = 0; lev < S; ++lev) {
+        const int mask = 16 >> lev;
+        const int half = NP >> (lev + 1);
+        const bool upper = (lane & mask) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double keep = upper ? v[i + half] : v[i];
+            const double give = upper ? v[i] : v[i + half];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, give, mask);
+        }
     }
+#pragma unroll
+    for (int lev = S; lev < 5; ++lev) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16 >> lev);
+    return v[0];
+}
+
+// Every accumulator of a warp_butterfly result into acc[] of every lane.
+template <int NA>
+__device__ __forceinline__ void gather_butterfly(double v, double* acc) {
+    constexpr int S = Butterfly<NA>::SPLITS;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = __shfl_sync(0xffffffffu, v, a << (5 - S));
 }
 
 __device__ __forceinline__ int64_t clamp_off(int64_t v, int64_t n) {
@@ -291,10 +334,12 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
 
 // Reduce the tile partials of one group (lane l holds tile g0 + l) or, with
 // `stride` = kGroupTiles, the group partials of one segment (lane l adds groups
-// l, l+32, ... in that order), then the fixed shuffle tree.
+// l, l+32, ... in that order), then the butterfly; returns this lane's share
+// (accumulator acc_index<NA>(lane)).
 template <int NA>
-__device__ __forceinline__ void reduce_partials(const double* partials, int64_t first, int64_t count,
-                                                int64_t stride, int lane, double* acc) {
+__device__ __forceinline__ double reduce_partials(const double* partials, int64_t first, int64_t count,
+                                                  int64_t stride, int lane) {
+    double acc[NA];
 #pragma unroll
     for (int a = 0; a < NA; ++a) acc[a] = 0.0;
 #pragma unroll 4
@@ -303,7 +348,15 @@ __device__ __forceinline__ void reduce_partials(const double* partials, int64_t 
 #pragma unroll
         for (int a = 0; a < NA; ++a) acc[a] += __ldcg(p + a);
     }
-    warp_tree<NA>(acc);
+    return warp_butterfly<NA>(acc, lane);
+}
+
+// Lanes whose butterfly share is the first copy of an accumulator store it.
+template <int NA>
+__device__ __forceinline__ void store_share(double v, int lane, double* dst) {
+    constexpr int S = Butterfly<NA>::SPLITS;
+    const int a = acc_index<NA>(lane);
+    if ((lane & ((1 << (5 - S)) - 1)) == 0 && a < NA) dst[a] = v;
 }
 
 // Blocks of any whole number of warps (1..kMaxWarps); each warp keeps a copy of
@@ -445,35 +498,34 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                 __syncwarp();
             }
             acc[0] += log_of(prod, esum, &mt);
-            warp_tree<NA>(acc);
+            const double share = warp_butterfly<NA>(acc, lane);
 
             // level 1: the warp that completes a group of kGroupTiles tiles
             // reduces it into the partial slot of the group's first tile
             const int64_t g0 = t0 + ((tile - t0) / kGroupTiles) * kGroupTiles;
             const int64_t g1 = g0 + kGroupTiles < t1 ? g0 + kGroupTiles : t1;
             int last = 0;
-            if (lane == 0) {
-#pragma unroll
-                for (int a = 0; a < NA; ++a) partials[tile * NA + a] = acc[a];
-                __threadfence();
-                last = atomicAdd(gcount + g0, 1u) + 1u == (unsigned)(g1 - g0);
-            }
+            store_share<NA>(share, lane, partials + tile * NA);
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) last = atomicAdd(gcount + g0, 1u) + 1u == (unsigned)(g1 - g0);
             if (!__shfl_sync(0xffffffffu, last, 0)) continue;
             __threadfence();
-            reduce_partials<NA>(partials, g0, g1 - g0, 1, lane, acc);
+            const double gshare = reduce_partials<NA>(partials, g0, g1 - g0, 1, lane);
             // level 2: the warp that completes a segment's last group adds the
             // segment's group partials and writes its NLL and gradient
             const int64_t n_groups = (t1 - t0 + kGroupTiles - 1) / kGroupTiles;
+            __syncwarp();   // every lane has read the group's tile partials
+            store_share<NA>(gshare, lane, partials + g0 * NA);
+            __threadfence();
+            __syncwarp();
             if (lane == 0) {
                 gcount[g0] = 0u;
-#pragma unroll
-                for (int a = 0; a < NA; ++a) partials[g0 * NA + a] = acc[a];
-                __threadfence();
                 last = atomicAdd(counters + seg, 1u) + 1u == (unsigned)n_groups;
             }
             if (!__shfl_sync(0xffffffffu, last, 0)) continue;
             __threadfence();
-            reduce_partials<NA>(partials, t0, n_groups, kGroupTiles, lane, acc);
+            gather_butterfly<NA>(reduce_partials<NA>(partials, t0, n_groups, kGroupTiles, lane), acc);
             if (lane == 0) {
                 finalize<KIND, GRAD, CACHED>(wc.c, acc, n_par, out + (size_t)seg * out_stride);
                 counters[seg] = 0u;
