@@ -51,13 +51,14 @@ WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 # as nll.cu evaluates it (FMA = 2 flops; each function call counts its cost in
 # DFMA issue slots measured live by ipa_calibrate_fp64, times 2 flops):
 #   every event: tau, 2E (exp), T2, the angular products f'_k (sincos, one
-#     sqrt), A' (10 terms), P, 1/P, sum r, r T2, S_k (10), r A', u, Y1..Y3;
+#     sqrt), A' (10 terms), P, 1/P (an FP32 seed and one FP64 Newton step: 2
+#     FMA), sum r, r T2, S_k (10), r A', u, Y1..Y3;
 #     unweighted: one multiply into the lane's log product; weighted: w log P;
 #   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma):
 #     the Gaussian (exp), the erfcx argument and erfcx, g X;
 #   unweighted, once per lane and 512-event tile (16 events): the log of the
 #     product and its exponent term.
-OPS_EVENT_4D = {"fma": 27, "mul": 21, "add": 4, "exp_fast": 1, "sincos_fast": 1, "sqrt": 1, "rcp": 1}
+OPS_EVENT_4D = {"fma": 29, "mul": 21, "add": 4, "exp_fast": 1, "sincos_fast": 1, "sqrt": 1}
 OPS_UNWEIGHTED = {"mul": 1}
 OPS_WEIGHTED = {"fma": 1, "mul": 1, "log_fast": 1}
 OPS_NEAR_PEAK = {"mul": 4, "add": 2, "exp_fast": 1, "erfcx_poly": 1}

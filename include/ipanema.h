@@ -304,6 +304,22 @@ ipa_status ipa_launch_config_set(const ipa_model* model, int64_t n_events, int32
  * [9..12] cost of the library's own table-driven exp, log, sincos and erfcx. */
 ipa_status ipa_calibrate_fp64(double* results, void* stream);
 
+/* The library's own FP64 elementary functions, evaluated elementwise: test
+ * support with no counterpart in the paper (the likelihood kernel calls these
+ * functions; their accuracy is tested against the CPU's libm).
+ *   IPA_MATH_EXP    table-driven exp (library exp above 709)
+ *   IPA_MATH_LOG    table-driven log (library log for zero, negative,
+ *                   subnormal, infinite and NaN arguments)
+ *   IPA_MATH_SIN,
+ *   IPA_MATH_COS    table-driven sincos (library sincos for |x| >= 1e5)
+ *   IPA_MATH_ERFCX  piecewise polynomial on [0, 6.25], library erfcx above
+ *   IPA_MATH_RCP    1/x from an FP32 seed and one FP64 Newton step
+ * x_dev, y_dev: device arrays of n doubles (caller-owned).  IPA_ERR_ARG for an
+ * unknown fn or NULL arrays with n > 0.  Asynchronous on `stream`. */
+enum { IPA_MATH_EXP = 0, IPA_MATH_LOG = 1, IPA_MATH_SIN = 2, IPA_MATH_COS = 3, IPA_MATH_ERFCX = 4,
+       IPA_MATH_RCP = 5 };
+ipa_status ipa_math_eval(int32_t fn, const double* x_dev, double* y_dev, int64_t n, void* stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* ipa_last_error(void);
 

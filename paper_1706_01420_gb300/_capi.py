@@ -17,6 +17,7 @@ IPA_MODEL_TIME1D, IPA_MODEL_ANGTIME4D = 1, 2
 IPA_GAMMA, IPA_SIGMA, IPA_MU, IPA_FB, IPA_A0SQ, IPA_APESQ, IPA_DPA, IPA_DPE, IPA_FS, IPA_DS = range(10)
 IPA_NPAR_1D, IPA_NPAR_4D, IPA_MAX_PAR = 4, 10, 16
 IPA_NOALLOC_MAX_EVENTS = 8388608
+IPA_MATH_EXP, IPA_MATH_LOG, IPA_MATH_SIN, IPA_MATH_COS, IPA_MATH_ERFCX, IPA_MATH_RCP = range(6)
 IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)
 STATUS_NAMES = {0: "IPA_OK", -1: "IPA_ERR_ARG", -2: "IPA_ERR_OOM", -3: "IPA_ERR_CUDA",
                 -4: "IPA_ERR_TIMEOUT", -5: "IPA_ERR_BUSY", 1: "IPA_PENDING"}
@@ -74,6 +75,7 @@ PROTOTYPES = {
     "ipa_launch_config_set": (c_int32, [POINTER(ipa_model), c_int64, c_int32, c_int32, c_int32,
                                         POINTER(ipa_launch_config)]),
     "ipa_calibrate_fp64": (c_int32, [POINTER(c_double), c_void_p]),
+    "ipa_math_eval": (c_int32, [c_int32, c_void_p, c_void_p, c_int64, c_void_p]),
     "ipa_last_error": (c_char_p, []),
     "ipa_version": (c_char_p, []),
 }

@@ -294,5 +294,13 @@ def ipa_calibrate_fp64(stream=None) -> dict:
     return dict(zip(names, list(r)))
 
 
+def ipa_math_eval(fn: int, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """The library's own FP64 function `fn` (C.IPA_MATH_*) elementwise on a CUDA tensor."""
+    y = torch.empty_like(x)
+    _check(_lib().ipa_math_eval(int(fn), _ptr(x, name="x"), _ptr(y, name="y"), x.numel(), _stream(stream)),
+           "ipa_math_eval")
+    return y
+
+
 def ipa_version() -> str:
     return _lib().ipa_version().decode()

@@ -156,3 +156,42 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     results[8] = cpb[0] / sec[0] * 1e-6;
     return IPA_OK;
 }
+
+namespace ipa {
+namespace {
+
+// The library's own FP64 functions, one element per thread.
+__global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    __shared__ MathTables mt;
+    load_math_tables(&mt);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        double r;
+        switch (fn) {
+        case IPA_MATH_EXP: r = exp_fast(v, &mt); break;
+        case IPA_MATH_LOG: r = log_fast(v, &mt); break;
+        case IPA_MATH_SIN: { double s, c; sincos_fast(v, &mt, &s, &c); r = s; break; }
+        case IPA_MATH_COS: { double s, c; sincos_fast(v, &mt, &s, &c); r = c; break; }
+        case IPA_MATH_ERFCX: r = erfcx_fast(v, &mt); break;
+        default: r = rcp_newton(v); break;
+        }
+        y[i] = r;
+    }
+}
+
+}  // namespace
+}  // namespace ipa
+
+extern "C" ipa_status ipa_math_eval(int32_t fn, const double* x_dev, double* y_dev, int64_t n, void* stream) {
+    using namespace ipa;
+    if (fn < IPA_MATH_EXP || fn > IPA_MATH_RCP || n < 0 || (n > 0 && (!x_dev || !y_dev))) {
+        set_error("ipa_math_eval: bad arguments");
+        return IPA_ERR_ARG;
+    }
+    if (n == 0) return IPA_OK;
+    const int64_t blocks = (n + 255) / 256;
+    const int grid = (int)(blocks < 4096 ? blocks : 4096);
+    math_eval_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(fn, x_dev, y_dev, n);
+    return cuda_fail(cudaGetLastError(), "math eval kernel launch");
+}

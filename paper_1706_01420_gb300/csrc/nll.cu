@@ -201,7 +201,9 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
     else
         log_mul(P, prod, esum);
     if (GRAD) {
-        const double r = WEIGHTED ? w / P : 1.0 / P;
+        // r = w / P feeds only the adjoint sums; its ~6e-14 relative error
+        // (rcp_newton) is far inside the gradient's tolerance
+        const double r = WEIGHTED ? w * rcp_newton(P) : rcp_newton(P);
         acc[1] += r;
         const double rT = r * T2;
         constexpr int kD = KIND == IPA_MODEL_ANGTIME4D ? 12 : 3;
@@ -296,8 +298,10 @@ __device__ __forceinline__ int find_segment(const int64_t* seg_tiles, int n_seg,
 // cs D_sigma = cs Gamma^2 sigma SH - 2 cG (Y3 / sigma + Gamma sigma Y2) and
 // cs D_mu = cs Gamma SH - 2 cG Y2 (Y1..Y3 = acc[kD..kD+2]).
 template <int KIND, bool GRAD, bool CACHED>
-__device__ void finalize(const Consts& c, const double* acc, int n_par, double* out) {
-    out[0] = -acc[0];
+__device__ void finalize(const Consts& c, const double* acc, int n_par, double* out, int lane) {
+    // every lane holds acc; lane j writes component j (0: the NLL, 1 + j: the
+    // derivative in parameter j), computing only what that component needs
+    if (lane == 0) out[0] = -acc[0];
     if (!GRAD) return;
     const double Q = acc[1];
     constexpr int kD = KIND == IPA_MODEL_ANGTIME4D ? 12 : 3;
@@ -315,20 +319,21 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
     const double csSH = c.cs * SH;
     const double Y1 = acc[kD], Y2 = acc[kD + 1], Y3 = acc[kD + 2];
     const double tcG = 2.0 * c.cG;
-    double csD[3];
-    csD[0] = fma(c.Gs2, csSH, -fma(tcG * c.s2, Y2, Y1));
-    csD[1] = fma(c.G2s, csSH, -tcG * fma(c.inv_s, Y3, c.Gsig * Y2));
-    csD[2] = fma(c.Gamma, csSH, -tcG * Y2);
-    for (int j = 0; j < 3; ++j) out[1 + j] = fma(c.dlnIT[j], csSH, -csD[j]);
-    out[1 + IPA_FB] = fma(SH, c.inv_ITIO, -Q * c.inv_V);
-    if (KIND == IPA_MODEL_ANGTIME4D) {
-        for (int j = 0; j < 6; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 10; ++k) s = fma(c.dh[k][j], S[k], s);
-            out[1 + IPA_A0SQ + j] = -c.cs * s;
-        }
+    if (lane < 3) {
+        double csD;
+        if (lane == 0) csD = fma(c.Gs2, csSH, -fma(tcG * c.s2, Y2, Y1));
+        else if (lane == 1) csD = fma(c.G2s, csSH, -tcG * fma(c.inv_s, Y3, c.Gsig * Y2));
+        else csD = fma(c.Gamma, csSH, -tcG * Y2);
+        out[1 + lane] = fma(c.dlnIT[lane], csSH, -csD);
+    } else if (lane == IPA_FB) {
+        out[1 + IPA_FB] = fma(SH, c.inv_ITIO, -Q * c.inv_V);
+    } else if (KIND == IPA_MODEL_ANGTIME4D && lane < IPA_NPAR_4D) {
+        const int j = lane - IPA_A0SQ;
+        double s = 0.0;
+        for (int k = 0; k < 10; ++k) s = fma(c.dh[k][j], S[k], s);
+        out[1 + lane] = -c.cs * s;
     }
-    for (int j = (KIND == IPA_MODEL_ANGTIME4D ? IPA_NPAR_4D : IPA_NPAR_1D); j < n_par; ++j)
+    for (int j = (KIND == IPA_MODEL_ANGTIME4D ? IPA_NPAR_4D : IPA_NPAR_1D) + lane; j < n_par; j += 32)
         out[1 + j] = 0.0;
 }
 
@@ -526,10 +531,8 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             if (!__shfl_sync(0xffffffffu, last, 0)) continue;
             __threadfence();
             gather_butterfly<NA>(reduce_partials<NA>(partials, t0, n_groups, kGroupTiles, lane), acc);
-            if (lane == 0) {
-                finalize<KIND, GRAD, CACHED>(wc.c, acc, n_par, out + (size_t)seg * out_stride);
-                counters[seg] = 0u;
-            }
+            finalize<KIND, GRAD, CACHED>(wc.c, acc, n_par, out + (size_t)seg * out_stride, lane);
+            if (lane == 0) counters[seg] = 0u;
         }
     }
     if (lane == 0) {
