@@ -48,21 +48,25 @@ METRIC = "NLL+grad Gevents/s"
 WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 
 # FP64 operations of the fused 4D NLL+gradient kernel, counted from the formula
-# as nll.cu evaluates it (FMA = 2 flops; each function call counts its cost in
-# DFMA issue slots measured live by ipa_calibrate_fp64, times 2 flops):
-#   every event: tau, 2E (exp), T2, the angular products f'_k (sincos, one
+# as nll.cu evaluates it (FMA = 2 flops; each FP64 function call counts its
+# cost in DFMA issue slots measured live by ipa_calibrate_fp64, times 2 flops).
+# exp and sin/cos run on the integer pipe (int_math.cuh) and count no FP64
+# operation; only their arguments do:
+#   every event: tau, the exponent of 2E, T2, the angular products f'_k (one
 #     sqrt), A' (10 terms), P, 1/P (an FP32 seed and one FP64 Newton step: 2
 #     FMA), sum r, r T2, S_k (10), r A', u, Y1..Y3;
 #     unweighted: one multiply into the lane's log product; weighted: w log P;
 #   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma):
-#     the Gaussian (exp), the erfcx argument and erfcx, g X;
+#     the Gaussian's exponent, the erfcx argument and erfcx, g X;
 #   unweighted, once per lane and 512-event tile (16 events): the log of the
 #     product and its exponent term.
-OPS_EVENT_4D = {"fma": 29, "mul": 21, "add": 4, "exp_fast": 1, "sincos_fast": 1, "sqrt": 1}
+OPS_EVENT_4D = {"fma": 29, "mul": 21, "add": 4, "sqrt": 1}
 OPS_UNWEIGHTED = {"mul": 1}
 OPS_WEIGHTED = {"fma": 1, "mul": 1, "log_fast": 1}
-OPS_NEAR_PEAK = {"mul": 4, "add": 2, "exp_fast": 1, "erfcx_poly": 1}
+OPS_NEAR_PEAK = {"mul": 4, "add": 2, "erfcx_poly": 1}
 OPS_LANE_TILE = {"fma": 2, "log_fast": 1}
+# integer-pipe calls per event (reported with their stand-alone time, not counted)
+INT_CALLS_EVENT = {"exp_int": 1, "sincos_int": 1}
 
 
 def _flops(ops: dict, cal: dict) -> float:
@@ -345,6 +349,7 @@ def main():
     peak_dfma_derived = 2.0 * 152 * 2070e6          # DFMA/s: 2 per clock per SM x 152 SMs x 2070 MHz
     achieved = fpe * N_EVENTS / (kernel_ms * 1e-3) / 1e12
     peak = 2.0 * peak_dfma_derived / 1e12
+    ops_achieved = spe * N_EVENTS / (kernel_ms * 1e-3) / 1e9
     traffic = kernel_traffic(N_EVENTS)
 
     # e2e: pinned host columns -> device, call, result -> host, every step
@@ -387,28 +392,31 @@ def main():
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "Gevents/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 88,
                 "ms_per_step": e2e_ms},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": ops_achieved, "peak": peak_dfma_derived / 1e9,
+                     "unit": "G FP64 op/s", "frac": ops_achieved * 1e9 / peak_dfma_derived, "traffic": traffic,
                      "kernel": "nll_kernel<4D, grad>", "kernel_ms": kernel_ms,
-                     "flops_per_event": fpe, "near_peak_fraction": near,
-                     "fp64_issue": {"slots_per_event": spe, "unit": "G FP64 ops/s",
-                                    "achieved": spe * N_EVENTS / (kernel_ms * 1e-3) / 1e9,
-                                    "peak": peak_dfma_derived / 1e9,
-                                    "frac": spe * N_EVENTS / (kernel_ms * 1e-3) / peak_dfma_derived},
-                     "peak_note": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops (derived); "
-                                  f"DFMA loop measured {cal['dfma_per_s'] * 2e-12:.3f} TFLOP/s at "
-                                  f"{cal['sm_mhz']:.0f} MHz, {cal['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM",
+                     "fp64_ops_per_event": spe, "near_peak_fraction": near,
+                     "peak_note": "FP64 pipe: 2 operations/clk/SM x 152 SMs x 2070 MHz (derived); DFMA loop "
+                                  f"measured {cal['dfma_per_s'] * 1e-9:.0f} G/s at {cal['sm_mhz']:.0f} MHz, "
+                                  f"{cal['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM",
+                     "flops": {"per_event": fpe, "achieved_tflops": achieved, "peak_tflops": peak,
+                               "frac": achieved / peak},
                      "fp64_costs_dfma_slots": {k: round(cal[k], 2) for k in
                                                ("exp_fast", "erfcx_poly", "sincos_fast", "log_fast", "sqrt",
-                                                "rcp", "exp", "erfc", "log", "sincos")}},
+                                                "rcp", "exp", "erfc", "log", "sincos")},
+                     "int_pipe_calls_per_event": {"exp_int": 1.0 + near, "sincos_int": 1.0},
+                     "int_pipe_time_alone_dfma_slots": {k: round(cal[k], 2) for k in ("exp_int", "sincos_int")}},
         "wall_s_timed_region": wall,
     }
     line.update(extras)
     if "large" in line:
         lg = line["large"]
-        fpe_w = flops_per_event(cal, lg.pop("near_peak_fraction"), weighted=True)
-        lg["flops_per_event"] = fpe_w
-        lg["roofline_frac"] = fpe_w * lg["events"] / (lg["nll_grad_ms"] * 1e-3) / 1e12 / peak
+        near_l = lg.pop("near_peak_fraction")
+        spe_w = slots_per_event(cal, near_l, weighted=True)
+        lg["fp64_ops_per_event"] = spe_w
+        lg["roofline_frac"] = spe_w * lg["events"] / (lg["nll_grad_ms"] * 1e-3) / peak_dfma_derived
+        lg["flops_frac"] = flops_per_event(cal, near_l, weighted=True) * lg["events"] / (
+            lg["nll_grad_ms"] * 1e-3) / 1e12 / peak
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
         print(json.dumps(line))

@@ -298,10 +298,13 @@ ipa_status ipa_launch_config_set(const ipa_model* model, int64_t n_events, int32
                                  int32_t cached, const ipa_launch_config* cfg);
 
 /* FP64 roofline calibration on the current device (blocking, ~1 s).
- * results (host, 13 doubles): [0] DFMA per clock per SM, [1] DFMA per second
+ * results (host, 15 doubles): [0] DFMA per clock per SM, [1] DFMA per second
  * for the whole GPU, [2..7] cost of one CUDA exp, erfc, log, sincos, sqrt and
  * reciprocal in DFMA issue slots, [8] SM clock during the DFMA run [MHz],
- * [9..12] cost of the library's own table-driven exp, log, sincos and erfcx. */
+ * [9..12] cost of the library's own table-driven exp, log, sincos and erfcx,
+ * [13..14] time of the library's integer-pipe exp and sincos run alone, in
+ * DFMA slots (they use no FP64 instruction; in the likelihood kernel they
+ * overlap the FP64 work). */
 ipa_status ipa_calibrate_fp64(double* results, void* stream);
 
 /* The library's own FP64 elementary functions, evaluated elementwise: test

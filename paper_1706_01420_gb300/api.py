@@ -287,10 +287,10 @@ def ipa_launch_config_set(model: C.ipa_model, n_events: int, cfg: dict, n_seg: i
 
 def ipa_calibrate_fp64(stream=None) -> dict:
     """DFMA rate and FP64 math-function costs of the current GPU (see the header)."""
-    r = (ctypes.c_double * 13)()
+    r = (ctypes.c_double * 15)()
     _check(_lib().ipa_calibrate_fp64(r, _stream(stream)), "ipa_calibrate_fp64")
     names = ["dfma_per_clk_per_sm", "dfma_per_s", "exp", "erfc", "log", "sincos", "sqrt", "rcp", "sm_mhz",
-             "exp_fast", "log_fast", "sincos_fast", "erfcx_poly"]
+             "exp_fast", "log_fast", "sincos_fast", "erfcx_poly", "exp_int", "sincos_int"]
     return dict(zip(names, list(r)))
 
 

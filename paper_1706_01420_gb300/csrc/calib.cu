@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "fp64_math.cuh"
+#include "int_math.cuh"
 #include "ipa_internal.cuh"
 
 namespace ipa {
@@ -53,6 +54,14 @@ calib_kernel(const double* __restrict__ in, double* __restrict__ out, int iters,
                 x[k] = s + c;
             }
             if (OP == 10) x[k] = erfcx_poly(x[k], &mt) - 0.25;  // stays in [0, 1]
+            // the integer-pipe functions (int_math.cuh): their time alone, in DFMA
+            // slots (in the likelihood kernel it overlaps the FP64 work)
+            if (OP == 11) x[k] = exp_int(x[k], &mt) * 1e-3;
+            if (OP == 12) {
+                double s, c;
+                sincos_int(x[k], &mt, &s, &c);
+                x[k] = s + c;
+            }
         }
     }
     const long long c1 = clock64();
@@ -95,11 +104,12 @@ ipa_status run_one(const double* in, double* out, long long* cyc, int blocks, in
 }  // namespace
 }  // namespace ipa
 
-// results (host, 13 doubles):
+// results (host, 15 doubles):
 //   [0] DFMA per clock per SM, [1] DFMA per second (whole GPU),
 //   [2..7] cost in DFMA slots of the library exp, erfc, log, sincos, sqrt, 1/x,
 //   [8] SM clock during the DFMA run [MHz],
-//   [9..12] cost of this library's exp_fast, log_fast, sincos_fast, erfcx_poly.
+//   [9..12] cost of this library's exp_fast, log_fast, sincos_fast, erfcx_poly,
+//   [13..14] time of exp_int and sincos_int alone, in DFMA slots.
 extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     using namespace ipa;
     if (!results) {
@@ -124,8 +134,8 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
         return st;
     }
     cudaMemsetAsync(in, 0, sizeof(double) * n, s);
-    double sec[11], cpb[11];
-    const int iters[11] = {4096, 256, 128, 256, 256, 512, 512, 256, 256, 256, 256};
+    double sec[13], cpb[13];
+    const int iters[13] = {4096, 256, 128, 256, 256, 512, 512, 256, 256, 256, 256, 256, 256};
     st = run_one<0>(in, out, cyc, blocks, iters[0], s, &sec[0], &cpb[0]);
     if (st == IPA_OK) st = run_one<1>(in, out, cyc, blocks, iters[1], s, &sec[1], &cpb[1]);
     if (st == IPA_OK) st = run_one<2>(in, out, cyc, blocks, iters[2], s, &sec[2], &cpb[2]);
@@ -137,6 +147,8 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     if (st == IPA_OK) st = run_one<8>(in, out, cyc, blocks, iters[8], s, &sec[8], &cpb[8]);
     if (st == IPA_OK) st = run_one<9>(in, out, cyc, blocks, iters[9], s, &sec[9], &cpb[9]);
     if (st == IPA_OK) st = run_one<10>(in, out, cyc, blocks, iters[10], s, &sec[10], &cpb[10]);
+    if (st == IPA_OK) st = run_one<11>(in, out, cyc, blocks, iters[11], s, &sec[11], &cpb[11]);
+    if (st == IPA_OK) st = run_one<12>(in, out, cyc, blocks, iters[12], s, &sec[12], &cpb[12]);
     cudaFree(in);
     cudaFree(out);
     cudaFree(cyc);
@@ -147,8 +159,8 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     results[1] = ops_per_sm * sms / sec[0];
     const double dfma_time_per_op = sec[0] / (ops_per_sm * sms);
     // each loop body adds one FP64 operation besides the call, except erfc
-    const double extra[11] = {0.0, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
-    for (int f = 1; f < 11; ++f) {
+    const double extra[13] = {0.0, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0};
+    for (int f = 1; f < 13; ++f) {
         const double calls = (double)blocks * kCalThreads * iters[f] * 8.0;
         const double cost = (sec[f] / calls) / dfma_time_per_op - extra[f];
         results[f < 7 ? 1 + f : 2 + f] = cost;
@@ -169,10 +181,10 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
         const double v = x[i];
         double r;
         switch (fn) {
-        case IPA_MATH_EXP: r = exp_fast(v, &mt); break;
+        case IPA_MATH_EXP: r = exp_int(v, &mt); break;
         case IPA_MATH_LOG: r = log_fast(v, &mt); break;
-        case IPA_MATH_SIN: { double s, c; sincos_fast(v, &mt, &s, &c); r = s; break; }
-        case IPA_MATH_COS: { double s, c; sincos_fast(v, &mt, &s, &c); r = c; break; }
+        case IPA_MATH_SIN: { double s, c; sincos_int(v, &mt, &s, &c); r = s; break; }
+        case IPA_MATH_COS: { double s, c; sincos_int(v, &mt, &s, &c); r = c; break; }
         case IPA_MATH_ERFCX: r = erfcx_fast(v, &mt); break;
         default: r = rcp_newton(v); break;
         }

@@ -35,6 +35,8 @@ struct MathTables {
     double sn[64];
     double cs[64];
     double ex[fp64tab::kErfcxPieces * fp64tab::kErfcxCoeffs];
+    long long sq[65], cq[65];   // sin, cos (j pi/32) in Q62 (int_math.cuh)
+    long long eq[64];           // 2^(j/64) in Q62 (int_math.cuh)
 };
 
 // Block-cooperative copy of the tables into shared memory (caller syncs).
@@ -50,6 +52,11 @@ __device__ __forceinline__ void load_math_tables(MathTables* t) {
         t->ltab[i] = kLogTab[i];
     }
     for (int i = threadIdx.x; i < kErfcxPieces * kErfcxCoeffs; i += blockDim.x) t->ex[i] = kErfcxTab[i];
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) {
+        t->sq[i] = kSinQ62[i];
+        t->cq[i] = kCosQ62[i];
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) t->eq[i] = kExp2Q62[i];
 }
 
 // 1.5 * 2^52: adding it rounds a double of magnitude < 2^51 to an integer held

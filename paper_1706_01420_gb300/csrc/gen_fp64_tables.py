@@ -11,6 +11,15 @@ with mpmath and rounded once to double.
           k/2 (k = 0..12), each the degree-13 Chebyshev interpolant on
           [k/2 - 0.26, k/2 + 0.26] written as monomials in u = x - k/2.
 
+and the fixed-point tables and constants of the integer-pipe functions
+(int_math.cuh), each the exact value rounded once to an integer:
+
+  sincos: round(sin(j pi/32) 2^62), round(cos(j pi/32) 2^62), j = 0..64;
+          2/pi and pi/32 in Q64; the Taylor coefficients 1/3!, .., 1/9! of sin
+          and 1/2!, .., 1/8! of cos in Q64
+  exp:    round(2^(j/64) 2^62), j = 0..63; 64/ln2 in Q56; ln2/64 in Q128 as
+          two 64-bit words; 1/2!, .., 1/6! in Q63
+
 Run: python paper_1706_01420_gb300/csrc/gen_fp64_tables.py  (rewrites the header)
 """
 from __future__ import annotations
@@ -60,6 +69,18 @@ def erfcx(x):
     return mp.exp(x * x) * mp.erfc(x)
 
 
+def q(x, bits: int) -> int:
+    """round(x 2^bits) as a Python integer."""
+    return int(mp.nint(mp.mpf(x) * mp.power(2, bits)))
+
+
+def fmt_int(vals, per_line=3, suffix="ll"):
+    out = []
+    for i in range(0, len(vals), per_line):
+        out.append("    " + ", ".join(f"{v}{suffix}" for v in vals[i:i + per_line]) + ",")
+    return "\n".join(out)
+
+
 def fmt(vals, per_line=3):
     out = []
     for i in range(0, len(vals), per_line):
@@ -78,13 +99,19 @@ def main():
     cos_tab = [d(mp.cos(j * mp.pi / 32)) for j in range(64)]
     inv_pi_32 = d(32 / mp.pi)
     pi_32_hi, pi_32_lo = split(mp.pi / 32)
+    sin_q62 = [q(mp.sin(j * mp.pi / 32), 62) for j in range(65)]
+    cos_q62 = [q(mp.cos(j * mp.pi / 32), 62) for j in range(65)]
+    exp2_q62 = [q(mp.power(2, mp.mpf(j) / 64), 62) for j in range(64)]
+    ln2_64_q128 = q(ln2 / 64, 128)
+    fact = [mp.factorial(n) for n in range(10)]
     erfcx_tab = []
     for k in range(ERFCX_PIECES):
         c = mp.mpf(k) / 2
         coef = cheb_monomial(erfcx, c - ERFCX_HALF, c + ERFCX_HALF, ERFCX_DEG)
         erfcx_tab.extend(d(v) for v in coef)
 
-    text = f"""// Generated by gen_fp64_tables.py (mpmath, 60 digits, rounded once to double).
+    text = f"""// Generated by gen_fp64_tables.py (mpmath, 60 digits, rounded once to double
+// or to an integer).
 // Do not edit by hand.
 #pragma once
 
@@ -121,6 +148,38 @@ __device__ const double kSinTab[64] = {{
 }};
 __device__ const double kCosTab[64] = {{
 {fmt(cos_tab)}
+}};
+
+// ---- fixed-point tables and constants (int_math.cuh) ----
+constexpr unsigned long long kTwoOverPiQ64 = {q(2 / mp.pi, 64)}ull;     // 2/pi
+constexpr unsigned long long kPiOver32Q64 = {q(mp.pi / 32, 64)}ull;     // pi/32
+constexpr unsigned long long kSinC3Q64 = {q(1 / fact[3], 64)}ull;
+constexpr unsigned long long kSinC5Q64 = {q(1 / fact[5], 64)}ull;
+constexpr unsigned long long kSinC7Q64 = {q(1 / fact[7], 64)}ull;
+constexpr unsigned long long kSinC9Q64 = {q(1 / fact[9], 64)}ull;
+constexpr unsigned long long kCosC2Q64 = {q(1 / fact[2], 64)}ull;
+constexpr unsigned long long kCosC4Q64 = {q(1 / fact[4], 64)}ull;
+constexpr unsigned long long kCosC6Q64 = {q(1 / fact[6], 64)}ull;
+constexpr unsigned long long kCosC8Q64 = {q(1 / fact[8], 64)}ull;
+constexpr unsigned long long kInvLn2x64Q56 = {q(64 / ln2, 56)}ull;     // 64/ln2
+constexpr unsigned long long kLn2d64Q128Hi = {ln2_64_q128 >> 64}ull;   // ln2/64, bits 2^-1..2^-64
+constexpr unsigned long long kLn2d64Q128Lo = {ln2_64_q128 & ((1 << 64) - 1)}ull;   // bits 2^-65..2^-128
+constexpr long long kExpC2Q63 = {q(1 / fact[2], 63)}ll;
+constexpr long long kExpC3Q63 = {q(1 / fact[3], 63)}ll;
+constexpr long long kExpC4Q63 = {q(1 / fact[4], 63)}ll;
+constexpr long long kExpC5Q63 = {q(1 / fact[5], 63)}ll;
+constexpr long long kExpC6Q63 = {q(1 / fact[6], 63)}ll;
+
+// round(sin(j pi/32) 2^62), round(cos(j pi/32) 2^62), j = 0..64
+__device__ const long long kSinQ62[65] = {{
+{fmt_int(sin_q62)}
+}};
+__device__ const long long kCosQ62[65] = {{
+{fmt_int(cos_q62)}
+}};
+// round(2^(j/64) 2^62)
+__device__ const long long kExp2Q62[64] = {{
+{fmt_int(exp2_q62)}
 }};
 
 // erfcx piece k (centre k/2): coefficients of u^0 .. u^{ERFCX_DEG}

@@ -1,0 +1,118 @@
+// FP64 sin/cos and exp computed on the integer pipe.
+//
+// On this GPU the FP64 pipe issues 2 operations per clock per SM and is what
+// bounds the likelihood kernel, while the integer pipe issues 64.  These
+// functions take a double, do the range reduction and the polynomial in
+// 64-bit fixed point (64 x 64 -> 128-bit products on the integer pipe, no
+// FP64 instruction) and round the fixed-point result once to a double:
+//
+//   sincos_int  |phi| < 4: phi in Q61, k = nearest multiple of pi/32,
+//               r = phi - k pi/32 in Q64 (|r| <= pi/64), Taylor polynomials of
+//               sin r to r^9 and cos r to r^8 (truncation below 1e-19), then
+//               sin phi = S_k cos r + C_k sin r, cos phi = C_k cos r - S_k sin r
+//               with S_k, C_k = sin, cos (k pi/32) in Q62.  Absolute error
+//               before the final rounding: a few 2^-62 (the angular functions
+//               need absolute, not relative, accuracy).
+//   exp_int     -705 < a < 709: |a| in Q53 (exact for |a| >= 1/2, within
+//               2^-53 otherwise), k = nearest integer to a 64/ln2,
+//               r = a - k ln2/64 in Q64 with ln2/64 to 128 bits (|r| <=
+//               ln2/128), e^r - 1 to r^6 (truncation below 3e-20), times
+//               2^(j/64) (Q62, j = k mod 64) and 2^floor(k/64).  Relative error
+//               before the final rounding: about 2^-53 from the input
+//               quantisation for |a| < 1/2, a few 2^-62 otherwise.
+//
+// Outside these ranges both fall back to the table-driven FP64 functions.
+#pragma once
+
+#include "fp64_math.cuh"
+
+namespace ipa {
+
+// Signed Q62 value v to the nearest double, times 2^e2 (|v| < 2^63; the result
+// must be a normal double).
+__device__ __forceinline__ double q62_to_double(long long v, int e2) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    a <<= lz;                                               // leading one at bit 63
+    unsigned long long m = a >> 11;                         // 53 bits
+    const unsigned long long rem = a & 0x7FFull;
+    m += (rem > 0x400ull) || (rem == 0x400ull && (m & 1ull));   // nearest, ties to even
+    // value = m 2^(1 - lz - 52 + e2); m includes the hidden bit, which adds one to
+    // the exponent field (and a rounding carry to 2^53 adds another)
+    const long long field = (long long)(1 - lz + e2 + 1022);
+    return __longlong_as_double((long long)(sign | (((unsigned long long)field << 52) + m)));
+}
+
+// sin and cos of phi for |phi| < 4 (else the table-driven sincos_fast).
+__device__ __forceinline__ void sincos_int(double phi, const MathTables* t, double* s, double* c) {
+    using namespace fp64tab;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(phi);
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    if (E > 1) {                                            // |phi| >= 4, inf, NaN
+        sincos_fast(phi, t, s, c);
+        return;
+    }
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = E + 9;                                   // |phi| in Q61
+    const unsigned long long X = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
+    const unsigned long long U = __umul64hi(X, kTwoOverPiQ64);        // |phi| 32/pi in Q57
+    const unsigned long long k = (U + (1ull << 56)) >> 57;
+    const long long rq = (long long)(U - (k << 57));                   // |rq| <= 2^56
+    const bool rneg = rq < 0;
+    const unsigned long long ra = rneg ? (unsigned long long)(-rq) : (unsigned long long)rq;
+    const unsigned long long r = __umul64hi(ra << 7, kPiOver32Q64);   // |r| in Q64
+    const unsigned long long z = __umul64hi(r, r);                     // r^2
+    unsigned long long p = kSinC9Q64;
+    p = kSinC7Q64 - __umul64hi(z, p);
+    p = kSinC5Q64 - __umul64hi(z, p);
+    p = kSinC3Q64 - __umul64hi(z, p);
+    const long long sr = (long long)(r - __umul64hi(r, __umul64hi(z, p)));   // |sin r| in Q64, < 2^60
+    unsigned long long q = kCosC8Q64;
+    q = kCosC6Q64 - __umul64hi(z, q);
+    q = kCosC4Q64 - __umul64hi(z, q);
+    q = kCosC2Q64 - __umul64hi(z, q);
+    const long long cm = (long long)__umul64hi(z, q);                  // 1 - cos r in Q64, < 2^54
+    const long long srs = rneg ? -sr : sr;
+    const long long Sk = t->sq[k], Ck = t->cq[k];                      // Q62
+    // S_k (1 - cm) + C_k sin r and C_k (1 - cm) - S_k sin r, in Q62
+    const long long sv = Sk - __mul64hi(Sk, cm) + __mul64hi(Ck, srs);
+    const long long cv = Ck - __mul64hi(Ck, cm) - __mul64hi(Sk, srs);
+    const double sd = q62_to_double(sv, 0);
+    *s = (b >> 63) ? -sd : sd;
+    *c = q62_to_double(cv, 0);
+}
+
+// e^a for -705 < a < 709 (else the table-driven exp_fast).
+__device__ __forceinline__ double exp_int(double a, const MathTables* t) {
+    using namespace fp64tab;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    const bool neg = (b >> 63) != 0;
+    if (E > 9 || (neg ? below_neg(a, -705.0) : above(a, 709.0))) return exp_fast(a, t);
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = E + 1;                                   // |a| in Q53
+    const unsigned long long A = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
+    // k = round(|a| 64/ln2): A (Q53) x 64/ln2 (Q56) >> 64 is Q45
+    const unsigned long long P = __umul64hi(A, kInvLn2x64Q56);
+    const unsigned long long k = (P + (1ull << 44)) >> 45;
+    // r = |a| - k ln2/64 in Q64, from A << 11 minus k times ln2/64 to 128 bits
+    const unsigned __int128 kl = (unsigned __int128)k * kLn2d64Q128Hi +
+                                 (((unsigned __int128)k * kLn2d64Q128Lo) >> 64);
+    const long long r = (long long)(((__int128)A << 11) - (__int128)kl);
+    const long long rs = neg ? -r : r;
+    const long long ks = neg ? -(long long)k : (long long)k;
+    // e^rs - 1 = rs + rs^2 (1/2 + rs (1/6 + rs (1/24 + rs (1/120 + rs/720))))  (Q63 inner)
+    long long v = kExpC6Q63;
+    v = kExpC5Q63 + __mul64hi(rs, v);
+    v = kExpC4Q63 + __mul64hi(rs, v);
+    v = kExpC3Q63 + __mul64hi(rs, v);
+    v = kExpC2Q63 + __mul64hi(rs, v);
+    const long long pm = rs + (__mul64hi(__mul64hi(rs, v), rs) << 1);   // Q64
+    const long long T = t->eq[ks & 63];                                  // 2^(j/64) in Q62
+    const long long y = T + __mul64hi(T, pm);                            // Q62
+    return q62_to_double(y, (int)(ks >> 6));
+}
+
+}  // namespace ipa

@@ -20,7 +20,9 @@
 //     erfc(z) = exp(-z^2) erfcx(z) for z >= 0, with exp(-Gamma tau + Gamma^2
 //     sigma^2/2) exp(-z^2) = exp(-tau^2/(2 sigma^2)): the Gaussian factor that
 //     the gradient needs anyway replaces the exponential inside erfc;
-//   * exp, log, sincos and erfcx are table-driven FP64 (fp64_math.cuh);
+//   * sin/cos and exp run on the integer pipe in 64-bit fixed point and are
+//     rounded once to double (int_math.cuh); log and erfcx are table-driven
+//     FP64 (fp64_math.cuh);
 //   * sin(theta_K) sin(theta_mu) is one square root; the constant factors of
 //     the ten angular functions are folded into the amplitude coefficients.
 //
@@ -36,6 +38,7 @@
 #include <math.h>
 
 #include "fp64_math.cuh"
+#include "int_math.cuh"
 #include "ipa_internal.cuh"
 
 namespace ipa {
@@ -73,7 +76,7 @@ static_assert((IPA_TILE_EVENTS / 32) % kSub == 0, "events per lane must be a mul
 __device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi, const MathTables* mt,
                                                double f[10]) {
     double sp, cp;
-    sincos_fast(phi, mt, &sp, &cp);
+    sincos_int(phi, mt, &sp, &cp);
     const double sk2 = fma(-ck, ck, 1.0);
     const double cl2 = cl * cl;
     const double sl2 = 1.0 - cl2;
@@ -101,7 +104,7 @@ __device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi,
 // (z < 0) or gX (z >= 0).  Events with t > tcut have 2 g(tau) = 2E to 1e-17
 // relative and a Gaussian below 1e-17; they are given (0, +0).
 __device__ __forceinline__ double2 gauss_erfcx(const Consts& c, double tau, const MathTables* mt) {
-    const double g = exp_fast(-(tau * tau) * c.k_g, mt);
+    const double g = exp_int(-(tau * tau) * c.k_g, mt);
     const double z = (c.Gs2 - tau) * c.k_z;
     const double x = fabs(z);
     const bool zneg = negative(z);
@@ -183,7 +186,7 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
                                       double w, double2 ge, double* acc, double* prod, int* esum) {
     const Consts& c = wc.c;
     const double tau = t - c.mu;
-    const double E2 = exp_fast(fma(-c.Gamma, tau, wc.c2), mt);
+    const double E2 = exp_int(fma(-c.Gamma, tau, wc.c2), mt);
     const long long gb = __double_as_longlong(ge.y);
     const double T2 = gb >= 0 ? E2 - ge.x : ge.x;
     const double Gx = __longlong_as_double(gb & 0x7FFFFFFFFFFFFFFFll);
