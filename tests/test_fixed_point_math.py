@@ -1,0 +1,154 @@
+"""CPU checks of the integer-pipe exp and sin/cos (int_math.cuh): the generated
+fixed-point tables and constants equal their exact values rounded once, and a
+step-by-step integer emulation of the two algorithms (Python integers with the
+64-bit wrap-around and 64x64->128-bit high products of the CUDA code) meets the
+accuracy stated in int_math.cuh against 50-digit mpmath.  The GPU results of
+the same functions are checked against libm in tests/test_gpu_math.py."""
+import math
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+mp = pytest.importorskip("mpmath")
+mp.mp.dps = 50
+TABLES = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1706_01420_gb300",
+                      "csrc", "fp64_tables.cuh")
+M64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def tab():
+    src = open(TABLES).read()
+
+    def const(name):
+        return int(re.search(name + r" = (-?\d+)u?ll", src).group(1))
+
+    def arr(name):
+        body = re.search(name + r"\[\d+\] = \{(.*?)\};", src, re.S).group(1)
+        return [int(x.strip().rstrip("l").rstrip("u")) for x in body.split(",") if x.strip()]
+
+    names = ["kTwoOverPiQ64", "kPiOver32Q64", "kSinC3Q64", "kSinC5Q64", "kSinC7Q64", "kSinC9Q64", "kCosC2Q64",
+             "kCosC4Q64", "kCosC6Q64", "kCosC8Q64", "kInvLn2x64Q56", "kLn2d64Q128Hi", "kLn2d64Q128Lo",
+             "kExpC2Q63", "kExpC3Q63", "kExpC4Q63", "kExpC5Q63", "kExpC6Q63"]
+    t = {n: const(n) for n in names}
+    t["S"], t["C"], t["E"] = arr("kSinQ62"), arr("kCosQ62"), arr("kExp2Q62")
+    return t
+
+
+def _q(x, bits):
+    return int(mp.nint(mp.mpf(x) * mp.power(2, bits)))
+
+
+def test_tables_are_exact_values_rounded_once(tab):
+    assert tab["kTwoOverPiQ64"] == _q(2 / mp.pi, 64) and tab["kPiOver32Q64"] == _q(mp.pi / 32, 64)
+    assert tab["kInvLn2x64Q56"] == _q(64 / mp.log(2), 56)
+    assert (tab["kLn2d64Q128Hi"] << 64) + tab["kLn2d64Q128Lo"] == _q(mp.log(2) / 64, 128)
+    for n, k in ((3, "kSinC3Q64"), (5, "kSinC5Q64"), (7, "kSinC7Q64"), (9, "kSinC9Q64"), (2, "kCosC2Q64"),
+                 (4, "kCosC4Q64"), (6, "kCosC6Q64"), (8, "kCosC8Q64")):
+        assert tab[k] == _q(1 / mp.factorial(n), 64)
+    for n in range(2, 7):
+        assert tab[f"kExpC{n}Q63"] == _q(1 / mp.factorial(n), 63)
+    assert tab["S"] == [_q(mp.sin(j * mp.pi / 32), 62) for j in range(65)]
+    assert tab["C"] == [_q(mp.cos(j * mp.pi / 32), 62) for j in range(65)]
+    assert tab["E"] == [_q(mp.power(2, mp.mpf(j) / 64), 62) for j in range(64)]
+
+
+def _s64(x):
+    x &= M64
+    return x - (1 << 64) if x >> 63 else x
+
+
+def _umulhi(a, b):
+    return ((a & M64) * (b & M64)) >> 64
+
+
+def _mulhi(a, b):
+    return (_s64(a) * _s64(b)) >> 64
+
+
+def _bits(x):
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def _q62_to_double(v, e2):
+    if v == 0:
+        return 0.0
+    sign = 1 << 63 if v < 0 else 0
+    a = -v if v < 0 else v
+    lz = 64 - a.bit_length()
+    a = (a << lz) & M64
+    m, rem = a >> 11, a & 0x7FF
+    m += 1 if (rem > 0x400 or (rem == 0x400 and (m & 1))) else 0
+    return struct.unpack("<d", struct.pack("<Q", (sign | (((1 - lz + e2 + 1022) << 52) + m)) & M64))[0]
+
+
+def _sincos(t, phi):
+    b = _bits(phi)
+    E = ((b >> 52) & 0x7FF) - 1023
+    M = (b & 0xFFFFFFFFFFFFF) | (1 << 52)
+    sh = E + 9
+    X = (M << sh) & M64 if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    U = _umulhi(X, t["kTwoOverPiQ64"])
+    k = (U + (1 << 56)) >> 57
+    rq = _s64(U - (k << 57))
+    ra = -rq if rq < 0 else rq
+    r = _umulhi((ra << 7) & M64, t["kPiOver32Q64"])
+    z = _umulhi(r, r)
+    p = t["kSinC9Q64"]
+    for c in ("kSinC7Q64", "kSinC5Q64", "kSinC3Q64"):
+        p = (t[c] - _umulhi(z, p)) & M64
+    sr = _s64(r - _umulhi(r, _umulhi(z, p)))
+    q = t["kCosC8Q64"]
+    for c in ("kCosC6Q64", "kCosC4Q64", "kCosC2Q64"):
+        q = (t[c] - _umulhi(z, q)) & M64
+    cm = _s64(_umulhi(z, q))
+    srs = -sr if rq < 0 else sr
+    Sk, Ck = t["S"][k], t["C"][k]
+    sd = _q62_to_double(_s64(Sk - _mulhi(Sk, cm) + _mulhi(Ck, srs)), 0)
+    return (-sd if b >> 63 else sd), _q62_to_double(_s64(Ck - _mulhi(Ck, cm) - _mulhi(Sk, srs)), 0)
+
+
+def _exp(t, a):
+    b = _bits(a)
+    E = ((b >> 52) & 0x7FF) - 1023
+    neg = b >> 63
+    M = (b & 0xFFFFFFFFFFFFF) | (1 << 52)
+    sh = E + 1
+    A = (M << sh) & M64 if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    k = (_umulhi(A, t["kInvLn2x64Q56"]) + (1 << 44)) >> 45
+    kl = k * t["kLn2d64Q128Hi"] + ((k * t["kLn2d64Q128Lo"]) >> 64)
+    r = _s64((A << 11) - kl)
+    rs, ks = (-r, -k) if neg else (r, k)
+    v = t["kExpC6Q63"]
+    for c in ("kExpC5Q63", "kExpC4Q63", "kExpC3Q63", "kExpC2Q63"):
+        v = _s64(t[c] + _mulhi(rs, v))
+    pm = _s64(rs + _s64(_mulhi(_mulhi(rs, v), rs) << 1))
+    T = t["E"][ks & 63]
+    return _q62_to_double(_s64(T + _mulhi(T, pm)), ks >> 6)
+
+
+def test_sincos_emulation_accuracy(tab):
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.uniform(-np.pi, np.pi, 4000), rng.uniform(-3.999, 3.999, 1000),
+                         [0.0, -0.0, 1e-300, np.pi, -np.pi, np.pi / 2, 3.999, 1e-10, -1e-17]])
+    worst = 0.0
+    for x in xs:
+        s, c = _sincos(tab, float(x))
+        worst = max(worst, abs(float(mp.mpf(s) - mp.sin(mp.mpf(float(x))))),
+                    abs(float(mp.mpf(c) - mp.cos(mp.mpf(float(x))))))
+    # a few 2^-62 before the final rounding, half an ulp of 1 after it
+    assert worst <= 6e-17, worst
+
+
+def test_exp_emulation_accuracy(tab):
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.uniform(-704.9, 708.9, 4000), rng.uniform(-1, 1, 1000), rng.uniform(-1e-3, 1e-3, 500),
+                         [0.0, -0.0, 1e-300, -704.99, 708.99, 0.5, -0.5, 1.0]])
+    worst = 0.0
+    for x in xs:
+        ref = mp.exp(mp.mpf(float(x)))
+        worst = max(worst, abs(float((mp.mpf(_exp(tab, float(x))) - ref) / math.ulp(float(ref)))))
+    assert worst <= 1.5, worst
