@@ -50,23 +50,24 @@ WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 # FP64 operations of the fused 4D NLL+gradient kernel, counted from the formula
 # as nll.cu evaluates it (FMA = 2 flops; each FP64 function call counts its
 # cost in DFMA issue slots measured live by ipa_calibrate_fp64, times 2 flops).
-# exp and sin/cos run on the integer pipe (int_math.cuh) and count no FP64
-# operation; only their arguments do:
-#   every event: tau, the exponent of 2E, T2, the angular products f'_k (one
-#     sqrt), A' (10 terms), P, 1/P (an FP32 seed and one FP64 Newton step: 2
-#     FMA), sum r, r T2, S_k (10), r A', u, Y1..Y3;
+# exp and the angular basis (sin/cos, the ten products, the square root and
+# the amplitude sum A) run on the integer pipe in fixed point (int_math.cuh)
+# and count no FP64 operation; only their arguments and results do:
+#   every event: tau, the exponent of 2E, T2, A' = A cs/2, P, 1/P (an FP32
+#     seed and one FP64 Newton step: 2 FMA), sum r, r T2, S_k (10), r A', u,
+#     Y1..Y3;
 #     unweighted: one multiply into the lane's log product; weighted: w log P;
 #   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma):
 #     the Gaussian's exponent, the erfcx argument and erfcx, g X;
 #   unweighted, once per lane and 512-event tile (16 events): the log of the
 #     product and its exponent term.
-OPS_EVENT_4D = {"fma": 29, "mul": 21, "add": 4, "sqrt": 1}
+# (Angles within 2^-17 of |cos| = 1, about 1.5e-5 of the events, take the FP64
+# basis instead; they are not counted.)
+OPS_EVENT_4D = {"fma": 17, "mul": 4, "add": 3}
 OPS_UNWEIGHTED = {"mul": 1}
 OPS_WEIGHTED = {"fma": 1, "mul": 1, "log_fast": 1}
 OPS_NEAR_PEAK = {"mul": 4, "add": 2, "erfcx_poly": 1}
 OPS_LANE_TILE = {"fma": 2, "log_fast": 1}
-# integer-pipe calls per event (reported with their stand-alone time, not counted)
-INT_CALLS_EVENT = {"exp_int": 1, "sincos_int": 1}
 
 
 def _flops(ops: dict, cal: dict) -> float:
@@ -404,7 +405,7 @@ def main():
                      "fp64_costs_dfma_slots": {k: round(cal[k], 2) for k in
                                                ("exp_fast", "erfcx_poly", "sincos_fast", "log_fast", "sqrt",
                                                 "rcp", "exp", "erfc", "log", "sincos")},
-                     "int_pipe_calls_per_event": {"exp_int": 1.0 + near, "sincos_int": 1.0},
+                     "int_pipe_calls_per_event": {"exp_int": 1.0 + near, "angular_basis_q62": 1.0},
                      "int_pipe_time_alone_dfma_slots": {k: round(cal[k], 2) for k in ("exp_int", "sincos_int")}},
         "wall_s_timed_region": wall,
     }

@@ -45,15 +45,12 @@ __device__ __forceinline__ double q62_to_double(long long v, int e2) {
     return __longlong_as_double((long long)(sign | (((unsigned long long)field << 52) + m)));
 }
 
-// sin and cos of phi for |phi| < 4 (else the table-driven sincos_fast).
-__device__ __forceinline__ void sincos_int(double phi, const MathTables* t, double* s, double* c) {
+// sin and cos of |phi| in signed Q62 (|phi| < 4, the caller checks), before
+// the sign of phi is applied to the sine.
+__device__ __forceinline__ void sincos_q62(unsigned long long b, const MathTables* t, long long* sv,
+                                           long long* cv) {
     using namespace fp64tab;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(phi);
     const int E = (int)((b >> 52) & 0x7FFull) - 1023;
-    if (E > 1) {                                            // |phi| >= 4, inf, NaN
-        sincos_fast(phi, t, s, c);
-        return;
-    }
     const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
     const int sh = E + 9;                                   // |phi| in Q61
     const unsigned long long X = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
@@ -77,8 +74,19 @@ __device__ __forceinline__ void sincos_int(double phi, const MathTables* t, doub
     const long long srs = rneg ? -sr : sr;
     const long long Sk = t->sq[k], Ck = t->cq[k];                      // Q62
     // S_k (1 - cm) + C_k sin r and C_k (1 - cm) - S_k sin r, in Q62
-    const long long sv = Sk - __mul64hi(Sk, cm) + __mul64hi(Ck, srs);
-    const long long cv = Ck - __mul64hi(Ck, cm) - __mul64hi(Sk, srs);
+    *sv = Sk - __mul64hi(Sk, cm) + __mul64hi(Ck, srs);
+    *cv = Ck - __mul64hi(Ck, cm) - __mul64hi(Sk, srs);
+}
+
+// sin and cos of phi for |phi| < 4 (else the table-driven sincos_fast).
+__device__ __forceinline__ void sincos_int(double phi, const MathTables* t, double* s, double* c) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(phi);
+    if ((int)((b >> 52) & 0x7FFull) - 1023 > 1) {           // |phi| >= 4, inf, NaN
+        sincos_fast(phi, t, s, c);
+        return;
+    }
+    long long sv, cv;
+    sincos_q62(b, t, &sv, &cv);
     const double sd = q62_to_double(sv, 0);
     *s = (b >> 63) ? -sd : sd;
     *c = q62_to_double(cv, 0);
@@ -113,6 +121,94 @@ __device__ __forceinline__ double exp_int(double a, const MathTables* t) {
     const long long T = t->eq[ks & 63];                                  // 2^(j/64) in Q62
     const long long y = T + __mul64hi(T, pm);                            // Q62
     return q62_to_double(y, (int)(ks >> 6));
+}
+
+// x in signed Q62 for |x| <= 1 (the caller checks): exact when |x| >= 2^-10,
+// truncated to 2^-62 below.
+__device__ __forceinline__ long long to_q62(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int sh = (int)((b >> 52) & 0x7FFull) - 1023 + 10;
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const long long v = (long long)(sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull));
+    return (b >> 63) ? -v : v;
+}
+
+// (a b) in Q62 for a, b in signed Q62 with |a b| < 2: the high product shifted
+// left by 2 (the two lowest bits are lost: error below 2^-60).
+__device__ __forceinline__ long long mul_q62(long long a, long long b) { return __mul64hi(a, b) << 2; }
+
+constexpr long long kOneQ62 = 1ll << 62;
+
+// sqrt(x) in Q62 for x in [0, 1] given in Q124 (a product of two Q62 values,
+// so that small x keep their relative precision): an FP32 seed refined by two
+// Newton steps on the exact 128-bit residual (relative error about 2^-60, plus
+// 2^-62 absolute from the final shift).
+__device__ __forceinline__ long long sqrt_q124(unsigned __int128 X) {
+    if (X == 0) return 0;
+    const unsigned long long xh = (unsigned long long)(X >> 64), xl = (unsigned long long)X;
+    const int lz = xh ? __clzll((long long)xh) : 64 + __clzll((long long)xl);
+    const int d = 124 - (127 - lz);                    // >= 0: x <= 1
+    const int s = d & ~1;                              // even shift: xn = Xn 2^-124 in [1/2, 2)
+    const unsigned __int128 Xn = X << s;
+    const int top = 127 - lz + s;                      // 123 or 124
+    const unsigned fb = ((unsigned)(top - 124 + 127) << 23) | ((unsigned)(Xn >> (top - 23)) & 0x7FFFFFu);
+    const float y0f = rsqrtf(__uint_as_float(fb));     // ~1/sqrt(xn) in (0.7, 1.42)
+    const unsigned yb = __float_as_uint(y0f);
+    const int ye = (int)((yb >> 23) & 0xFF) - 127;     // -1 or 0
+    const long long Y0 = (long long)(((unsigned long long)((yb & 0x7FFFFF) | 0x800000)) << (39 + ye));
+    long long Q = mul_q62((long long)(Xn >> 62), Y0);  // ~sqrt(xn) in Q62
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const __int128 R = (__int128)Xn - (__int128)Q * Q;               // residual in Q124
+        Q += __mul64hi((long long)(R >> 62), Y0) << 1;                    // + R y0 / 2
+    }
+    return Q >> (s >> 1);
+}
+
+// 1 - x^2 in Q62 for x in signed Q62, |x| <= 1, from the exact square
+// (error below 2^-62).
+__device__ __forceinline__ long long one_minus_sq_q62(long long x) {
+    return (long long)((((unsigned __int128)1 << 124) - (unsigned __int128)((__int128)x * x)) >> 62);
+}
+
+// Whether basis_q62 keeps its accuracy for these angles: |phi| < 4 and
+// |cos thK|, |cos thmu| < 1 - 2^-17, so that sin^2 = 1 - cos^2 >= 2^-16 and its
+// fixed-point error (2^-60 absolute) stays below 2^-44 relative.  Outside (about
+// 1.5e-5 of uniformly distributed angles, and invalid |cos| > 1 or NaN) the
+// caller uses the FP64 basis.
+__device__ __forceinline__ bool basis_q62_ok(double ck, double cl, double phi) {
+    constexpr double kMaxCos = 1.0 - 0x1p-17;
+    return abs_below(ck, kMaxCos) && abs_below(cl, kMaxCos) && abs_below(phi, 4.0);
+}
+
+// The ten unscaled angular products f'_k (sec. 4 helicity basis, without their
+// constant factors) in signed Q62 (absolute error a few 2^-60), for angles
+// that pass basis_q62_ok.  sin thK sin thmu = sqrt((1 - cos^2 thK)(1 - cos^2 thmu)).
+__device__ __forceinline__ void basis_q62(double ck, double cl, double phi, const MathTables* t, long long F[10]) {
+    const unsigned long long pb = (unsigned long long)__double_as_longlong(phi);
+    long long sp, cp;
+    sincos_q62(pb, t, &sp, &cp);
+    if (pb >> 63) sp = -sp;
+    const long long CK = to_q62(ck), CL = to_q62(cl);
+    const long long sk2 = one_minus_sq_q62(CK), sl2 = one_minus_sq_q62(CL);
+    const long long ck2 = kOneQ62 - sk2, cl2 = kOneQ62 - sl2;
+    const long long cp2 = mul_q62(cp, cp);
+    const unsigned __int128 sksl2_124 = (unsigned __int128)((__int128)sk2 * sl2);
+    const long long sksl2 = (long long)(sksl2_124 >> 62);
+    const long long q = sqrt_q124(sksl2_124);
+    const long long slcp2 = mul_q62(sl2, cp2);
+    F[0] = mul_q62(ck2, sl2);
+    F[1] = mul_q62(sk2, kOneQ62 - slcp2);
+    F[2] = mul_q62(sk2, slcp2 + cl2);
+    F[3] = mul_q62(sksl2, mul_q62(sp, cp));
+    const long long a = mul_q62(q, mul_q62(CK, CL));
+    F[4] = mul_q62(a, cp);
+    F[5] = mul_q62(a, sp);
+    F[6] = sl2;
+    const long long bq = mul_q62(q, CL);
+    F[7] = mul_q62(bq, cp);
+    F[8] = mul_q62(bq, sp);
+    F[9] = mul_q62(CK, sl2);
 }
 
 }  // namespace ipa

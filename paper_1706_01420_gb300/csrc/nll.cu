@@ -65,6 +65,9 @@ struct WarpConsts {
     double aq;
     double c2;
     double tcut;     // t above it: z < -6.25, the Gaussian-erfcx term is below 1e-17 of T
+    long long hcq[10];   // h_k c_k in Q62 (the fixed-point amplitude sum)
+    int fixed;           // every |h_k c_k| < 2 and finite: the fixed-point path may be used
+    int pad_;
 };
 
 // Decay-time events per compaction round of one lane (see nll_kernel).
@@ -172,10 +175,18 @@ __device__ __forceinline__ double log_of(double prod, int esum, const MathTables
     return fma(ed, fp64tab::kLn2Hi, fma(ed, fp64tab::kLn2Lo, log_fast(prod, mt)));
 }
 
+// A' = sum_k hq_k f_k in FP64 (cached basis, or angles outside basis_q62_ok).
+__device__ __forceinline__ double amplitude_sum(const double* hq, const double* f) {
+    double Ap = hq[0] * f[0];
+#pragma unroll
+    for (int k = 1; k < 10; ++k) Ap = fma(hq[k], f[k], Ap);
+    return Ap;
+}
+
 // One event: the log term (w log P added to acc[0], or for w = 1 exactly, P
 // folded into the lane's product) and the adjoint sums.  For the 4D model f
 // holds either the unscaled products f'_k (CACHED = false) or the cached basis
-// f_k (CACHED = true); wc.hq carries the matching coefficients; ge is the
+// f_k (CACHED = true); Ap = (cs/2) A (wc.aq for the 1D model); ge is the
 // event's gauss_erfcx value or (0, +0).
 // Accumulators (kD = 12 for 4D, 3 for 1D), with r = w / P and A' = (cs/2) A:
 //   acc[1] = sum r,  acc[2 + k] = sum r T2 f_k (4D) or acc[2] = sum r T2 (1D),
@@ -183,19 +194,13 @@ __device__ __forceinline__ double log_of(double prod, int esum, const MathTables
 // the derivatives in Gamma, sigma and mu are linear in these (finalize).
 template <int KIND, bool GRAD, bool CACHED, bool WEIGHTED>
 __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt, double t, const double* f,
-                                      double w, double2 ge, double* acc, double* prod, int* esum) {
+                                      double Ap, double w, double2 ge, double* acc, double* prod, int* esum) {
     const Consts& c = wc.c;
     const double tau = t - c.mu;
     const double E2 = exp_int(fma(-c.Gamma, tau, wc.c2), mt);
     const long long gb = __double_as_longlong(ge.y);
     const double T2 = gb >= 0 ? E2 - ge.x : ge.x;
     const double Gx = __longlong_as_double(gb & 0x7FFFFFFFFFFFFFFFll);
-    double Ap = wc.aq;
-    if (KIND == IPA_MODEL_ANGTIME4D) {
-        Ap = wc.hq[0] * f[0];
-#pragma unroll
-        for (int k = 1; k < 10; ++k) Ap = fma(wc.hq[k], f[k], Ap);
-    }
     const double P = fma(T2, Ap, c.cb);
     // events of weight exactly 1 (all events without a weight column) join the
     // lane's log product, so a column of ones gives the same bits as no column
@@ -439,6 +444,14 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                     const double tc = wc.c.mu + (wc.c.Gs2 + 6.25 / wc.c.k_z);
                     wc.tcut = tc == tc ? tc : INFINITY;    // NaN constants: every event takes the full path
                 }
+                // h_k c_k in Q62 for the fixed-point amplitude sum; non-finite or
+                // |h_k c_k| >= 2 (non-physical theta) keeps the FP64 path, which
+                // propagates NaN
+                const double hc = lane < 10 ? wc.c.h[lane] * kBasisScale[lane] : 0.0;
+                const bool hc_ok = abs_below(hc, 2.0);
+                if (lane < 10) wc.hcq[lane] = hc_ok ? to_q62(hc) : 0;
+                const bool all_ok = __all_sync(0xffffffffu, hc_ok) && abs_below(wc.c.cs, 1e300);
+                if (lane == 0) wc.fixed = all_ok ? 1 : 0;
                 __syncwarp();
                 cur = seg;
             }
@@ -492,15 +505,33 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                                                             : make_double2(0.0, 0.0);
                         const double w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
                         double f[10];
+                        double Ap = wc.aq;
                         if (KIND == IPA_MODEL_ANGTIME4D) {
                             if (CACHED) {
 #pragma unroll
                                 for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
+                                Ap = amplitude_sum(wc.hq, f);
                             } else {
-                                basis_unscaled(__ldg(cols.ck + e), __ldg(cols.cl + e), __ldg(cols.phi + e), &mt, f);
+                                const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
+                                if (wc.fixed && basis_q62_ok(ck, cl, phi)) {
+                                    // the angular products and A on the integer pipe
+                                    long long F[10];
+                                    basis_q62(ck, cl, phi, &mt, F);
+                                    long long Af = 0;
+#pragma unroll
+                                    for (int k = 0; k < 10; ++k) {
+                                        f[k] = q62_to_double(F[k], 0);
+                                        Af += __mul64hi(wc.hcq[k], F[k]);
+                                    }
+                                    Ap = q62_to_double(Af, 2) * wc.aq;      // Af is Q60
+                                } else {
+                                    basis_unscaled(ck, cl, phi, &mt, f);
+                                    Ap = amplitude_sum(wc.hq, f);
+                                }
                             }
                         }
-                        event<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, __ldg(cols.t + e), f, w, ge, acc, &prod, &esum);
+                        event<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, __ldg(cols.t + e), f, Ap, w, ge, acc, &prod,
+                                                            &esum);
                     }
                 }
                 __syncwarp();
