@@ -10,6 +10,9 @@ namespace {
 __global__ void __launch_bounds__(128) consts_block_kernel(ModelDev m, const double* __restrict__ theta,
                                                            Consts* __restrict__ out) {
     __shared__ ConstsBlockScratch S;
+    // the likelihood kernel that follows may start now (it waits for this
+    // kernel's results before reading them)
+    asm volatile("griddepcontrol.launch_dependents;");
     const int s = blockIdx.x;
     compute_consts_block(m, theta + (size_t)s * m.n_par, out + s, &S);
 }
@@ -17,6 +20,7 @@ __global__ void __launch_bounds__(128) consts_block_kernel(ModelDev m, const dou
 // One thread per fit (many fits: throughput).
 __global__ void consts_thread_kernel(ModelDev m, const double* __restrict__ theta, int n_seg,
                                      Consts* __restrict__ out) {
+    asm volatile("griddepcontrol.launch_dependents;");
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n_seg) compute_consts_thread(m, theta + (size_t)s * m.n_par, out + s);
 }

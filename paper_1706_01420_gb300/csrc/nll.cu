@@ -394,6 +394,9 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
 
     load_math_tables(&mt);
     __syncthreads();
+    // Launched as a programmatic dependent of the constants kernel: the table
+    // load above overlaps it; everything below waits for its results.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     const bool single = seg_begin == nullptr;
     const int64_t total = single ? (n + kTile - 1) / kTile : __ldg(seg_tiles + n_seg);
@@ -646,10 +649,22 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
         grid = need < grid ? need : grid;
     }
     if (grid < 1) grid = 1;
-    nll_kernel<KIND, GRAD, CACHED, WEIGHTED><<<(unsigned)grid, 32 * W, smem, st>>>(
-        cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->gcount, sc->work,
-        out, n_par, K);
-    return cuda_fail(cudaGetLastError(), "likelihood kernel launch");
+    // programmatic dependent launch: blocks may start (and load their tables)
+    // while the constants kernel that precedes every launch is still running
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(32u * W);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cuda_fail(cudaLaunchKernelEx(&lc, nll_kernel<KIND, GRAD, CACHED, WEIGHTED>, cols, n, seg_begin, seg_end,
+                                        seg_tiles, n_seg, consts, sc->partials, sc->counters, sc->gcount, sc->work,
+                                        out, n_par, K),
+                     "likelihood kernel launch");
 }
 
 }  // namespace
