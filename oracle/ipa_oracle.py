@@ -52,12 +52,12 @@ I_OMEGA = 16.0 * math.pi / 9.0   # integral of A over the angles when sum |A_i|^
 
 IDX = {"Gamma": 0, "sigma": 1, "mu": 2, "f_b": 3, "A0sq": 4, "Apesq": 5,
        "delta_pa": 6, "delta_pe": 7, "F_S": 8, "delta_S": 9}
-NPAR = {"1d": 4, "4d": 10}
+NPAR = {"1d": 4, "4d": 10, "tag": 8}
 
 
 @dataclass
 class Model:
-    kind: str            # "1d" or "4d"
+    kind: str            # "1d", "4d" or "tag" (flavour-tagged decay time, oracle/tagged.py)
     t_lo: float
     t_hi: float
 
@@ -69,6 +69,8 @@ class Model:
     def volume(self) -> float:
         """Volume of the observable box (background density is 1/V)."""
         dt = self.t_hi - self.t_lo
+        if self.kind == "tag":
+            return 2.0 * dt              # decay time x tag q = +-1
         return dt if self.kind == "1d" else dt * 2.0 * 2.0 * 2.0 * math.pi
 
 
@@ -267,6 +269,9 @@ def _cols(model: Model, ev: dict):
 
 def pdf(model: Model, ev: dict, theta) -> np.ndarray:
     """Normalised per-event density P(t[, Omega])."""
+    if model.kind == "tag":
+        from . import tagged
+        return tagged.pdf(model, ev, theta)
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu, f_b = theta[:4]
     t, _ = _cols(model, ev)
@@ -288,6 +293,9 @@ def nll(model: Model, ev: dict, theta) -> float:
 
 def nll_grad_terms(model: Model, ev: dict, theta):
     """Per-event terms: (w log P, and -w (dP/dtheta_j) / P as an (npar, N) array)."""
+    if model.kind == "tag":
+        from . import tagged
+        return tagged.nll_grad_terms(model, ev, theta)
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu, f_b = theta[:4]
     t, w = _cols(model, ev)
@@ -379,6 +387,14 @@ def angular_envelope(theta) -> float:
 
 def toy_one(model: Model, theta, seed: int, toy: int, n_sig: int, n_bkg: int,
             chunk: int = 1 << 16) -> dict:
+    if model.kind == "tag":
+        from . import tagged
+        return tagged.toy_one(model, theta, seed, toy, n_sig, n_bkg, chunk)
+    return _toy_one_angular(model, theta, seed, toy, n_sig, n_bkg, chunk)
+
+
+def _toy_one_angular(model: Model, theta, seed: int, toy: int, n_sig: int, n_bkg: int,
+                     chunk: int = 1 << 16) -> dict:
     """One pseudo-experiment: n_sig accepted signal candidates then n_bkg background events.
 
     Signal candidate j of toy k draws Philox calls counter (j_lo, j_hi, k, c), c = 0,1,2:
