@@ -65,10 +65,29 @@ typedef enum {
 
 typedef enum {
     IPA_MODEL_TIME1D = 1,     /* decay time only: P(t)                              */
-    IPA_MODEL_ANGTIME4D = 2   /* decay time x helicity angles: P(t, ck, cl, phi)    */
+    IPA_MODEL_ANGTIME4D = 2,  /* decay time x helicity angles: P(t, ck, cl, phi)    */
+    IPA_MODEL_TAGGED1D = 3    /* flavour-tagged decay time with B_s oscillation: P(t, q) */
 } ipa_model_kind;
 
-/* Parameter indices (theta layout).  1D uses the first 4, 4D all 10. */
+/* The tagged model (Sec. 4, the B_s -> J/psi phi example, whose time-dependent
+ * fit has the oscillation frequency Dm_s, the widths Gamma and DG and the
+ * CP-violating phase as parameters; Sec. 2 and the symbolic-programming
+ * section for the Faddeeva function that the oscillating terms convolved with
+ * the Gaussian resolution need).  The paper prints no formula; this library
+ * takes the tagged decay rate of a CP-even final state with |lambda| = 1,
+ *   S(t, q) = e^{-Gamma t} [cosh(DG t / 2) - cos(phi_s) sinh(DG t / 2)
+ *                          + q (1 - 2 omega) sin(phi_s) sin(Dm t)],  t >= 0,
+ * convolved with a Gaussian (sigma, offset mu).  With Gamma_H,L = Gamma -+ DG/2
+ * and g(tau; z) = int_0^inf e^{-z u} G(tau - u) du (complex z),
+ *   S = (1 - c)/2 g(tau; Gamma_H) + (1 + c)/2 g(tau; Gamma_L)
+ *       + q (1 - 2 omega) s Im g(tau; Gamma - i Dm),   c, s = cos, sin phi_s,
+ * normalised over [t_lo, t_hi] and both tags by N = (1 - c) I(Gamma_H) +
+ * (1 + c) I(Gamma_L), and P(t, q) = (1 - f_b) S / N + f_b / (2 (t_hi - t_lo)).
+ * Parameters: Gamma, sigma, mu, f_b, DG, Dm, phi_s, omega (IPA_GAMMA ..
+ * IPA_OMEGA).  Events carry t and q = +1.0 or -1.0. */
+
+/* Parameter indices (theta layout).  1D uses the first 4, 4D all 10, the
+ * tagged model the first 4 and its own 4 to 7. */
 enum {
     IPA_GAMMA = 0,   /* decay width Gamma [1/ps]                   */
     IPA_SIGMA = 1,   /* Gaussian time resolution sigma [ps]        */
@@ -80,8 +99,13 @@ enum {
     IPA_DPE = 7,     /* strong phase delta_perp [rad]              */
     IPA_FS = 8,      /* S-wave fraction F_S                        */
     IPA_DS = 9,      /* S-wave phase delta_S [rad]; delta_0 = 0    */
+    IPA_DG = 4,      /* tagged: width difference DG = Gamma_L - Gamma_H [1/ps] */
+    IPA_DM = 5,      /* tagged: mass difference Dm_s [1/ps]        */
+    IPA_PHIS = 6,    /* tagged: CP-violating phase phi_s [rad]     */
+    IPA_OMEGA = 7,   /* tagged: mistag probability omega           */
     IPA_NPAR_1D = 4,
     IPA_NPAR_4D = 10,
+    IPA_NPAR_TAGGED = 8,
     IPA_MAX_PAR = 16
 };
 
@@ -94,29 +118,33 @@ typedef struct {
 } ipa_param;
 
 /* An event set (Cat of App. C): n events as FP64 SoA device columns.
- * t is required; ck, cl, phi are required for the 4D model and ignored for 1D;
- * w may be NULL (unit weights).  fk may be NULL, or hold the angular basis of
- * these events written by ipa_angular_basis (10 columns of fk_stride doubles);
- * 4D likelihood and fit calls then read it instead of evaluating the angular
+ * t is required; ck, cl, phi are required for the 4D model and ignored
+ * otherwise; q (the flavour tag, +1.0 or -1.0) is required for the tagged
+ * model and ignored otherwise; w may be NULL (unit weights).  Every column is
+ * 16-byte aligned.  fk may be NULL, or hold the angular basis of these events
+ * written by ipa_angular_basis (10 columns of fk_stride doubles); 4D
+ * likelihood and fit calls then read it instead of evaluating the angular
  * functions. */
 typedef struct {
     int64_t n;
     const double *t, *ck, *cl, *phi, *w;
     const double* fk;
     int64_t fk_stride;
+    const double* q;
 } ipa_events;
 
 /* Writable event columns for the generator; `capacity` is the number of
- * events each non-NULL column can hold. */
+ * events each non-NULL column can hold (q: the tagged model's tag). */
 typedef struct {
     int64_t capacity;
     double *t, *ck, *cl, *phi;
+    double* q;
 } ipa_event_buffers;
 
 /* The model: its kind, number of parameters and the decay-time range. */
 typedef struct {
     int32_t kind;      /* ipa_model_kind */
-    int32_t n_par;     /* IPA_NPAR_1D or IPA_NPAR_4D (set by ipa_model_init) */
+    int32_t n_par;     /* IPA_NPAR_1D, IPA_NPAR_4D or IPA_NPAR_TAGGED (set by ipa_model_init) */
     double t_lo, t_hi; /* decay-time range [ps], t_lo < t_hi */
 } ipa_model;
 
@@ -134,7 +162,7 @@ enum {
 ipa_status ipa_model_init(ipa_model* m, int32_t kind, double t_lo, double t_hi);
 
 /* NLL = -sum_e w_e log P_e (Sec. 3: per-event PDF, log of the mixture, sum of
- * logs; Sec. 4: the 4D model).  theta_dev: n_par doubles (device).
+ * logs; Sec. 4: the 4D and the tagged model).  theta_dev: n_par doubles (device).
  * out_dev: 1 double (device).  The sum is a fixed-order FP64 tree over
  * 512-event tiles: the result does not depend on launch geometry.  n = 0
  * gives 0.  Uses library scratch (ipa_reserve). */
@@ -174,6 +202,12 @@ ipa_status ipa_angular_basis(const ipa_model* model, const ipa_events* ev, doubl
  * (seed lo32, seed hi32) and counters (j lo32, j hi32, k, c) for c = 0,1,2;
  * the toy keeps the first n_sig[k] accepted candidates in increasing j.
  * Background event i uses counters (i lo32, i hi32, k, 4) and (.., 5).
+ * Tagged model: candidate j draws (t, u) from call 0 and the tag from the
+ * first uniform u_q of call 1 (q = +1 if u_q <= 1/2, else -1) and is kept iff
+ * u M_S < S(t - mu, q), M_S = (1 - c)/2 M(Gamma_H) + (1 + c)/2 M(Gamma_L) +
+ * |(1 - 2 omega) s| M(Gamma) with M(x) = min(1, e^{-x (t_lo - mu) + x^2
+ * sigma^2 / 2}); background event i takes t and q from call 4; out->t and
+ * out->q are written.
  * Candidates are built with IEEE-exact operations only, so a stream is
  * reproducible bit for bit.  n_sig, n_bkg, offsets: n_toys int64 each
  * (device).  For 1D only out->t is written.  A toy with a negative count or
@@ -322,6 +356,17 @@ ipa_status ipa_calibrate_fp64(double* results, void* stream);
 enum { IPA_MATH_EXP = 0, IPA_MATH_LOG = 1, IPA_MATH_SIN = 2, IPA_MATH_COS = 3, IPA_MATH_ERFCX = 4,
        IPA_MATH_RCP = 5 };
 ipa_status ipa_math_eval(int32_t fn, const double* x_dev, double* y_dev, int64_t n, void* stream);
+
+/* The Faddeeva function w(z) = exp(-z^2) erfc(-i z) as the tagged model's
+ * kernels evaluate it (Sec. 2 and the symbolic-programming section: the
+ * oscillating decay-time terms convolved with the Gaussian resolution need
+ * it): for Im z >= 0 Weideman's rational approximation with N = 40 terms
+ * (SIAM J. Numer. Anal. 31 (1994) 1497), relative error below 1e-15; for
+ * Im z < 0 the reflection w(z) = 2 exp(-z^2) - w(-z), which overflows where
+ * exp(-z^2) does.  Test support: z_dev and w_dev hold n complex numbers as
+ * (re, im) pairs of doubles (device, caller-owned).  IPA_ERR_ARG for NULL
+ * arrays with n > 0.  Asynchronous on `stream`. */
+ipa_status ipa_faddeeva(const double* z_dev, double* w_dev, int64_t n, void* stream);
 
 /* Text of the calling thread's last error ("" if none). */
 const char* ipa_last_error(void);

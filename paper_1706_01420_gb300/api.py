@@ -62,15 +62,19 @@ def model_4d(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
     return ipa_model_init(C.IPA_MODEL_ANGTIME4D, t_lo, t_hi)
 
 
+def model_tagged(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
+    return ipa_model_init(C.IPA_MODEL_TAGGED1D, t_lo, t_hi)
+
+
 def ipa_events(ev: dict) -> C.ipa_events:
-    """dict of CUDA float64 columns (t[, ck, cl, phi][, w][, fk]) -> ipa_events.
+    """dict of CUDA float64 columns (t[, ck, cl, phi][, q][, w][, fk]) -> ipa_events.
 
     fk, if present, is the (10, stride) tensor written by ipa_angular_basis."""
     t = ev["t"]
     e = C.ipa_events()
     e.n = int(t.numel())
     e.t = _ptr(t, name="t")
-    for k in ("ck", "cl", "phi", "w"):
+    for k in ("ck", "cl", "phi", "w", "q"):
         v = ev.get(k)
         setattr(e, k, _ptr(v, name=k) if v is not None else None)
     fk = ev.get("fk")
@@ -139,7 +143,7 @@ def ipa_toygen(model: C.ipa_model, theta: torch.Tensor, seed: int, n_sig: torch.
     """Fill the columns of `out` (dict of CUDA float64 tensors of equal length)."""
     b = C.ipa_event_buffers()
     b.capacity = int(out["t"].numel())
-    for k in ("t", "ck", "cl", "phi"):
+    for k in ("t", "ck", "cl", "phi", "q"):
         v = out.get(k)
         setattr(b, k, _ptr(v, name=k) if v is not None else None)
     _check(_lib().ipa_toygen(ctypes.byref(model), _ptr(theta, name="theta"), ctypes.c_uint64(seed),
@@ -212,7 +216,7 @@ def ipa_serve_submit(server, ev: dict, params: list[Param]) -> int:
     """Submit one fit; ev holds host numpy arrays or CUDA tensors (copied before return)."""
     e = C.ipa_events()
     keep = []
-    for k in ("t", "ck", "cl", "phi", "w"):
+    for k in ("t", "ck", "cl", "phi", "w", "q"):
         v = ev.get(k)
         if v is None:
             setattr(e, k, None)
@@ -300,6 +304,17 @@ def ipa_math_eval(fn: int, x: torch.Tensor, stream=None) -> torch.Tensor:
     _check(_lib().ipa_math_eval(int(fn), _ptr(x, name="x"), _ptr(y, name="y"), x.numel(), _stream(stream)),
            "ipa_math_eval")
     return y
+
+
+def ipa_faddeeva(z: torch.Tensor, stream=None) -> torch.Tensor:
+    """w(z) = exp(-z^2) erfc(-i z) elementwise, as the tagged model's kernels evaluate it;
+    z is a complex128 CUDA tensor."""
+    if not (isinstance(z, torch.Tensor) and z.is_cuda and z.dtype == torch.complex128):
+        raise IpaError("z must be a complex128 CUDA tensor")
+    zr = torch.view_as_real(z.contiguous()).contiguous()
+    wr = torch.empty_like(zr)
+    _check(_lib().ipa_faddeeva(zr.data_ptr(), wr.data_ptr(), z.numel(), _stream(stream)), "ipa_faddeeva")
+    return torch.view_as_complex(wr)
 
 
 def ipa_version() -> str:

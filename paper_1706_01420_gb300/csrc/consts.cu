@@ -29,6 +29,7 @@ __global__ void consts_thread_kernel(ModelDev m, const double* __restrict__ thet
 ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
                          cudaStream_t st) {
     if (n_seg <= 0) return IPA_OK;
+    if (m.kind == IPA_MODEL_TAGGED1D) return launch_tag_consts(m, theta, n_seg, out, st);
     if (n_seg >= 64) {
         consts_thread_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
         return cuda_fail(cudaGetLastError(), "consts kernel launch");

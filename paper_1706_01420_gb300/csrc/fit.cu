@@ -47,12 +47,12 @@ struct GraphKey {
     unsigned tune = 0;             // launch-geometry table version the graph was captured with
     double t_lo = 0.0, t_hi = 0.0;
     int64_t n = 0, fk_stride = 0;
-    const void* ptr[15] = {};
+    const void* ptr[16] = {};
     bool operator==(const GraphKey& o) const {
         if (kind != o.kind || n_par != o.n_par || n_fits != o.n_fits || max_rounds != o.max_rounds ||
             tune != o.tune || t_lo != o.t_lo || t_hi != o.t_hi || n != o.n || fk_stride != o.fk_stride)
             return false;
-        for (int i = 0; i < 15; ++i)
+        for (int i = 0; i < 16; ++i)
             if (ptr[i] != o.ptr[i]) return false;
         return true;
     }
@@ -180,7 +180,7 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     init_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, theta_io_dev, c.states, c.theta_eval, c.active);
     if ((st = cuda_fail(cudaGetLastError(), "fit init")) != IPA_OK) return done(st);
 
-    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
     // one pass = tile map, constants, segmented NLL+grad, state update
     auto pass = [&](int k) -> ipa_status {
         ipa_status q;
@@ -207,9 +207,9 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     key.n = ev->n;
     key.fk_stride = ev->fk_stride;
     key.tune = tune_epoch();
-    const void* ptrs[15] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, sc->partials, sc->counters, sc->gcount,
-                            sc->work, sc->seg_tiles, sc->consts, c.states, c.seg_off, (const void*)s};
-    for (int i = 0; i < 15; ++i) key.ptr[i] = ptrs[i];
+    const void* ptrs[16] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->q, sc->partials, sc->counters,
+                            sc->gcount, sc->work, sc->seg_tiles, sc->consts, c.states, c.seg_off, (const void*)s};
+    for (int i = 0; i < 16; ++i) key.ptr[i] = ptrs[i];
 
     if (!(c.have_key && c.key == key)) {
         // Preferred: the whole minimisation as ONE graph launch.  A conditional

@@ -11,7 +11,16 @@ with mpmath and rounded once to double.
           k/2 (k = 0..12), each the degree-13 Chebyshev interpolant on
           [k/2 - 0.26, k/2 + 0.26] written as monomials in u = x - k/2.
 
-and the fixed-point tables and constants of the integer-pipe functions
+the coefficients of the Faddeeva function (faddeeva.cuh), Weideman's rational
+approximation (SIAM J. Numer. Anal. 31 (1994) 1497) with N = 40 and
+L = 2^(-1/4) sqrt(N):
+
+  a_n = (1/pi) int_0^pi psi(theta) cos(n theta) dtheta,  n = 1..N,
+  psi = exp(-t^2) (L^2 + t^2) at t = L tan(theta / 2),
+
+by the midpoint rule with 1024 nodes (psi is smooth and periodic, so the rule
+converges geometrically; 512 nodes give the same doubles), and
+the fixed-point tables and constants of the integer-pipe functions
 (int_math.cuh), each the exact value rounded once to an integer:
 
   sincos: round(sin(j pi/32) 2^62), round(cos(j pi/32) 2^62), j = 0..64;
@@ -88,6 +97,23 @@ def fmt(vals, per_line=3):
     return "\n".join(out)
 
 
+WEID_N = 40
+WEID_NODES = 1024
+
+
+def weideman(n_terms: int, nodes: int):
+    """L and the Fourier cosine coefficients a_1..a_N of psi (see the docstring)."""
+    L = mp.power(2, mp.mpf(-1) / 4) * mp.sqrt(n_terms)
+    th = [mp.pi * (k + mp.mpf(1) / 2) / nodes for k in range(nodes)]
+    psi = []
+    for t in th:
+        x = L * mp.tan(t / 2)
+        psi.append(mp.exp(-x * x) * (L * L + x * x))
+    # (1/pi) * (pi / nodes) * sum: the midpoint rule on (0, pi)
+    a = [mp.fsum(psi[k] * mp.cos(n * th[k]) for k in range(nodes)) / nodes for n in range(1, n_terms + 1)]
+    return L, a
+
+
 def main():
     exp_tab = [d(mp.power(2, mp.mpf(j) / 64)) for j in range(64)]
     ln2 = mp.log(2)
@@ -109,6 +135,9 @@ def main():
         c = mp.mpf(k) / 2
         coef = cheb_monomial(erfcx, c - ERFCX_HALF, c + ERFCX_HALF, ERFCX_DEG)
         erfcx_tab.extend(d(v) for v in coef)
+
+    weid_L, weid_a = weideman(WEID_N, WEID_NODES)
+    weid_a = [d(v) for v in weid_a]
 
     text = f"""// Generated by gen_fp64_tables.py (mpmath, 60 digits, rounded once to double
 // or to an integer).
@@ -185,6 +214,14 @@ __device__ const long long kExp2Q62[64] = {{
 // erfcx piece k (centre k/2): coefficients of u^0 .. u^{ERFCX_DEG}
 __device__ const double kErfcxTab[{ERFCX_PIECES * (ERFCX_DEG + 1)}] = {{
 {fmt(erfcx_tab, 2)}
+}};
+
+// Faddeeva function (faddeeva.cuh): Weideman's N = {WEID_N} coefficients a_1..a_N and L
+constexpr int kWeidN = {WEID_N};
+constexpr double kWeidL = {d(weid_L)!r};
+constexpr double kInvSqrtPi = {d(1 / mp.sqrt(mp.pi))!r};
+static __constant__ double kWeidA[{WEID_N}] = {{
+{fmt(weid_a)}
 }};
 
 }}  // namespace fp64tab

@@ -22,6 +22,11 @@ constexpr int kTile = IPA_TILE_EVENTS;
 constexpr int kGroupTiles = 32;
 constexpr int kBlock = 256;   // threads per block of the generator and helper kernels
 
+// Parameters of a model kind.
+__host__ __device__ constexpr int npar_of(int kind) {
+    return kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D : (kind == IPA_MODEL_TAGGED1D ? IPA_NPAR_TAGGED : IPA_NPAR_4D);
+}
+
 // Number of FP64 accumulators per tile.
 //   NLL only:   L = sum w log P
 //   1D + grad:  L, Q = sum w/P, S = sum (w/P) T, D_Gamma, D_sigma, D_mu
@@ -69,6 +74,7 @@ struct Cols {
     const double *t, *ck, *cl, *phi, *w;
     const double* fk = nullptr;   // cached angular basis (10 columns) or nullptr
     int64_t fk_stride = 0;
+    const double* q = nullptr;    // flavour tag (tagged model)
 };
 
 // ---- host-side helpers (runtime.cu) ----
@@ -99,6 +105,8 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out);
 // consts.cu: theta (n_seg x n_par) -> Consts[n_seg]
 ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out,
                          cudaStream_t s);
+// tagged.cu: the same for the tagged model (a TagConsts record in each slot)
+ipa_status launch_tag_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out, cudaStream_t s);
 
 // Launch geometry of the likelihood kernel (tune.cu picks it; no result
 // depends on it).
@@ -115,6 +123,11 @@ inline int64_t tile_estimate(int64_t n, int n_seg) {
 // Configuration for a launch over about `tiles` tiles (table entry of the
 // autotuner for this kernel variant and size, else the built-in default).
 LaunchCfg launch_cfg(int kind, bool grad, bool cached, bool segmented, int64_t tiles);
+// Blocks of a likelihood launch: cfg's resident warps per SM (or one tile take
+// per warp, ceil(takes / SMs)) in blocks of W warps, capped by `per_sm` resident
+// blocks per SM, and for one segment by the blocks that find a tile (tiles
+// taken K at a time).
+int64_t launch_grid(const LaunchCfg& cfg, int W, int K, int per_sm, int64_t tiles, bool single);
 // Incremented whenever a table entry changes (cached CUDA graphs that hold a
 // likelihood launch compare it to know when to re-capture).
 unsigned tune_epoch();
@@ -128,6 +141,14 @@ ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t s,
                       const LaunchCfg* cfg = nullptr);
+// tagged.cu: launch_nll for the tagged model
+ipa_status launch_tag_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
+                          const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
+                          const Consts* consts, Scratch* sc, double* out, cudaStream_t s, const LaunchCfg* cfg);
+// toygen.cu / tagged.cu: the tagged model's generator over consts[0]
+ipa_status launch_tag_toygen(const ModelDev& m, const Consts* consts, uint64_t seed, int n_toys,
+                             const int64_t* n_sig, const int64_t* n_bkg, const int64_t* offsets,
+                             const ipa_event_buffers* out, cudaStream_t s);
 // nll.cu: seg_tiles[s] = sum_{r<s} ceil(size_r / kTile), s = 0..n_seg, with the
 // ranges clamped to [0, n]; segments with active[r] == 0 get no tiles (active may
 // be NULL).

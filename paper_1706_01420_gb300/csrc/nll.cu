@@ -40,6 +40,7 @@
 #include "fp64_math.cuh"
 #include "int_math.cuh"
 #include "ipa_internal.cuh"
+#include "tile_reduce.cuh"
 
 namespace ipa {
 namespace {
@@ -120,61 +121,6 @@ __device__ __forceinline__ double2 gauss_erfcx(const Consts& c, double tau, cons
     return make_double2(g * X, zneg ? g : -g);
 }
 
-// t > c for any doubles with c not NaN (integer compare of order-preserving keys).
-__device__ __forceinline__ bool greater(double t, double c) {
-    const long long a = __double_as_longlong(t), b = __double_as_longlong(c);
-    const long long ka = a >= 0 ? a : (long long)(0x8000000000000000ull - (unsigned long long)a);
-    const long long kb = b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b);
-    return ka > kb;
-}
-
-// Position of the n-th (from 0) set bit of m; n < popc(m).
-__device__ __forceinline__ int nth_set(unsigned m, int n) {
-    int pos = 0;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const unsigned low = m & ((1u << w) - 1u);
-        const int cnt = __popc(low);
-        if (n >= cnt) {
-            n -= cnt;
-            m >>= w;
-            pos += w;
-        } else {
-            m = low;
-        }
-    }
-    return pos;
-}
-
-// P = m 2^e with m in [1, 2): *prod *= m and *esum += e, so that the log of the
-// product of a lane's P values is log(*prod) + *esum ln 2 (bit operations on
-// the integer pipe and one FP64 multiply per event instead of a log).  Zero,
-// subnormal, negative, infinite and NaN P give what the sum of logs gives:
-// -inf for +-0, the exact value for subnormals, +inf for +inf, NaN otherwise.
-__device__ __forceinline__ void log_mul(double P, double* prod, int* esum) {
-    const long long b = __double_as_longlong(P);
-    long long mb = (b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;
-    int e = (int)(b >> 52) - 1023;
-    if ((unsigned long long)(b - 0x0010000000000000ll) >= 0x7FE0000000000000ull) {
-        if (b > 0 && b < 0x0010000000000000ll) {
-            const int sh = __clzll(b) - 11;
-            mb = ((b << sh) & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll;
-            e = -1022 - sh;
-        } else {
-            mb = (b << 1) == 0 ? 0ll : (b == 0x7FF0000000000000ll ? b : 0x7FF8000000000000ll);
-            e = 0;
-        }
-    }
-    *prod *= __longlong_as_double(mb);
-    *esum += e;
-}
-
-// log(prod) + esum ln 2
-__device__ __forceinline__ double log_of(double prod, int esum, const MathTables* mt) {
-    const double ed = (double)esum;
-    return fma(ed, fp64tab::kLn2Hi, fma(ed, fp64tab::kLn2Lo, log_fast(prod, mt)));
-}
-
 // A' = sum_k hq_k f_k in FP64 (cached basis, or angles outside basis_q62_ok).
 __device__ __forceinline__ double amplitude_sum(const double* hq, const double* f) {
     double Ap = hq[0] * f[0];
@@ -229,73 +175,6 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
     }
 }
 
-// Butterfly reduction of NA accumulators over the 32 lanes of a warp (NA padded
-// to the power of two NP).  The first log2(NP) levels halve the values each
-// lane holds: at the level of lane bit j the lane keeps the half of its
-// values selected by that bit and adds the partner's copy of that half, so
-// every level costs NP / 2^(level+1) FP64 adds instead of NA.  The remaining
-// levels add the partner's value of the same accumulator.  Afterwards lane l
-// holds the full sum of accumulator acc_index<NA>(l) (two or more lanes hold
-// each, with identical bits: addition is commutative), in an order fixed by
-// the lane pairing.  NA = 15: 16 adds and 16 shuffles per warp instead of 75.
-template <int NA>
-struct Butterfly {
-    static constexpr int NP = NA <= 1 ? 1 : NA <= 2 ? 2 : NA <= 4 ? 4 : NA <= 8 ? 8 : 16;
-    static constexpr int SPLITS = NP == 1 ? 0 : NP == 2 ? 1 : NP == 4 ? 2 : NP == 8 ? 3 : 4;
-};
-
-template <int NA>
-__device__ __forceinline__ int acc_index(int lane) {
-    constexpr int S = Butterfly<NA>::SPLITS;
-    return (lane >> (5 - S)) & ((1 << S) - 1);
-}
-
-template <int NA>
-__device__ __forceinline__ double warp_butterfly(const double* acc, int lane) {
-    constexpr int NP = Butterfly<NA>::NP;
-    constexpr int S = Butterfly<NA>::SPLITS;
-    double v[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) v[a] = a < NA ? acc[a] : 0.0;
-#pragma unroll
-    for (int lev = 0; lev < S; ++lev) {
-        const int mask = 16 >> lev;
-        const int half = NP >> (lev + 1);
-        const bool upper = (lane & mask) != 0;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const double keep = upper ? v[i + half] : v[i];
-            const double give = upper ? v[i] : v[i + half];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, give, mask);
-        }
-    }
-#pragma unroll
-    for (int lev = S; lev < 5; ++lev) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16 >> lev);
-    return v[0];
-}
-
-// Every accumulator of a warp_butterfly result into acc[] of every lane.
-template <int NA>
-__device__ __forceinline__ void gather_butterfly(double v, double* acc) {
-    constexpr int S = Butterfly<NA>::SPLITS;
-#pragma unroll
-    for (int a = 0; a < NA; ++a) acc[a] = __shfl_sync(0xffffffffu, v, a << (5 - S));
-}
-
-__device__ __forceinline__ int64_t clamp_off(int64_t v, int64_t n) {
-    return v < 0 ? 0 : (v > n ? n : v);
-}
-
-// Segment s covers tiles [seg_tiles[s], seg_tiles[s+1]); find s for `tile`.
-__device__ __forceinline__ int find_segment(const int64_t* seg_tiles, int n_seg, int64_t tile) {
-    int lo = 0, hi = n_seg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(seg_tiles + mid) <= tile) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Write NLL (and gradient) of one segment from its reduced accumulators.
 // With S_k = sum r T f_k and SH = sum_k h_k S_k = sum r T A (A = 1 in 1D), and
 // D_j = sum r A dT/dtheta_j where
@@ -343,33 +222,6 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
     }
     for (int j = (KIND == IPA_MODEL_ANGTIME4D ? IPA_NPAR_4D : IPA_NPAR_1D) + lane; j < n_par; j += 32)
         out[1 + j] = 0.0;
-}
-
-// Reduce the tile partials of one group (lane l holds tile g0 + l) or, with
-// `stride` = kGroupTiles, the group partials of one segment (lane l adds groups
-// l, l+32, ... in that order), then the butterfly; returns this lane's share
-// (accumulator acc_index<NA>(lane)).
-template <int NA>
-__device__ __forceinline__ double reduce_partials(const double* partials, int64_t first, int64_t count,
-                                                  int64_t stride, int lane) {
-    double acc[NA];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) acc[a] = 0.0;
-#pragma unroll 4
-    for (int64_t i = lane; i < count; i += 32) {
-        const double* p = partials + (first + i * stride) * NA;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) acc[a] += __ldcg(p + a);
-    }
-    return warp_butterfly<NA>(acc, lane);
-}
-
-// Lanes whose butterfly share is the first copy of an accumulator store it.
-template <int NA>
-__device__ __forceinline__ void store_share(double v, int lane, double* dst) {
-    constexpr int S = Butterfly<NA>::SPLITS;
-    const int a = acc_index<NA>(lane);
-    if ((lane & ((1 << (5 - S)) - 1)) == 0 && a < NA) dst[a] = v;
 }
 
 // Blocks of any whole number of warps (1..kMaxWarps); each warp keeps a copy of
@@ -541,44 +393,14 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             }
             acc[0] += log_of(prod, esum, &mt);
             const double share = warp_butterfly<NA>(acc, lane);
-
-            // level 1: the warp that completes a group of kGroupTiles tiles
-            // reduces it into the partial slot of the group's first tile
-            const int64_t g0 = t0 + ((tile - t0) / kGroupTiles) * kGroupTiles;
-            const int64_t g1 = g0 + kGroupTiles < t1 ? g0 + kGroupTiles : t1;
-            int last = 0;
-            store_share<NA>(share, lane, partials + tile * NA);
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) last = atomicAdd(gcount + g0, 1u) + 1u == (unsigned)(g1 - g0);
-            if (!__shfl_sync(0xffffffffu, last, 0)) continue;
-            __threadfence();
-            const double gshare = reduce_partials<NA>(partials, g0, g1 - g0, 1, lane);
-            // level 2: the warp that completes a segment's last group adds the
-            // segment's group partials and writes its NLL and gradient
-            const int64_t n_groups = (t1 - t0 + kGroupTiles - 1) / kGroupTiles;
-            __syncwarp();   // every lane has read the group's tile partials
-            store_share<NA>(gshare, lane, partials + g0 * NA);
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) {
-                gcount[g0] = 0u;
-                last = atomicAdd(counters + seg, 1u) + 1u == (unsigned)n_groups;
-            }
-            if (!__shfl_sync(0xffffffffu, last, 0)) continue;
-            __threadfence();
-            gather_butterfly<NA>(reduce_partials<NA>(partials, t0, n_groups, kGroupTiles, lane), acc);
+            // the group and segment levels; the warp that completes the
+            // segment writes its NLL and gradient
+            if (!tile_commit<NA>(share, lane, tile, t0, t1, seg, partials, gcount, counters, acc)) continue;
             finalize<KIND, GRAD, CACHED>(wc.c, acc, n_par, out + (size_t)seg * out_stride, lane);
             if (lane == 0) counters[seg] = 0u;
         }
     }
-    if (lane == 0) {
-        const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
-        if (atomicAdd(work + 1, 1u) == n_warps - 1u) {
-            work[0] = 0u;
-            work[1] = 0u;
-        }
-    }
+    work_done(work, lane);
 }
 
 // seg_tiles[s] = sum_{r<s} tiles(r), tiles(r) = ceil(size_r / kTile) for an active
@@ -638,17 +460,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
             &v, nll_kernel<KIND, GRAD, CACHED, WEIGHTED>, 32 * W, smem);
         per_sm = e == cudaSuccess && v >= 1 ? v : 1;
     }
-    const int64_t sms = sm_count();
-    const int64_t units = (tiles + K - 1) / K;
-    int64_t want = cfg.warps_per_sm > 0 ? cfg.warps_per_sm : (units + sms - 1) / sms;
-    if (want > (int64_t)per_sm * W) want = (int64_t)per_sm * W;
-    if (want < 1) want = 1;
-    int64_t grid = sms * ((want + W - 1) / W);
-    if (single) {
-        const int64_t need = (units + W - 1) / W;   // blocks beyond this find no tile
-        grid = need < grid ? need : grid;
-    }
-    if (grid < 1) grid = 1;
+    const int64_t grid = launch_grid(cfg, W, K, per_sm, tiles, single);
     // programmatic dependent launch: blocks may start (and load their tables)
     // while the constants kernel that precedes every launch is still running
     cudaLaunchConfig_t lc = {};
@@ -691,6 +503,8 @@ ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t st, const LaunchCfg* cfg) {
     const int P = m.n_par;
+    if (m.kind == IPA_MODEL_TAGGED1D)
+        return launch_tag_nll(m, grad, cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, st, cfg);
     if (m.kind == IPA_MODEL_TIME1D)
         return grad ? launch_w<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
                     : launch_w<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
@@ -773,7 +587,7 @@ ipa_status run(const ipa_model* model, const ipa_events* ev, const int64_t* seg_
         if ((st = launch_seg_tiles(seg_off, seg_off + 1, nullptr, n_seg, ev->n, sc->seg_tiles, s)) != IPA_OK)
             return st;
     }
-    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
     return launch_nll(m, grad, cols, ev->n, seg_off, seg_off ? seg_off + 1 : nullptr,
                       seg_off ? sc->seg_tiles : nullptr, n_seg, sc->consts, sc, out, s);
 }

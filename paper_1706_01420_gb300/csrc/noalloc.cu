@@ -95,6 +95,6 @@ extern "C" ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_eve
         return st;
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     if ((st = launch_consts(m, theta_dev, 1, sc.consts, s)) != IPA_OK) return st;
-    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
     return launch_nll(m, true, cols, ev->n, nullptr, nullptr, nullptr, 1, sc.consts, &sc, out_dev, s);
 }

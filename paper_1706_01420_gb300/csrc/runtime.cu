@@ -59,11 +59,11 @@ ipa_status check_model(const ipa_model* m) {
         set_error("model is NULL");
         return IPA_ERR_ARG;
     }
-    if (m->kind != IPA_MODEL_TIME1D && m->kind != IPA_MODEL_ANGTIME4D) {
+    if (m->kind != IPA_MODEL_TIME1D && m->kind != IPA_MODEL_ANGTIME4D && m->kind != IPA_MODEL_TAGGED1D) {
         set_error("unknown model kind %d", m->kind);
         return IPA_ERR_ARG;
     }
-    const int want = m->kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D : IPA_NPAR_4D;
+    const int want = npar_of(m->kind);
     if (m->n_par != want) {
         set_error("model n_par %d, expected %d (use ipa_model_init)", m->n_par, want);
         return IPA_ERR_ARG;
@@ -87,9 +87,10 @@ ipa_status check_events(const ipa_model* m, const ipa_events* ev) {
         return IPA_ERR_ARG;
     }
     if (ev->n == 0) return IPA_OK;
-    const double* need[4] = {ev->t, ev->ck, ev->cl, ev->phi};
-    const int n_need = m->kind == IPA_MODEL_TIME1D ? 1 : 4;
-    const char* names[4] = {"t", "ck", "cl", "phi"};
+    const bool tag = m->kind == IPA_MODEL_TAGGED1D;
+    const double* need[4] = {ev->t, tag ? ev->q : ev->ck, ev->cl, ev->phi};
+    const int n_need = m->kind == IPA_MODEL_ANGTIME4D ? 4 : (tag ? 2 : 1);
+    const char* names[4] = {"t", tag ? "q" : "ck", "cl", "phi"};
     for (int i = 0; i < n_need; ++i) {
         if (!need[i]) {
             set_error("event column %s is NULL", names[i]);
@@ -204,7 +205,7 @@ extern "C" ipa_status ipa_model_init(ipa_model* m, int32_t kind, double t_lo, do
         ipa::set_error("model is NULL");
         return IPA_ERR_ARG;
     }
-    if (kind != IPA_MODEL_TIME1D && kind != IPA_MODEL_ANGTIME4D) {
+    if (kind != IPA_MODEL_TIME1D && kind != IPA_MODEL_ANGTIME4D && kind != IPA_MODEL_TAGGED1D) {
         ipa::set_error("unknown model kind %d", kind);
         return IPA_ERR_ARG;
     }
@@ -213,7 +214,7 @@ extern "C" ipa_status ipa_model_init(ipa_model* m, int32_t kind, double t_lo, do
         return IPA_ERR_ARG;
     }
     m->kind = kind;
-    m->n_par = kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D : IPA_NPAR_4D;
+    m->n_par = ipa::npar_of(kind);
     m->t_lo = t_lo;
     m->t_hi = t_hi;
     return IPA_OK;

@@ -134,6 +134,10 @@ void arena_free(ipa_server* s, int64_t off, int64_t n) {
     s->free_ranges[o] = l;
 }
 
+// Event columns kept in the arena besides the weights (arena[4]): t, then
+// ck, cl, phi (4D) or the tag q in arena[1] (tagged model).
+int arena_cols(int kind) { return kind == IPA_MODEL_ANGTIME4D ? 4 : (kind == IPA_MODEL_TAGGED1D ? 2 : 1); }
+
 // One pass over every slot (inactive slots have no tiles and are skipped).
 ipa_status server_pass(ipa_server* s) {
     const ModelDev m{s->model.kind, s->model.n_par, s->model.t_lo, s->model.t_hi};
@@ -143,8 +147,9 @@ ipa_status server_pass(ipa_server* s) {
         return q;
     if ((q = launch_consts(m, s->d_theta_eval, s->max_slots, s->sc.consts, s->stream)) != IPA_OK) return q;
     const bool four = s->model.kind == IPA_MODEL_ANGTIME4D;
+    const bool tag = s->model.kind == IPA_MODEL_TAGGED1D;
     const Cols cols{s->arena[0], four ? s->arena[1] : nullptr, four ? s->arena[2] : nullptr,
-                    four ? s->arena[3] : nullptr, s->arena[4]};
+                    four ? s->arena[3] : nullptr, s->arena[4], nullptr, 0, tag ? s->arena[1] : nullptr};
     if ((q = launch_nll(m, true, cols, s->arena_cap, s->d_begin, s->d_end, s->sc.seg_tiles, s->max_slots,
                         s->sc.consts, &s->sc, s->d_res, s->stream)) != IPA_OK)
         return q;
@@ -202,7 +207,7 @@ void worker_main(ipa_server* s) {
         }
         ipa_status st = IPA_OK;
         // upload admitted fits: events into the arena, spec and start point into the slot
-        const int n_cols = s->model.kind == IPA_MODEL_ANGTIME4D ? 4 : 1;
+        const int n_cols = arena_cols(s->model.kind);
         for (Request* r : admitted) {
             for (int c = 0; c < n_cols && st == IPA_OK; ++c) {
                 if (r->n > 0)
@@ -354,7 +359,7 @@ extern "C" ipa_status ipa_server_create(const ipa_model* model, size_t hbm_budge
     cudaGetDevice(&s->device);
     const int P = s->P;
     const size_t S = (size_t)max_slots;
-    const int n_cols = model->kind == IPA_MODEL_ANGTIME4D ? 4 : 1;
+    const int n_cols = arena_cols(model->kind);
     st = cuda_fail(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking), "server stream");
     for (int c = 0; c < 5 && st == IPA_OK; ++c)
         if (c < n_cols || c == 4) st = dalloc(&s->arena[c], (size_t)cap, "server arena");
@@ -435,8 +440,9 @@ extern "C" ipa_status ipa_serve_submit(ipa_server* s, const ipa_events* ev, cons
         return IPA_ERR_ARG;
     }
     // the events are copied, so any alignment is accepted
-    if (!ev || ev->n < 0 || (ev->n > 0 && (!ev->t || (s->model.kind == IPA_MODEL_ANGTIME4D &&
-                                                      (!ev->ck || !ev->cl || !ev->phi))))) {
+    if (!ev || ev->n < 0 ||
+        (ev->n > 0 && (!ev->t || (s->model.kind == IPA_MODEL_ANGTIME4D && (!ev->ck || !ev->cl || !ev->phi)) ||
+                       (s->model.kind == IPA_MODEL_TAGGED1D && !ev->q)))) {
         set_error("ipa_serve_submit: missing event columns or negative count");
         return IPA_ERR_ARG;
     }
@@ -454,8 +460,8 @@ extern "C" ipa_status ipa_serve_submit(ipa_server* s, const ipa_events* ev, cons
     for (int p = 0; p < s->P; ++p) r->theta0[p] = spec[p].value;
     r->n = ev->n;
     r->weighted = ev->w != nullptr;
-    const double* src[5] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w};
-    const int n_cols = s->model.kind == IPA_MODEL_ANGTIME4D ? 4 : 1;
+    const double* src[5] = {ev->t, s->model.kind == IPA_MODEL_TAGGED1D ? ev->q : ev->ck, ev->cl, ev->phi, ev->w};
+    const int n_cols = arena_cols(s->model.kind);
     for (int c = 0; c < 5; ++c) {
         if ((c >= n_cols && c != 4) || !src[c] || r->n == 0) continue;
         r->cols[c].resize((size_t)r->n);

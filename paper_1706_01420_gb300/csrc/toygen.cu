@@ -34,6 +34,7 @@
 
 #include "consts.cuh"
 #include "ipa_internal.cuh"
+#include "tagged.cuh"
 
 namespace ipa {
 namespace {
@@ -324,7 +325,82 @@ toygen_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, uint32
     }
 }
 
+// The tagged model: candidate j of toy k takes (t, u) from call 0 and the tag
+// from the first uniform of call 1 (q = +1 if u_q <= 1/2, else -1), and is
+// kept iff u M_S < S(t - mu, q), S evaluated in FP64 with the exact forms of
+// tagged.cuh (no filter: the FP64 test runs for every candidate).  Background
+// event i takes t and q from call 4.
+__global__ void __launch_bounds__(kBlock)
+toygen_tag_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, uint32_t k1, int n_toys,
+                  const int64_t* __restrict__ n_sig, const int64_t* __restrict__ n_bkg,
+                  const int64_t* __restrict__ offsets, int64_t capacity, double* __restrict__ ot,
+                  double* __restrict__ oq) {
+    __shared__ __align__(16) TagConsts c;
+    __shared__ int warp_sums[kBlock / 32];
+    {
+        const double* src = reinterpret_cast<const double*>(consts);
+        double* dst = reinterpret_cast<double*>(&c);
+        for (int i = threadIdx.x; i < kTagConstsDoubles; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const double span = __dsub_rn(m.t_hi, m.t_lo);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int toy = blockIdx.x; toy < n_toys; toy += gridDim.x) {
+        const int64_t ns = n_sig[toy], nb = n_bkg[toy], off = offsets[toy];
+        if (ns < 0 || nb < 0 || off < 0 || off + ns + nb > capacity) continue;   // skipped
+        const bool usable = isfinite(c.MS) && c.MS > 0.0 && isfinite(c.N) && c.N > 0.0;
+        const uint64_t budget = usable ? (uint64_t)ns * 65536ull + (1ull << 22) : 0ull;
+        int64_t got = 0;
+        uint64_t j0 = 0;
+        for (; got < ns && j0 < budget; j0 += kChunk) {
+            const uint64_t jt = j0 + (uint64_t)threadIdx.x * kPerThread;
+            unsigned mask = 0;
+#pragma unroll 1
+            for (int i = 0; i < kPerThread; ++i) {
+                const uint64_t j = jt + i;
+                const U4 a = draw(j, (uint32_t)toy, 0u, k0, k1);
+                const U4 b = draw(j, (uint32_t)toy, 1u, k0, k1);
+                const double t = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+                const double q = u01(b.x, b.y) <= 0.5 ? 1.0 : -1.0;
+                if (__dmul_rn(u01(a.z, a.w), c.MS) < tag_signal(c, t, q)) mask |= 1u << i;
+            }
+            int total;
+            const int before = block_exclusive_scan(__popc(mask), warp_sums, &total);
+            int rank = 0;
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int64_t pos = got + before + rank;
+                ++rank;
+                if (pos >= ns) break;
+                const uint64_t j = jt + i;
+                const U4 a = draw(j, (uint32_t)toy, 0u, k0, k1);
+                const U4 b = draw(j, (uint32_t)toy, 1u, k0, k1);
+                ot[off + pos] = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+                oq[off + pos] = u01(b.x, b.y) <= 0.5 ? 1.0 : -1.0;
+            }
+            got += total;
+        }
+        for (int64_t pos = got + threadIdx.x; pos < ns; pos += blockDim.x) ot[off + pos] = oq[off + pos] = nan;
+        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+            const U4 a = draw((uint64_t)i, (uint32_t)toy, 4u, k0, k1);
+            const int64_t pos = off + ns + i;
+            ot[pos] = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+            oq[pos] = u01(a.z, a.w) <= 0.5 ? 1.0 : -1.0;
+        }
+    }
+}
+
 }  // namespace
+
+ipa_status launch_tag_toygen(const ModelDev& m, const Consts* consts, uint64_t seed, int n_toys,
+                             const int64_t* n_sig, const int64_t* n_bkg, const int64_t* offsets,
+                             const ipa_event_buffers* out, cudaStream_t s) {
+    toygen_tag_kernel<<<n_toys, kBlock, 0, s>>>(m, consts, (uint32_t)seed, (uint32_t)(seed >> 32), n_toys, n_sig,
+                                                n_bkg, offsets, out->capacity, out->t, out->q);
+    return cuda_fail(cudaGetLastError(), "tagged toygen kernel launch");
+}
+
 }  // namespace ipa
 
 extern "C" ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev, uint64_t seed,
@@ -348,11 +424,17 @@ extern "C" ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev
         set_error("ipa_toygen: the 4D model needs ck, cl and phi output columns");
         return IPA_ERR_ARG;
     }
+    const bool tag = model->kind == IPA_MODEL_TAGGED1D;
+    if (tag && !out->q) {
+        set_error("ipa_toygen: the tagged model needs a q output column");
+        return IPA_ERR_ARG;
+    }
     Scratch* sc = nullptr;
     if ((st = scratch_get(1, 2, &sc)) != IPA_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     if ((st = launch_consts(m, theta_dev, 1, sc->consts, s)) != IPA_OK) return st;
+    if (tag) return launch_tag_toygen(m, sc->consts, seed, n_toys, n_sig_dev, n_bkg_dev, offsets_dev, out, s);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int grid = n_toys;
     if (four)

@@ -61,6 +61,20 @@ void to_public(const LaunchCfg& c, float ms, ipa_launch_config* p) {
 
 }  // namespace
 
+int64_t launch_grid(const LaunchCfg& cfg, int W, int K, int per_sm, int64_t tiles, bool single) {
+    const int64_t sms = sm_count();
+    const int64_t units = (tiles + K - 1) / K;
+    int64_t want = cfg.warps_per_sm > 0 ? cfg.warps_per_sm : (units + sms - 1) / sms;
+    if (want > (int64_t)per_sm * W) want = (int64_t)per_sm * W;
+    if (want < 1) want = 1;
+    int64_t grid = sms * ((want + W - 1) / W);
+    if (single) {
+        const int64_t need = (units + W - 1) / W;   // blocks beyond this find no tile
+        grid = need < grid ? need : grid;
+    }
+    return grid < 1 ? 1 : grid;
+}
+
 LaunchCfg launch_cfg(int kind, bool grad, bool cached, bool segmented, int64_t tiles) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const auto& t = g_table[device()];
@@ -150,7 +164,7 @@ extern "C" ipa_status ipa_autotune(const ipa_model* model, const ipa_events* ev,
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride};
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
     const int64_t* b = seg_off_dev;
     const int64_t* e = seg_off_dev ? seg_off_dev + 1 : nullptr;
     st = launch_consts(m, theta_dev, n_seg, sc->consts, s);

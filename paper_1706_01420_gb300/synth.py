@@ -17,6 +17,9 @@ Recipes (all FP64, structure-of-arrays, one numpy Generator per call):
   uniform on [-pi, pi] (the flat-acceptance ranges of the helicity angles).
   Events distributed like the full angular PDF come from the toy generator
   instead (``ipa_toygen`` on the GPU, the oracle's generator on the CPU).
+* flavour tags (tagged model): ``q = +1`` or ``-1`` with probability 1/2 each,
+  independent of the time (a tag-blind sample; tagged samples distributed like
+  the model come from the generators, as for the angles).
 * weights: ``Normal(1, 0.2)``, the per-event weights of the serving workload.
 * toy sizes: ``N_k ~ Poisson(mean)`` per toy, then ``n_bkg ~ Binomial(N_k,
   f_b)``; the split is drawn on the host, as Example 5 of the paper advises
@@ -77,6 +80,23 @@ def events_4d(n: int, seed: int = 0, t_lo: float = 0.0, t_hi: float = 15.0,
     cl = rng.uniform(-1.0, 1.0, n)
     phi = rng.uniform(-math.pi, math.pi, n)
     cols = {"t": t, "ck": ck, "cl": cl, "phi": phi}
+    if weighted:
+        cols["w"] = weights(n, seed + 7919)
+    return cols
+
+
+TRUTH_TAGGED = {"Gamma": 0.66, "sigma": 0.045, "mu": 0.0, "f_b": 0.1,
+                "DG": 0.085, "Dm": 17.77, "phi_s": 0.8, "omega": 0.3}
+
+
+def events_tagged(n: int, seed: int = 0, t_lo: float = 0.0, t_hi: float = 15.0,
+                  truth: dict | None = None, weighted: bool = False) -> dict:
+    """SoA columns t, q (and w) for the flavour-tagged workload."""
+    p = dict(TRUTH_TAGGED if truth is None else truth)
+    rng = np.random.default_rng(seed)
+    t = _times(rng, n, t_lo, t_hi, p["Gamma"], p["sigma"], p["mu"], p["f_b"])
+    q = np.where(rng.random(n) < 0.5, 1.0, -1.0)
+    cols = {"t": t, "q": q}
     if weighted:
         cols["w"] = weights(n, seed + 7919)
     return cols
