@@ -15,7 +15,10 @@ Also reported on the same JSON line:
   roofline      FP64-pipe roofline of the fused kernel (bound "alu");
   cpu_baseline  the CPU oracle on a bounded sample of the same workload;
   fit / toygen / batch   full fit of the 1e6-event sample, 4D toy generation
-                of the 4096-toy batch, batched toy fits vs one-fit-at-a-time.
+                of the 4096-toy batch, batched toy fits vs one-fit-at-a-time;
+  large / serve large weighted event sets, the fit server under load;
+  tagged        the flavour-tagged model with B_s oscillation (1e6 events):
+                NLL+grad rate and roofline, generator, batched fits, CPU oracle.
 
 `--impl reference` times the CPU oracle on the same workload and metric.
 Multi-GPU (torchrun): every rank runs an independent replica (the path is one
@@ -75,6 +78,27 @@ OPS_LANE_TILE = {"fma": 2, "log_fast": 1}
 # each charged its measured cost: the FP64 work the kernel avoids by moving
 # functions to the integer pipe and by the algebra above.
 OPS_LIBRARY_4D = {"fma": 32, "mul": 30, "add": 6, "exp": 2, "erfc": 1, "log": 1, "sincos": 1, "sqrt": 1, "rcp": 1}
+
+
+# The flavour-tagged model (IPA_MODEL_TAGGED1D, tagged.cu), counted the same way:
+#   every event: tau, three exponents (integer-pipe exp), the oscillation phase
+#     and its sine/cosine (table-driven FP64), 2 gH, 2 gL, 2 g (complex), q qD
+#     and P, 1/P, and the 12 adjoint sums;
+#   events with t <= tcut (mu + max(Gamma_H, Gamma_L, Gamma) sigma^2 +
+#     sqrt(39.1 + (Dm sigma)^2 / 2) sqrt2 sigma): the Gaussian's exponent, three
+#     erfc arguments, two erfcx and the Faddeeva function (39 complex Horner
+#     steps, one division), and the five products stored for the event.
+OPS_TAG_EVENT = {"fma": 17, "mul": 8, "add": 9, "sincos_fast": 1}
+OPS_TAG_SLOW = {"fma": 125, "mul": 58, "add": 5, "erfcx_poly": 2, "rcp": 1}
+TH_TAG = np.array([0.66, 0.045, 0.0, 0.1, 0.085, 17.77, 0.8, 0.3])
+
+
+def tag_slow_fraction(t, theta) -> float:
+    Gamma, sigma, mu, _, DG, Dm = (float(v) for v in theta[:6])
+    rmax = max(Gamma - DG / 2, Gamma + DG / 2, Gamma)
+    beta = Dm * sigma / math.sqrt(2.0)
+    tcut = mu + rmax * sigma * sigma + math.sqrt(39.1 + beta * beta) * math.sqrt(2.0) * sigma
+    return float(np.mean(np.asarray(t) <= tcut))
 
 
 def _flops(ops: dict, cal: dict) -> float:
@@ -249,9 +273,20 @@ def cpu_baseline(budget_s: float = 12.0) -> dict:
         O.nll_grad(model, cols, TH4)
         reps += 1
     dt = time.perf_counter() - t0
+    # the tagged model's oracle on 2e4 events (about a second)
+    from oracle import tagged as T
+    cols_t = synth.events_tagged(20_000, 0)
+    model_t = O.Model("tag", 0.0, 15.0)
+    reps_t, t1 = 0, time.perf_counter()
+    while reps_t == 0 or time.perf_counter() - t1 < 1.0:
+        T.nll_grad(model_t, cols_t, TH_TAG)
+        reps_t += 1
+    dt_t = time.perf_counter() - t1
     return {"value": n * reps / dt / 1e9, "unit": "Gevents/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} NLL+grad passes over {n} events of the 4D workload "
-                      f"({dt:.1f} s, numpy/scipy FP64, single thread)"}
+                      f"({dt:.1f} s, numpy/scipy FP64, single thread)",
+            "tagged": {"value": 20_000 * reps_t / dt_t / 1e9, "unit": "Gevents/s",
+                       "sample": f"{reps_t} NLL+grad passes over 20000 events of the tagged workload"}}
 
 
 def main():
@@ -264,9 +299,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="untimed: 4 ipa_nll_grad calls on 8e6 4D events (256 MB, > L2), for ncu")
+    ap.add_argument("--profile-case-tagged", action="store_true",
+                    help="untimed: 4 ipa_nll_grad calls on 8e6 tagged events (128 MB, > L2), for ncu")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
+    if args.profile_case_tagged:
+        return profile_case_tagged()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -386,7 +425,7 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(api, synth, torch, dev, m, ev, theta)
+        extras = run_extras(api, synth, torch, dev, m, ev, theta, cal)
 
     clocks = clk.summary()
     line = {
@@ -467,7 +506,25 @@ def profile_case() -> int:
     return 0
 
 
-def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
+def profile_case_tagged() -> int:
+    """The tagged model's small fixed case for Nsight Compute (inputs larger than L2)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1706_01420_gb300 import api, synth
+    n = 8_000_000
+    ev = {k: torch.tensor(v, device="cuda") for k, v in synth.events_tagged(n, 3).items()}
+    m = api.model_tagged(0.0, 15.0)
+    theta = torch.tensor(TH_TAG, device="cuda")
+    for _ in range(4):
+        out = api.ipa_nll_grad(m, ev, theta)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "ipa_nll_grad tagged", "events": n, "nll": float(out[0]),
+                      "slow_fraction": tag_slow_fraction(ev["t"].cpu().numpy(), TH_TAG)}))
+    return 0
+
+
+def run_extras(api, synth, torch, dev, m, ev, theta, cal) -> dict:
     """Fit of the 1e6 sample, 4096-toy generation, batched vs one-at-a-time toy fits."""
     out = {}
     lo = [0.3, 0.01, -0.1, 0.0, 0.2, 0.05, 0.0, 0.0, 0.0, -3.2]
@@ -551,7 +608,87 @@ def run_extras(api, synth, torch, dev, m, ev, theta) -> dict:
     del cols, rb, thb
     out["large"] = run_large(api, synth, torch, dev, m, theta, params)
     out["serve"] = run_serve(api, synth, torch, dev, m, theta, params)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out["tagged"] = run_tagged(api, synth, torch, dev, cal, flush)
     return out
+
+
+def run_tagged(api, synth, torch, dev, cal, flush, steps: int = 50) -> dict:
+    """The flavour-tagged model with B_s oscillation: 1e6 events of its PDF (50
+    toys of 2e4 from ipa_toygen, timed), NLL+grad per step with L2 flushed, its
+    FP64-pipe roofline, and batched fits of the 50 toys (omega held).  The CPU
+    oracle's rate on this model is part of cpu_baseline."""
+    m = api.model_tagged(0.0, 15.0)
+    theta = torch.tensor(TH_TAG, device=dev)
+    d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
+    n_toys, per = 50, 20000
+    n_bkg = np.full(n_toys, per // 10, dtype=np.int64)
+    n_sig = np.full(n_toys, per, dtype=np.int64) - n_bkg
+    off = np.arange(n_toys + 1, dtype=np.int64) * per
+    n = n_toys * per
+    ev = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in ("t", "q")}
+    api.ipa_toygen(m, theta, 7, d64(n_sig[:2]), d64(n_bkg[:2]), d64(off[:2]), ev)   # warm-up
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    api.ipa_toygen(m, theta, 7, d64(n_sig), d64(n_bkg), d64(off[:-1]), ev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    toygen_s = e0.elapsed_time(e1) * 1e-3
+    picked = api.ipa_autotune(m, ev, theta, grad=True, stream=stream)
+    out = torch.empty(9, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        api.ipa_nll_grad(m, ev, theta, out)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        api.ipa_nll_grad(m, ev, theta, out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    cons = []
+    empty = {"t": ev["t"][:0], "q": ev["q"][:0]}
+    for i in range(20):
+        flush.fill_(float(i))
+        e0.record(stream)
+        api.ipa_nll(m, empty, theta, out)                 # constants kernel only (n = 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cons.append(e0.elapsed_time(e1))
+    kernel_ms = max(ms - statistics.median(cons), 1e-6)
+    t_h = ev["t"].cpu().numpy()
+    slow = tag_slow_fraction(t_h, TH_TAG)
+    spe = (_slots(OPS_TAG_EVENT, cal) + slow * _slots(OPS_TAG_SLOW, cal) + _slots(OPS_UNWEIGHTED, cal)
+           + _slots(OPS_LANE_TILE, cal) / 16.0)
+    peak = 2.0 * 152 * 2070e6
+    ops = spe * n / (kernel_ms * 1e-3)
+    # batched fits of the 50 toys: Gamma, f_b, DG, Dm, phi_s free; sigma, mu, omega held
+    lo = [0.3, 0.01, -0.1, 0.0, -0.5, 10.0, -3.1, 0.0]
+    hi = [1.5, 0.2, 0.1, 0.5, 0.5, 25.0, 3.1, 0.5]
+    step = [0.01, 0.003, 0.002, 0.005, 0.02, 0.05, 0.1, 0.01]
+    free = (0, 3, 4, 5, 6)
+    params = [api.Param(float(TH_TAG[i]), lo[i], hi[i], step[i], fixed=i not in free) for i in range(8)]
+    thb = torch.tensor(np.tile(TH_TAG, (n_toys, 1)), device=dev)
+    api.ipa_fit_batch(m, ev, d64(off[:3]), params, thb[:2].clone(), max_iter=200, tol=1e-8)   # graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = api.ipa_fit_batch(m, ev, d64(off), params, thb, max_iter=200, tol=1e-8)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    st = r["status"].cpu().numpy()
+    return {"workload": "flavour-tagged decay time with B_s oscillation, 1e6 FP64 SoA events (t, q), "
+                        "8 params, ipa_nll_grad", "events": n, "launch": picked,
+            "nll_grad_ms": ms, "Gevents_per_s": n / (ms * 1e-3) / 1e9, "kernel_ms": kernel_ms,
+            "slow_fraction": slow, "fp64_ops_per_event": spe,
+            "roofline": {"bound": "alu", "achieved": ops / 1e9, "peak": peak / 1e9, "unit": "G FP64 op/s",
+                         "frac": ops / peak, "kernel": "tag_kernel<grad>"},
+            "toygen": {"toys": n_toys, "events": n, "s": toygen_s, "Mevents_per_s": n / toygen_s / 1e6},
+            "batch_fit": {"toys": n_toys, "s": fit_s, "fits_per_s": n_toys / fit_s,
+                          "status_counts": np.bincount(st, minlength=5).tolist(),
+                          "passes_mean": float(r["passes"].float().mean())}}
 
 
 def run_serve(api, synth, torch, dev, m, theta, params, n_req: int = 60,
