@@ -42,17 +42,19 @@ __global__ void continue_kernel(cudaGraphConditionalHandle handle, const int* n_
 // the last call: a graph reads only workspace and scratch buffers and the event
 // columns, so consecutive fits of the same event set (one toy after another)
 // reuse it without capturing again.
+constexpr int kKeyPtrs = 18;
 struct GraphKey {
-    int kind = 0, n_par = 0, n_fits = 0, max_rounds = 0;
+    int kind = 0, n_par = 0, n_fits = 0, max_rounds = 0, spec_stride = 0;
     unsigned tune = 0;             // launch-geometry table version the graph was captured with
     double t_lo = 0.0, t_hi = 0.0;
     int64_t n = 0, fk_stride = 0;
-    const void* ptr[16] = {};
+    const void* ptr[kKeyPtrs] = {};
     bool operator==(const GraphKey& o) const {
         if (kind != o.kind || n_par != o.n_par || n_fits != o.n_fits || max_rounds != o.max_rounds ||
-            tune != o.tune || t_lo != o.t_lo || t_hi != o.t_hi || n != o.n || fk_stride != o.fk_stride)
+            spec_stride != o.spec_stride || tune != o.tune || t_lo != o.t_lo || t_hi != o.t_hi || n != o.n ||
+            fk_stride != o.fk_stride)
             return false;
-        for (int i = 0; i < 16; ++i)
+        for (int i = 0; i < kKeyPtrs; ++i)
             if (ptr[i] != o.ptr[i]) return false;
         return true;
     }
@@ -61,12 +63,10 @@ struct GraphKey {
 struct FitContext {
     std::mutex mu;
     int cap = 0;                   // fits the buffers hold
-    Spec* spec = nullptr;
     State* states = nullptr;
     double* theta_eval = nullptr;
     double* res = nullptr;
     int* active = nullptr;
-    int64_t* seg_off = nullptr;
     int* nact = nullptr;           // kGraphSteps pass counts + the loop-body counter
     int* h_nact = nullptr;         // pinned copy of the pass counts (host-loop fallback)
     cudaEvent_t order = nullptr;
@@ -99,7 +99,6 @@ ipa_status ensure_capacity(FitContext& c, int n_fits, int P) {
     }
     if (!c.nact) {
         ipa_status st = cuda_fail(cudaMalloc(&c.nact, sizeof(int) * (kGraphSteps + 1)), "fit count");
-        if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.spec, sizeof(Spec)), "fit spec");
         if (st == IPA_OK) st = cuda_fail(cudaMallocHost(&c.h_nact, sizeof(int) * kGraphSteps), "pinned count");
         if (st != IPA_OK) return st;
     }
@@ -112,87 +111,101 @@ ipa_status ensure_capacity(FitContext& c, int n_fits, int P) {
     cudaFree(c.theta_eval);
     cudaFree(c.res);
     cudaFree(c.active);
-    cudaFree(c.seg_off);
     c.states = nullptr;
     c.theta_eval = c.res = nullptr;
     c.active = nullptr;
-    c.seg_off = nullptr;
     c.cap = 0;
     const size_t n = (size_t)cap;
     ipa_status st = cuda_fail(cudaMalloc(&c.states, sizeof(State) * n), "fit state");
     if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.theta_eval, sizeof(double) * n * kMaxP), "fit theta");
     if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.res, sizeof(double) * n * (1 + kMaxP)), "fit results");
     if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.active, sizeof(int) * n), "fit mask");
-    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.seg_off, sizeof(int64_t) * (n + 1)), "fit offsets");
     if (st == IPA_OK) c.cap = cap;
     (void)P;
     return st;
 }
 
-}  // namespace
-}  // namespace ipa
+// ipa_fit_batch's specification and offsets in device memory (per device,
+// grow-only; the mutex spans a whole call).
+struct BatchArgs {
+    std::mutex mu;
+    Spec* spec = nullptr;
+    int64_t* seg_off = nullptr;
+    int cap = 0;
+};
 
-extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev,
-                                    const int64_t* seg_off_dev, int32_t n_fits, const ipa_param* spec,
-                                    double* theta_io_dev, double* err_out_dev, double* nll_out_dev,
-                                    int32_t* fit_status_dev, int32_t* iters_out_dev,
-                                    int32_t* passes_out_dev, int32_t max_iter, double tol, void* stream) {
-    using namespace ipa;
-    ipa_status st = check_model(model);
-    if (st != IPA_OK) return st;
-    if ((st = check_events(model, ev)) != IPA_OK) return st;
-    if (n_fits < 1 || !seg_off_dev || !spec || !theta_io_dev || max_iter < 1 || !(tol > 0.0)) {
-        set_error("ipa_fit_batch: bad arguments");
-        return IPA_ERR_ARG;
+BatchArgs* batch_args_of_device() {
+    static BatchArgs args[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    return &args[dev];
+}
+
+// Grow the arguments buffer to n_fits fits (the caller holds a.mu).
+ipa_status batch_args_reserve(BatchArgs& a, int n_fits) {
+    if (!a.spec && cudaMalloc(&a.spec, sizeof(Spec)) != cudaSuccess) {
+        a.spec = nullptr;
+        set_error("fit spec allocation failed");
+        return IPA_ERR_OOM;
     }
-    Spec sp{};
-    if ((st = build_spec(model, spec, max_iter, tol, &sp)) != IPA_OK) return st;
+    if (n_fits <= a.cap) return IPA_OK;
+    int cap = a.cap ? a.cap : 64;
+    while (cap < n_fits) cap *= 2;
+    cudaDeviceSynchronize();
+    cudaFree(a.seg_off);
+    a.seg_off = nullptr;
+    a.cap = 0;
+    ipa_status st = cuda_fail(cudaMalloc(&a.seg_off, sizeof(int64_t) * ((size_t)cap + 1)), "fit offsets");
+    if (st == IPA_OK) a.cap = cap;
+    return st;
+}
 
+}  // namespace
+
+ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, const int64_t* begin,
+                   const int64_t* end, const Spec* specs, int spec_stride, int max_passes, int64_t tiles_bound,
+                   double* theta_io_dev, double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
+                   int32_t* iters_out_dev, int32_t* passes_out_dev, cudaStream_t user) {
     // The fit runs on a library stream (capturable even when the caller passes the
     // legacy default stream), ordered after the caller's stream by an event.
-    cudaStream_t user = static_cast<cudaStream_t>(stream);
     cudaStream_t s = fit_stream();
     FitContext* cp = fit_context();
     if (!s || !cp) return IPA_ERR_CUDA;
     FitContext& c = *cp;
     std::lock_guard<std::mutex> lk(c.mu);      // one fit call per device at a time
+    ipa_status st;
     if ((st = ensure_capacity(c, n_fits, model->n_par)) != IPA_OK) return st;
     cudaEventRecord(c.order, user);
     cudaStreamWaitEvent(s, c.order, 0);
 
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     Scratch* sc = nullptr;
-    if ((st = scratch_get((ev->n + kTile - 1) / kTile + n_fits, n_fits + 1, &sc)) != IPA_OK) return st;
+    if ((st = scratch_get(tiles_bound, n_fits + 1, &sc)) != IPA_OK) return st;
     int* n_active = c.nact;
     int* d_rounds = c.nact + kGraphSteps;
-    const int max_rounds = (sp.max_passes + kGraphSteps - 1) / kGraphSteps + 2;
+    const int max_rounds = (max_passes + kGraphSteps - 1) / kGraphSteps + 2;
     auto done = [&](ipa_status r) -> ipa_status {
         cudaStreamSynchronize(s);
         return r;
     };
 
     const int fb = 128, fg = (n_fits + fb - 1) / fb;
-    if ((st = cuda_fail(cudaMemcpyAsync(c.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s), "fit spec copy")) != IPA_OK)
-        return done(st);
-    if ((st = cuda_fail(cudaMemcpyAsync(c.seg_off, seg_off_dev, sizeof(int64_t) * (n_fits + 1),
-                                        cudaMemcpyDeviceToDevice, s), "fit offsets copy")) != IPA_OK)
-        return done(st);
-    init_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, theta_io_dev, c.states, c.theta_eval, c.active);
+    init_kernel<<<fg, fb, 0, s>>>(specs, spec_stride, n_fits, theta_io_dev, c.states, c.theta_eval, c.active);
     if ((st = cuda_fail(cudaGetLastError(), "fit init")) != IPA_OK) return done(st);
 
     const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
     // one pass = tile map, constants, segmented NLL+grad, state update
     auto pass = [&](int k) -> ipa_status {
         ipa_status q;
-        if ((q = launch_seg_tiles(c.seg_off, c.seg_off + 1, c.active, n_fits, ev->n, sc->seg_tiles, s)) != IPA_OK)
+        if ((q = launch_seg_tiles(begin, end, c.active, n_fits, ev->n, sc->seg_tiles, s)) != IPA_OK)
             return q;
         if ((q = launch_consts(m, c.theta_eval, n_fits, sc->consts, s)) != IPA_OK) return q;
-        if ((q = launch_nll(m, true, cols, ev->n, c.seg_off, c.seg_off + 1, sc->seg_tiles, n_fits,
-                            sc->consts, sc, c.res, s)) != IPA_OK)
+        if ((q = launch_nll(m, true, cols, ev->n, begin, end, sc->seg_tiles, n_fits, sc->consts, sc, c.res, s)) !=
+            IPA_OK)
             return q;
         if ((q = cuda_fail(cudaMemsetAsync(n_active + k, 0, sizeof(int), s), "fit count reset")) != IPA_OK)
             return q;
-        qn_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, c.seg_off, c.seg_off + 1, c.res, c.states, c.theta_eval,
+        qn_kernel<<<fg, fb, 0, s>>>(specs, spec_stride, n_fits, begin, end, c.res, c.states, c.theta_eval,
                                     c.active, n_active + k);
         return cuda_fail(cudaGetLastError(), "fit step");
     };
@@ -202,15 +215,16 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
     key.n_par = m.n_par;
     key.n_fits = n_fits;
     key.max_rounds = max_rounds;
+    key.spec_stride = spec_stride;
     key.t_lo = m.t_lo;
     key.t_hi = m.t_hi;
     key.n = ev->n;
     key.fk_stride = ev->fk_stride;
     key.tune = tune_epoch();
-    const void* ptrs[16] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->q, sc->partials, sc->counters,
-                            sc->gcount, sc->work, sc->seg_tiles, sc->consts, c.states, c.seg_off, (const void*)s};
-    for (int i = 0; i < 16; ++i) key.ptr[i] = ptrs[i];
-
+    const void* ptrs[kKeyPtrs] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->q, sc->partials, sc->counters,
+                                  sc->gcount, sc->work, sc->seg_tiles, sc->consts, c.states, begin, end, specs,
+                                  (const void*)s};
+    for (int i = 0; i < kKeyPtrs; ++i) key.ptr[i] = ptrs[i];
     if (!(c.have_key && c.key == key)) {
         // Preferred: the whole minimisation as ONE graph launch.  A conditional
         // WHILE node repeats a body of kGraphSteps passes; the last kernel of the
@@ -283,13 +297,50 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
         }
     }
     if (st != IPA_OK) return done(st);
-    final_kernel<<<fg, fb, 0, s>>>(c.spec, 0, n_fits, c.states, theta_io_dev, err_out_dev, nll_out_dev,
+    final_kernel<<<fg, fb, 0, s>>>(specs, spec_stride, n_fits, c.states, theta_io_dev, err_out_dev, nll_out_dev,
                                    fit_status_dev, iters_out_dev, passes_out_dev);
     st = cuda_fail(cudaGetLastError(), "fit final");
     st = done(st);
     if (st == IPA_OK) st = cuda_fail(cudaGetLastError(), "fit final sync");
-    trace("{\"call\": \"ipa_fit_batch\", \"n_fits\": %d, \"events\": %lld, \"loop\": \"%s\"}", n_fits,
+    trace("{\"call\": \"fit_run\", \"n_fits\": %d, \"events\": %lld, \"loop\": \"%s\"}", n_fits,
           (long long)ev->n, c.one_launch && c.exec ? "device" : "host");
     // later work on the caller's stream sees the results: the call is blocking
+    return st;
+}
+
+}  // namespace ipa
+
+extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev,
+                                    const int64_t* seg_off_dev, int32_t n_fits, const ipa_param* spec,
+                                    double* theta_io_dev, double* err_out_dev, double* nll_out_dev,
+                                    int32_t* fit_status_dev, int32_t* iters_out_dev,
+                                    int32_t* passes_out_dev, int32_t max_iter, double tol, void* stream) {
+    using namespace ipa;
+    ipa_status st = check_model(model);
+    if (st != IPA_OK) return st;
+    if ((st = check_events(model, ev)) != IPA_OK) return st;
+    if (n_fits < 1 || !seg_off_dev || !spec || !theta_io_dev || max_iter < 1 || !(tol > 0.0)) {
+        set_error("ipa_fit_batch: bad arguments");
+        return IPA_ERR_ARG;
+    }
+    Spec sp{};
+    if ((st = build_spec(model, spec, max_iter, tol, &sp)) != IPA_OK) return st;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    BatchArgs* ap = batch_args_of_device();
+    if (!ap) return IPA_ERR_CUDA;
+    BatchArgs& a = *ap;
+    std::lock_guard<std::mutex> lk(a.mu);
+    if ((st = batch_args_reserve(a, n_fits)) != IPA_OK) return st;
+    // the specification and the offsets, in library buffers ordered on the caller's stream
+    if ((st = cuda_fail(cudaMemcpyAsync(a.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, user),
+                        "fit spec copy")) != IPA_OK)
+        return st;
+    if ((st = cuda_fail(cudaMemcpyAsync(a.seg_off, seg_off_dev, sizeof(int64_t) * (n_fits + 1),
+                                        cudaMemcpyDeviceToDevice, user), "fit offsets copy")) != IPA_OK)
+        return st;
+    st = fit_run(model, ev, n_fits, a.seg_off, a.seg_off + 1, a.spec, 0, sp.max_passes,
+                 (ev->n + kTile - 1) / kTile + n_fits, theta_io_dev, err_out_dev, nll_out_dev, fit_status_dev,
+                 iters_out_dev, passes_out_dev, user);
+    trace("{\"call\": \"ipa_fit_batch\", \"n_fits\": %d, \"events\": %lld}", n_fits, (long long)ev->n);
     return st;
 }

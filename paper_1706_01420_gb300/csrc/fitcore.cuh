@@ -25,7 +25,6 @@
 #include "ipa_internal.cuh"
 
 namespace ipa {
-namespace {
 
 constexpr int kMaxP = 10;          // parameters of the largest model
 constexpr double kSwitch = 1e-3;   // BFGS -> finite-difference Newton (decrement, sigma units)
@@ -53,6 +52,21 @@ struct State {
     double f, gd, alpha;
     int phase, iter, passes, hess_j, newton, status, scaled, onesided, rehess;
 };
+
+// fit.cu: run n_fits fits to the end.  Fit i minimises the NLL of events
+// [begin[i], end[i]) with specs[i * spec_stride] (device arrays the caller
+// keeps unchanged until the call returns; ranges may overlap, e.g. several
+// fits of the same events with different fixed parameters), starting at
+// theta_io[i] (n_par values, device) and writing the result back there;
+// err, nll, status, iters, passes as in ipa_fit_batch (device, may be NULL).
+// tiles_bound >= the sum over fits of their 512-event tiles.  Ordered after
+// the caller's `stream`; blocks until the fits end.
+ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, const int64_t* begin,
+                   const int64_t* end, const Spec* specs, int spec_stride, int max_passes, int64_t tiles_bound,
+                   double* theta_io, double* err, double* nll, int32_t* status, int32_t* iters, int32_t* passes,
+                   cudaStream_t stream);
+
+namespace {
 
 __device__ inline double clampd(double v, double lo, double hi) { return fmin(fmax(v, lo), hi); }
 
