@@ -605,6 +605,7 @@ def run_extras(api, synth, torch, dev, m, ev, theta, cal) -> dict:
                     "converged": int(ok.sum()), "status_counts": np.bincount(st, minlength=5).tolist(),
                     "pull_mean_width": pulls}
     out["autotuned"] = tune
+    out["errors"] = run_errors(api, torch, dev, m, cols, off, params, rb)
     del cols, rb, thb
     out["large"] = run_large(api, synth, torch, dev, m, theta, params)
     out["serve"] = run_serve(api, synth, torch, dev, m, theta, params)
@@ -689,6 +690,37 @@ def run_tagged(api, synth, torch, dev, cal, flush, steps: int = 50) -> dict:
             "batch_fit": {"toys": n_toys, "s": fit_s, "fits_per_s": n_toys / fit_s,
                           "status_counts": np.bincount(st, minlength=5).tolist(),
                           "passes_mean": float(r["passes"].float().mean())}}
+
+
+def run_errors(api, torch, dev, m, cols, off, params, rb, n_minos: int = 64) -> dict:
+    """HESSE of every fit of the toy batch, and MINOS of all ten parameters of
+    the first n_minos toys, at the batch's minima (ipa_hesse, ipa_minos)."""
+    d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
+    n_toys = int(rb["theta"].shape[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = api.ipa_hesse(m, cols, d64(off), params, rb["theta"])
+    torch.cuda.synchronize()
+    t_h = time.perf_counter() - t0
+    st_h = hs["status"].cpu().numpy()
+    # agreement of the HESSE errors with the minimiser's own (both from the Hessian at the minimum)
+    ok = (rb["status"] == 0).cpu().numpy() & (st_h == 0)
+    rel = (hs["err"][ok] / rb["err"][ok] - 1).abs().max().item() if ok.any() else float("nan")
+    sub = d64(off[:n_minos + 1])
+    t0 = time.perf_counter()
+    mn = api.ipa_minos(m, cols, sub, params, rb["theta"][:n_minos].contiguous(), rb["nll"][:n_minos].contiguous(),
+                       hs["cov"][:n_minos].contiguous(), list(range(10)))
+    torch.cuda.synchronize()
+    t_m = time.perf_counter() - t0
+    st_m = mn["status"].cpu().numpy().ravel()
+    asym = (mn["hi"] + mn["lo"]).abs() / (mn["hi"] - mn["lo"]).clamp_min(1e-300)
+    return {"hesse": {"fits": n_toys, "s": t_h, "fits_per_s": n_toys / t_h,
+                      "status_counts": np.bincount(st_h, minlength=4).tolist(),
+                      "max_rel_diff_vs_fit_errors": rel},
+            "minos": {"fits": n_minos, "parameters": 10, "probes": n_minos * 20, "s": t_m,
+                      "intervals_per_s": n_minos * 10 / t_m,
+                      "status_counts": np.bincount(st_m, minlength=6).tolist(),
+                      "median_asymmetry": float(asym.median())}}
 
 
 def run_serve(api, synth, torch, dev, m, theta, params, n_req: int = 60,

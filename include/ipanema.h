@@ -235,6 +235,54 @@ ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int
                          int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
                          void* stream);
 
+/* HESSE on the device (Sec. 3-4: the errors and the correlation matrix that
+ * follow each MIGRAD minimum, Figs. 2 and 4).  For each fit, the Hessian of
+ * the NLL over the free parameters at theta_dev (n_fits x n_par, device; the
+ * minima from ipa_fit_batch, or any point) by central differences of the
+ * analytic gradient (one-sided, +h and +2h, where theta - h would leave the
+ * lower limit), in two batched passes: steps of 1e-3 of each parameter's step,
+ * then 2e-3 of the errors that gives.  Outputs (device, n_fits blocks,
+ * row-major): cov_out_dev n_par x n_par = H^-1 (zero rows and columns for fixed
+ * parameters); corr_out_dev n_par x n_par correlations (may be NULL);
+ * err_out_dev n_par = sqrt(diag) (may be NULL); status_out_dev (may be NULL):
+ * 0 positive definite, 1 made positive definite by a diagonal shift, 3 not
+ * finite (outputs NaN).  Segments and spec (host: limits, steps, the fixed
+ * flags; values unused) as in ipa_fit_batch.  Blocks until done. */
+ipa_status ipa_hesse(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev, int32_t n_fits,
+                     const ipa_param* spec, const double* theta_dev, double* cov_out_dev, double* corr_out_dev,
+                     double* err_out_dev, int32_t* status_out_dev, void* stream);
+
+/* MINOS status of one side of one parameter's interval. */
+enum {
+    IPA_MINOS_OK = 0,            /* |NLL_profile - NLL_min - up| < tol                   */
+    IPA_MINOS_MAXROUNDS = 1,     /* max_rounds reached; the last point is reported       */
+    IPA_MINOS_AT_LIMIT = 2,      /* the profile stays below the threshold up to the limit */
+    IPA_MINOS_FIT_FAILED = 3,    /* a constrained fit failed, or no HESSE error to start  */
+    IPA_MINOS_NEW_MINIMUM = 4,   /* a constrained fit went below NLL_min - tol           */
+    IPA_MINOS_NOT_SCANNED = 5
+};
+
+/* MINOS profile-likelihood intervals on the device.  For each fit and each
+ * parameter p with scan[p] != 0 (host, n_par flags; p must be free), the
+ * points x_lo < theta_p < x_hi where the NLL minimised over every other free
+ * parameter with theta_p fixed at x rises by `up` (0.5 for 1 sigma) above
+ * nll_min_dev[f].  theta_min_dev (n_fits x n_par), nll_min_dev (n_fits) and
+ * cov_dev (n_fits x n_par x n_par, from ipa_hesse) describe the minima
+ * (device).  All fits, parameters and sides advance together: each round is
+ * one batched constrained fit (the minimiser of ipa_fit_batch with max_iter
+ * and fit_tol) per open probe, started at the conditional mean of the
+ * Gaussian approximation, then a secant step on sqrt(2 (NLL_profile -
+ * NLL_min)); a probe ends when |NLL_profile - NLL_min - up| < tol or after
+ * max_rounds rounds.  Outputs (device): lo_out_dev, hi_out_dev (n_fits x
+ * n_par): x_lo - theta_p (negative) and x_hi - theta_p, 0 where not scanned;
+ * status_out_dev (n_fits x n_par x 2: lower, upper; may be NULL):
+ * IPA_MINOS_*.  Blocks until done. */
+ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev, int32_t n_fits,
+                     const ipa_param* spec, const double* theta_min_dev, const double* nll_min_dev,
+                     const double* cov_dev, const int32_t* scan, double up, double tol, int32_t max_rounds,
+                     int32_t max_iter, double fit_tol, double* lo_out_dev, double* hi_out_dev,
+                     int32_t* status_out_dev, void* stream);
+
 /* Fit server (continuous batching).  Fits of different sizes are submitted
  * as they arrive; each is admitted into a device slot when a slot and a
  * contiguous range of the event arena (the HBM budget, 40 bytes per event) are

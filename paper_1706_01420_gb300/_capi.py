@@ -20,6 +20,8 @@ IPA_NPAR_1D, IPA_NPAR_4D, IPA_NPAR_TAGGED, IPA_MAX_PAR = 4, 10, 8, 16
 IPA_NOALLOC_MAX_EVENTS = 8388608
 IPA_MATH_EXP, IPA_MATH_LOG, IPA_MATH_SIN, IPA_MATH_COS, IPA_MATH_ERFCX, IPA_MATH_RCP = range(6)
 IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)
+(IPA_MINOS_OK, IPA_MINOS_MAXROUNDS, IPA_MINOS_AT_LIMIT, IPA_MINOS_FIT_FAILED, IPA_MINOS_NEW_MINIMUM,
+ IPA_MINOS_NOT_SCANNED) = range(6)
 STATUS_NAMES = {0: "IPA_OK", -1: "IPA_ERR_ARG", -2: "IPA_ERR_OOM", -3: "IPA_ERR_CUDA",
                 -4: "IPA_ERR_TIMEOUT", -5: "IPA_ERR_BUSY", 1: "IPA_PENDING"}
 
@@ -61,6 +63,11 @@ PROTOTYPES = {
     "ipa_fit_batch": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
                                 POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_int32, c_double, c_void_p]),
+    "ipa_hesse": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),
+                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ipa_minos": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),
+                            c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_double, c_double, c_int32, c_int32,
+                            c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ipa_nll_grad_noalloc": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
     "ipa_server_create": (c_int32, [POINTER(ipa_model), c_size_t, c_int32, c_int32, c_double,
                                     POINTER(c_void_p)]),

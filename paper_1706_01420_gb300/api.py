@@ -194,6 +194,44 @@ def ipa_fit_batch(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: l
     return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters, "passes": passes}
 
 
+def ipa_hesse(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[Param],
+              theta: torch.Tensor, stream=None) -> dict:
+    """Covariance, correlation matrix, errors and status of each fit at theta (n_fits x n_par)."""
+    n_fits = int(seg_off.numel()) - 1
+    P = model.n_par
+    dev = theta.device
+    cov = torch.empty(n_fits, P, P, dtype=torch.float64, device=dev)
+    corr = torch.empty(n_fits, P, P, dtype=torch.float64, device=dev)
+    err = torch.empty(n_fits, P, dtype=torch.float64, device=dev)
+    status = torch.empty(n_fits, dtype=torch.int32, device=dev)
+    e = ipa_events(ev)
+    _check(_lib().ipa_hesse(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"), n_fits,
+                            _spec(params), _ptr(theta, name="theta"), _ptr(cov, name="cov"),
+                            _ptr(corr, name="corr"), _ptr(err, name="err"), _ptr(status, torch.int32, "status"),
+                            _stream(stream)), "ipa_hesse")
+    return {"cov": cov, "corr": corr, "err": err, "status": status}
+
+
+def ipa_minos(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[Param], theta_min: torch.Tensor,
+              nll_min: torch.Tensor, cov: torch.Tensor, scan: list[int], up: float = 0.5, tol: float = 1e-7,
+              max_rounds: int = 12, max_iter: int = 200, fit_tol: float = 1e-9, stream=None) -> dict:
+    """MINOS intervals (lower and upper signed errors, statuses) of the parameters in `scan`."""
+    n_fits = int(seg_off.numel()) - 1
+    P = model.n_par
+    dev = theta_min.device
+    lo = torch.empty(n_fits, P, dtype=torch.float64, device=dev)
+    hi = torch.empty(n_fits, P, dtype=torch.float64, device=dev)
+    status = torch.empty(n_fits, P, 2, dtype=torch.int32, device=dev)
+    flags = (ctypes.c_int32 * P)(*[1 if p in scan else 0 for p in range(P)])
+    e = ipa_events(ev)
+    _check(_lib().ipa_minos(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"), n_fits,
+                            _spec(params), _ptr(theta_min, name="theta_min"), _ptr(nll_min, name="nll_min"),
+                            _ptr(cov, name="cov"), flags, up, tol, max_rounds, max_iter, fit_tol,
+                            _ptr(lo, name="lo"), _ptr(hi, name="hi"), _ptr(status, torch.int32, "status"),
+                            _stream(stream)), "ipa_minos")
+    return {"lo": lo, "hi": hi, "status": status}
+
+
 def _host_or_dev_ptr(x, name):
     """Pointer of a C-contiguous float64 numpy array (host) or CUDA tensor (device)."""
     import numpy as np

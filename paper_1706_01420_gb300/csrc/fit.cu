@@ -165,7 +165,7 @@ ipa_status batch_args_reserve(BatchArgs& a, int n_fits) {
 ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, const int64_t* begin,
                    const int64_t* end, const Spec* specs, int spec_stride, int max_passes, int64_t tiles_bound,
                    double* theta_io_dev, double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
-                   int32_t* iters_out_dev, int32_t* passes_out_dev, cudaStream_t user) {
+                   int32_t* iters_out_dev, int32_t* passes_out_dev, cudaStream_t user, const char* who) {
     // The fit runs on a library stream (capturable even when the caller passes the
     // legacy default stream), ordered after the caller's stream by an event.
     cudaStream_t s = fit_stream();
@@ -302,7 +302,7 @@ ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, con
     st = cuda_fail(cudaGetLastError(), "fit final");
     st = done(st);
     if (st == IPA_OK) st = cuda_fail(cudaGetLastError(), "fit final sync");
-    trace("{\"call\": \"fit_run\", \"n_fits\": %d, \"events\": %lld, \"loop\": \"%s\"}", n_fits,
+    trace("{\"call\": \"%s\", \"n_fits\": %d, \"events\": %lld, \"loop\": \"%s\"}", who, n_fits,
           (long long)ev->n, c.one_launch && c.exec ? "device" : "host");
     // later work on the caller's stream sees the results: the call is blocking
     return st;
@@ -340,7 +340,6 @@ extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev
         return st;
     st = fit_run(model, ev, n_fits, a.seg_off, a.seg_off + 1, a.spec, 0, sp.max_passes,
                  (ev->n + kTile - 1) / kTile + n_fits, theta_io_dev, err_out_dev, nll_out_dev, fit_status_dev,
-                 iters_out_dev, passes_out_dev, user);
-    trace("{\"call\": \"ipa_fit_batch\", \"n_fits\": %d, \"events\": %lld}", n_fits, (long long)ev->n);
+                 iters_out_dev, passes_out_dev, user, "ipa_fit_batch");
     return st;
 }

@@ -60,11 +60,12 @@ struct State {
 // theta_io[i] (n_par values, device) and writing the result back there;
 // err, nll, status, iters, passes as in ipa_fit_batch (device, may be NULL).
 // tiles_bound >= the sum over fits of their 512-event tiles.  Ordered after
-// the caller's `stream`; blocks until the fits end.
+// the caller's `stream`; blocks until the fits end.  `who` names the call in
+// the IPA_TRACE record.
 ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, const int64_t* begin,
                    const int64_t* end, const Spec* specs, int spec_stride, int max_passes, int64_t tiles_bound,
                    double* theta_io, double* err, double* nll, int32_t* status, int32_t* iters, int32_t* passes,
-                   cudaStream_t stream);
+                   cudaStream_t stream, const char* who);
 
 namespace {
 

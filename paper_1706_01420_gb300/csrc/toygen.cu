@@ -34,13 +34,12 @@
 
 #include "consts.cuh"
 #include "ipa_internal.cuh"
+#include "philox.cuh"
 #include "tagged.cuh"
 
 namespace ipa {
 namespace {
 
-constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
-constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 constexpr int kPerThread = 16;             // candidates per thread per chunk (bits of a mask)
 constexpr int kChunk = kBlock * kPerThread;
 constexpr double kPi = 3.14159265358979323846;
@@ -48,34 +47,6 @@ constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double k2OverSqrt6 = 0.81649658092772603273;
 constexpr double k2OverSqrt3 = 1.15470053837925152902;
 
-struct U4 {
-    uint32_t x, y, z, w;
-};
-
-// Philox-4x32 with 10 rounds.  Round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2,
-// c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); key bumped by (W0, W1) between rounds.
-__device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k0 += kW0;
-            k1 += kW1;
-        }
-        const uint32_t lo0 = kM0 * c.x, hi0 = __umulhi(kM0, c.x);
-        const uint32_t lo1 = kM1 * c.z, hi1 = __umulhi(kM1, c.z);
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-    }
-    return c;
-}
-
-__device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
-    const unsigned long long v = ((((unsigned long long)a) << 32) | b) >> 11;
-    return __dmul_rn(__ull2double_rn(v + 1ull), 0x1p-53);
-}
-
-__device__ __forceinline__ U4 draw(uint64_t idx, uint32_t toy, uint32_t call, uint32_t k0, uint32_t k1) {
-    return philox(U4{(uint32_t)idx, (uint32_t)(idx >> 32), toy, call}, k0, k1);
-}
 
 // A(Omega) = sum_k h_k f_k, evaluated as the oracle's definition (Sec. 4).
 __device__ __forceinline__ double angular_pdf(const Consts& c, double ck, double cl, double phi) {
