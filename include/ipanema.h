@@ -283,6 +283,48 @@ ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t
                      int32_t max_iter, double fit_tol, double* lo_out_dev, double* hi_out_dev,
                      int32_t* status_out_dev, void* stream);
 
+/* ---- binned workloads (Example 4 "CLs" and the toolkit's generateBinned and
+ * Gaussian smearing) ----
+ *
+ * Poisson pseudo-experiments of a histogram (generateBinned): counts_out_dev
+ * [k * n_bins + i] ~ Poisson(lambda_dev[i]) for toy toy0 + k, k < n_toys
+ * (int32, device, caller-owned; lambda_dev n_bins doubles, device).  Bin i of
+ * toy k under `hypothesis` h (0 or 1) inverts the Poisson CDF with uniforms
+ * from Philox-4x32-10, key = (seed lo32, seed hi32), counter (i lo32, i hi32,
+ * k, 8 + 2^16 h + m/2) for piece m of a mean split into ceil(lambda / 400)
+ * equal pieces above 400; every step is a correctly rounded IEEE operation,
+ * so the counts are reproducible bit for bit.  lambda <= 0 gives 0.
+ * IPA_ERR_ARG for negative sizes, a hypothesis other than 0 or 1, or NULL
+ * arrays.  Asynchronous on `stream`. */
+ipa_status ipa_binned_generate(const double* lambda_dev, int64_t n_bins, uint64_t seed, int32_t hypothesis,
+                               int32_t toy0, int32_t n_toys, int32_t* counts_out_dev, void* stream);
+
+/* Gaussian smearing of a histogram (the binned resolution convolution):
+ * out_i = sum_{|d| <= R} K_d hist_{i-d}, R = ceil(8 sigma / bin_width), bins
+ * outside the histogram contributing nothing, K_d = exp(-(d bin_width)^2 /
+ * (2 sigma^2)) normalised to unit sum.  hist_dev, out_dev: n_bins doubles
+ * (device, distinct).  IPA_ERR_ARG for non-positive width or sigma, sigma
+ * above 1.25e6 bins, or aliased arrays.  Asynchronous on `stream`. */
+ipa_status ipa_binned_smear(const double* hist_dev, int64_t n_bins, double bin_width, double sigma, double* out_dev,
+                            void* stream);
+
+/* CL_b, CL_s+b and CL_s of a binned search (Example 4; the modified
+ * frequentist method of its references): with expected signal s_dev and
+ * background b_dev per bin (n_bins doubles each, device, b > 0 in every bin)
+ * and the observed counts data_dev (n_bins int32, device), the statistic
+ * X = sum_i n_i ln(1 + s_i / b_i) (the data-dependent part of -2 ln Q,
+ * Q = L(s+b) / L(b)) of n_toys toys under the background-only (h = 0, mean
+ * b) and the signal-plus-background hypothesis (h = 1, mean s + b), drawn as
+ * in ipa_binned_generate with toys 0..n_toys-1, gives CL_b = P_b(X <= X_obs),
+ * CL_s+b = P_s+b(X <= X_obs), CL_s = CL_s+b / CL_b (NaN when CL_b = 0).
+ * Outputs (device): cl_out_dev[3] = (CL_b, CL_s+b, CL_s); counts_out_dev[2]
+ * the toy counts behind them (may be NULL); x_out_dev (2 n_toys + 1: X of the
+ * b toys, of the s+b toys, X_obs; may be NULL).  Toys are drawn on the fly,
+ * one block per toy: nothing of size n_toys x n_bins is stored.
+ * Asynchronous on `stream`. */
+ipa_status ipa_cls(const double* s_dev, const double* b_dev, int64_t n_bins, const int32_t* data_dev, int32_t n_toys,
+                   uint64_t seed, double* cl_out_dev, int64_t* counts_out_dev, double* x_out_dev, void* stream);
+
 /* Fit server (continuous batching).  Fits of different sizes are submitted
  * as they arrive; each is admitted into a device slot when a slot and a
  * contiguous range of the event arena (the HBM budget, 40 bytes per event) are

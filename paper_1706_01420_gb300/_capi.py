@@ -68,6 +68,10 @@ PROTOTYPES = {
     "ipa_minos": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),
                             c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_double, c_double, c_int32, c_int32,
                             c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ipa_binned_generate": (c_int32, [c_void_p, c_int64, c_uint64, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "ipa_binned_smear": (c_int32, [c_void_p, c_int64, c_double, c_double, c_void_p, c_void_p]),
+    "ipa_cls": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_uint64, c_void_p, c_void_p, c_void_p,
+                          c_void_p]),
     "ipa_nll_grad_noalloc": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
     "ipa_server_create": (c_int32, [POINTER(ipa_model), c_size_t, c_int32, c_int32, c_double,
                                     POINTER(c_void_p)]),

@@ -232,6 +232,41 @@ def ipa_minos(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[
     return {"lo": lo, "hi": hi, "status": status}
 
 
+def ipa_binned_generate(lam: torch.Tensor, seed: int, n_toys: int, toy0: int = 0, hypothesis: int = 0,
+                        stream=None) -> torch.Tensor:
+    """(n_toys, n_bins) int32 Poisson counts of the bin means lam (generateBinned)."""
+    n_bins = int(lam.numel())
+    out = torch.empty(n_toys, n_bins, dtype=torch.int32, device=lam.device)
+    _check(_lib().ipa_binned_generate(_ptr(lam, name="lambda"), n_bins, ctypes.c_uint64(seed), hypothesis, toy0,
+                                      n_toys, _ptr(out, torch.int32, "counts"), _stream(stream)),
+           "ipa_binned_generate")
+    return out
+
+
+def ipa_binned_smear(hist: torch.Tensor, bin_width: float, sigma: float, stream=None) -> torch.Tensor:
+    """The histogram convolved with a Gaussian of width sigma (same binning)."""
+    out = torch.empty_like(hist)
+    _check(_lib().ipa_binned_smear(_ptr(hist, name="hist"), int(hist.numel()), bin_width, sigma,
+                                   _ptr(out, name="out"), _stream(stream)), "ipa_binned_smear")
+    return out
+
+
+def ipa_cls(s: torch.Tensor, b: torch.Tensor, data: torch.Tensor, n_toys: int, seed: int, with_x: bool = False,
+            stream=None) -> dict:
+    """CL_b, CL_s+b, CL_s of the observed counts `data` (int32) for signal s over background b."""
+    n_bins = int(s.numel())
+    cl = torch.empty(3, dtype=torch.float64, device=s.device)
+    counts = torch.empty(2, dtype=torch.int64, device=s.device)
+    x = torch.empty(2 * n_toys + 1, dtype=torch.float64, device=s.device) if with_x else None
+    _check(_lib().ipa_cls(_ptr(s, name="s"), _ptr(b, name="b"), n_bins, _ptr(data, torch.int32, "data"), n_toys,
+                          ctypes.c_uint64(seed), _ptr(cl, name="cl"), _ptr(counts, torch.int64, "counts"),
+                          _ptr(x, name="x") if x is not None else None, _stream(stream)), "ipa_cls")
+    out = {"cl_b": cl[0], "cl_sb": cl[1], "cl_s": cl[2], "counts": counts}
+    if x is not None:
+        out["x_b"], out["x_sb"], out["x_obs"] = x[:n_toys], x[n_toys:2 * n_toys], x[2 * n_toys]
+    return out
+
+
 def _host_or_dev_ptr(x, name):
     """Pointer of a C-contiguous float64 numpy array (host) or CUDA tensor (device)."""
     import numpy as np
