@@ -294,8 +294,11 @@ ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t
  * k, 8 + 2^16 h + m/2) for piece m of a mean split into ceil(lambda / 400)
  * equal pieces above 400; every step is a correctly rounded IEEE operation,
  * so the counts are reproducible bit for bit.  lambda <= 0 gives 0.
+ * The CDF of each bin is tabulated once per call (the recurrence depends only
+ * on the mean), so a draw is one Philox block and a few comparisons.
  * IPA_ERR_ARG for negative sizes, a hypothesis other than 0 or 1, or NULL
- * arrays.  Asynchronous on `stream`. */
+ * arrays.  Synchronises `stream` once (to size the tables), then runs
+ * asynchronously on it. */
 ipa_status ipa_binned_generate(const double* lambda_dev, int64_t n_bins, uint64_t seed, int32_t hypothesis,
                                int32_t toy0, int32_t n_toys, int32_t* counts_out_dev, void* stream);
 
@@ -320,8 +323,8 @@ ipa_status ipa_binned_smear(const double* hist_dev, int64_t n_bins, double bin_w
  * Outputs (device): cl_out_dev[3] = (CL_b, CL_s+b, CL_s); counts_out_dev[2]
  * the toy counts behind them (may be NULL); x_out_dev (2 n_toys + 1: X of the
  * b toys, of the s+b toys, X_obs; may be NULL).  Toys are drawn on the fly,
- * one block per toy: nothing of size n_toys x n_bins is stored.
- * Asynchronous on `stream`. */
+ * one block per toy: nothing of size n_toys x n_bins is stored.  Synchronises
+ * `stream` twice (to size the CDF tables), then runs asynchronously on it. */
 ipa_status ipa_cls(const double* s_dev, const double* b_dev, int64_t n_bins, const int32_t* data_dev, int32_t n_toys,
                    uint64_t seed, double* cl_out_dev, int64_t* counts_out_dev, double* x_out_dev, void* stream);
 
@@ -438,7 +441,9 @@ ipa_status ipa_calibrate_fp64(double* results, void* stream);
  *   IPA_MATH_LOG    table-driven log (library log for zero, negative,
  *                   subnormal, infinite and NaN arguments)
  *   IPA_MATH_SIN,
- *   IPA_MATH_COS    table-driven sincos (library sincos for |x| >= 1e5)
+ *   IPA_MATH_COS    integer-pipe sincos for |x| < 1024 (the angles and the
+ *                   oscillation phase), table-driven above, library sincos
+ *                   for |x| >= 1e5
  *   IPA_MATH_ERFCX  piecewise polynomial on [0, 6.25], library erfcx above
  *   IPA_MATH_RCP    1/x from an FP32 seed and one FP64 Newton step
  * x_dev, y_dev: device arrays of n doubles (caller-owned).  IPA_ERR_ARG for an

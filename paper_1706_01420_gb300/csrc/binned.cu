@@ -10,7 +10,9 @@
 //   n = 0, p = exp(-nu), F = p;  while u > F and p > 0 and n < cap:
 //   n += 1, p = (p nu) / n, F += p;   cap = floor(nu + 40 sqrt(nu) + 100).
 // Every step is a correctly rounded IEEE operation (no contraction), so the
-// counts are reproducible bit for bit.
+// counts are reproducible bit for bit.  The recurrence depends only on the
+// bin's mean, so it runs once per bin and call into a CDF table (BinTable);
+// a draw is then one Philox block and a few comparisons.
 //
 // CLs.  With w_i = ln(1 + s_i / b_i), X = sum_i n_i w_i (the data-dependent part
 // of -2 ln Q, Q = L(s+b) / L(b)); CL_s+b = P_s+b(X <= X_obs), CL_b =
@@ -33,59 +35,134 @@ __device__ __forceinline__ uint32_t binned_call(int hyp, int m) {
     return kBinnedCall + ((uint32_t)hyp << 16) + (uint32_t)(m >> 1);
 }
 
-// One piece: inversion with its exp(-nu) given.
-__device__ __forceinline__ int poisson_piece(double nu, double p0, double u) {
-    int n = 0;
-    double p = p0, F = p0;
-    const double cap = floor(__dadd_rn(__dadd_rn(nu, __dmul_rn(40.0, sqrt(nu))), 100.0));
-    while (u > F && p > 0.0 && (double)n < cap) {
-        n += 1;
-        p = __ddiv_rn(__dmul_rn(p, nu), (double)n);
-        F = __dadd_rn(F, p);
-    }
-    return n;
-}
-
-// Pieces of a bin mean: M, nu = lambda / M and exp(-nu).
-struct BinMean {
-    double nu, p0;
-    int M;
+// The inversion of one bin, tabulated once per call and shared by every toy:
+// with nu = lambda / M, p_0 = exp(-nu), cap = floor(nu + 40 sqrt(nu) + 100), the
+// recurrence p_n = (p_{n-1} nu) / n, F_n = F_{n-1} + p_n (each step correctly
+// rounded) gives the CDF values F_0, F_1, ...  A draw with uniform u is the
+// first n with u <= F_n, or `stop` (the n where the recurrence ends, p = 0 or
+// n = cap) when u exceeds them all.  The table keeps F_0 .. F_{len-1}, up to
+// the point past the mode where adding p_n no longer changes F (after that no
+// u changes the outcome before `stop`), so a draw compares u with the same
+// values in the same order as the plain sequential loop, and the counts are
+// those of that loop bit for bit.
+struct BinTable {
+    int64_t off;    // first entry in the flat CDF array
+    double nu;      // mean of one piece
+    int M;          // pieces (0 for a non-positive mean)
+    int len;        // entries F_0 .. F_{len-1}
+    int stop;       // the draw when u > F_{len-1}
+    int pad_;
 };
 
-__device__ __forceinline__ BinMean bin_mean(double lam) {
-    BinMean b;
+// Run the recurrence of one bin: entries and stop index; with F != nullptr
+// also write the entries.
+__device__ inline void bin_recurrence(double lam, BinTable* t, double* F) {
     if (!(lam > 0.0)) {
-        b.M = 0;
-        b.nu = 0.0;
-        b.p0 = 1.0;
-        return b;
+        t->M = 0;
+        t->nu = 0.0;
+        t->len = 0;
+        t->stop = 0;
+        return;
     }
     const double Md = ceil(lam / kPiece);
-    b.M = Md < 1.0 ? 1 : (int)Md;
-    b.nu = __ddiv_rn(lam, (double)b.M);
-    b.p0 = exp(-b.nu);
-    return b;
+    const int M = Md < 1.0 ? 1 : (int)Md;
+    const double nu = __ddiv_rn(lam, (double)M);
+    const double cap = floor(__dadd_rn(__dadd_rn(nu, __dmul_rn(40.0, sqrt(nu))), 100.0));
+    double p = exp(-nu), f = p;
+    int n = 0, len = 1;
+    bool settled = false;
+    if (F) F[0] = f;
+    // u <= 1 < any F would end the loop anyway; u > F runs it to p = 0 or n = cap
+    while (p > 0.0 && (double)n < cap) {
+        n += 1;
+        p = __ddiv_rn(__dmul_rn(p, nu), (double)n);
+        const double g = __dadd_rn(f, p);
+        if (!settled) {
+            if (g == f && (double)n > nu) {
+                settled = true;
+            } else {
+                if (F) F[len] = g;
+                ++len;
+            }
+        }
+        f = g;
+    }
+    t->M = M;
+    t->nu = nu;
+    t->len = len;
+    t->stop = n;
 }
 
-__device__ __forceinline__ int poisson_bin(const BinMean& bm, uint64_t i, uint32_t toy, int hyp, uint32_t k0,
-                                           uint32_t k1) {
+__device__ __forceinline__ int table_draw(const BinTable& t, const double* __restrict__ F, double u) {
+    const double* f = F + t.off;
+    int j = 0;
+    while (j < t.len && u > __ldg(f + j)) ++j;
+    return j < t.len ? j : t.stop;
+}
+
+__device__ __forceinline__ int poisson_bin(const BinTable& t, const double* __restrict__ F, uint64_t i, uint32_t toy,
+                                           int hyp, uint32_t k0, uint32_t k1) {
     int n = 0;
-    for (int m = 0; m < bm.M; ++m) {
+    for (int m = 0; m < t.M; ++m) {
         const U4 r = draw(i, toy, binned_call(hyp, m), k0, k1);
         const double u = (m & 1) ? u01(r.z, r.w) : u01(r.x, r.y);
-        n += poisson_piece(bm.nu, bm.p0, u);
+        n += table_draw(t, F, u);
     }
     return n;
+}
+
+__global__ void table_size_kernel(const double* __restrict__ lam, const double* __restrict__ add, int64_t n_bins,
+                                  BinTable* __restrict__ tab) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bins; i += (int64_t)gridDim.x * blockDim.x) {
+        const double l = add ? __ldg(lam + i) + __ldg(add + i) : __ldg(lam + i);
+        BinTable t{};
+        bin_recurrence(l, &t, nullptr);
+        tab[i] = t;
+    }
+}
+
+// off[i] = sum_{r<i} len_r (one block: a sequential run per thread, then a
+// block scan of the run totals); *total = the sum.
+__global__ void table_offsets_kernel(BinTable* __restrict__ tab, int64_t n_bins, int64_t* __restrict__ total) {
+    __shared__ int64_t run[1024];
+    const int nt = blockDim.x;
+    const int64_t per = (n_bins + nt - 1) / nt;
+    const int64_t b = threadIdx.x * per;
+    const int64_t e = b + per < n_bins ? b + per : n_bins;
+    int64_t sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += tab[i].len;
+    run[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        const int64_t v = threadIdx.x >= d ? run[threadIdx.x - d] : 0;
+        __syncthreads();
+        run[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t acc = threadIdx.x ? run[threadIdx.x - 1] : 0;
+    for (int64_t i = b; i < e; ++i) {
+        tab[i].off = acc;
+        acc += tab[i].len;
+    }
+    if (threadIdx.x == nt - 1) *total = run[nt - 1];
+}
+
+__global__ void table_fill_kernel(const double* __restrict__ lam, const double* __restrict__ add, int64_t n_bins,
+                                  const BinTable* __restrict__ tab, double* __restrict__ F) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bins; i += (int64_t)gridDim.x * blockDim.x) {
+        const double l = add ? __ldg(lam + i) + __ldg(add + i) : __ldg(lam + i);
+        BinTable t{};
+        bin_recurrence(l, &t, F + tab[i].off);
+    }
 }
 
 __global__ void __launch_bounds__(kBinBlock)
-generate_kernel(const double* __restrict__ lam, int64_t n_bins, uint32_t k0, uint32_t k1, int hyp, int toy0,
-                int n_toys, int32_t* __restrict__ counts) {
+generate_kernel(const BinTable* __restrict__ tab, const double* __restrict__ F, int64_t n_bins, uint32_t k0,
+                uint32_t k1, int hyp, int toy0, int n_toys, int32_t* __restrict__ counts) {
     const int64_t total = n_bins * (int64_t)n_toys;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = x / n_bins, i = x - k * n_bins;
-        const BinMean bm = bin_mean(__ldg(lam + i));
-        counts[x] = poisson_bin(bm, (uint64_t)i, (uint32_t)(toy0 + k), hyp, k0, k1);
+        counts[x] = poisson_bin(tab[i], F, (uint64_t)i, (uint32_t)(toy0 + k), hyp, k0, k1);
     }
 }
 
@@ -124,15 +201,11 @@ smear_kernel(const double* __restrict__ h, int64_t n_bins, int R, const double* 
     }
 }
 
-// Per bin: w_i and the pieces of both hypotheses' means.
-__global__ void cls_prepare_kernel(const double* __restrict__ s, const double* __restrict__ b, int64_t n_bins,
-                                   double* __restrict__ w, BinMean* __restrict__ mb, BinMean* __restrict__ msb) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bins; i += (int64_t)gridDim.x * blockDim.x) {
-        const double si = __ldg(s + i), bi = __ldg(b + i);
-        w[i] = log1p(si / bi);
-        mb[i] = bin_mean(bi);
-        msb[i] = bin_mean(si + bi);
-    }
+// w_i = ln(1 + s_i / b_i).
+__global__ void cls_weights_kernel(const double* __restrict__ s, const double* __restrict__ b, int64_t n_bins,
+                                   double* __restrict__ w) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bins; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = log1p(__ldg(s + i) / __ldg(b + i));
 }
 
 // Fixed-order block sum (every thread gets the total).
@@ -150,8 +223,9 @@ __device__ __forceinline__ double block_sum(double v, double* part) {
 
 // X of toy k under hypothesis h (blocks stride over toys); toy index -1: the data.
 __global__ void __launch_bounds__(kBinBlock)
-cls_toys_kernel(const BinMean* __restrict__ mean, const double* __restrict__ w, int64_t n_bins, uint32_t k0,
-                uint32_t k1, int hyp, int n_toys, const int32_t* __restrict__ data, double* __restrict__ x_out) {
+cls_toys_kernel(const BinTable* __restrict__ tab, const double* __restrict__ F, const double* __restrict__ w,
+                int64_t n_bins, uint32_t k0, uint32_t k1, int hyp, int n_toys, const int32_t* __restrict__ data,
+                double* __restrict__ x_out) {
     __shared__ double part[kBinBlock / 32];
     const int first = data ? 0 : blockIdx.x;
     const int stride = data ? 1 : gridDim.x;
@@ -159,7 +233,7 @@ cls_toys_kernel(const BinMean* __restrict__ mean, const double* __restrict__ w, 
     for (int k = first; k < last; k += stride) {
         double acc = 0.0;
         for (int64_t i = threadIdx.x; i < n_bins; i += blockDim.x) {
-            const int n = data ? __ldg(data + i) : poisson_bin(mean[i], (uint64_t)i, (uint32_t)k, hyp, k0, k1);
+            const int n = data ? __ldg(data + i) : poisson_bin(tab[i], F, (uint64_t)i, (uint32_t)k, hyp, k0, k1);
             if (n) acc = fma((double)n, __ldg(w + i), acc);
         }
         const double X = block_sum(acc, part);
@@ -199,10 +273,35 @@ __global__ void cls_final_kernel(const unsigned long long* __restrict__ cnt, int
     }
 }
 
+// The CDF tables of the bin means lam (+ add, if given), in stream-ordered
+// allocations the caller frees with cudaFreeAsync.  Synchronises the stream
+// once (the size of the flat table).
+ipa_status build_tables(const double* lam, const double* add, int64_t n_bins, cudaStream_t s, BinTable** tab,
+                        double** F, int64_t* scratch_total, int64_t* host_total);
+
 int grid_for(int64_t work) {
     const int64_t g = (work + kBinBlock - 1) / kBinBlock;
     const int64_t cap = (int64_t)sm_count() * 16;
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+ipa_status build_tables(const double* lam, const double* add, int64_t n_bins, cudaStream_t s, BinTable** tab,
+                        double** F, int64_t* scratch_total, int64_t* host_total) {
+    *tab = nullptr;
+    *F = nullptr;
+    ipa_status st = cuda_fail(cudaMallocAsync((void**)tab, sizeof(BinTable) * (size_t)n_bins, s), "binned tables");
+    if (st != IPA_OK) return st;
+    table_size_kernel<<<grid_for(n_bins), kBinBlock, 0, s>>>(lam, add, n_bins, *tab);
+    table_offsets_kernel<<<1, 1024, 0, s>>>(*tab, n_bins, scratch_total);
+    if ((st = cuda_fail(cudaMemcpyAsync(host_total, scratch_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+                        "binned table size")) != IPA_OK)
+        return st;
+    if ((st = cuda_fail(cudaStreamSynchronize(s), "binned table size")) != IPA_OK) return st;
+    if ((st = cuda_fail(cudaMallocAsync((void**)F, sizeof(double) * (size_t)(*host_total > 0 ? *host_total : 1), s),
+                        "binned tables")) != IPA_OK)
+        return st;
+    table_fill_kernel<<<grid_for(n_bins), kBinBlock, 0, s>>>(lam, add, n_bins, *tab, *F);
+    return cuda_fail(cudaGetLastError(), "binned table launch");
 }
 
 }  // namespace
@@ -218,10 +317,23 @@ extern "C" ipa_status ipa_binned_generate(const double* lambda_dev, int64_t n_bi
     }
     if (n_bins == 0 || n_toys == 0) return IPA_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    generate_kernel<<<grid_for(n_bins * n_toys), kBinBlock, 0, s>>>(lambda_dev, n_bins, (uint32_t)seed,
-                                                                    (uint32_t)(seed >> 32), hypothesis, toy0, n_toys,
-                                                                    counts_out_dev);
-    return cuda_fail(cudaGetLastError(), "binned generator launch");
+    int64_t* total = nullptr;
+    ipa_status st = cuda_fail(cudaMallocAsync((void**)&total, sizeof(int64_t), s), "binned scratch");
+    if (st != IPA_OK) return st;
+    BinTable* tab = nullptr;
+    double* F = nullptr;
+    int64_t h_total = 0;
+    st = build_tables(lambda_dev, nullptr, n_bins, s, &tab, &F, total, &h_total);
+    if (st == IPA_OK) {
+        generate_kernel<<<grid_for(n_bins * n_toys), kBinBlock, 0, s>>>(tab, F, n_bins, (uint32_t)seed,
+                                                                        (uint32_t)(seed >> 32), hypothesis, toy0,
+                                                                        n_toys, counts_out_dev);
+        st = cuda_fail(cudaGetLastError(), "binned generator launch");
+    }
+    if (F) cudaFreeAsync(F, s);
+    if (tab) cudaFreeAsync(tab, s);
+    cudaFreeAsync(total, s);
+    return st;
 }
 
 extern "C" ipa_status ipa_binned_smear(const double* hist_dev, int64_t n_bins, double bin_width, double sigma,
@@ -260,27 +372,36 @@ extern "C" ipa_status ipa_cls(const double* s_dev, const double* b_dev, int64_t 
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t nb = (size_t)n_bins, nt = (size_t)n_toys;
-    // per bin: w, two BinMeans; per toy: X under b and s+b, X_obs; two counters
-    const size_t bytes = nb * (sizeof(double) + 2 * sizeof(BinMean)) + (x_out_dev ? 0 : (2 * nt + 1) * sizeof(double)) +
-                         2 * sizeof(unsigned long long) + 64;
+    // two counters, the table size, w per bin, X per toy (unless the caller keeps them)
+    const size_t bytes = 32 + nb * sizeof(double) + (x_out_dev ? 0 : (2 * nt + 1) * sizeof(double));
     unsigned char* buf = nullptr;
     ipa_status st = cuda_fail(cudaMallocAsync((void**)&buf, bytes, s), "cls scratch alloc");
     if (st != IPA_OK) return st;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(buf);
-    double* w = reinterpret_cast<double*>(buf + 16);
-    BinMean* mb = reinterpret_cast<BinMean*>(w + nb);
-    BinMean* msb = mb + nb;
-    double* x = x_out_dev ? x_out_dev : reinterpret_cast<double*>(msb + nb);
+    int64_t* total = reinterpret_cast<int64_t*>(buf + 16);
+    double* w = reinterpret_cast<double*>(buf + 32);
+    double* x = x_out_dev ? x_out_dev : w + nb;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
-    cls_prepare_kernel<<<grid_for(n_bins), kBinBlock, 0, s>>>(s_dev, b_dev, n_bins, w, mb, msb);
-    const int gt = n_toys < sm_count() * 8 ? n_toys : sm_count() * 8;
-    cls_toys_kernel<<<gt, kBinBlock, 0, s>>>(mb, w, n_bins, k0, k1, 0, n_toys, nullptr, x);
-    cls_toys_kernel<<<gt, kBinBlock, 0, s>>>(msb, w, n_bins, k0, k1, 1, n_toys, nullptr, x + nt);
-    cls_toys_kernel<<<1, kBinBlock, 0, s>>>(mb, w, n_bins, k0, k1, 0, 1, data_dev, x + 2 * nt);
-    cls_count_kernel<<<grid_for(n_toys), kBinBlock, 0, s>>>(x, x + nt, x + 2 * nt, n_toys, cnt);
-    cls_final_kernel<<<1, 1, 0, s>>>(cnt, n_toys, cl_out_dev, counts_out_dev);
-    st = cuda_fail(cudaGetLastError(), "cls launch");
+    BinTable *tb = nullptr, *tsb = nullptr;
+    double *Fb = nullptr, *Fsb = nullptr;
+    int64_t h_total = 0;
+    st = build_tables(b_dev, nullptr, n_bins, s, &tb, &Fb, total, &h_total);
+    if (st == IPA_OK) st = build_tables(s_dev, b_dev, n_bins, s, &tsb, &Fsb, total, &h_total);
+    if (st == IPA_OK) {
+        cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s);
+        cls_weights_kernel<<<grid_for(n_bins), kBinBlock, 0, s>>>(s_dev, b_dev, n_bins, w);
+        const int gt = n_toys < sm_count() * 8 ? n_toys : sm_count() * 8;
+        cls_toys_kernel<<<gt, kBinBlock, 0, s>>>(tb, Fb, w, n_bins, k0, k1, 0, n_toys, nullptr, x);
+        cls_toys_kernel<<<gt, kBinBlock, 0, s>>>(tsb, Fsb, w, n_bins, k0, k1, 1, n_toys, nullptr, x + nt);
+        cls_toys_kernel<<<1, kBinBlock, 0, s>>>(tb, Fb, w, n_bins, k0, k1, 0, 1, data_dev, x + 2 * nt);
+        cls_count_kernel<<<grid_for(n_toys), kBinBlock, 0, s>>>(x, x + nt, x + 2 * nt, n_toys, cnt);
+        cls_final_kernel<<<1, 1, 0, s>>>(cnt, n_toys, cl_out_dev, counts_out_dev);
+        st = cuda_fail(cudaGetLastError(), "cls launch");
+    }
+    if (Fb) cudaFreeAsync(Fb, s);
+    if (tb) cudaFreeAsync(tb, s);
+    if (Fsb) cudaFreeAsync(Fsb, s);
+    if (tsb) cudaFreeAsync(tsb, s);
     cudaFreeAsync(buf, s);
     return st;
 }

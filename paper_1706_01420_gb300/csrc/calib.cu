@@ -183,8 +183,8 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
         switch (fn) {
         case IPA_MATH_EXP: r = exp_int(v, &mt); break;
         case IPA_MATH_LOG: r = log_fast(v, &mt); break;
-        case IPA_MATH_SIN: { double s, c; sincos_int(v, &mt, &s, &c); r = s; break; }
-        case IPA_MATH_COS: { double s, c; sincos_int(v, &mt, &s, &c); r = c; break; }
+        case IPA_MATH_SIN: { double s, c; sincos_int_wide(v, &mt, &s, &c); r = s; break; }
+        case IPA_MATH_COS: { double s, c; sincos_int_wide(v, &mt, &s, &c); r = c; break; }
         case IPA_MATH_ERFCX: r = erfcx_fast(v, &mt); break;
         default: r = rcp_newton(v); break;
         }

@@ -24,7 +24,8 @@ the fixed-point tables and constants of the integer-pipe functions
 (int_math.cuh), each the exact value rounded once to an integer:
 
   sincos: round(sin(j pi/32) 2^62), round(cos(j pi/32) 2^62), j = 0..64;
-          2/pi and pi/32 in Q64; the Taylor coefficients 1/3!, .., 1/9! of sin
+          2/pi and pi/32 in Q64; 32/pi in Q59 and pi/32 in Q128 as two
+          64-bit words (the wide-range reduction); the Taylor coefficients 1/3!, .., 1/9! of sin
           and 1/2!, .., 1/8! of cos in Q64
   exp:    round(2^(j/64) 2^62), j = 0..63; 64/ln2 in Q56; ln2/64 in Q128 as
           two 64-bit words; 1/2!, .., 1/6! in Q63
@@ -182,6 +183,9 @@ __device__ const double kCosTab[64] = {{
 // ---- fixed-point tables and constants (int_math.cuh) ----
 constexpr unsigned long long kTwoOverPiQ64 = {q(2 / mp.pi, 64)}ull;     // 2/pi
 constexpr unsigned long long kPiOver32Q64 = {q(mp.pi / 32, 64)}ull;     // pi/32
+constexpr unsigned long long k32OverPiQ59 = {q(32 / mp.pi, 59)}ull;     // 32/pi
+constexpr unsigned long long kPiOver32Q128Hi = {q(mp.pi / 32, 128) >> 64}ull;   // pi/32, bits 2^-1..2^-64
+constexpr unsigned long long kPiOver32Q128Lo = {q(mp.pi / 32, 128) & ((1 << 64) - 1)}ull;   // bits 2^-65..2^-128
 constexpr unsigned long long kSinC3Q64 = {q(1 / fact[3], 64)}ull;
 constexpr unsigned long long kSinC5Q64 = {q(1 / fact[5], 64)}ull;
 constexpr unsigned long long kSinC7Q64 = {q(1 / fact[7], 64)}ull;

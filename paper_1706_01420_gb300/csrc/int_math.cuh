@@ -6,7 +6,8 @@
 // 64-bit fixed point (64 x 64 -> 128-bit products on the integer pipe, no
 // FP64 instruction) and round the fixed-point result once to a double:
 //
-//   sincos_int  |phi| < 4: phi in Q61, k = nearest multiple of pi/32,
+//   sincos_int  |phi| < 4 (sincos_int_wide: |phi| < 1024, for phases): phi in
+//               Q61 (Q53), k = nearest multiple of pi/32,
 //               r = phi - k pi/32 in Q64 (|r| <= pi/64), Taylor polynomials of
 //               sin r to r^9 and cos r to r^8 (truncation below 1e-19), then
 //               sin phi = S_k cos r + C_k sin r, cos phi = C_k cos r - S_k sin r
@@ -45,21 +46,12 @@ __device__ __forceinline__ double q62_to_double(long long v, int e2) {
     return __longlong_as_double((long long)(sign | (((unsigned long long)field << 52) + m)));
 }
 
-// sin and cos of |phi| in signed Q62 (|phi| < 4, the caller checks), before
-// the sign of phi is applied to the sine.
-__device__ __forceinline__ void sincos_q62(unsigned long long b, const MathTables* t, long long* sv,
-                                           long long* cv) {
+// sin(k pi/32 +- r) and cos(k pi/32 +- r) in Q62 from k (0..64) and |r| in
+// Q64 (|r| <= pi/64; rneg: the sign of r): Taylor polynomials of sin r and
+// 1 - cos r, then the angle-addition formulas with S_k, C_k from the tables.
+__device__ __forceinline__ void sincos_poly_q62(int k, unsigned long long r, bool rneg, const MathTables* t,
+                                                long long* sv, long long* cv) {
     using namespace fp64tab;
-    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
-    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-    const int sh = E + 9;                                   // |phi| in Q61
-    const unsigned long long X = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
-    const unsigned long long U = __umul64hi(X, kTwoOverPiQ64);        // |phi| 32/pi in Q57
-    const unsigned long long k = (U + (1ull << 56)) >> 57;
-    const long long rq = (long long)(U - (k << 57));                   // |rq| <= 2^56
-    const bool rneg = rq < 0;
-    const unsigned long long ra = rneg ? (unsigned long long)(-rq) : (unsigned long long)rq;
-    const unsigned long long r = __umul64hi(ra << 7, kPiOver32Q64);   // |r| in Q64
     const unsigned long long z = __umul64hi(r, r);                     // r^2
     unsigned long long p = kSinC9Q64;
     p = kSinC7Q64 - __umul64hi(z, p);
@@ -78,6 +70,24 @@ __device__ __forceinline__ void sincos_q62(unsigned long long b, const MathTable
     *cv = Ck - __mul64hi(Ck, cm) - __mul64hi(Sk, srs);
 }
 
+// sin and cos of |phi| in signed Q62 (|phi| < 4, the caller checks), before
+// the sign of phi is applied to the sine.
+__device__ __forceinline__ void sincos_q62(unsigned long long b, const MathTables* t, long long* sv,
+                                           long long* cv) {
+    using namespace fp64tab;
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = E + 9;                                   // |phi| in Q61
+    const unsigned long long X = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
+    const unsigned long long U = __umul64hi(X, kTwoOverPiQ64);        // |phi| 32/pi in Q57
+    const unsigned long long k = (U + (1ull << 56)) >> 57;
+    const long long rq = (long long)(U - (k << 57));                   // |rq| <= 2^56
+    const bool rneg = rq < 0;
+    const unsigned long long ra = rneg ? (unsigned long long)(-rq) : (unsigned long long)rq;
+    const unsigned long long r = __umul64hi(ra << 7, kPiOver32Q64);   // |r| in Q64
+    sincos_poly_q62((int)k, r, rneg, t, sv, cv);
+}
+
 // sin and cos of phi for |phi| < 4 (else the table-driven sincos_fast).
 __device__ __forceinline__ void sincos_int(double phi, const MathTables* t, double* s, double* c) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(phi);
@@ -87,6 +97,36 @@ __device__ __forceinline__ void sincos_int(double phi, const MathTables* t, doub
     }
     long long sv, cv;
     sincos_q62(b, t, &sv, &cv);
+    const double sd = q62_to_double(sv, 0);
+    *s = (b >> 63) ? -sd : sd;
+    *c = q62_to_double(cv, 0);
+}
+
+// sin and cos of phi for |phi| < 1024 (else the table-driven sincos_fast), for
+// phases such as Dm t: |phi| in Q53 (exact for |phi| >= 1/2, within 2^-53
+// otherwise), k = nearest integer to |phi| 32/pi, r = |phi| - k pi/32 in Q64
+// with pi/32 to 128 bits (error below 2^-110), then the polynomials of
+// sincos_poly_q62 with the table entry k mod 64.
+__device__ __forceinline__ void sincos_int_wide(double phi, const MathTables* t, double* s, double* c) {
+    using namespace fp64tab;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(phi);
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    if (E > 9) {                                            // |phi| >= 1024, inf, NaN
+        sincos_fast(phi, t, s, c);
+        return;
+    }
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = E + 1;                                   // |phi| in Q53
+    const unsigned long long A = sh >= 0 ? M << sh : (sh > -64 ? M >> -sh : 0ull);
+    // k = round(|phi| 32/pi): A (Q53) x 32/pi (Q59) >> 64 is Q48
+    const unsigned long long P = __umul64hi(A, k32OverPiQ59);
+    const unsigned long long k = (P + (1ull << 47)) >> 48;
+    const unsigned __int128 kl = (unsigned __int128)k * kPiOver32Q128Hi +
+                                 (((unsigned __int128)k * kPiOver32Q128Lo) >> 64);
+    const long long r = (long long)(((__int128)A << 11) - (__int128)kl);    // Q64, |r| <= pi/64
+    const bool rneg = r < 0;
+    long long sv, cv;
+    sincos_poly_q62((int)(k & 63ull), rneg ? (unsigned long long)(-r) : (unsigned long long)r, rneg, t, &sv, &cv);
     const double sd = q62_to_double(sv, 0);
     *s = (b >> 63) ? -sd : sd;
     *c = q62_to_double(cv, 0);

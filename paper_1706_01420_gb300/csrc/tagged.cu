@@ -7,7 +7,7 @@
 // term is below 1e-17 of its exponential and
 //   2 gH = exp(-Gamma_H tau + Gamma_H^2 sigma^2/2 + ln2),  2 gL likewise,
 //   2 g  = exp(-Gamma tau + (Gamma^2 - Dm^2) sigma^2/2 + ln2) e^{i (Dm tau - Gamma Dm sigma^2)}:
-// three exponentials on the integer pipe and one sine/cosine pair.  Events
+// three exponentials and one sine/cosine pair, all on the integer pipe.  Events
 // with t <= tcut (up to about six resolution widths past the peak) also need
 // the Gaussian, two erfcx and one Faddeeva function; as in the 4D kernel they
 // are listed by ballot and evaluated 32 to a pass into the warp's buffer, so
@@ -77,7 +77,7 @@ __device__ __forceinline__ void tag_event(const TagConsts& c, const MathTables* 
     const double E2L = exp_int(fma(-c.GL, tau, c.cL2), mt);
     const double E2C = exp_int(fma(-c.Gamma, tau, c.cC2), mt);
     double sn, cn;
-    sincos_fast(fma(c.Dm, tau, -c.ph0), mt, &sn, &cn);
+    sincos_int_wide(fma(c.Dm, tau, -c.ph0), mt, &sn, &cn);
     const long long bH = __double_as_longlong(sl.xH), bL = __double_as_longlong(sl.xL);
     const long long bG = __double_as_longlong(sl.gx);
     const double T2H = bH < 0 ? -sl.xH : E2H - sl.xH;

@@ -32,7 +32,8 @@ def tab():
 
     names = ["kTwoOverPiQ64", "kPiOver32Q64", "kSinC3Q64", "kSinC5Q64", "kSinC7Q64", "kSinC9Q64", "kCosC2Q64",
              "kCosC4Q64", "kCosC6Q64", "kCosC8Q64", "kInvLn2x64Q56", "kLn2d64Q128Hi", "kLn2d64Q128Lo",
-             "kExpC2Q63", "kExpC3Q63", "kExpC4Q63", "kExpC5Q63", "kExpC6Q63"]
+             "kExpC2Q63", "kExpC3Q63", "kExpC4Q63", "kExpC5Q63", "kExpC6Q63", "k32OverPiQ59",
+             "kPiOver32Q128Hi", "kPiOver32Q128Lo"]
     t = {n: const(n) for n in names}
     t["S"], t["C"], t["E"] = arr("kSinQ62"), arr("kCosQ62"), arr("kExp2Q62")
     return t
@@ -46,6 +47,8 @@ def test_tables_are_exact_values_rounded_once(tab):
     assert tab["kTwoOverPiQ64"] == _q(2 / mp.pi, 64) and tab["kPiOver32Q64"] == _q(mp.pi / 32, 64)
     assert tab["kInvLn2x64Q56"] == _q(64 / mp.log(2), 56)
     assert (tab["kLn2d64Q128Hi"] << 64) + tab["kLn2d64Q128Lo"] == _q(mp.log(2) / 64, 128)
+    assert (tab["kPiOver32Q128Hi"] << 64) + tab["kPiOver32Q128Lo"] == _q(mp.pi / 32, 128)
+    assert tab["k32OverPiQ59"] == _q(32 / mp.pi, 59)
     for n, k in ((3, "kSinC3Q64"), (5, "kSinC5Q64"), (7, "kSinC7Q64"), (9, "kSinC9Q64"), (2, "kCosC2Q64"),
                  (4, "kCosC4Q64"), (6, "kCosC6Q64"), (8, "kCosC8Q64")):
         assert tab[k] == _q(1 / mp.factorial(n), 64)
@@ -109,6 +112,47 @@ def _sincos(t, phi):
     Sk, Ck = t["S"][k], t["C"][k]
     sd = _q62_to_double(_s64(Sk - _mulhi(Sk, cm) + _mulhi(Ck, srs)), 0)
     return (-sd if b >> 63 else sd), _q62_to_double(_s64(Ck - _mulhi(Ck, cm) - _mulhi(Sk, srs)), 0)
+
+
+def _sincos_wide(t, phi):
+    """sincos_int_wide: |phi| < 1024 in Q53, k = round(|phi| 32/pi), r in Q64 with
+    pi/32 to 128 bits, then the same polynomials and table (entry k mod 64)."""
+    b = _bits(phi)
+    E = ((b >> 52) & 0x7FF) - 1023
+    M = (b & 0xFFFFFFFFFFFFF) | (1 << 52)
+    sh = E + 1
+    A = (M << sh) & M64 if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    k = (_umulhi(A, t["k32OverPiQ59"]) + (1 << 47)) >> 48
+    kl = k * t["kPiOver32Q128Hi"] + ((k * t["kPiOver32Q128Lo"]) >> 64)
+    r = _s64((A << 11) - kl)
+    ra = -r if r < 0 else r
+    z = _umulhi(ra, ra)
+    p = t["kSinC9Q64"]
+    for c in ("kSinC7Q64", "kSinC5Q64", "kSinC3Q64"):
+        p = (t[c] - _umulhi(z, p)) & M64
+    sr = _s64(ra - _umulhi(ra, _umulhi(z, p)))
+    q = t["kCosC8Q64"]
+    for c in ("kCosC6Q64", "kCosC4Q64", "kCosC2Q64"):
+        q = (t[c] - _umulhi(z, q)) & M64
+    cm = _s64(_umulhi(z, q))
+    srs = -sr if r < 0 else sr
+    Sk, Ck = t["S"][k & 63], t["C"][k & 63]
+    sd = _q62_to_double(_s64(Sk - _mulhi(Sk, cm) + _mulhi(Ck, srs)), 0)
+    return (-sd if b >> 63 else sd), _q62_to_double(_s64(Ck - _mulhi(Ck, cm) - _mulhi(Sk, srs)), 0)
+
+
+def test_wide_sincos_emulation_accuracy(tab):
+    """Phases up to 1024 (Dm t of the tagged model reaches a few hundred)."""
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([rng.uniform(-1023.9, 1023.9, 3000), rng.uniform(-4, 4, 500),
+                         [0.0, 1e-300, 0.5, 1023.99, -1023.99, 100 * np.pi, 201.0625, 266.55]])
+    worst = 0.0
+    with mp.workdps(60):
+        for x in xs:
+            s, c = _sincos_wide(tab, float(x))
+            worst = max(worst, abs(float(mp.mpf(s) - mp.sin(mp.mpf(float(x))))),
+                        abs(float(mp.mpf(c) - mp.cos(mp.mpf(float(x))))))
+    assert worst <= 6e-17, worst
 
 
 def _exp(t, a):
