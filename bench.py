@@ -82,13 +82,13 @@ OPS_LIBRARY_4D = {"fma": 32, "mul": 30, "add": 6, "exp": 2, "erfc": 1, "log": 1,
 
 # The flavour-tagged model (IPA_MODEL_TAGGED1D, tagged.cu), counted the same way:
 #   every event: tau, three exponents (integer-pipe exp), the oscillation phase
-#     and its sine/cosine (table-driven FP64), 2 gH, 2 gL, 2 g (complex), q qD
-#     and P, 1/P, and the 12 adjoint sums;
+#     (its sine and cosine on the integer pipe), 2 gH, 2 gL, 2 g (complex),
+#     q qD and P, 1/P, and the 12 adjoint sums;
 #   events with t <= tcut (mu + max(Gamma_H, Gamma_L, Gamma) sigma^2 +
 #     sqrt(39.1 + (Dm sigma)^2 / 2) sqrt2 sigma): the Gaussian's exponent, three
 #     erfc arguments, two erfcx and the Faddeeva function (39 complex Horner
 #     steps, one division), and the five products stored for the event.
-OPS_TAG_EVENT = {"fma": 17, "mul": 8, "add": 9, "sincos_fast": 1}
+OPS_TAG_EVENT = {"fma": 17, "mul": 8, "add": 9}
 OPS_TAG_SLOW = {"fma": 125, "mul": 58, "add": 5, "erfcx_poly": 2, "rcp": 1}
 TH_TAG = np.array([0.66, 0.045, 0.0, 0.1, 0.085, 17.77, 0.8, 0.3])
 
