@@ -52,12 +52,13 @@ I_OMEGA = 16.0 * math.pi / 9.0   # integral of A over the angles when sum |A_i|^
 
 IDX = {"Gamma": 0, "sigma": 1, "mu": 2, "f_b": 3, "A0sq": 4, "Apesq": 5,
        "delta_pa": 6, "delta_pe": 7, "F_S": 8, "delta_S": 9}
-NPAR = {"1d": 4, "4d": 10, "tag": 8}
+NPAR = {"1d": 4, "4d": 10, "tag": 8, "phis": 14}
 
 
 @dataclass
 class Model:
-    kind: str            # "1d", "4d" or "tag" (flavour-tagged decay time, oracle/tagged.py)
+    kind: str            # "1d", "4d", "tag" (flavour-tagged decay time, oracle/tagged.py) or
+                         # "phis" (time-dependent angular model with tagging, oracle/phis.py)
     t_lo: float
     t_hi: float
 
@@ -71,6 +72,8 @@ class Model:
         dt = self.t_hi - self.t_lo
         if self.kind == "tag":
             return 2.0 * dt              # decay time x tag q = +-1
+        if self.kind == "phis":
+            return 2.0 * dt * 2.0 * 2.0 * 2.0 * math.pi   # decay time x angles x tag
         return dt if self.kind == "1d" else dt * 2.0 * 2.0 * 2.0 * math.pi
 
 
@@ -272,6 +275,9 @@ def pdf(model: Model, ev: dict, theta) -> np.ndarray:
     if model.kind == "tag":
         from . import tagged
         return tagged.pdf(model, ev, theta)
+    if model.kind == "phis":
+        from . import phis
+        return phis.pdf(model, ev, theta)
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu, f_b = theta[:4]
     t, _ = _cols(model, ev)
@@ -296,6 +302,9 @@ def nll_grad_terms(model: Model, ev: dict, theta):
     if model.kind == "tag":
         from . import tagged
         return tagged.nll_grad_terms(model, ev, theta)
+    if model.kind == "phis":
+        from . import phis
+        return phis.nll_grad_terms(model, ev, theta)
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu, f_b = theta[:4]
     t, w = _cols(model, ev)

@@ -1,0 +1,239 @@
+"""Plain FP64 CPU oracle of the full time-dependent angular model of
+B_s -> J/psi K K with flavour tagging (test infrastructure only, like the rest
+of ``oracle/``: only tests, the smoke check and the bench's CPU legs use it).
+
+The method (arXiv:1706.01420, Sec. 4, Example 2): the phi_s fit of
+B_s -> J/psi K K in decay time and the three helicity angles, P wave (three
+polarisations) and S wave, with the widths Gamma_L, Gamma_H (the cosh and
+sinh terms), the flavour-tagged oscillation Delta m_s and the CP-violating
+phase; the resolution-convolved oscillation uses the Faddeeva function
+(Sec. 2).  The paper prints no formula; the reading here is the plain time
+evolution of the transversity amplitudes:
+
+* amplitudes A_i, i = 0, para, perp, S, as in the 4D model (``ipa_oracle``:
+  |A_i|^2 from A0sq, Apesq with the P wave scaled by 1 - F_S, |A_S|^2 = F_S,
+  delta_0 = 0), CP eigenvalues eta = (+1, +1, -1, -1);
+* a B_s produced at t = 0 decays with A_i(t) = A_i [g+(t) + eta_i lambda g-(t)],
+  a anti-B_s with A_i [g-(t) + eta_i lambda g+(t)] (the common factor p/q
+  dropped, |q/p| = 1, |lambda| = 1), lambda = e^{-i phi_s},
+  g+-(t) = (e^{-i m_L t - Gamma_L t/2} +- e^{-i m_H t - Gamma_H t/2}) / 2,
+  Gamma_L,H = Gamma +- DG/2, Dm = m_H - m_L;
+* the ten angular terms are the bilinears of the 4D model with A_i -> A_i(t):
+  |A_0|^2, |A_pa|^2, |A_pe|^2, Im(A_pa* A_pe), Re(A_0* A_pa), Im(A_0* A_pe),
+  |A_S|^2, Re(A_S* A_pa), Im(A_S* A_pe), Re(A_S* A_0), each times f_k(Omega);
+* the products of g's are sums of exponentials,
+  |g+-|^2 = (E_L + E_H +- 2 E_c) / 4,  g+* g- = (E_L - E_H + 2i E_s) / 4,
+  g-* g+ = (E_L - E_H - 2i E_s) / 4,  E_L,H = e^{-Gamma_L,H t},
+  E_c + i E_s = e^{-Gamma t} e^{i Dm t};
+  with the Gaussian resolution (sigma, offset mu) each becomes its
+  convolution: E_L,H -> g(tau; Gamma_L,H), E_c + i E_s -> g(tau; Gamma - i Dm)
+  (``tagged.conv_c``);
+* tag q = +1 (B_s) or -1, mistag omega: rate(q) = (1 - omega) R_q + omega R_-q;
+* normalisation over t in [t_lo, t_hi], the angles and both tags (the
+  oscillating terms cancel in the sum over tags and the interference terms in
+  the angular integral): N = (16 pi / 9) sum_i |A_i|^2 [(1 + eta_i c) I(Gamma_L)
+  + (1 - eta_i c) I(Gamma_H)], c = cos phi_s;
+* P = (1 - f_b) rate / N + f_b / (2 (t_hi - t_lo) 8 pi).
+
+Parameters (ABI order): Gamma, sigma, mu, f_b, A0sq, Apesq, delta_pa,
+delta_pe, F_S, delta_S, DG, Dm, phi_s, omega.  Events: t, ck, cl, phi, q.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import ipa_oracle as O
+from . import tagged as T
+
+NPAR = 14
+ETA = (1.0, 1.0, -1.0, -1.0)
+# (i, j, part) of the ten bilinears conj(A_i) A_j, part 'r' = Re, 'i' = Im
+PAIRS = ((0, 0, "r"), (1, 1, "r"), (2, 2, "r"), (1, 2, "i"), (0, 1, "r"), (0, 2, "i"), (3, 3, "r"),
+         (3, 1, "r"), (3, 2, "i"), (3, 0, "r"))
+ANG = (4, 5, 6, 7, 8, 9)   # the six amplitude parameters
+
+
+def amplitudes(theta, grad: bool = True):
+    """(A_0, A_pa, A_pe, A_S) and dA/d(A0sq, Apesq, delta_pa, delta_pe, F_S, delta_S), shape (4, 6)
+    (None without grad; the derivatives need every magnitude above zero)."""
+    x0, xe, dpa, dpe, F, dS = (float(theta[i]) for i in ANG)
+    xa = 1.0 - x0 - xe
+    s = 1.0 - F
+    e_pa, e_pe, e_S = np.exp(1j * dpa), np.exp(1j * dpe), np.exp(1j * dS)
+    r0, ra, re, rF = math.sqrt(s * x0), math.sqrt(s * xa), math.sqrt(s * xe), math.sqrt(F)
+    A = np.array([r0, ra * e_pa, re * e_pe, rF * e_S], dtype=complex)
+    if not grad:
+        return A, None
+    dA = np.zeros((4, 6), dtype=complex)
+    # d sqrt(s x) / dx = s / (2 sqrt(s x)); d/dF of sqrt(s x) = -x / (2 sqrt(s x)); xa = 1 - x0 - xe
+    dA[0, 0] = s / (2.0 * r0)
+    dA[1, 0] = -s / (2.0 * ra) * e_pa
+    dA[1, 1] = -s / (2.0 * ra) * e_pa
+    dA[2, 1] = s / (2.0 * re) * e_pe
+    dA[1, 2] = 1j * A[1]
+    dA[2, 3] = 1j * A[2]
+    dA[0, 4] = -x0 / (2.0 * r0)
+    dA[1, 4] = -xa / (2.0 * ra) * e_pa
+    dA[2, 4] = -xe / (2.0 * re) * e_pe
+    dA[3, 4] = 1.0 / (2.0 * rF) * e_S
+    dA[3, 5] = 1j * A[3]
+    return A, dA
+
+
+def _products(gL, gH, gc):
+    """|g+|^2, |g-|^2, g+* g-, g-* g+ (convolved)."""
+    PP = 0.25 * (gL + gH + 2.0 * gc.real)
+    MM = 0.25 * (gL + gH - 2.0 * gc.real)
+    PM = 0.25 * (gL - gH + 2j * gc.imag)
+    MP = 0.25 * (gL - gH - 2j * gc.imag)
+    return PP, MM, PM, MP
+
+
+def _observed(b, ei, ej, lam, q, om, PP, MM, PM, MP):
+    """(1 - omega) R_q + omega R_-q of the bilinear conj(A_i(t)) A_j(t) with b = conj(A_i) A_j."""
+    X = b * (PP + ej * lam * PM + ei * np.conj(lam) * MP + ei * ej * MM)     # B_s at t = 0
+    Y = b * (MM + ej * lam * MP + ei * np.conj(lam) * PM + ei * ej * PP)     # anti-B_s at t = 0
+    Rq = np.where(q > 0, X, Y)
+    Rm = np.where(q > 0, Y, X)
+    return (1.0 - om) * Rq + om * Rm, X, Y
+
+
+def _part(z, p):
+    return z.real if p == "r" else z.imag
+
+
+def rate(model: O.Model, ev: dict, theta):
+    """Unnormalised rate(t, Omega, q) (each event's own tag)."""
+    return rate_grad(model, ev, theta, grad=False)[0]
+
+
+def rate_grad(model: O.Model, ev: dict, theta, grad: bool = True):
+    """rate and d rate / d theta (14 rows; the f_b row is zero; None without grad)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    Gamma, sigma, mu = (float(theta[i]) for i in range(3))
+    DG, Dm, phi, om = (float(theta[i]) for i in range(10, 14))
+    GL, GH = Gamma + 0.5 * DG, Gamma - 0.5 * DG
+    z = complex(Gamma, -Dm)
+    t = np.asarray(ev["t"], dtype=np.float64)
+    q = np.asarray(ev["q"], dtype=np.float64)
+    tau = t - mu
+    f = O.angular_basis(ev["ck"], ev["cl"], ev["phi"])
+    cL = T.conv_c_grad(tau, GL, sigma)       # (g, dg/dz, dg/dsigma, dg/dtau)
+    cH = T.conv_c_grad(tau, GH, sigma)
+    cC = T.conv_c_grad(tau, z, sigma)
+    gL, gH = cL[0].real, cH[0].real
+    gc = cC[0]
+    A, dA = amplitudes(theta, grad)
+    lam = complex(math.cos(phi), -math.sin(phi))
+    dlam = -1j * lam
+    PP, MM, PM, MP = _products(gL, gH, gc)
+    n = t.size
+    R = np.zeros(n)
+    dR = np.zeros((NPAR, n))
+
+    # derivatives of (gL, gH, gc) in the time parameters: Gamma, sigma, mu, DG, Dm
+    tg = {
+        0: (cL[1].real, cH[1].real, cC[1]),
+        1: (cL[2].real, cH[2].real, cC[2]),
+        2: (-cL[3].real, -cH[3].real, -cC[3]),
+        10: (0.5 * cL[1].real, -0.5 * cH[1].real, 0.0 * cC[1]),
+        11: (0.0 * gL, 0.0 * gH, -1j * cC[1]),
+    }
+    dprod = {j: _products(*v) for j, v in tg.items()}
+    for k, (i, j, p) in enumerate(PAIRS):
+        b = np.conj(A[i]) * A[j]
+        ei, ej = ETA[i], ETA[j]
+        Ok, X, Y = _observed(b, ei, ej, lam, q, om, PP, MM, PM, MP)
+        R += f[k] * _part(Ok, p)
+        if not grad:
+            continue
+        # amplitude parameters
+        for a in range(6):
+            db = np.conj(dA[i, a]) * A[j] + np.conj(A[i]) * dA[j, a]
+            if db != 0:
+                dO = _observed(db, ei, ej, lam, q, om, PP, MM, PM, MP)[0]
+                dR[ANG[a]] += f[k] * _part(dO, p)
+        # phi_s: d lambda = -i lambda, d conj(lambda) = conj(d lambda)
+        Xd = b * (ej * dlam * PM + ei * np.conj(dlam) * MP)
+        Yd = b * (ej * dlam * MP + ei * np.conj(dlam) * PM)
+        dO = (1.0 - om) * np.where(q > 0, Xd, Yd) + om * np.where(q > 0, Yd, Xd)
+        dR[12] += f[k] * _part(dO, p)
+        # omega
+        dR[13] += f[k] * _part(np.where(q > 0, Y - X, X - Y), p)
+        # time parameters
+        for jj, (dPP, dMM, dPM, dMP) in dprod.items():
+            dO = _observed(b, ei, ej, lam, q, om, dPP, dMM, dPM, dMP)[0]
+            dR[jj] += f[k] * _part(dO, p)
+    return R, (dR if grad else None)
+
+
+def norm_grad(model: O.Model, theta):
+    """N and dN/dtheta (14 entries)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    Gamma, sigma, mu = (float(theta[i]) for i in range(3))
+    DG, phi = float(theta[10]), float(theta[12])
+    GL, GH = Gamma + 0.5 * DG, Gamma - 0.5 * DG
+    c, s = math.cos(phi), math.sin(phi)
+    IL = O.time_norm_grad(GL, sigma, mu, model.t_lo, model.t_hi)   # (I, dGamma, dsigma, dmu)
+    IH = O.time_norm_grad(GH, sigma, mu, model.t_lo, model.t_hi)
+    A, _ = amplitudes(theta, grad=False)
+    m2 = np.abs(A) ** 2
+    # d|A_i|^2 / d(A0sq, Apesq, delta_pa, delta_pe, F_S, delta_S), from |A_i|^2 = (1 - F) x_i, F
+    x0, xe, F = float(theta[4]), float(theta[5]), float(theta[8])
+    xa = 1.0 - x0 - xe
+    dm2 = np.array([[1 - F, 0, 0, 0, -x0, 0], [-(1 - F), -(1 - F), 0, 0, -xa, 0],
+                    [0, 1 - F, 0, 0, -xe, 0], [0, 0, 0, 0, 1.0, 0]])
+    eta = np.array(ETA)
+    wL, wH = float(np.sum(m2 * (1 + eta * c))), float(np.sum(m2 * (1 - eta * c)))
+    K = 16.0 * math.pi / 9.0
+    N = K * (wL * IL[0] + wH * IH[0])
+    d = np.zeros(NPAR)
+    d[0] = K * (wL * IL[1] + wH * IH[1])
+    d[1] = K * (wL * IL[2] + wH * IH[2])
+    d[2] = K * (wL * IL[3] + wH * IH[3])
+    d[10] = K * (0.5 * wL * IL[1] - 0.5 * wH * IH[1])
+    for a in range(6):
+        dwL = float(np.sum(dm2[:, a] * (1 + eta * c)))
+        dwH = float(np.sum(dm2[:, a] * (1 - eta * c)))
+        d[ANG[a]] = K * (dwL * IL[0] + dwH * IH[0])
+    d[12] = K * (float(np.sum(m2 * (-eta * s))) * IL[0] + float(np.sum(m2 * (eta * s))) * IH[0])
+    return N, d
+
+
+def volume(model: O.Model) -> float:
+    return 2.0 * (model.t_hi - model.t_lo) * 8.0 * math.pi
+
+
+def pdf(model: O.Model, ev: dict, theta) -> np.ndarray:
+    N, _ = norm_grad(model, theta)
+    R = rate(model, ev, theta)
+    f_b = float(theta[3])
+    return (1.0 - f_b) * R / N + f_b / volume(model)
+
+
+def nll_grad_terms(model: O.Model, ev: dict, theta):
+    """Per-event w log P and -w (dP/dtheta_j) / P (a (14, N) array)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    f_b = float(theta[3])
+    t = np.asarray(ev["t"], dtype=np.float64)
+    w = ev.get("w")
+    w = np.ones_like(t) if w is None else np.asarray(w, dtype=np.float64)
+    N, dN = norm_grad(model, theta)
+    R, dR = rate_grad(model, ev, theta)
+    V = volume(model)
+    P = (1.0 - f_b) * R / N + f_b / V
+    dP = (1.0 - f_b) * (dR / N - np.outer(dN, R) / (N * N))
+    dP[3] = -R / N + 1.0 / V
+    return w * np.log(P), -w * dP / P
+
+
+def nll(model: O.Model, ev: dict, theta) -> float:
+    logl, _ = nll_grad_terms(model, ev, theta)
+    return -math.fsum(logl)
+
+
+def nll_grad(model: O.Model, ev: dict, theta):
+    logl, terms = nll_grad_terms(model, ev, theta)
+    return -math.fsum(logl), np.array([math.fsum(row) for row in terms])
