@@ -612,6 +612,7 @@ def run_extras(api, synth, torch, dev, m, ev, theta, cal) -> dict:
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     out["tagged"] = run_tagged(api, synth, torch, dev, cal, flush)
     out["cls"] = run_cls(api, torch, dev)
+    out["phis"] = run_phis(api, synth, torch, dev, flush)
     return out
 
 
@@ -722,6 +723,39 @@ def run_errors(api, torch, dev, m, cols, off, params, rb, n_minos: int = 64) -> 
                       "intervals_per_s": n_minos * 10 / t_m,
                       "status_counts": np.bincount(st_m, minlength=6).tolist(),
                       "median_asymmetry": float(asym.median())}}
+
+
+TH_PHIS = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3])
+
+
+def run_phis(api, synth, torch, dev, flush, steps: int = 30) -> dict:
+    """The time-dependent angular model with tagging (14 parameters) on 1e6
+    synthetic events (t, angles, tag): NLL+grad per step with L2 flushed, the
+    raw and the cached angular basis."""
+    m = api.model_phis(0.0, 15.0)
+    ev = {k: torch.tensor(v, device=dev) for k, v in synth.events_phis(1_000_000, 11).items()}
+    theta = torch.tensor(TH_PHIS, device=dev)
+    out = torch.empty(15, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {"workload": "time-dependent angular model with tagging, 1e6 FP64 SoA events (t, 3 angles, q), "
+                       "14 params, ipa_nll_grad", "events": 1_000_000}
+    for name, evx in (("raw", ev), ("cached_basis", dict(ev, fk=api.ipa_angular_basis(m, ev)))):
+        res["launch_" + name] = api.ipa_autotune(m, evx, theta, grad=True, stream=stream)
+        for _ in range(3):
+            api.ipa_nll_grad(m, evx, theta, out)
+        torch.cuda.synchronize()
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            a[i].record(stream)
+            api.ipa_nll_grad(m, evx, theta, out)
+            b[i].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
+        res["nll_grad_ms_" + name] = ms
+        res["Gevents_per_s_" + name] = 1e6 / (ms * 1e-3) / 1e9
+    return res
 
 
 def run_cls(api, torch, dev, n_bins: int = 10000, n_toys: int = 10000) -> dict:

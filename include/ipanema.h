@@ -66,8 +66,25 @@ typedef enum {
 typedef enum {
     IPA_MODEL_TIME1D = 1,     /* decay time only: P(t)                              */
     IPA_MODEL_ANGTIME4D = 2,  /* decay time x helicity angles: P(t, ck, cl, phi)    */
-    IPA_MODEL_TAGGED1D = 3    /* flavour-tagged decay time with B_s oscillation: P(t, q) */
+    IPA_MODEL_TAGGED1D = 3,   /* flavour-tagged decay time with B_s oscillation: P(t, q) */
+    IPA_MODEL_PHIS = 4        /* time-dependent angular model with tagging: P(t, ck, cl, phi, q) */
 } ipa_model_kind;
+
+/* The full time-dependent angular model (Sec. 4, the phi_s fit of
+ * B_s -> J/psi K K: P wave and S wave, Gamma_L and Gamma_H, flavour-tagged
+ * Dm oscillation, the CP phase; Sec. 2 for the convolution of the
+ * oscillation with the resolution).  The paper prints no formula; this
+ * library evolves the transversity amplitudes of the 4D model in time:
+ * A_i(t) = A_i [g+(t) + eta_i lambda g-(t)] for a B_s at t = 0 and
+ * A_i [g-(t) + eta_i lambda g+(t)] for a anti-B_s, eta = (+1, +1, -1, -1) for
+ * (0, para, perp, S), lambda = e^{-i phi_s}; the ten angular terms are the
+ * bilinears of the 4D model with A_i -> A_i(t), whose products of g+- are
+ * sums of e^{-Gamma_L t}, e^{-Gamma_H t} and e^{-Gamma t} e^{i Dm t}, each
+ * convolved with the Gaussian resolution; a tag q = +-1 with mistag omega
+ * mixes the two initial flavours; normalised over t, the angles and both
+ * tags, plus a flat background f_b.  Parameters: the ten of the 4D model,
+ * then DG, Dm, phi_s, omega (IPA_PHIS_DG .. IPA_PHIS_OMEGA).  Events carry
+ * t, ck, cl, phi and q. */
 
 /* The tagged model (Sec. 4, the B_s -> J/psi phi example, whose time-dependent
  * fit has the oscillation frequency Dm_s, the widths Gamma and DG and the
@@ -86,8 +103,9 @@ typedef enum {
  * Parameters: Gamma, sigma, mu, f_b, DG, Dm, phi_s, omega (IPA_GAMMA ..
  * IPA_OMEGA).  Events carry t and q = +1.0 or -1.0. */
 
-/* Parameter indices (theta layout).  1D uses the first 4, 4D all 10, the
- * tagged model the first 4 and its own 4 to 7. */
+/* Parameter indices (theta layout).  1D uses the first 4, 4D the first 10,
+ * the tagged model the first 4 and its own 4 to 7, the phi_s model the ten
+ * of the 4D model and 10 to 13. */
 enum {
     IPA_GAMMA = 0,   /* decay width Gamma [1/ps]                   */
     IPA_SIGMA = 1,   /* Gaussian time resolution sigma [ps]        */
@@ -103,9 +121,14 @@ enum {
     IPA_DM = 5,      /* tagged: mass difference Dm_s [1/ps]        */
     IPA_PHIS = 6,    /* tagged: CP-violating phase phi_s [rad]     */
     IPA_OMEGA = 7,   /* tagged: mistag probability omega           */
+    IPA_PHIS_DG = 10,    /* phi_s model: DG = Gamma_L - Gamma_H [1/ps]  */
+    IPA_PHIS_DM = 11,    /* phi_s model: Dm_s [1/ps]                    */
+    IPA_PHIS_PHIS = 12,  /* phi_s model: phi_s [rad]                    */
+    IPA_PHIS_OMEGA = 13, /* phi_s model: mistag probability omega       */
     IPA_NPAR_1D = 4,
     IPA_NPAR_4D = 10,
     IPA_NPAR_TAGGED = 8,
+    IPA_NPAR_PHIS = 14,
     IPA_MAX_PAR = 16
 };
 
@@ -120,7 +143,8 @@ typedef struct {
 /* An event set (Cat of App. C): n events as FP64 SoA device columns.
  * t is required; ck, cl, phi are required for the 4D model and ignored
  * otherwise; q (the flavour tag, +1.0 or -1.0) is required for the tagged
- * model and ignored otherwise; w may be NULL (unit weights).  Every column is
+ * and the phi_s models and ignored otherwise; w may be NULL (unit weights).
+ * The phi_s model needs t, ck, cl, phi and q.  Every column is
  * 16-byte aligned.  fk may be NULL, or hold the angular basis of these events
  * written by ipa_angular_basis (10 columns of fk_stride doubles); 4D
  * likelihood and fit calls then read it instead of evaluating the angular
@@ -144,7 +168,7 @@ typedef struct {
 /* The model: its kind, number of parameters and the decay-time range. */
 typedef struct {
     int32_t kind;      /* ipa_model_kind */
-    int32_t n_par;     /* IPA_NPAR_1D, IPA_NPAR_4D or IPA_NPAR_TAGGED (set by ipa_model_init) */
+    int32_t n_par;     /* IPA_NPAR_1D, _4D, _TAGGED or _PHIS (set by ipa_model_init) */
     double t_lo, t_hi; /* decay-time range [ps], t_lo < t_hi */
 } ipa_model;
 

@@ -13,10 +13,11 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_size_t, c_ui
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libipanema.so")
 
 IPA_OK, IPA_ERR_ARG, IPA_ERR_OOM, IPA_ERR_CUDA, IPA_ERR_TIMEOUT, IPA_ERR_BUSY, IPA_PENDING = 0, -1, -2, -3, -4, -5, 1
-IPA_MODEL_TIME1D, IPA_MODEL_ANGTIME4D, IPA_MODEL_TAGGED1D = 1, 2, 3
+IPA_MODEL_TIME1D, IPA_MODEL_ANGTIME4D, IPA_MODEL_TAGGED1D, IPA_MODEL_PHIS = 1, 2, 3, 4
 IPA_GAMMA, IPA_SIGMA, IPA_MU, IPA_FB, IPA_A0SQ, IPA_APESQ, IPA_DPA, IPA_DPE, IPA_FS, IPA_DS = range(10)
 IPA_DG, IPA_DM, IPA_PHIS, IPA_OMEGA = 4, 5, 6, 7
-IPA_NPAR_1D, IPA_NPAR_4D, IPA_NPAR_TAGGED, IPA_MAX_PAR = 4, 10, 8, 16
+IPA_PHIS_DG, IPA_PHIS_DM, IPA_PHIS_PHIS, IPA_PHIS_OMEGA = 10, 11, 12, 13
+IPA_NPAR_1D, IPA_NPAR_4D, IPA_NPAR_TAGGED, IPA_NPAR_PHIS, IPA_MAX_PAR = 4, 10, 8, 14, 16
 IPA_NOALLOC_MAX_EVENTS = 8388608
 IPA_MATH_EXP, IPA_MATH_LOG, IPA_MATH_SIN, IPA_MATH_COS, IPA_MATH_ERFCX, IPA_MATH_RCP = range(6)
 IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)

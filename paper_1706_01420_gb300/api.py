@@ -66,6 +66,11 @@ def model_tagged(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
     return ipa_model_init(C.IPA_MODEL_TAGGED1D, t_lo, t_hi)
 
 
+def model_phis(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
+    """The time-dependent angular model with flavour tagging (14 parameters)."""
+    return ipa_model_init(C.IPA_MODEL_PHIS, t_lo, t_hi)
+
+
 def ipa_events(ev: dict) -> C.ipa_events:
     """dict of CUDA float64 columns (t[, ck, cl, phi][, q][, w][, fk]) -> ipa_events.
 

@@ -30,6 +30,7 @@ ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Cons
                          cudaStream_t st) {
     if (n_seg <= 0) return IPA_OK;
     if (m.kind == IPA_MODEL_TAGGED1D) return launch_tag_consts(m, theta, n_seg, out, st);
+    if (m.kind == IPA_MODEL_PHIS) return launch_phis_consts(m, theta, n_seg, out, st);
     if (n_seg >= 64) {
         consts_thread_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
         return cuda_fail(cudaGetLastError(), "consts kernel launch");

@@ -26,7 +26,7 @@
 
 namespace ipa {
 
-constexpr int kMaxP = 10;          // parameters of the largest model
+constexpr int kMaxP = 16;          // parameters of the largest model (IPA_MAX_PAR)
 constexpr double kSwitch = 1e-3;   // BFGS -> finite-difference Newton (decrement, sigma units)
 constexpr double kRehess = 2e-3;   // Newton moved further than this (sigma units): Hessian again
 enum Phase { kInit = 0, kLS = 1, kHess = 2, kNewton = 3, kDone = 4 };

@@ -24,16 +24,26 @@ constexpr int kBlock = 256;   // threads per block of the generator and helper k
 
 // Parameters of a model kind.
 __host__ __device__ constexpr int npar_of(int kind) {
-    return kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D : (kind == IPA_MODEL_TAGGED1D ? IPA_NPAR_TAGGED : IPA_NPAR_4D);
+    return kind == IPA_MODEL_TIME1D ? IPA_NPAR_1D
+           : kind == IPA_MODEL_TAGGED1D ? IPA_NPAR_TAGGED
+           : kind == IPA_MODEL_PHIS ? IPA_NPAR_PHIS : IPA_NPAR_4D;
 }
 
 // Number of FP64 accumulators per tile.
-//   NLL only:   L = sum w log P
-//   1D + grad:  L, Q = sum w/P, S = sum (w/P) T, D_Gamma, D_sigma, D_mu
-//   4D + grad:  L, Q, S_1..S_10 = sum (w/P) T f_k, D_Gamma, D_sigma, D_mu
+//   NLL only:      L = sum w log P
+//   1D + grad:     L, Q = sum w/P, S = sum (w/P) T, D_Gamma, D_sigma, D_mu
+//   4D + grad:     L, Q, S_1..S_10 = sum (w/P) T f_k, D_Gamma, D_sigma, D_mu
+//   tagged + grad: 13 (tagged.cu);  phi_s + grad: 47 (phis.cu)
 __host__ __device__ constexpr int n_acc(int kind, bool grad) {
-    return !grad ? 1 : (kind == IPA_MODEL_TIME1D ? 6 : 15);
+    return !grad ? 1
+                 : (kind == IPA_MODEL_TIME1D ? 6
+                    : kind == IPA_MODEL_TAGGED1D ? 13 : kind == IPA_MODEL_PHIS ? 47 : 15);
 }
+// Doubles per tile that the partials buffers of the library scratch hold (the
+// largest n_acc); the server's and the no-allocation scratch hold
+// kSmallAcc per tile and serve only the models that need no more.
+constexpr int kMaxAcc = 47;
+constexpr int kSmallAcc = 15;
 
 // Parameter-derived constants of one fit (step a1 of the hot path), computed
 // once per call on the device from theta and read by every event tile.
@@ -141,6 +151,11 @@ ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                       const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                       const Consts* consts, Scratch* sc, double* out, cudaStream_t s,
                       const LaunchCfg* cfg = nullptr);
+// phis.cu: constants and launch_nll of the phi_s model
+ipa_status launch_phis_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out, cudaStream_t s);
+ipa_status launch_phis_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
+                           const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
+                           const Consts* consts, Scratch* sc, double* out, cudaStream_t s, const LaunchCfg* cfg);
 // tagged.cu: launch_nll for the tagged model
 ipa_status launch_tag_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                           const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,

@@ -39,6 +39,7 @@
 
 #include "fp64_math.cuh"
 #include "int_math.cuh"
+#include "angular.cuh"
 #include "ipa_internal.cuh"
 #include "tile_reduce.cuh"
 
@@ -47,12 +48,6 @@ namespace {
 
 constexpr int kNllBlock = 128;                       // threads per block of the basis kernel
 constexpr int kPerLane = kTile / 32;                 // events per lane per tile
-
-// Constant factors c_k of f_k = c_k f'_k, where f'_k is the product of
-// sines and cosines the kernel evaluates (sec. 4 helicity basis).
-__device__ const double kBasisScale[10] = {
-    1.0, 0.5, 0.5, 1.0, 1.41421356237309504880, -1.41421356237309504880, 1.0 / 3.0,
-    0.81649658092772603273, -0.81649658092772603273, 1.15470053837925152902};
 
 // Per-warp copy of a segment's constants in shared memory, with the factors
 // the event loop multiplies by folded in:
@@ -75,31 +70,6 @@ struct WarpConsts {
 constexpr int kSub = 4;
 static_assert(kSub == 4, "a compaction round keeps four ballot masks");
 static_assert((IPA_TILE_EVENTS / 32) % kSub == 0, "events per lane must be a multiple of kSub");
-
-// f'_k(cos thK, cos thmu, phi): f_k without its constant factor.
-__device__ __forceinline__ void basis_unscaled(double ck, double cl, double phi, const MathTables* mt,
-                                               double f[10]) {
-    double sp, cp;
-    sincos_int(phi, mt, &sp, &cp);
-    const double sk2 = fma(-ck, ck, 1.0);
-    const double cl2 = cl * cl;
-    const double sl2 = 1.0 - cl2;
-    const double cp2 = cp * cp;
-    const double sksl2 = sk2 * sl2;
-    const double q = sqrt(sksl2);                  // sin thK sin thmu
-    f[0] = ck * ck * sl2;
-    f[1] = sk2 * fma(-sl2, cp2, 1.0);
-    f[2] = sk2 * fma(sl2, cp2, cl2);               // sk2 (1 - sl2 sp^2)
-    f[3] = sksl2 * (sp * cp);
-    const double a = q * (ck * cl);
-    f[4] = a * cp;
-    f[5] = a * sp;
-    f[6] = sl2;
-    const double b = q * cl;
-    f[7] = b * cp;
-    f[8] = b * sp;
-    f[9] = ck * sl2;
-}
 
 // The part of the decay-time factor that needs the Gaussian and erfcx, for an
 // event with t <= tcut (z >= -6.25 up to rounding): with g = exp(-tau^2 /
@@ -505,6 +475,8 @@ ipa_status launch_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
     const int P = m.n_par;
     if (m.kind == IPA_MODEL_TAGGED1D)
         return launch_tag_nll(m, grad, cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, st, cfg);
+    if (m.kind == IPA_MODEL_PHIS)
+        return launch_phis_nll(m, grad, cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, st, cfg);
     if (m.kind == IPA_MODEL_TIME1D)
         return grad ? launch_w<IPA_MODEL_TIME1D, true, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg)
                     : launch_w<IPA_MODEL_TIME1D, false, false>(cols, n, seg_begin, seg_end, seg_tiles, n_seg, consts, sc, out, P, st, cfg);
@@ -537,7 +509,7 @@ extern "C" ipa_status ipa_angular_basis(const ipa_model* model, const ipa_events
     using namespace ipa;
     ipa_status st = check_model(model);
     if (st != IPA_OK) return st;
-    if (model->kind != IPA_MODEL_ANGTIME4D) {
+    if (model->kind != IPA_MODEL_ANGTIME4D && model->kind != IPA_MODEL_PHIS) {
         set_error("ipa_angular_basis: the model has no angles");
         return IPA_ERR_ARG;
     }

@@ -28,7 +28,7 @@ constexpr int64_t kNoAllocMaxTiles = kNoAllocMaxEvents / kTile + 1;
 constexpr size_t kConstsBytes = 1024;     // one Consts record, padded
 constexpr size_t kCounterBytes = 256;     // completion counter and the two work counters, padded
 constexpr size_t kGroupBytes = ((size_t)kNoAllocMaxTiles * sizeof(unsigned) + 255) / 256 * 256;  // group counters
-constexpr size_t kPartialsBytes = (size_t)kNoAllocMaxTiles * 15 * sizeof(double);
+constexpr size_t kPartialsBytes = (size_t)kNoAllocMaxTiles * kSmallAcc * sizeof(double);
 static_assert(sizeof(Consts) <= kConstsBytes, "Consts must fit its slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kConstsBytes + kCounterBytes + kGroupBytes + kPartialsBytes];
@@ -70,6 +70,11 @@ extern "C" ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_eve
         set_error("theta and out must be device pointers");
         return IPA_ERR_ARG;
     }
+    if (n_acc(model->kind, true) > kSmallAcc) {
+        set_error("ipa_nll_grad_noalloc: the phi_s model needs more scratch per tile than the fixed "
+                  "array holds (use ipa_nll_grad)");
+        return IPA_ERR_ARG;
+    }
     if (ev->n > kNoAllocMaxEvents) {
         set_error("ipa_nll_grad_noalloc: %lld events exceed the fixed scratch of %lld events "
                   "(use ipa_nll_grad)", (long long)ev->n, (long long)kNoAllocMaxEvents);
@@ -83,7 +88,7 @@ extern "C" ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_eve
     sc.work = sc.counters + 1;
     sc.gcount = reinterpret_cast<unsigned*>(base + kConstsBytes + kCounterBytes);
     sc.partials = reinterpret_cast<double*>(base + kConstsBytes + kCounterBytes + kGroupBytes);
-    sc.partials_cap = (size_t)kNoAllocMaxTiles * 15;
+    sc.partials_cap = (size_t)kNoAllocMaxTiles * kSmallAcc;
     sc.seg_cap = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = cuda_fail(cudaMemsetAsync(sc.counters, 0, 3 * sizeof(unsigned), s), "counter clear")) != IPA_OK)

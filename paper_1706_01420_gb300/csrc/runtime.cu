@@ -59,7 +59,8 @@ ipa_status check_model(const ipa_model* m) {
         set_error("model is NULL");
         return IPA_ERR_ARG;
     }
-    if (m->kind != IPA_MODEL_TIME1D && m->kind != IPA_MODEL_ANGTIME4D && m->kind != IPA_MODEL_TAGGED1D) {
+    if (m->kind != IPA_MODEL_TIME1D && m->kind != IPA_MODEL_ANGTIME4D && m->kind != IPA_MODEL_TAGGED1D &&
+        m->kind != IPA_MODEL_PHIS) {
         set_error("unknown model kind %d", m->kind);
         return IPA_ERR_ARG;
     }
@@ -88,9 +89,9 @@ ipa_status check_events(const ipa_model* m, const ipa_events* ev) {
     }
     if (ev->n == 0) return IPA_OK;
     const bool tag = m->kind == IPA_MODEL_TAGGED1D;
-    const double* need[4] = {ev->t, tag ? ev->q : ev->ck, ev->cl, ev->phi};
-    const int n_need = m->kind == IPA_MODEL_ANGTIME4D ? 4 : (tag ? 2 : 1);
-    const char* names[4] = {"t", tag ? "q" : "ck", "cl", "phi"};
+    const double* need[5] = {ev->t, tag ? ev->q : ev->ck, ev->cl, ev->phi, ev->q};
+    const int n_need = m->kind == IPA_MODEL_PHIS ? 5 : (m->kind == IPA_MODEL_ANGTIME4D ? 4 : (tag ? 2 : 1));
+    const char* names[5] = {"t", tag ? "q" : "ck", "cl", "phi", "q"};
     for (int i = 0; i < n_need; ++i) {
         if (!need[i]) {
             set_error("event column %s is NULL", names[i]);
@@ -106,7 +107,7 @@ ipa_status check_events(const ipa_model* m, const ipa_events* ev) {
         return IPA_ERR_ARG;
     }
     if (ev->fk) {
-        if (m->kind != IPA_MODEL_ANGTIME4D) {
+        if (m->kind != IPA_MODEL_ANGTIME4D && m->kind != IPA_MODEL_PHIS) {
             set_error("an angular basis was given for a model without angles");
             return IPA_ERR_ARG;
         }
@@ -140,7 +141,7 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if ((int)g_scratch.size() <= dev) g_scratch.resize(dev + 1);
     Scratch& s = g_scratch[dev];
-    const size_t need_p = (size_t)(tiles < 1 ? 1 : tiles) * 15;
+    const size_t need_p = (size_t)(tiles < 1 ? 1 : tiles) * kMaxAcc;
     const size_t need_s = (size_t)(segs < 2 ? 2 : segs);
     if (need_p > s.partials_cap) {
         size_t cap = s.partials_cap ? s.partials_cap : (size_t)1 << 16;
@@ -156,7 +157,7 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
         if ((st = cuda_fail(cudaMalloc(&s.partials, cap * sizeof(double)), "scratch partials")) != IPA_OK)
             return st;
         // one group counter per tile; zero between calls (kernels reset what they use)
-        const size_t n_tiles = cap / 15 + 1;
+        const size_t n_tiles = cap / kMaxAcc + 1;
         if ((st = cuda_fail(cudaMalloc(&s.gcount, n_tiles * sizeof(unsigned)), "scratch group counters")) != IPA_OK)
             return st;
         if ((st = cuda_fail(cudaMemset(s.gcount, 0, n_tiles * sizeof(unsigned)), "scratch memset")) != IPA_OK)
@@ -205,7 +206,8 @@ extern "C" ipa_status ipa_model_init(ipa_model* m, int32_t kind, double t_lo, do
         ipa::set_error("model is NULL");
         return IPA_ERR_ARG;
     }
-    if (kind != IPA_MODEL_TIME1D && kind != IPA_MODEL_ANGTIME4D && kind != IPA_MODEL_TAGGED1D) {
+    if (kind != IPA_MODEL_TIME1D && kind != IPA_MODEL_ANGTIME4D && kind != IPA_MODEL_TAGGED1D &&
+        kind != IPA_MODEL_PHIS) {
         ipa::set_error("unknown model kind %d", kind);
         return IPA_ERR_ARG;
     }

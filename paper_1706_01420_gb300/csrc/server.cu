@@ -340,6 +340,10 @@ extern "C" ipa_status ipa_server_create(const ipa_model* model, size_t hbm_budge
     using namespace ipa;
     ipa_status st = check_model(model);
     if (st != IPA_OK) return st;
+    if (model->kind == IPA_MODEL_PHIS || n_acc(model->kind, true) > kSmallAcc) {
+        set_error("ipa_server_create: the phi_s model is not served (fit it with ipa_fit_batch)");
+        return IPA_ERR_ARG;
+    }
     if (!out || max_slots < 1 || max_slots > 65536 || max_iter < 1 || !(tol > 0.0)) {
         set_error("ipa_server_create: bad arguments");
         return IPA_ERR_ARG;
@@ -378,13 +382,13 @@ extern "C" ipa_status ipa_server_create(const ipa_model* model, size_t hbm_budge
     if (st == IPA_OK) st = dalloc(&s->d_out_iters, S, "server out");
     if (st == IPA_OK) st = dalloc(&s->d_out_passes, S, "server out");
     const size_t tiles = (size_t)(cap / kTile + max_slots + 1);
-    if (st == IPA_OK) st = dalloc(&s->sc.partials, tiles * 15, "server partials");
+    if (st == IPA_OK) st = dalloc(&s->sc.partials, tiles * kSmallAcc, "server partials");
     if (st == IPA_OK) st = dalloc(&s->sc.counters, S + 1, "server counters");
     if (st == IPA_OK) st = dalloc(&s->sc.gcount, tiles, "server group counters");
     if (st == IPA_OK) st = dalloc(&s->sc.work, 2, "server work counters");
     if (st == IPA_OK) st = dalloc(&s->sc.seg_tiles, S + 1, "server tiles");
     if (st == IPA_OK) st = dalloc(&s->sc.consts, S, "server consts");
-    s->sc.partials_cap = tiles * 15;
+    s->sc.partials_cap = tiles * kSmallAcc;
     s->sc.seg_cap = S + 1;
     if (st == IPA_OK) st = halloc(&s->h_begin, S, "server pinned");
     if (st == IPA_OK) st = halloc(&s->h_end, S, "server pinned");

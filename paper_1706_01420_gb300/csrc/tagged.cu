@@ -35,38 +35,6 @@ constexpr int kSub = 4;
 static_assert(kPerLane % kSub == 0, "events per lane must be a multiple of kSub");
 constexpr int kMaxWarps = 8;
 
-// The slow-branch values of one event (t <= tcut), with Gx = exp(-tau^2 /
-// (2 sigma^2)):
-//   xH = Gx erfcx(|uH|), xL = Gx erfcx(|uL|)  (uH,L = (Gamma_H,L sigma^2 - tau) k_z),
-//   (wr, wi) = Gx w(+-beta + i |a|)          (a = (Gamma sigma^2 - tau) k_z),
-//   gx = Gx.
-// The sign bits of xH, xL and gx carry uH >= 0, uL >= 0 and a >= 0: then 2g is
-// the stored value itself, otherwise 2 E minus it.  Events with t > tcut use
-// all zeros (2g = 2E, Gaussian 0).
-struct TagSlow {
-    double xH, xL, wr, wi, gx;
-};
-
-__device__ __forceinline__ double with_sign(double v, bool set) {
-    return __longlong_as_double(__double_as_longlong(v) | ((long long)set << 63));
-}
-
-__device__ __forceinline__ TagSlow tag_slow(const TagConsts& c, double tau, const MathTables* mt) {
-    const double gx = exp_int(-(tau * tau) * c.k_g, mt);
-    const double uH = (c.uH0 - tau) * c.k_z, uL = (c.uL0 - tau) * c.k_z, a = (c.uC0 - tau) * c.k_z;
-    const double XH = erfcx_fast(fabs(uH), mt), XL = erfcx_fast(fabs(uL), mt);
-    const bool ap = !negative(a);
-    double wr, wi;
-    faddeeva_uhp(ap ? c.beta : -c.beta, fabs(a), &wr, &wi);
-    TagSlow s;
-    s.xH = with_sign(gx * XH, !negative(uH));
-    s.xL = with_sign(gx * XL, !negative(uL));
-    s.wr = gx * wr;
-    s.wi = gx * wi;
-    s.gx = with_sign(gx, ap);
-    return s;
-}
-
 // One event: w log P into acc[0] (or, for w = 1 exactly, P into the lane's
 // log product) and the 12 adjoint sums into acc[1..12].
 template <bool GRAD, bool WEIGHTED>

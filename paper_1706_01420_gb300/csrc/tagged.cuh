@@ -25,6 +25,8 @@
 
 #include "consts.cuh"
 #include "faddeeva.cuh"
+#include "fp64_math.cuh"
+#include "int_math.cuh"
 #include "ipa_internal.cuh"
 
 namespace ipa {
@@ -150,6 +152,40 @@ __device__ inline void compute_tag_consts(const ModelDev& m, const double* th, T
     c->MS = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(0.5, __dsub_rn(1.0, cn)), MH),
                                 __dmul_rn(__dmul_rn(0.5, __dadd_rn(1.0, cn)), ML)),
                       __dmul_rn(fabs(__dmul_rn(D, sn)), MC));
+}
+
+// The slow-branch values of one event (t <= tcut), with Gx = exp(-tau^2 /
+// (2 sigma^2)):
+//   xH = Gx erfcx(|uH|), xL = Gx erfcx(|uL|)  (uH,L = (Gamma_H,L sigma^2 - tau) k_z),
+//   (wr, wi) = Gx w(+-beta + i |a|)          (a = (Gamma sigma^2 - tau) k_z),
+//   gx = Gx.
+// The sign bits of xH, xL and gx carry uH >= 0, uL >= 0 and a >= 0: then 2g is
+// the stored value itself, otherwise 2 E minus it.  Events with t > tcut use
+// all zeros (2g = 2E, Gaussian 0).  C is any constants record with the
+// fields read below (TagConsts, PhisConsts).
+struct TagSlow {
+    double xH, xL, wr, wi, gx;
+};
+
+__device__ __forceinline__ double with_sign(double v, bool set) {
+    return __longlong_as_double(__double_as_longlong(v) | ((long long)set << 63));
+}
+
+template <class C>
+__device__ __forceinline__ TagSlow tag_slow(const C& c, double tau, const MathTables* mt) {
+    const double gx = exp_int(-(tau * tau) * c.k_g, mt);
+    const double uH = (c.uH0 - tau) * c.k_z, uL = (c.uL0 - tau) * c.k_z, a = (c.uC0 - tau) * c.k_z;
+    const double XH = erfcx_fast(fabs(uH), mt), XL = erfcx_fast(fabs(uL), mt);
+    const bool ap = !negative(a);
+    double wr, wi;
+    faddeeva_uhp(ap ? c.beta : -c.beta, fabs(a), &wr, &wi);
+    TagSlow s;
+    s.xH = with_sign(gx * XH, !negative(uH));
+    s.xL = with_sign(gx * XL, !negative(uL));
+    s.wr = gx * wr;
+    s.wi = gx * wi;
+    s.gx = with_sign(gx, ap);
+    return s;
 }
 
 // 2 g(tau; x) for real x, exact form (library exp and erfcx).

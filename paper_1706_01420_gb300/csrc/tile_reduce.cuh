@@ -84,6 +84,7 @@ __device__ __forceinline__ double log_of(double prod, int esum, const MathTables
 // the lane pairing.  NA = 15: 16 adds and 16 shuffles per warp instead of 75.
 template <int NA>
 struct Butterfly {
+    static_assert(NA <= 16, "the butterfly takes at most 16 accumulators (see warp_allreduce_wide)");
     static constexpr int NP = NA <= 1 ? 1 : NA <= 2 ? 2 : NA <= 4 ? 4 : NA <= 8 ? 8 : 16;
     static constexpr int SPLITS = NP == 1 ? 0 : NP == 2 ? 1 : NP == 4 ? 2 : NP == 8 ? 3 : 4;
 };
@@ -200,6 +201,73 @@ __device__ __forceinline__ bool tile_commit(double share, int lane, int64_t tile
     if (!__shfl_sync(0xffffffffu, last, 0)) return false;
     __threadfence();
     gather_butterfly<NA>(reduce_partials<NA>(partials, t0, n_groups, kGroupTiles, lane), acc);
+    return true;
+}
+
+// ---- the same protocol for more accumulators than the butterfly takes (16) ----
+// Every lane ends with every sum: each accumulator goes through the full xor
+// butterfly (at each level both partners add the same two values, so all lanes
+// hold identical bits).  Costs 5 shuffles and adds per accumulator and tile.
+template <int NA>
+__device__ __forceinline__ void warp_allreduce_wide(double* acc) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    }
+}
+
+// Lane l stores accumulators l, l + 32, ... (register indices fixed at compile time).
+template <int NA>
+__device__ __forceinline__ void store_wide(const double* acc, int lane, double* dst) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+        if ((a & 31) == lane) dst[a] = acc[a];
+}
+
+// acc = the warp's sums of the partials of `count` tiles (lane l adds tiles
+// l, l+32, ... of first + i * stride in that order), on every lane.
+template <int NA>
+__device__ __forceinline__ void reduce_partials_wide(const double* partials, int64_t first, int64_t count,
+                                                     int64_t stride, double* acc) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = 0.0;
+    for (int64_t i = lane; i < count; i += 32) {
+        const double* p = partials + (first + i * stride) * NA;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] += __ldcg(p + a);
+    }
+    warp_allreduce_wide<NA>(acc);
+}
+
+// tile_commit for acc already reduced by warp_allreduce_wide: the group and
+// segment levels in the same order; true with acc = the segment's totals.
+template <int NA>
+__device__ __forceinline__ bool tile_commit_wide(int lane, int64_t tile, int64_t t0, int64_t t1, int seg,
+                                                 double* partials, unsigned* gcount, unsigned* counters, double* acc) {
+    const int64_t g0 = t0 + ((tile - t0) / kGroupTiles) * kGroupTiles;
+    const int64_t g1 = g0 + kGroupTiles < t1 ? g0 + kGroupTiles : t1;
+    int last = 0;
+    store_wide<NA>(acc, lane, partials + tile * NA);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) last = atomicAdd(gcount + g0, 1u) + 1u == (unsigned)(g1 - g0);
+    if (!__shfl_sync(0xffffffffu, last, 0)) return false;
+    __threadfence();
+    reduce_partials_wide<NA>(partials, g0, g1 - g0, 1, acc);
+    const int64_t n_groups = (t1 - t0 + kGroupTiles - 1) / kGroupTiles;
+    __syncwarp();   // every lane has read the group's tile partials
+    store_wide<NA>(acc, lane, partials + g0 * NA);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        gcount[g0] = 0u;
+        last = atomicAdd(counters + seg, 1u) + 1u == (unsigned)n_groups;
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return false;
+    __threadfence();
+    reduce_partials_wide<NA>(partials, t0, n_groups, kGroupTiles, acc);
     return true;
 }
 

@@ -395,6 +395,10 @@ extern "C" ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev
         set_error("ipa_toygen: the 4D model needs ck, cl and phi output columns");
         return IPA_ERR_ARG;
     }
+    if (model->kind == IPA_MODEL_PHIS) {
+        set_error("ipa_toygen: no generator for the phi_s model");
+        return IPA_ERR_ARG;
+    }
     const bool tag = model->kind == IPA_MODEL_TAGGED1D;
     if (tag && !out->q) {
         set_error("ipa_toygen: the tagged model needs a q output column");

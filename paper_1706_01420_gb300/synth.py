@@ -102,6 +102,16 @@ def events_tagged(n: int, seed: int = 0, t_lo: float = 0.0, t_hi: float = 15.0,
     return cols
 
 
+def events_phis(n: int, seed: int = 0, t_lo: float = 0.0, t_hi: float = 15.0, truth: dict | None = None,
+                weighted: bool = False) -> dict:
+    """SoA columns t, ck, cl, phi, q (and w) for the time-dependent angular model
+    with tagging: the 4D recipe plus a tag-blind q."""
+    cols = events_4d(n, seed, t_lo=t_lo, t_hi=t_hi, truth=truth, weighted=weighted)
+    rng = np.random.default_rng(seed + 104729)
+    cols["q"] = np.where(rng.random(n) < 0.5, 1.0, -1.0)
+    return cols
+
+
 def weights(n: int, seed: int = 0, mean: float = 1.0, sd: float = 0.2) -> np.ndarray:
     """Per-event weights ~ Normal(mean, sd)."""
     return np.random.default_rng(seed).normal(mean, sd, n)
