@@ -301,11 +301,15 @@ def main():
                     help="untimed: 4 ipa_nll_grad calls on 8e6 4D events (256 MB, > L2), for ncu")
     ap.add_argument("--profile-case-tagged", action="store_true",
                     help="untimed: 4 ipa_nll_grad calls on 8e6 tagged events (128 MB, > L2), for ncu")
+    ap.add_argument("--profile-case-phis", action="store_true",
+                    help="untimed: 4 ipa_nll_grad calls on 8e6 phi_s-model events (320 MB, > L2), for ncu")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
     if args.profile_case_tagged:
         return profile_case_tagged()
+    if args.profile_case_phis:
+        return profile_case_phis()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -521,6 +525,23 @@ def profile_case_tagged() -> int:
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "ipa_nll_grad tagged", "events": n, "nll": float(out[0]),
                       "slow_fraction": tag_slow_fraction(ev["t"].cpu().numpy(), TH_TAG)}))
+    return 0
+
+
+def profile_case_phis() -> int:
+    """The phi_s model's small fixed case for Nsight Compute (inputs larger than L2)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1706_01420_gb300 import api, synth
+    n = 8_000_000
+    ev = {k: torch.tensor(v, device="cuda") for k, v in synth.events_phis(n, 3).items()}
+    m = api.model_phis(0.0, 15.0)
+    theta = torch.tensor(TH_PHIS, device="cuda")
+    for _ in range(4):
+        out = api.ipa_nll_grad(m, ev, theta)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "ipa_nll_grad phi_s model", "events": n, "nll": float(out[0])}))
     return 0
 
 
