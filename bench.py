@@ -746,7 +746,7 @@ def run_errors(api, torch, dev, m, cols, off, params, rb, n_minos: int = 64) -> 
                       "median_asymmetry": float(asym.median())}}
 
 
-TH_PHIS = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3])
+TH_PHIS = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3, 0.8, 0.0])
 
 
 def run_phis(api, synth, torch, dev, flush, steps: int = 30) -> dict:
@@ -759,7 +759,7 @@ def run_phis(api, synth, torch, dev, flush, steps: int = 30) -> dict:
     out = torch.empty(15, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     res = {"workload": "time-dependent angular model with tagging, 1e6 FP64 SoA events (t, 3 angles, q), "
-                       "14 params, ipa_nll_grad", "events": 1_000_000}
+                       "16 params, ipa_nll_grad", "events": 1_000_000}
     for name, evx in (("raw", ev), ("cached_basis", dict(ev, fk=api.ipa_angular_basis(m, ev)))):
         res["launch_" + name] = api.ipa_autotune(m, evx, theta, grad=True, stream=stream)
         for _ in range(3):

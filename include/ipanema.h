@@ -82,9 +82,15 @@ typedef enum {
  * sums of e^{-Gamma_L t}, e^{-Gamma_H t} and e^{-Gamma t} e^{i Dm t}, each
  * convolved with the Gaussian resolution; a tag q = +-1 with mistag omega
  * mixes the two initial flavours; normalised over t, the angles and both
- * tags, plus a flat background f_b.  Parameters: the ten of the 4D model,
- * then DG, Dm, phi_s, omega (IPA_PHIS_DG .. IPA_PHIS_OMEGA).  Events carry
- * t, ck, cl, phi and q. */
+ * tags, plus a flat background f_b; the three S-P interference terms carry a
+ * factor C_SP (the overlap of the S- and P-wave lineshapes in a m(KK)
+ * category, usually held at its computed value).  Parameters: the ten of the
+ * 4D model, then DG, Dm, phi_s, omega, C_SP and the tag-normalisation
+ * selector Q (IPA_PHIS_DG .. IPA_PHIS_QNORM).  With Q = 0 the PDF is
+ * normalised over t, the angles and both tags; with Q = +1 or -1 over the one
+ * tag (a category holding the events of one flavour, as in a simultaneous fit
+ * over m(KK) bins times B flavours, Sec. 4 Example 2): the events of such a
+ * segment must all carry that tag.  Events carry t, ck, cl, phi and q. */
 
 /* The tagged model (Sec. 4, the B_s -> J/psi phi example, whose time-dependent
  * fit has the oscillation frequency Dm_s, the widths Gamma and DG and the
@@ -105,7 +111,7 @@ typedef enum {
 
 /* Parameter indices (theta layout).  1D uses the first 4, 4D the first 10,
  * the tagged model the first 4 and its own 4 to 7, the phi_s model the ten
- * of the 4D model and 10 to 13. */
+ * of the 4D model and 10 to 15. */
 enum {
     IPA_GAMMA = 0,   /* decay width Gamma [1/ps]                   */
     IPA_SIGMA = 1,   /* Gaussian time resolution sigma [ps]        */
@@ -125,11 +131,14 @@ enum {
     IPA_PHIS_DM = 11,    /* phi_s model: Dm_s [1/ps]                    */
     IPA_PHIS_PHIS = 12,  /* phi_s model: phi_s [rad]                    */
     IPA_PHIS_OMEGA = 13, /* phi_s model: mistag probability omega       */
+    IPA_PHIS_CSP = 14,   /* phi_s model: C_SP factor of the three S-P interference terms */
+    IPA_PHIS_QNORM = 15, /* phi_s model: normalisation over both tags (0) or over the tag
+                            +1 (> 0) or -1 (< 0) alone; a selector, held fixed (gradient 0) */
     IPA_NPAR_1D = 4,
     IPA_NPAR_4D = 10,
     IPA_NPAR_TAGGED = 8,
-    IPA_NPAR_PHIS = 14,
-    IPA_MAX_PAR = 16
+    IPA_NPAR_PHIS = 16,
+    IPA_MAX_PAR = 32     /* parameters of a fit (a joint fit over categories included) */
 };
 
 /* One fit parameter (Parameter / Free of App. B): start value, limits, step,
@@ -255,6 +264,49 @@ ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev, uint64_t 
  * max_iter iterations.  Blocks the calling thread until all fits end. */
 ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
                          int32_t n_fits, const ipa_param* spec, double* theta_io_dev,
+                         double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
+                         int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
+                         void* stream);
+
+/* A simultaneous fit over categories (Sec. 4, Example 2: one -2 log L summed
+ * over 12 categories, six m(KK) bins times two B flavours, that share most
+ * parameters while the S-wave parameters are per bin and C_SP is a constant of
+ * each bin; App. B: the Cat and ParamBox classes).  Every fit has n_cat
+ * categories; category c of fit i is the event segment i * n_cat + c of
+ * seg_off_dev (n_fits * n_cat + 1 int64 offsets, device, as in
+ * ipa_nll_grad_segmented).  A fit has n_joint parameters theta_J
+ * (1 <= n_joint <= IPA_MAX_PAR); category c evaluates the model at
+ *   theta_c[p] = theta_J[map[c * n_par + p]]   where map[...] >= 0,
+ *   theta_c[p] = value[c * n_par + p]           where map[...] == -1,
+ * and the fit's NLL is sum_c NLL_c(theta_c), its gradient
+ * dNLL/dtheta_J[j] = sum over (c, p) with map = j of dNLL_c/dtheta_c[p], both
+ * summed in a fixed order (c ascending, then p ascending), so results do not
+ * depend on the launch geometry.  map and value are host arrays of
+ * n_cat x n_par (the model's n_par), read during the call.  IPA_ERR_ARG when
+ * an entry of map is outside [-1, n_joint) or a joint parameter is used by no
+ * category. */
+typedef struct ipa_joint {
+    int32_t n_cat;          /* categories per fit (>= 1) */
+    int32_t n_joint;        /* parameters of a fit */
+    const int32_t* map;     /* host, n_cat x n_par: joint index or -1 */
+    const double* value;    /* host, n_cat x n_par: the constant where map is -1 (may be NULL if none is) */
+} ipa_joint;
+
+/* The joint NLL and gradient of n_fits simultaneous fits at theta_dev
+ * (n_fits x n_joint, device): out_dev (device) receives 1 + n_joint doubles per
+ * fit (NLL, then dNLL/dtheta_J).  Each category's NLL and gradient is
+ * bitwise that of ipa_nll_grad_segmented at its theta_c. */
+ipa_status ipa_nll_grad_joint(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                              int32_t n_fits, const ipa_joint* joint, const double* theta_dev, double* out_dev,
+                              void* stream);
+
+/* Fit n_fits simultaneous fits at once: ipa_fit_batch's minimiser over the
+ * joint parameters.  spec (host): n_joint parameters (start value, limits,
+ * step, fixed flag); theta_io_dev n_fits x n_joint (start values in, fitted
+ * values out); err_out_dev n_fits x n_joint; the other outputs as in
+ * ipa_fit_batch (IPA_FIT_EMPTY when all of a fit's categories are empty). */
+ipa_status ipa_fit_joint(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                         int32_t n_fits, const ipa_joint* joint, const ipa_param* spec, double* theta_io_dev,
                          double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
                          int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
                          void* stream);

@@ -478,6 +478,11 @@ class FitResult:
 
 def hessian_fd(model: Model, ev: dict, theta, free, rel=1e-4):
     """Central finite difference of the analytic gradient over the free parameters."""
+    return hessian_fd_function(lambda th: nll_grad(model, ev, th), theta, free, rel)
+
+
+def hessian_fd_function(fn, theta, free, rel=1e-4):
+    """The same for any function fn(theta) -> (value, gradient)."""
     theta = np.asarray(theta, dtype=np.float64)
     free = list(free)
     H = np.zeros((len(free), len(free)))
@@ -486,15 +491,23 @@ def hessian_fd(model: Model, ev: dict, theta, free, rel=1e-4):
         tp, tm = theta.copy(), theta.copy()
         tp[j] += h
         tm[j] -= h
-        gp = nll_grad(model, ev, tp)[1][free]
-        gm = nll_grad(model, ev, tm)[1][free]
+        gp = fn(tp)[1][free]
+        gm = fn(tm)[1][free]
         H[:, a] = (gp - gm) / (2.0 * h)
     return 0.5 * (H + H.T)
 
 
 def fit(model: Model, ev: dict, theta0, free, lo=None, hi=None,
         tol=1e-10, max_iter=100) -> FitResult:
-    """Minimise the NLL over the free parameters by damped Newton steps.
+    """Minimise the NLL over the free parameters by damped Newton steps
+    (``fit_function`` applied to the model's NLL and gradient)."""
+    return fit_function(lambda th: nll_grad(model, ev, th), model.npar, theta0, free, lo=lo, hi=hi, tol=tol,
+                        max_iter=max_iter)
+
+
+def fit_function(fn, n, theta0, free, lo=None, hi=None, tol=1e-10, max_iter=100) -> FitResult:
+    """Minimise fn(theta) -> (value, gradient) over the free parameters by damped
+    Newton steps.
 
     Stops when the Newton decrement sqrt(g^T H^-1 g) (the step length in units
     of the parameter errors) is below ``tol``.  Errors are sqrt(diag(H^-1)),
@@ -502,14 +515,13 @@ def fit(model: Model, ev: dict, theta0, free, lo=None, hi=None,
     """
     theta = np.asarray(theta0, dtype=np.float64).copy()
     free = list(free)
-    n = model.npar
     lo = np.full(n, -np.inf) if lo is None else np.asarray(lo, dtype=np.float64)
     hi = np.full(n, np.inf) if hi is None else np.asarray(hi, dtype=np.float64)
-    f, g = nll_grad(model, ev, theta)
+    f, g = fn(theta)
     status = "MAXITER"
     it = 0
     for it in range(1, max_iter + 1):
-        H = hessian_fd(model, ev, theta, free)
+        H = hessian_fd_function(fn, theta, free)
         gf = g[free]
         # modified Newton: shift an indefinite Hessian until it is positive definite
         lam_min, lam_max = np.linalg.eigvalsh(H)[[0, -1]]
@@ -524,7 +536,7 @@ def fit(model: Model, ev: dict, theta0, free, lo=None, hi=None,
         while lam > 1e-6:
             trial = theta.copy()
             trial[free] = np.clip(theta[free] + lam * step, lo[free], hi[free])
-            ft, gt = nll_grad(model, ev, trial)
+            ft, gt = fn(trial)
             if ft <= f:
                 break
             lam *= 0.5
@@ -532,7 +544,7 @@ def fit(model: Model, ev: dict, theta0, free, lo=None, hi=None,
             status = "CONVERGED" if (definite and dec < 1e-6) else "LINESEARCH"
             break
         theta, f, g = trial, ft, gt
-    H = hessian_fd(model, ev, theta, free)
+    H = hessian_fd_function(fn, theta, free)
     cov = np.linalg.inv(H)
     err = np.zeros(n)
     err[free] = np.sqrt(np.maximum(np.diag(cov), 0.0))

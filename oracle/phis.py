@@ -35,8 +35,22 @@ evolution of the transversity amplitudes:
   + (1 - eta_i c) I(Gamma_H)], c = cos phi_s;
 * P = (1 - f_b) rate / N + f_b / (2 (t_hi - t_lo) 8 pi).
 
+* the three S-P interference terms carry a factor C_SP (the overlap of the S-
+  and P-wave lineshapes in a m(KK) category; 1 for one category covering the
+  whole range).
+* a category holding the events of one flavour (Example 2 fits six m(KK) bins
+  times the two B flavours, each category with its own integral) is
+  normalised over that tag only: selector Q = +1 or -1 (Q = 0: both tags).
+  Summed over the angles only the |A_i|^2 terms remain, and their tag-odd
+  part is q D eta_i |A_i|^2 sin(phi_s) Im g(tau; Gamma - i Dm), so
+  N_Q = N / 2 + Q K D sin(phi_s) (sum_i eta_i |A_i|^2) Im I_c with
+  I_c = int g(t - mu; Gamma - i Dm) dt over [t_lo, t_hi] and K = 16 pi / 9;
+  the background's volume is halved.  I_c comes from the antiderivative
+  (Phi - g) / z of the complex convolution (g' = G - z g).
+
 Parameters (ABI order): Gamma, sigma, mu, f_b, A0sq, Apesq, delta_pa,
-delta_pe, F_S, delta_S, DG, Dm, phi_s, omega.  Events: t, ck, cl, phi, q.
+delta_pe, F_S, delta_S, DG, Dm, phi_s, omega, C_SP, Q (a selector held fixed:
+its gradient component is 0).  Events: t, ck, cl, phi, q.
 """
 from __future__ import annotations
 
@@ -47,7 +61,9 @@ import numpy as np
 from . import ipa_oracle as O
 from . import tagged as T
 
-NPAR = 14
+NPAR = 16
+QNORM = 15                  # the tag-normalisation selector
+SP_TERMS = (7, 8, 9)       # the S-P interference terms, scaled by C_SP
 ETA = (1.0, 1.0, -1.0, -1.0)
 # (i, j, part) of the ten bilinears conj(A_i) A_j, part 'r' = Re, 'i' = Im
 PAIRS = ((0, 0, "r"), (1, 1, "r"), (2, 2, "r"), (1, 2, "i"), (0, 1, "r"), (0, 2, "i"), (3, 3, "r"),
@@ -110,7 +126,7 @@ def rate(model: O.Model, ev: dict, theta):
 
 
 def rate_grad(model: O.Model, ev: dict, theta, grad: bool = True):
-    """rate and d rate / d theta (14 rows; the f_b row is zero; None without grad)."""
+    """rate and d rate / d theta (16 rows; the f_b and selector rows are zero; None without grad)."""
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu = (float(theta[i]) for i in range(3))
     DG, Dm, phi, om = (float(theta[i]) for i in range(10, 14))
@@ -142,16 +158,23 @@ def rate_grad(model: O.Model, ev: dict, theta, grad: bool = True):
         11: (0.0 * gL, 0.0 * gH, -1j * cC[1]),
     }
     dprod = {j: _products(*v) for j, v in tg.items()}
+    csp = float(theta[14])
     for k, (i, j, p) in enumerate(PAIRS):
         b = np.conj(A[i]) * A[j]
         ei, ej = ETA[i], ETA[j]
         Ok, X, Y = _observed(b, ei, ej, lam, q, om, PP, MM, PM, MP)
+        if k in SP_TERMS:
+            dR[14] += f[k] * _part(Ok, p)
+            b = csp * b
+            Ok, X, Y = _observed(b, ei, ej, lam, q, om, PP, MM, PM, MP)
         R += f[k] * _part(Ok, p)
         if not grad:
             continue
         # amplitude parameters
         for a in range(6):
             db = np.conj(dA[i, a]) * A[j] + np.conj(A[i]) * dA[j, a]
+            if k in SP_TERMS:
+                db = csp * db
             if db != 0:
                 dO = _observed(db, ei, ej, lam, q, om, PP, MM, PM, MP)[0]
                 dR[ANG[a]] += f[k] * _part(dO, p)
@@ -169,8 +192,33 @@ def rate_grad(model: O.Model, ev: dict, theta, grad: bool = True):
     return R, (dR if grad else None)
 
 
+def time_norm_c_grad(z, sigma, mu, t_lo, t_hi):
+    """(I_c, dI_c/dz, dI_c/dsigma, dI_c/dmu) of I_c = int_{t_lo}^{t_hi} g(t - mu; z) dt for
+    complex z, from the antiderivative F = (Phi(tau / sigma) - g(tau; z)) / z and
+    dF/dz = -(F + dg/dz) / z, dF/dsigma = (-(tau / sigma) G - dg/dsigma) / z,
+    dF/dmu = -g (the real case of ``ipa_oracle.time_norm_grad`` with z complex)."""
+    z = complex(z)
+    out = np.zeros(4, dtype=complex)
+    for sgn, t in ((1.0, t_hi), (-1.0, t_lo)):
+        tau = t - mu
+        g, dg_dz, dg_ds, _ = (complex(v[0]) for v in T.conv_c_grad(tau, z, sigma))
+        G = float(O.gauss(tau, sigma))
+        Fv = (float(O.normal_cdf(tau / sigma)) - g) / z
+        out[0] += sgn * Fv
+        out[1] += sgn * (-(Fv + dg_dz) / z)
+        out[2] += sgn * ((-(tau / sigma) * G - dg_ds) / z)
+        out[3] += sgn * (-g)
+    return out
+
+
+def _tag_of(theta) -> float:
+    """The normalisation's tag: 0 (both tags), +1 or -1 (the sign of the selector)."""
+    Q = float(theta[QNORM])
+    return 0.0 if Q == 0.0 else math.copysign(1.0, Q)
+
+
 def norm_grad(model: O.Model, theta):
-    """N and dN/dtheta (14 entries)."""
+    """N and dN/dtheta (16 entries): over both tags, or over the selected tag."""
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu = (float(theta[i]) for i in range(3))
     DG, phi = float(theta[10]), float(theta[12])
@@ -199,22 +247,44 @@ def norm_grad(model: O.Model, theta):
         dwH = float(np.sum(dm2[:, a] * (1 - eta * c)))
         d[ANG[a]] = K * (dwL * IL[0] + dwH * IH[0])
     d[12] = K * (float(np.sum(m2 * (-eta * s))) * IL[0] + float(np.sum(m2 * (eta * s))) * IH[0])
+    Q = _tag_of(theta)
+    if Q == 0.0:
+        return N, d
+    # one tag: half the even part plus the tag-odd part Q K D s W Im I_c
+    Dm, om = float(theta[11]), float(theta[13])
+    D = 1.0 - 2.0 * om
+    W = float(np.sum(eta * m2))
+    Ic = time_norm_c_grad(complex(Gamma, -Dm), sigma, mu, model.t_lo, model.t_hi)
+    odd = K * D * s * W
+    N = 0.5 * N + Q * odd * Ic[0].imag
+    d = 0.5 * d
+    d[0] += Q * odd * Ic[1].imag                 # d/dGamma = d/dz
+    d[1] += Q * odd * Ic[2].imag
+    d[2] += Q * odd * Ic[3].imag
+    d[11] += Q * odd * (-1j * Ic[1]).imag        # d/dDm = -i d/dz
+    d[12] += Q * K * D * c * W * Ic[0].imag
+    d[13] += Q * K * (-2.0) * s * W * Ic[0].imag
+    for a in range(6):
+        d[ANG[a]] += Q * K * D * s * float(np.sum(eta * dm2[:, a])) * Ic[0].imag
     return N, d
 
 
-def volume(model: O.Model) -> float:
-    return 2.0 * (model.t_hi - model.t_lo) * 8.0 * math.pi
+def volume(model: O.Model, theta=None) -> float:
+    """Volume of (t, the angles, the tags) the background is flat over: one tag
+    when theta selects one."""
+    v = 2.0 * (model.t_hi - model.t_lo) * 8.0 * math.pi
+    return v if theta is None or _tag_of(theta) == 0.0 else 0.5 * v
 
 
 def pdf(model: O.Model, ev: dict, theta) -> np.ndarray:
     N, _ = norm_grad(model, theta)
     R = rate(model, ev, theta)
     f_b = float(theta[3])
-    return (1.0 - f_b) * R / N + f_b / volume(model)
+    return (1.0 - f_b) * R / N + f_b / volume(model, theta)
 
 
 def nll_grad_terms(model: O.Model, ev: dict, theta):
-    """Per-event w log P and -w (dP/dtheta_j) / P (a (14, N) array)."""
+    """Per-event w log P and -w (dP/dtheta_j) / P (a (16, N) array)."""
     theta = np.asarray(theta, dtype=np.float64)
     f_b = float(theta[3])
     t = np.asarray(ev["t"], dtype=np.float64)
@@ -222,7 +292,7 @@ def nll_grad_terms(model: O.Model, ev: dict, theta):
     w = np.ones_like(t) if w is None else np.asarray(w, dtype=np.float64)
     N, dN = norm_grad(model, theta)
     R, dR = rate_grad(model, ev, theta)
-    V = volume(model)
+    V = volume(model, theta)
     P = (1.0 - f_b) * R / N + f_b / V
     dP = (1.0 - f_b) * (dR / N - np.outer(dN, R) / (N * N))
     dP[3] = -R / N + 1.0 / V

@@ -16,8 +16,8 @@ IPA_OK, IPA_ERR_ARG, IPA_ERR_OOM, IPA_ERR_CUDA, IPA_ERR_TIMEOUT, IPA_ERR_BUSY, I
 IPA_MODEL_TIME1D, IPA_MODEL_ANGTIME4D, IPA_MODEL_TAGGED1D, IPA_MODEL_PHIS = 1, 2, 3, 4
 IPA_GAMMA, IPA_SIGMA, IPA_MU, IPA_FB, IPA_A0SQ, IPA_APESQ, IPA_DPA, IPA_DPE, IPA_FS, IPA_DS = range(10)
 IPA_DG, IPA_DM, IPA_PHIS, IPA_OMEGA = 4, 5, 6, 7
-IPA_PHIS_DG, IPA_PHIS_DM, IPA_PHIS_PHIS, IPA_PHIS_OMEGA = 10, 11, 12, 13
-IPA_NPAR_1D, IPA_NPAR_4D, IPA_NPAR_TAGGED, IPA_NPAR_PHIS, IPA_MAX_PAR = 4, 10, 8, 14, 16
+IPA_PHIS_DG, IPA_PHIS_DM, IPA_PHIS_PHIS, IPA_PHIS_OMEGA, IPA_PHIS_CSP, IPA_PHIS_QNORM = 10, 11, 12, 13, 14, 15
+IPA_NPAR_1D, IPA_NPAR_4D, IPA_NPAR_TAGGED, IPA_NPAR_PHIS, IPA_MAX_PAR = 4, 10, 8, 16, 32
 IPA_NOALLOC_MAX_EVENTS = 8388608
 IPA_MATH_EXP, IPA_MATH_LOG, IPA_MATH_SIN, IPA_MATH_COS, IPA_MATH_ERFCX, IPA_MATH_RCP = range(6)
 IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)
@@ -46,6 +46,10 @@ class ipa_param(ctypes.Structure):
                 ("fixed", c_int32), ("_pad", c_int32)]
 
 
+class ipa_joint(ctypes.Structure):
+    _fields_ = [("n_cat", c_int32), ("n_joint", c_int32), ("map", c_void_p), ("value", c_void_p)]
+
+
 class ipa_launch_config(ctypes.Structure):
     _fields_ = [("warps_per_block", c_int32), ("warps_per_sm", c_int32), ("tiles_per_take", c_int32),
                 ("ms", ctypes.c_float)]
@@ -64,6 +68,11 @@ PROTOTYPES = {
     "ipa_fit_batch": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
                                 POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_int32, c_double, c_void_p]),
+    "ipa_nll_grad_joint": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_joint),
+                                     c_void_p, c_void_p, c_void_p]),
+    "ipa_fit_joint": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_joint),
+                                POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_int32, c_double, c_void_p]),
     "ipa_hesse": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),
                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ipa_minos": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),

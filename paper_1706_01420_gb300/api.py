@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _capi as C
@@ -67,7 +68,7 @@ def model_tagged(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
 
 
 def model_phis(t_lo: float = 0.0, t_hi: float = 15.0) -> C.ipa_model:
-    """The time-dependent angular model with flavour tagging (14 parameters)."""
+    """The time-dependent angular model with flavour tagging (16 parameters)."""
     return ipa_model_init(C.IPA_MODEL_PHIS, t_lo, t_hi)
 
 
@@ -196,6 +197,71 @@ def ipa_fit_batch(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: l
                                 _ptr(iters, torch.int32, "iters"), _ptr(passes, torch.int32, "passes"),
                                 max_iter, tol, _stream(stream)),
            "ipa_fit_batch")
+    return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters, "passes": passes}
+
+
+class Joint:
+    """A simultaneous fit's category map (Sec. 4 Example 2; App. B, Cat and
+    ParamBox): jmap[c][p] is the joint parameter that model parameter p of
+    category c takes, or -1 for the constant value[c][p]."""
+
+    def __init__(self, jmap, value=None, n_joint: int | None = None):
+        self.map = np.ascontiguousarray(np.asarray(jmap, dtype=np.int32))
+        if self.map.ndim != 2:
+            raise ValueError("the joint map is n_cat x n_par")
+        self.value = None if value is None else np.ascontiguousarray(np.asarray(value, dtype=np.float64))
+        if self.value is not None and self.value.shape != self.map.shape:
+            raise ValueError("the joint values have the map's shape")
+        self.n_cat = self.map.shape[0]
+        self.n_joint = int(self.map.max()) + 1 if n_joint is None else int(n_joint)
+
+    def c_struct(self) -> C.ipa_joint:
+        j = C.ipa_joint()
+        j.n_cat, j.n_joint = self.n_cat, self.n_joint
+        j.map = self.map.ctypes.data
+        j.value = None if self.value is None else self.value.ctypes.data
+        return j
+
+
+def ipa_nll_grad_joint(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, joint: Joint, theta: torch.Tensor,
+                       stream=None) -> torch.Tensor:
+    """Joint NLL and gradient of n_fits simultaneous fits (theta: n_fits x n_joint;
+    segment i * n_cat + c is category c of fit i): an (n_fits, 1 + n_joint) tensor."""
+    n_seg = int(seg_off.numel()) - 1
+    if n_seg % joint.n_cat:
+        raise ValueError("the segments are not a whole number of fits")
+    n_fits = n_seg // joint.n_cat
+    theta = theta.reshape(n_fits, joint.n_joint)
+    out = torch.empty(n_fits, 1 + joint.n_joint, dtype=torch.float64, device=theta.device)
+    e, j = ipa_events(ev), joint.c_struct()
+    _check(_lib().ipa_nll_grad_joint(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
+                                     n_fits, ctypes.byref(j), _ptr(theta, name="theta"), _ptr(out, name="out"),
+                                     _stream(stream)),
+           "ipa_nll_grad_joint")
+    return out
+
+
+def ipa_fit_joint(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, joint: Joint, params: list[Param],
+                  theta: torch.Tensor, max_iter: int = 100, tol: float = 1e-9, stream=None) -> dict:
+    """Fit n_fits simultaneous fits; params: the n_joint joint parameters; theta
+    (n_fits x n_joint) holds the start values and receives the result."""
+    n_seg = int(seg_off.numel()) - 1
+    if n_seg % joint.n_cat or len(params) != joint.n_joint:
+        raise ValueError("segments or parameters do not match the joint map")
+    n_fits = n_seg // joint.n_cat
+    dev = theta.device
+    err = torch.zeros(n_fits, joint.n_joint, dtype=torch.float64, device=dev)
+    nll = torch.zeros(n_fits, dtype=torch.float64, device=dev)
+    status = torch.zeros(n_fits, dtype=torch.int32, device=dev)
+    iters = torch.zeros(n_fits, dtype=torch.int32, device=dev)
+    passes = torch.zeros(n_fits, dtype=torch.int32, device=dev)
+    e, j, spec = ipa_events(ev), joint.c_struct(), _spec(params)
+    _check(_lib().ipa_fit_joint(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
+                                n_fits, ctypes.byref(j), spec, _ptr(theta, name="theta"), _ptr(err, name="err"),
+                                _ptr(nll, name="nll"), _ptr(status, torch.int32, "status"),
+                                _ptr(iters, torch.int32, "iters"), _ptr(passes, torch.int32, "passes"),
+                                max_iter, tol, _stream(stream)),
+           "ipa_fit_joint")
     return {"theta": theta, "err": err, "nll": nll, "status": status, "iters": iters, "passes": passes}
 
 

@@ -42,17 +42,17 @@ __global__ void continue_kernel(cudaGraphConditionalHandle handle, const int* n_
 // the last call: a graph reads only workspace and scratch buffers and the event
 // columns, so consecutive fits of the same event set (one toy after another)
 // reuse it without capturing again.
-constexpr int kKeyPtrs = 18;
+constexpr int kKeyPtrs = 25;
 struct GraphKey {
-    int kind = 0, n_par = 0, n_fits = 0, max_rounds = 0, spec_stride = 0;
+    int kind = 0, n_par = 0, n_fits = 0, max_rounds = 0, spec_stride = 0, n_cat = 0, n_joint = 0;
     unsigned tune = 0;             // launch-geometry table version the graph was captured with
     double t_lo = 0.0, t_hi = 0.0;
     int64_t n = 0, fk_stride = 0;
     const void* ptr[kKeyPtrs] = {};
     bool operator==(const GraphKey& o) const {
         if (kind != o.kind || n_par != o.n_par || n_fits != o.n_fits || max_rounds != o.max_rounds ||
-            spec_stride != o.spec_stride || tune != o.tune || t_lo != o.t_lo || t_hi != o.t_hi || n != o.n ||
-            fk_stride != o.fk_stride)
+            spec_stride != o.spec_stride || n_cat != o.n_cat || n_joint != o.n_joint || tune != o.tune ||
+            t_lo != o.t_lo || t_hi != o.t_hi || n != o.n || fk_stride != o.fk_stride)
             return false;
         for (int i = 0; i < kKeyPtrs; ++i)
             if (ptr[i] != o.ptr[i]) return false;
@@ -165,7 +165,8 @@ ipa_status batch_args_reserve(BatchArgs& a, int n_fits) {
 ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, const int64_t* begin,
                    const int64_t* end, const Spec* specs, int spec_stride, int max_passes, int64_t tiles_bound,
                    double* theta_io_dev, double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev,
-                   int32_t* iters_out_dev, int32_t* passes_out_dev, cudaStream_t user, const char* who) {
+                   int32_t* iters_out_dev, int32_t* passes_out_dev, cudaStream_t user, const char* who,
+                   const JointDev* joint) {
     // The fit runs on a library stream (capturable even when the caller passes the
     // legacy default stream), ordered after the caller's stream by an event.
     cudaStream_t s = fit_stream();
@@ -180,7 +181,8 @@ ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, con
 
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     Scratch* sc = nullptr;
-    if ((st = scratch_get(tiles_bound, n_fits + 1, &sc)) != IPA_OK) return st;
+    const int n_seg = joint ? n_fits * joint->n_cat : n_fits;
+    if ((st = scratch_get(tiles_bound, n_seg + 1, &sc)) != IPA_OK) return st;
     int* n_active = c.nact;
     int* d_rounds = c.nact + kGraphSteps;
     const int max_rounds = (max_passes + kGraphSteps - 1) / kGraphSteps + 2;
@@ -195,14 +197,28 @@ ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, con
 
     const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
     // one pass = tile map, constants, segmented NLL+grad, state update
+    // (a joint fit: the categories' parameters from the joint ones, the NLL and
+    // gradient per category, their sums per fit)
     auto pass = [&](int k) -> ipa_status {
         ipa_status q;
-        if ((q = launch_seg_tiles(begin, end, c.active, n_fits, ev->n, sc->seg_tiles, s)) != IPA_OK)
-            return q;
-        if ((q = launch_consts(m, c.theta_eval, n_fits, sc->consts, s)) != IPA_OK) return q;
-        if ((q = launch_nll(m, true, cols, ev->n, begin, end, sc->seg_tiles, n_fits, sc->consts, sc, c.res, s)) !=
-            IPA_OK)
-            return q;
+        if (joint) {
+            if ((q = launch_joint_scatter(*joint, n_fits, c.theta_eval, c.active, s)) != IPA_OK) return q;
+            if ((q = launch_seg_tiles(joint->seg_begin, joint->seg_end, joint->seg_active, n_seg, ev->n,
+                                      sc->seg_tiles, s)) != IPA_OK)
+                return q;
+            if ((q = launch_consts(m, joint->theta_seg, n_seg, sc->consts, s)) != IPA_OK) return q;
+            if ((q = launch_nll(m, true, cols, ev->n, joint->seg_begin, joint->seg_end, sc->seg_tiles, n_seg,
+                                sc->consts, sc, joint->res_seg, s)) != IPA_OK)
+                return q;
+            if ((q = launch_joint_gather(*joint, n_fits, c.active, c.res, s)) != IPA_OK) return q;
+        } else {
+            if ((q = launch_seg_tiles(begin, end, c.active, n_fits, ev->n, sc->seg_tiles, s)) != IPA_OK)
+                return q;
+            if ((q = launch_consts(m, c.theta_eval, n_fits, sc->consts, s)) != IPA_OK) return q;
+            if ((q = launch_nll(m, true, cols, ev->n, begin, end, sc->seg_tiles, n_fits, sc->consts, sc, c.res,
+                                s)) != IPA_OK)
+                return q;
+        }
         if ((q = cuda_fail(cudaMemsetAsync(n_active + k, 0, sizeof(int), s), "fit count reset")) != IPA_OK)
             return q;
         qn_kernel<<<fg, fb, 0, s>>>(specs, spec_stride, n_fits, begin, end, c.res, c.states, c.theta_eval,
@@ -221,9 +237,18 @@ ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, con
     key.n = ev->n;
     key.fk_stride = ev->fk_stride;
     key.tune = tune_epoch();
+    key.n_cat = joint ? joint->n_cat : 0;
+    key.n_joint = joint ? joint->n_joint : 0;
     const void* ptrs[kKeyPtrs] = {ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->q, sc->partials, sc->counters,
                                   sc->gcount, sc->work, sc->seg_tiles, sc->consts, c.states, begin, end, specs,
-                                  (const void*)s};
+                                  (const void*)s,
+                                  joint ? (const void*)joint->map : nullptr,
+                                  joint ? (const void*)joint->value : nullptr,
+                                  joint ? (const void*)joint->seg_begin : nullptr,
+                                  joint ? (const void*)joint->seg_end : nullptr,
+                                  joint ? (const void*)joint->theta_seg : nullptr,
+                                  joint ? (const void*)joint->res_seg : nullptr,
+                                  joint ? (const void*)joint->seg_active : nullptr};
     for (int i = 0; i < kKeyPtrs; ++i) key.ptr[i] = ptrs[i];
     if (!(c.have_key && c.key == key)) {
         // Preferred: the whole minimisation as ONE graph launch.  A conditional

@@ -26,7 +26,7 @@
 
 namespace ipa {
 
-constexpr int kMaxP = 16;          // parameters of the largest model (IPA_MAX_PAR)
+constexpr int kMaxP = 32;          // parameters of a fit (IPA_MAX_PAR; joint fits over categories)
 constexpr double kSwitch = 1e-3;   // BFGS -> finite-difference Newton (decrement, sigma units)
 constexpr double kRehess = 2e-3;   // Newton moved further than this (sigma units): Hessian again
 enum Phase { kInit = 0, kLS = 1, kHess = 2, kNewton = 3, kDone = 4 };
@@ -43,7 +43,8 @@ struct State {
     double theta[kMaxP];      // current point (all parameters)
     double g[kMaxP];          // gradient at theta (free components)
     double Hinv[kMaxP * kMaxP];
-    double H[kMaxP * kMaxP];  // finite-difference Hessian (rows filled during HESS)
+    double H[kMaxP * kMaxP];  // finite-difference Hessian (rows filled during HESS, then symmetrised)
+    double W[kMaxP * kMaxP];  // Cholesky factor (work space of spd_inverse)
     double d[kMaxP];          // search direction (free components)
     double s_prev[kMaxP];     // step of the current trial (free components)
     double h[kMaxP];          // finite-difference steps
@@ -53,6 +54,30 @@ struct State {
     int phase, iter, passes, hess_j, newton, status, scaled, onesided, rehess;
 };
 
+// A simultaneous fit over categories (ipa_fit_joint): category c of fit i is
+// segment i * n_cat + c; category c evaluates the model at theta_c[p] =
+// theta_J[map[c][p]] (map >= 0) or value[c][p].  Device arrays; theta_seg,
+// res_seg and seg_active are work buffers of n_fits * n_cat segments.
+struct JointDev {
+    int n_cat = 0, n_model = 0, n_joint = 0;
+    const int32_t* map = nullptr;       // n_cat x n_model
+    const double* value = nullptr;      // n_cat x n_model
+    const int64_t* seg_begin = nullptr; // n_fits * n_cat
+    const int64_t* seg_end = nullptr;
+    double* theta_seg = nullptr;        // n_fits * n_cat x n_model
+    double* res_seg = nullptr;          // n_fits * n_cat x (1 + n_model)
+    int* seg_active = nullptr;          // n_fits * n_cat
+};
+
+// joint.cu: theta_seg (and seg_active = active[fit], or 1 without a mask) from
+// the joint parameters theta_joint (n_fits x n_joint); res_joint (n_fits x
+// (1 + n_joint)) from res_seg in the fixed order (c ascending, p ascending),
+// for the active fits (every fit without a mask).
+ipa_status launch_joint_scatter(const JointDev& j, int n_fits, const double* theta_joint, const int* active,
+                                cudaStream_t s);
+ipa_status launch_joint_gather(const JointDev& j, int n_fits, const int* active, double* res_joint,
+                               cudaStream_t s);
+
 // fit.cu: run n_fits fits to the end.  Fit i minimises the NLL of events
 // [begin[i], end[i]) with specs[i * spec_stride] (device arrays the caller
 // keeps unchanged until the call returns; ranges may overlap, e.g. several
@@ -61,11 +86,13 @@ struct State {
 // err, nll, status, iters, passes as in ipa_fit_batch (device, may be NULL).
 // tiles_bound >= the sum over fits of their 512-event tiles.  Ordered after
 // the caller's `stream`; blocks until the fits end.  `who` names the call in
-// the IPA_TRACE record.
+// the IPA_TRACE record.  With `joint`, fit i is a simultaneous fit over its
+// categories (its parameters the joint ones; [begin[i], end[i]) then only
+// decides whether the fit is empty) and tiles_bound covers all the segments.
 ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, const int64_t* begin,
                    const int64_t* end, const Spec* specs, int spec_stride, int max_passes, int64_t tiles_bound,
                    double* theta_io, double* err, double* nll, int32_t* status, int32_t* iters, int32_t* passes,
-                   cudaStream_t stream, const char* who);
+                   cudaStream_t stream, const char* who, const JointDev* joint = nullptr);
 
 namespace {
 
@@ -80,13 +107,14 @@ __device__ inline bool spec_ok(const Spec& sp) {
     return true;
 }
 
-// Cholesky solve of the n x n SPD matrix A (row-major, leading dim kMaxP):
-// writes A^-1 into inv.  Returns false if A is not positive definite.
-__device__ bool spd_inverse(const double* A, int n, double* inv) {
-    double L[kMaxP * kMaxP];
+// Cholesky solve of the n x n SPD matrix A + shift I (row-major, leading dim
+// kMaxP): writes (A + shift I)^-1 into inv, with the factor in L (n x kMaxP,
+// work space the caller provides, so that no kMaxP^2 array sits in local
+// memory).  Returns false if the matrix is not positive definite.
+__device__ bool spd_inverse(const double* A, int n, double shift, double* inv, double* L) {
     for (int i = 0; i < n; ++i) {
         for (int j = 0; j <= i; ++j) {
-            double s = A[i * kMaxP + j];
+            double s = i == j ? A[i * kMaxP + j] + shift : A[i * kMaxP + j];
             for (int k = 0; k < j; ++k) s -= L[i * kMaxP + k] * L[j * kMaxP + k];
             if (i == j) {
                 if (!(s > 0.0)) return false;
@@ -366,28 +394,26 @@ __global__ void qn_kernel(const Spec* __restrict__ specs, int spec_stride, int n
             set_hess_point(sp, S, theta_eval);
             break;
         }
-        // symmetrise, invert (shifting if not positive definite), then Newton
-        double Hs[kMaxP * kMaxP];
+        // symmetrise in place, invert (shifting the diagonal if not positive
+        // definite) into Hinv, then Newton
         for (int x = 0; x < n; ++x)
-            for (int z = 0; z < n; ++z)
-                Hs[x * kMaxP + z] = 0.5 * (S.H[x * kMaxP + z] + S.H[z * kMaxP + x]);
-        double inv[kMaxP * kMaxP];
-        bool pd = spd_inverse(Hs, n, inv);
+            for (int z = x + 1; z < n; ++z) {
+                const double v = 0.5 * (S.H[x * kMaxP + z] + S.H[z * kMaxP + x]);
+                S.H[x * kMaxP + z] = v;
+                S.H[z * kMaxP + x] = v;
+            }
+        bool pd = spd_inverse(S.H, n, 0.0, S.Hinv, S.W);
         double shift = 0.0;
         double dmax = 0.0;
-        for (int x = 0; x < n; ++x) dmax = fmax(dmax, fabs(Hs[x * kMaxP + x]));
+        for (int x = 0; x < n; ++x) dmax = fmax(dmax, fabs(S.H[x * kMaxP + x]));
         for (int k = 0; k < 40 && !pd; ++k) {
             shift = shift == 0.0 ? 1e-10 * dmax : shift * 4.0;
-            double Ht[kMaxP * kMaxP];
-            for (int x = 0; x < n * kMaxP; ++x) Ht[x] = Hs[x];
-            for (int x = 0; x < n; ++x) Ht[x * kMaxP + x] += shift;
-            pd = spd_inverse(Ht, n, inv);
+            pd = spd_inverse(S.H, n, shift, S.Hinv, S.W);
         }
         if (!pd) {
             finish(sp, S, IPA_FIT_BAD_PDF);
             break;
         }
-        for (int x = 0; x < n * kMaxP; ++x) S.Hinv[x] = inv[x];
         S.newton = 0;
         newton_step(sp, S, theta_eval);   // f and g at theta are those of the last accepted step
         break;
@@ -486,11 +512,12 @@ __global__ void final_kernel(const Spec* __restrict__ specs, int spec_stride, in
 
 // Host: the minimiser specification from the parameter array (Parameter /
 // Free of App. B): limits, steps (0 -> a tenth of the range, or of |value|+1),
-// the free-parameter list, tolerance and budgets.
+// the free-parameter list, tolerance and budgets.  n_par: the parameters of a
+// fit (0: the model's; a joint fit's n_joint otherwise).
 inline ipa_status build_spec(const ipa_model* model, const ipa_param* spec, int max_iter, double tol,
-                             Spec* out) {
+                             Spec* out, int n_par = 0) {
     Spec sp{};
-    sp.n_par = model->n_par;
+    sp.n_par = n_par > 0 ? n_par : model->n_par;
     sp.tol = tol;
     sp.max_iter = max_iter;
     for (int p = 0; p < sp.n_par; ++p) {

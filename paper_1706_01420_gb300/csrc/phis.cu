@@ -66,8 +66,11 @@ struct PhisConsts {
     double r0, ra, re, rF, rs;      // sqrt of x0, xa, xe, F, 1 - F
     double cw[6], sw[6];            // cos, sin of (dpe - dpa), dpa, dpe, (dpa - dS), (dpe - dS), dS
     double br[10], bi[10];          // Re, Im of b_k
-    double pad_;
+    double csp;                     // C_SP: factor of the S-P interference terms k = 7, 8, 9
 };
+
+// Row factor: C_SP for the S-P interference terms, 1 otherwise.
+__device__ __forceinline__ double row_scale(const PhisConsts& c, int k) { return k >= 7 ? c.csp : 1.0; }
 static_assert(sizeof(PhisConsts) <= sizeof(Consts), "PhisConsts must fit a Consts slot");
 static_assert(sizeof(PhisConsts) % 16 == 0, "PhisConsts must be a multiple of 16 bytes");
 constexpr int kPhisDoubles = sizeof(PhisConsts) / sizeof(double);
@@ -159,6 +162,61 @@ __device__ inline void b_deriv(const PhisConsts& c, int k, int a, double* dr, do
     *di = dm * sp + m * dpsi * cp;
 }
 
+// Complex antiderivative of the oscillating time function: F(tau) with
+// dF/dtau = g(tau; z), z = zr + i zi, F = (Phi(tau / sigma) - g) / z (from
+// g' = G - z g), and dF/dz, dF/dsigma, dF/dmu = -(F + dg/dz) / z,
+// (-(tau / sigma) G - dg/dsigma) / z, -g with dg/dz = (z s^2 - tau) g - s^2 G and
+// dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G.  g through the Faddeeva
+// function: 1/2 e^{-tau^2 / 2 s^2} w(x + i y) for y >= 0, else
+// e^{-z tau + z^2 s^2 / 2} - 1/2 e^{-tau^2 / 2 s^2} w(-x - i y), with
+// x + i y = i (z s^2 - tau) / (sqrt2 s).  Out: F, dF/dz, dF/dsigma, dF/dmu as
+// (re, im) pairs.
+__device__ inline void edge_c(double tau, double zr, double zi, double sigma, double* out) {
+    using namespace cdetail;
+    const double s2 = sigma * sigma;
+    const double y = (zr * s2 - tau) / (kSqrt2 * sigma), x = -zi * sigma / kSqrt2;
+    const double gx = exp(-tau * tau / (2.0 * s2));
+    double wr, wi, gr, gi;
+    if (y >= 0.0) {
+        faddeeva_uhp(x, y, &wr, &wi);
+        gr = 0.5 * gx * wr;
+        gi = 0.5 * gx * wi;
+    } else {
+        faddeeva_uhp(-x, -y, &wr, &wi);
+        const double a = -zr * tau + 0.5 * s2 * (zr * zr - zi * zi), b = -zi * tau + zr * zi * s2;
+        double sb, cb;
+        sincos(b, &sb, &cb);
+        const double ea = exp(a);
+        gr = ea * cb - 0.5 * gx * wr;
+        gi = ea * sb - 0.5 * gx * wi;
+    }
+    const double G = gx * kInvSqrt2Pi / sigma;
+    const double Phi = edge_phi(tau, sigma);
+    const double n2 = zr * zr + zi * zi, ir = zr / n2, ii = -zi / n2;     // 1/z
+    // F = (Phi - g) / z
+    const double nr = Phi - gr, ni = -gi;
+    const double Fr = nr * ir - ni * ii, Fi = nr * ii + ni * ir;
+    // dg/dz = (z s^2 - tau) g - s^2 G
+    const double pr = zr * s2 - tau, pi = zi * s2;
+    const double dzr = pr * gr - pi * gi - s2 * G, dzi = pr * gi + pi * gr;
+    // dF/dz = -(F + dg/dz) / z
+    const double ar = -(Fr + dzr), ai = -(Fi + dzi);
+    out[2] = ar * ir - ai * ii;
+    out[3] = ar * ii + ai * ir;
+    // dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G
+    const double z2r = (zr * zr - zi * zi) * sigma, z2i = 2.0 * zr * zi * sigma;
+    const double dsr = z2r * gr - z2i * gi - (zr * sigma + tau / sigma) * G;
+    const double dsi = z2r * gi + z2i * gr - zi * sigma * G;
+    // dF/dsigma = (-(tau / sigma) G - dg/dsigma) / z
+    const double br = -(tau / sigma) * G - dsr, bi = -dsi;
+    out[4] = br * ir - bi * ii;
+    out[5] = br * ii + bi * ir;
+    out[0] = Fr;
+    out[1] = Fi;
+    out[6] = -gr;
+    out[7] = -gi;
+}
+
 __device__ inline void compute_phis_consts(const ModelDev& md, const double* th, PhisConsts* c) {
     using namespace cdetail;
     const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
@@ -226,7 +284,7 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     const double Pe = sF * (1.0 - xe), Po = sF * xe + F;
     const double wL = Pe * (1.0 + cn) + Po * (1.0 - cn), wH = Pe * (1.0 - cn) + Po * (1.0 + cn);
     const double K = 16.0 * kPi / 9.0;
-    const double N = K * (wL * IL + wH * IH);
+    double N = K * (wL * IL + wH * IH);
     double dN[IPA_NPAR_PHIS];
     for (int j = 0; j < 3; ++j) dN[j] = K * (wL * (dFhL[j] - dFlL[j]) + wH * (dFhH[j] - dFlH[j]));
     dN[IPA_FB] = 0.0;
@@ -240,7 +298,32 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     dN[IPA_PHIS_DM] = 0.0;
     dN[IPA_PHIS_PHIS] = K * ((-Pe * sn + Po * sn) * IL + (Pe * sn - Po * sn) * IH);
     dN[IPA_PHIS_OMEGA] = 0.0;
-    const double V = 2.0 * (md.t_hi - md.t_lo) * 8.0 * kPi;
+    dN[IPA_PHIS_CSP] = 0.0;     // the interference terms integrate to zero over the angles
+    dN[IPA_PHIS_QNORM] = 0.0;
+    double V = 2.0 * (md.t_hi - md.t_lo) * 8.0 * kPi;
+    const double qsel = th[IPA_PHIS_QNORM];
+    if (qsel != 0.0) {
+        // one tag: N_Q = N / 2 + Q K D sin(phi_s) (Pe - Po) Im I_c, I_c the integral
+        // of g(t - mu; Gamma - i Dm) over the range; the background over one tag
+        const double Q = qsel > 0.0 ? 1.0 : -1.0;
+        double eh[8], el[8];
+        edge_c(md.t_hi - mu, Gamma, -Dm, sigma, eh);
+        edge_c(md.t_lo - mu, Gamma, -Dm, sigma, el);
+        const double Ii = eh[1] - el[1];
+        const double dzr = eh[2] - el[2], dzi = eh[3] - el[3];
+        const double W = Pe - Po, D = 1.0 - 2.0 * om;
+        const double odd = Q * K * D * sn * W;
+        N = 0.5 * N + odd * Ii;
+        for (int j = 0; j < IPA_NPAR_PHIS; ++j) dN[j] *= 0.5;
+        dN[IPA_GAMMA] += odd * dzi;                      // d/dGamma = d/dz
+        dN[IPA_SIGMA] += odd * (eh[5] - el[5]);
+        dN[IPA_MU] += odd * (eh[7] - el[7]);
+        dN[IPA_PHIS_DM] += odd * (-dzr);                 // d/dDm = -i d/dz: Im(-i u) = -Re u
+        dN[IPA_PHIS_PHIS] += Q * K * D * cn * W * Ii;
+        dN[IPA_PHIS_OMEGA] += Q * K * (-2.0) * sn * W * Ii;
+        for (int a = 0; a < 6; ++a) dN[IPA_A0SQ + a] += Q * K * D * sn * (dPe[a] - dPo[a]) * Ii;
+        V *= 0.5;
+    }
     const double inv_N = 1.0 / N;
     c->N = N;
     c->inv_N = inv_N;
@@ -248,7 +331,7 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     c->cs = (1.0 - fb) * inv_N;
     c->cb = fb / V;
     for (int j = 0; j < IPA_NPAR_PHIS; ++j) c->dlnN[j] = dN[j] * inv_N;
-    c->pad_ = 0.0;
+    c->csp = th[IPA_PHIS_CSP];
 }
 
 __global__ void phis_consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg, Consts* __restrict__ out) {
@@ -343,7 +426,8 @@ __device__ __forceinline__ void phis_event(const PhisWarp& pw, const MathTables*
 // (1/2) sum_kj C_kj S2_kj, the time sums D_t = cs sum r d rate / d theta_t:
 //   time parameters:            -D_t + cs dlnN_t SR,
 //   f_b:                        SR / N - Q / V,
-//   amplitudes, phi_s, omega:   -(cs/2) sum_kj dC_kj/dtheta S2_kj + cs dlnN SR.
+//   amplitudes, phi_s, omega, C_SP:  -(cs/2) sum_kj dC_kj/dtheta S2_kj + cs dlnN SR
+// (C rows 7, 8, 9 carry C_SP).
 template <bool GRAD, bool CACHED>
 __device__ __forceinline__ void phis_finalize(const PhisConsts& c, const double* acc, int n_par, double* out, int lane) {
     if (lane == 0) out[0] = -acc[0];
@@ -354,7 +438,7 @@ __device__ __forceinline__ void phis_finalize(const PhisConsts& c, const double*
     for (int k = 0; k < 10; ++k) {
         double row[4];
         c_row(k, c.br[k], c.bi[k], 1.0, c.c, c.s, 1.0, c.D, row);
-        const double sc = CACHED ? 1.0 : kBasisScale[k];
+        const double sc = row_scale(c, k) * (CACHED ? 1.0 : kBasisScale[k]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) SR = fma(row[j], sc * acc[kS + 4 * k + j], SR);
     }
@@ -367,6 +451,8 @@ __device__ __forceinline__ void phis_finalize(const PhisConsts& c, const double*
     double v;
     if (lane == IPA_FB) {
         v = fma(SR, c.inv_N, -acc[1] * c.inv_V);
+    } else if (lane == IPA_PHIS_QNORM) {
+        v = 0.0;
     } else if (lane < 3 || lane == IPA_PHIS_DG || lane == IPA_PHIS_DM) {
         // register operands only (an index computed from the lane would put acc in local memory)
         const double Dt = lane == 0 ? acc[kT] : lane == 1 ? acc[kT + 1] : lane == 2 ? acc[kT + 2]
@@ -377,16 +463,20 @@ __device__ __forceinline__ void phis_finalize(const PhisConsts& c, const double*
 #pragma unroll
         for (int k = 0; k < 10; ++k) {
             double row[4];
+            double rs = row_scale(c, k);
             if (lane == IPA_PHIS_PHIS) {
                 c_row(k, c.br[k], c.bi[k], 0.0, -c.s, c.c, 1.0, c.D, row);
             } else if (lane == IPA_PHIS_OMEGA) {
                 c_row(k, c.br[k], c.bi[k], 1.0, c.c, c.s, 0.0, -2.0, row);
+            } else if (lane == IPA_PHIS_CSP) {
+                c_row(k, c.br[k], c.bi[k], 1.0, c.c, c.s, 1.0, c.D, row);
+                rs = k >= 7 ? 1.0 : 0.0;
             } else {
                 double dr, di;
                 b_deriv(c, k, lane - IPA_A0SQ, &dr, &di);
                 c_row(k, dr, di, 1.0, c.c, c.s, 1.0, c.D, row);
             }
-            const double sc = CACHED ? 1.0 : kBasisScale[k];
+            const double sc = rs * (CACHED ? 1.0 : kBasisScale[k]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) dsum = fma(row[j], sc * acc[kS + 4 * k + j], dsum);
         }
@@ -452,7 +542,7 @@ phis_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin, const i
                 if (lane < 10) {
                     double row[4];
                     c_row(lane, pw.c.br[lane], pw.c.bi[lane], 1.0, pw.c.c, pw.c.s, 1.0, pw.c.D, row);
-                    const double sc = 0.5 * pw.c.cs * (CACHED ? 1.0 : kBasisScale[lane]);
+                    const double sc = 0.5 * pw.c.cs * row_scale(pw.c, lane) * (CACHED ? 1.0 : kBasisScale[lane]);
                     for (int j = 0; j < 4; ++j) pw.cq[4 * lane + j] = sc * row[j];
                 }
                 __syncwarp();

@@ -73,10 +73,12 @@ __global__ void hesse_first_steps_kernel(const Spec* __restrict__ spp, int n_fit
 
 // The Hessian of fit f from its virtual segments' gradients; stage 0 sets the
 // steps of stage 1 from the errors, stage 1 writes the outputs.
+// work: 3 kMaxP^2 doubles per fit (inverse, Cholesky factor, Hessian).
 __global__ void hesse_assemble_kernel(const Spec* __restrict__ spp, int n_fits, const double* __restrict__ theta,
                                       double* __restrict__ h, const double* __restrict__ vres, int stage,
-                                      double* __restrict__ cov, double* __restrict__ corr,
-                                      double* __restrict__ err, int32_t* __restrict__ status) {
+                                      double* __restrict__ work, double* __restrict__ cov,
+                                      double* __restrict__ corr, double* __restrict__ err,
+                                      int32_t* __restrict__ status) {
     const Spec& sp = *spp;
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n_fits) return;
@@ -84,7 +86,7 @@ __global__ void hesse_assemble_kernel(const Spec* __restrict__ spp, int n_fits, 
     const double* th = theta + (size_t)f * P;
     double* hf = h + (size_t)f * kMaxP;
     const double* rc = vres + (size_t)f * nv * (1 + P);
-    double H[kMaxP * kMaxP];
+    double* H = work + (size_t)n_fits * 2 * kMaxP * kMaxP + (size_t)f * kMaxP * kMaxP;
     bool finite = true;
     for (int a = 0; a < n; ++a) {
         const double* r1 = rc + (size_t)(1 + 2 * a) * (1 + P);
@@ -97,10 +99,16 @@ __global__ void hesse_assemble_kernel(const Spec* __restrict__ spp, int n_fits, 
             finite &= isfinite(H[a * kMaxP + b]);
         }
     }
-    double Hs[kMaxP * kMaxP], inv[kMaxP * kMaxP];
+    double* Hs = H;                                   // symmetrised in place
+    double* inv = work + (size_t)f * 2 * kMaxP * kMaxP;
+    double* L = inv + kMaxP * kMaxP;
     for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b) Hs[a * kMaxP + b] = 0.5 * (H[a * kMaxP + b] + H[b * kMaxP + a]);
-    bool pd = finite && spd_inverse(Hs, n, inv);
+        for (int b = a + 1; b < n; ++b) {
+            const double v = 0.5 * (H[a * kMaxP + b] + H[b * kMaxP + a]);
+            H[a * kMaxP + b] = v;
+            H[b * kMaxP + a] = v;
+        }
+    bool pd = finite && spd_inverse(Hs, n, 0.0, inv, L);
     int st = 0;
     if (finite && !pd) {
         // not positive definite: shift the diagonal until it is (status 1)
@@ -108,10 +116,7 @@ __global__ void hesse_assemble_kernel(const Spec* __restrict__ spp, int n_fits, 
         for (int a = 0; a < n; ++a) dmax = fmax(dmax, fabs(Hs[a * kMaxP + a]));
         for (int k = 0; k < 40 && !pd; ++k) {
             shift = shift == 0.0 ? 1e-10 * dmax : shift * 4.0;
-            double Ht[kMaxP * kMaxP];
-            for (int x = 0; x < n * kMaxP; ++x) Ht[x] = Hs[x];
-            for (int a = 0; a < n; ++a) Ht[a * kMaxP + a] += shift;
-            pd = spd_inverse(Ht, n, inv);
+            pd = spd_inverse(Hs, n, shift, inv, L);
         }
         st = 1;
     }
@@ -335,6 +340,7 @@ struct ProfileContext {
     int* h_open = nullptr;
     // HESSE
     double* h = nullptr;
+    double* hwork = nullptr;        // 3 kMaxP^2 per fit (hesse_assemble_kernel)
     int64_t *vbegin = nullptr, *vend = nullptr;
     double *vtheta = nullptr, *vres = nullptr;
     size_t cap_fit = 0, cap_v = 0;
@@ -375,6 +381,7 @@ ipa_status hesse_reserve(ProfileContext& c, size_t n_fits, size_t n_v, int P) {
     if (n_fits > c.cap_fit) {
         cudaDeviceSynchronize();
         st = grow(&c.h, n_fits * kMaxP, "hesse steps");
+        if (st == IPA_OK) st = grow(&c.hwork, n_fits * 3 * kMaxP * kMaxP, "hesse work");
         if (st == IPA_OK) c.cap_fit = n_fits;
     }
     if (st == IPA_OK && n_v > c.cap_v) {
@@ -467,8 +474,8 @@ extern "C" ipa_status ipa_hesse(const ipa_model* model, const ipa_events* ev, co
         if ((st = cuda_fail(cudaGetLastError(), "hesse points")) != IPA_OK) break;
         if ((st = virtual_pass(model, ev, (int)n_v, c.vbegin, c.vend, c.vtheta, tiles, true, c.vres, s)) != IPA_OK)
             break;
-        hesse_assemble_kernel<<<gf, kHesseBlock, 0, s>>>(c.spec, n_fits, theta_dev, c.h, c.vres, stage, cov_out_dev,
-                                                         corr_out_dev, err_out_dev, status_out_dev);
+        hesse_assemble_kernel<<<gf, kHesseBlock, 0, s>>>(c.spec, n_fits, theta_dev, c.h, c.vres, stage, c.hwork,
+                                                         cov_out_dev, corr_out_dev, err_out_dev, status_out_dev);
         st = cuda_fail(cudaGetLastError(), "hesse assemble");
     }
     // blocking: the library buffers are reused by the next call

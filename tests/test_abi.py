@@ -61,6 +61,42 @@ def test_model_init_and_host_argument_checks(lib):
     assert lib.ipa_version().startswith(b"ipanema")
 
 
+def test_joint_map_host_checks(lib):
+    """ipa_nll_grad_joint and ipa_fit_joint reject a bad category map on the host."""
+    import numpy as np
+    from paper_1706_01420_gb300 import _capi as C
+    m = C.ipa_model()
+    lib.ipa_model_init(ctypes.byref(m), C.IPA_MODEL_TIME1D, 0.0, 15.0)
+    ev = C.ipa_events()
+    ev.n = 10
+    ev.t = 16                      # never dereferenced: rejected on the host
+
+    def call(jmap, value=None, n_joint=None, n_fits=1):
+        jm = np.ascontiguousarray(np.asarray(jmap, dtype=np.int32))
+        j = C.ipa_joint()
+        j.n_cat = jm.shape[0]
+        j.n_joint = int(jm.max()) + 1 if n_joint is None else n_joint
+        j.map = jm.ctypes.data
+        v = None if value is None else np.ascontiguousarray(np.asarray(value, dtype=np.float64))
+        j.value = None if v is None else v.ctypes.data
+        return lib.ipa_nll_grad_joint(ctypes.byref(m), ctypes.byref(ev), 16, n_fits, ctypes.byref(j), 16, 16,
+                                      None)
+
+    assert call([[0, 1, 2, 4]]) == C.IPA_ERR_ARG                       # joint parameter 3 unused
+    assert b"used by no category" in lib.ipa_last_error()
+    assert call([[0, 1, 2, -2]]) == C.IPA_ERR_ARG                      # below -1
+    assert call([[0, 1, 2, 3]], n_joint=3) == C.IPA_ERR_ARG            # above n_joint
+    assert call([[0, 1, -1, 2]]) == C.IPA_ERR_ARG                      # a constant without values
+    assert b"no values" in lib.ipa_last_error()
+    assert call([[0] * 4], n_joint=33) == C.IPA_ERR_ARG                # more than IPA_MAX_PAR
+    assert call([[0, 1, 2, 3]], n_fits=0) == C.IPA_ERR_ARG
+    spec = (C.ipa_param * 4)()
+    jm = np.array([[0, 1, 2, 3], [0, 1, 2, 5]], dtype=np.int32)
+    j = C.ipa_joint(n_cat=2, n_joint=6, map=jm.ctypes.data, value=None)
+    assert lib.ipa_fit_joint(ctypes.byref(m), ctypes.byref(ev), 16, 1, ctypes.byref(j), spec, 16, None, None,
+                             None, None, None, 10, 1e-9, None) == C.IPA_ERR_ARG   # joint parameter 4 unused
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_1706_01420_gb300 import _capi
     saved = _capi._lib

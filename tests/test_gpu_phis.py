@@ -6,6 +6,7 @@
   a ragged tail, parameter points (phi_s = 0, omega = 1/2, a large S wave, a
   range before the resolution peak), weighted and not, the raw and the cached
   angular basis;
+* a category of one flavour (normalisation over the selected tag alone);
 * the gradient against fourth-order central differences of the GPU NLL;
 * segments bitwise equal to solo calls;
 * a batched fit within 1e-6 sigma of the oracle's fit on events drawn from the
@@ -20,12 +21,15 @@ from paper_1706_01420_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TH = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3])
+TH = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3, 0.8, 0.0])
 THETAS = {
     "truth": TH,
-    "phi_zero": np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.0, 0.3]),
-    "half_mistag": np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.5]),
-    "large_s_wave": np.array([0.7, 0.06, 0.01, 0.2, 0.4, 0.3, 2.0, -1.0, 0.3, -1.2, -0.1, 12.0, -2.0, 0.1]),
+    "phi_zero": np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.0, 0.3, 1.0, 0.0]),
+    "half_mistag": np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.5, 0.8,
+                             0.0]),
+    "large_s_wave": np.array([0.7, 0.06, 0.01, 0.2, 0.4, 0.3, 2.0, -1.0, 0.3, -1.2, -0.1, 12.0, -2.0, 0.1, 0.5, 0.0]),
+    "no_s_p_overlap": np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.1, 0.3, 0.085, 17.77, 0.8, 0.3, 0.0,
+                                0.0]),
 }
 
 
@@ -50,10 +54,10 @@ def grad_scale(F, m, ev, th):
     P = F.pdf(m, ev, th)
     cs = (1 - th[3]) / N
     r = w / P
-    out = np.zeros(14)
-    for j in range(14):
+    out = np.zeros(16)
+    for j in range(15):
         if j == 3:
-            out[j] = math.fsum(r * (np.abs(R) / N + 1 / F.volume(m)))
+            out[j] = math.fsum(r * (np.abs(R) / N + 1 / F.volume(m, th)))
         else:
             # each derivative row is a sum of ~10 angular terms of either sign:
             # allow the sum of their magnitudes through a factor 10 on |dR|
@@ -61,10 +65,15 @@ def grad_scale(F, m, ev, th):
     return out
 
 
-def _parity(env, n, seed, th, weighted=False, t_lo=0.0, cached=False):
+def _parity(env, n, seed, th, weighted=False, t_lo=0.0, cached=False, tag=0.0):
     O, F, G, torch, api = env
     m_o, m_g = O.Model("phis", t_lo, 15.0), api.model_phis(t_lo, 15.0)
     cols = synth.events_phis(n, seed, t_lo=t_lo, weighted=weighted)
+    if tag:
+        # a category of one flavour: every event carries the selected tag
+        th = th.copy()
+        th[15] = tag
+        cols["q"] = np.full(n, tag)
     ev = G.to_dev(cols)
     if cached and n:
         ev["fk"] = api.ipa_angular_basis(m_g, ev)
@@ -74,7 +83,7 @@ def _parity(env, n, seed, th, weighted=False, t_lo=0.0, cached=False):
     f_ref, g_ref = F.nll_grad(m_o, cols, th)
     logl, _ = F.nll_grad_terms(m_o, cols, th)
     labs = math.fsum(np.abs(logl)) if n else 1.0
-    scale = grad_scale(F, m_o, cols, th) if n else np.zeros(14)
+    scale = grad_scale(F, m_o, cols, th) if n else np.zeros(16)
     G.assert_nll_grad_close(got, f_ref, g_ref, scale, labs)
     assert abs(nll_only - f_ref) <= 1e-12 * labs
     return got
@@ -91,6 +100,13 @@ def test_parity_parameters(env, name, weighted):
     _parity(env, 12000, seed=3, th=THETAS[name], weighted=weighted)
 
 
+@pytest.mark.parametrize("tag", [1.0, -1.0])
+@pytest.mark.parametrize("name", ["truth", "large_s_wave"])
+def test_parity_one_tag_normalisation(env, name, tag):
+    _parity(env, 12000, seed=9, th=THETAS[name], weighted=True, tag=tag)
+    _parity(env, 4097, seed=10, th=THETAS[name], tag=tag, cached=True)
+
+
 def test_parity_cached_basis_and_early_range(env):
     _parity(env, 12000, seed=4, th=TH, cached=True)
     _parity(env, 12000, seed=6, th=THETAS["large_s_wave"], weighted=True, t_lo=-0.3, cached=True)
@@ -100,18 +116,26 @@ def test_gradient_matches_finite_differences(env):
     O, F, G, torch, api = env
     m = api.model_phis(0.0, 15.0)
     ev = G.to_dev(synth.events_phis(30000, 8, weighted=True))
-    th = TH + np.array([0.01, 0.002, 0.001, 0.02, 0.01, -0.01, 0.05, -0.05, 0.01, 0.1, 0.01, 0.05, 0.05, 0.01])
-    g = api.ipa_nll_grad(m, ev, torch.tensor(th, device="cuda")).cpu().numpy()[1:]
+    base = TH + np.array([0.01, 0.002, 0.001, 0.02, 0.01, -0.01, 0.05, -0.05, 0.01, 0.1, 0.01, 0.05, 0.05, 0.01,
+                          -0.05, 0.0])
+    for Q in (0.0, -1.0):
+        th = base.copy()
+        th[15] = Q
+        e = ev if Q == 0.0 else dict(ev, q=torch.full_like(ev["q"], Q))
+        g = api.ipa_nll_grad(m, e, torch.tensor(th, device="cuda")).cpu().numpy()[1:]
+        assert g[15] == 0.0
 
-    def f(j, d):
-        tt = th.copy()
-        tt[j] += d
-        return float(api.ipa_nll(m, ev, torch.tensor(tt, device="cuda")).cpu()[0])
+        def f(j, d):
+            tt = th.copy()
+            tt[j] += d
+            return float(api.ipa_nll(m, e, torch.tensor(tt, device="cuda")).cpu()[0])
 
-    for j in range(14):
-        h = 1e-5 * max(abs(th[j]), 1e-2)
-        fd = (8.0 * (f(j, h) - f(j, -h)) - (f(j, 2 * h) - f(j, -2 * h))) / (12.0 * h)
-        assert abs(fd - g[j]) <= 1e-6 * max(abs(g[j]), 1.0), (j, fd, g[j])
+        for j in range(15):
+            # steps of 1e-5 of the parameter's scale (at least 0.1): roundoff of the
+            # 3e4-event NLL stays below the 1e-6 bound
+            h = 1e-5 * max(abs(th[j]), 0.1)
+            fd = (8.0 * (f(j, h) - f(j, -h)) - (f(j, 2 * h) - f(j, -2 * h))) / (12.0 * h)
+            assert abs(fd - g[j]) <= 1e-6 * max(abs(g[j]), 1.0), (Q, j, fd, g[j])
 
 
 def test_segments_equal_solo(env):
@@ -154,17 +178,17 @@ def _sample(F, m, th, n, seed):
 
 
 def test_fit_matches_oracle_and_batch_equals_solo(env):
-    """sigma, mu and omega held; the eleven others free."""
+    """sigma, mu, omega, C_SP and the tag selector held; the eleven others free."""
     O, F, G, torch, api = env
     m_o, m = O.Model("phis", 0.0, 15.0), api.model_phis(0.0, 15.0)
     toys = [_sample(F, m_o, TH, 6000, 100 + k) for k in range(3)]
     free = [0, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12]
-    lo = np.array([0.3, 0.01, -0.1, 0.0, 0.2, 0.05, 0.0, 0.0, 0.0, -3.2, -0.5, 10.0, -3.1, 0.0])
-    hi = np.array([1.5, 0.2, 0.1, 0.5, 0.8, 0.5, 6.3, 6.3, 0.5, 3.2, 0.5, 25.0, 3.1, 0.5])
+    lo = np.array([0.3, 0.01, -0.1, 0.0, 0.2, 0.05, 0.0, 0.0, 0.0, -3.2, -0.5, 10.0, -3.1, 0.0, 0.0, -1.0])
+    hi = np.array([1.5, 0.2, 0.1, 0.5, 0.8, 0.5, 6.3, 6.3, 0.5, 3.2, 0.5, 25.0, 3.1, 0.5, 1.0, 1.0])
     step = (hi - lo) / 50
     start = TH.copy()
     params = [api.Param(float(start[i]), float(lo[i]), float(hi[i]), float(step[i]), fixed=i not in free)
-              for i in range(14)]
+              for i in range(16)]
     sizes = [t["t"].size for t in toys]
 
     def fit(sel):

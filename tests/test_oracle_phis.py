@@ -8,7 +8,9 @@
   independent construction that pins the 4D angular model), mixed by the
   mistag.  A wrong sign, eta, conjugate or product in any of the ten terms
   breaks this equality.
-* The PDF integrates to 1 over t, the angles and both tags.
+* The PDF integrates to 1 over t, the angles and both tags, or over the one
+  tag a category selects; the two one-tag normalisations add up to the
+  both-tag one; the complex time integral behind them equals quadrature.
 * A pure CP-even (CP-odd) P wave integrated over the angles is the tagged
   decay-time model at phi_s (phi_s + pi); omega = 1/2 makes it tag-blind.
 * The gradient equals fourth-order central differences of the NLL.
@@ -23,7 +25,7 @@ from scipy import integrate
 from tests.test_oracle_angular import d1
 
 S2 = math.sqrt(2.0)
-TH = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3])
+TH = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3, 0.8, 0.0])
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +53,7 @@ def random_theta(rng):
             break
     return np.array([rng.uniform(0.4, 1.0), 1e-7, 0.0, 0.1, x0, xe, *rng.uniform(-math.pi, math.pi, 2),
                      rng.uniform(0.01, 0.6), rng.uniform(-math.pi, math.pi), rng.uniform(-0.3, 0.3),
-                     rng.uniform(0.5, 25.0), rng.uniform(-math.pi, math.pi), rng.uniform(0.0, 0.5)])
+                     rng.uniform(0.5, 25.0), rng.uniform(-math.pi, math.pi), rng.uniform(0.0, 0.5), 1.0, 0.0])
 
 
 def test_matches_time_evolved_helicity_amplitudes(oracle, F):
@@ -90,10 +92,17 @@ def _angular_grid(n=4, nphi=8):
     return CK.ravel(), CL.ravel(), PH.ravel(), W.ravel()
 
 
-@pytest.mark.parametrize("th", [TH, np.array([1.2, 0.08, 0.02, 0.3, 0.3, 0.4, 1.0, -2.0, 0.2, -1.0, -0.1, 5.0,
-                                               -2.0, 0.1])])
-def test_pdf_integrates_to_one(oracle, F, th):
+TH2 = np.array([1.2, 0.08, 0.02, 0.3, 0.3, 0.4, 1.0, -2.0, 0.2, -1.0, -0.1, 5.0, -2.0, 0.1, 0.5, 0.0])
+
+
+@pytest.mark.parametrize("Q", [0.0, 1.0, -1.0])
+@pytest.mark.parametrize("th", [TH, TH2])
+def test_pdf_integrates_to_one(oracle, F, th, Q):
+    """Over t, the angles and both tags (Q = 0), or over the selected tag alone
+    (Q = +-1: a category of one flavour)."""
     m = oracle.Model("phis", 0.0, 15.0)
+    th = th.copy()
+    th[15] = Q
     ck, cl, ph, w = _angular_grid()
 
     def dens(t, q):
@@ -102,10 +111,50 @@ def test_pdf_integrates_to_one(oracle, F, th):
         return float(F.pdf(m, ev, th) @ w)
 
     tot = 0.0
-    for q in (-1.0, 1.0):
+    for q in ((-1.0, 1.0) if Q == 0.0 else (Q,)):
         tot += integrate.quad(lambda t: dens(t, q), 0.0, 15.0, limit=4000, points=[0.05, 0.2, 1.0, 3.0],
                               epsrel=1e-12)[0]
     assert abs(tot - 1.0) < 1e-9
+
+
+def test_one_tag_normalisations_add_up(oracle, F):
+    """N_+ + N_- = N over both tags, and so do the gradients; the two differ
+    (the tag-odd term is not zero at phi_s = 0.8 with Dm = 5)."""
+    m = oracle.Model("phis", 0.0, 15.0)
+    for th in (TH, TH2):
+        parts = []
+        for Q in (1.0, -1.0, 0.0):
+            tt = th.copy()
+            tt[15] = Q
+            parts.append(F.norm_grad(m, tt))
+        assert parts[0][0] + parts[1][0] == pytest.approx(parts[2][0], rel=1e-14)
+        np.testing.assert_allclose(parts[0][1] + parts[1][1], parts[2][1], rtol=1e-12, atol=1e-14)
+        assert abs(parts[0][0] - parts[1][0]) > 1e-4 * parts[2][0]
+
+
+@pytest.mark.parametrize("Dm", [17.77, 0.5])
+def test_complex_time_integral_matches_quadrature(oracle, F, Dm):
+    """I_c = int g(t - mu; Gamma - i Dm) dt against adaptive quadrature of the
+    convolution (both parts); its derivatives against central differences."""
+    from oracle import tagged
+    Gamma, sigma, mu, lo, hi = 0.66, 0.045, 0.01, 0.0, 15.0
+    z = complex(Gamma, -Dm)
+    got = F.time_norm_c_grad(z, sigma, mu, lo, hi)
+    edges = np.concatenate([[0.0, 0.05, 0.1, 0.2], np.arange(0.25, 15.0, 0.25), [15.0]])
+    for part in (np.real, np.imag):
+        ref = math.fsum(integrate.quad(lambda t: float(part(tagged.conv_c(t - mu, z, sigma)[0])), a, b,
+                                       limit=200, epsrel=1e-12, epsabs=1e-14)[0] for a, b in zip(edges[:-1], edges[1:]))
+        assert float(part(got[0])) == pytest.approx(ref, rel=1e-10, abs=1e-14)
+    h = 1e-5
+
+    def I(dz=0.0, ds=0.0, dmu=0.0):
+        return F.time_norm_c_grad(z + dz, sigma + ds, mu + dmu, lo, hi)[0]
+
+    assert abs((I(dz=h) - I(dz=-h)) / (2 * h) - got[1]) < 1e-8 * max(abs(got[1]), 1e-3)
+    assert abs((I(dz=1j * h) - I(dz=-1j * h)) / (2j * h) - got[1]) < 1e-8 * max(abs(got[1]), 1e-3)
+    hs = 1e-7
+    assert abs((I(ds=hs) - I(ds=-hs)) / (2 * hs) - got[2]) < 1e-6 * max(abs(got[2]), 1e-3)
+    assert abs((I(dmu=hs) - I(dmu=-hs)) / (2 * hs) - got[3]) < 1e-6 * max(abs(got[3]), 1e-3)
 
 
 @pytest.mark.parametrize("cp", ["even", "odd"])
@@ -124,6 +173,23 @@ def test_pure_p_wave_is_the_tagged_model(oracle, F, cp):
             got = float(F.pdf(m, ev, th) @ w)
             ref = float(tagged.pdf(mt, {"t": np.array([t]), "q": np.array([q])}, tt)[0])
             assert got == pytest.approx(ref, rel=1e-12), (cp, t, q)
+
+
+def test_csp_scales_the_s_p_interference(oracle, F):
+    """rate(C_SP) = rate(1) + (C_SP - 1) x (the three S-P interference terms),
+    the latter obtained as rate(1) - rate(0); the normalisation does not change."""
+    m = oracle.Model("phis", 0.0, 15.0)
+    rng = np.random.default_rng(4)
+    n = 300
+    ev = {"t": rng.uniform(0, 15, n), "ck": rng.uniform(-1, 1, n), "cl": rng.uniform(-1, 1, n),
+          "phi": rng.uniform(-math.pi, math.pi, n), "q": np.where(rng.uniform(size=n) < 0.5, 1.0, -1.0)}
+    r = {}
+    for csp in (0.0, 0.37, 1.0):
+        th = TH.copy()
+        th[14] = csp
+        r[csp] = F.rate(m, ev, th)
+        assert F.norm_grad(m, th)[0] == F.norm_grad(m, TH)[0]
+    np.testing.assert_allclose(r[0.37], r[0.0] + 0.37 * (r[1.0] - r[0.0]), rtol=1e-12, atol=1e-15)
 
 
 def test_half_mistag_is_tag_blind(oracle, F):
@@ -147,15 +213,21 @@ def test_gradient_matches_finite_differences(oracle, F):
           "phi": rng.uniform(-math.pi, math.pi, n), "q": np.where(rng.uniform(size=n) < 0.5, 1.0, -1.0),
           "w": rng.normal(1.0, 0.2, n)}
     ev["t"] = np.minimum(ev["t"], 14.9)
-    th = TH + np.array([0.01, 0.002, 0.001, 0.02, 0.01, -0.01, 0.05, -0.05, 0.01, 0.1, 0.01, 0.05, 0.05, 0.01])
-    f, g = F.nll_grad(m, ev, th)
+    base = TH + np.array([0.01, 0.002, 0.001, 0.02, 0.01, -0.01, 0.05, -0.05, 0.01, 0.1, 0.01, 0.05, 0.05, 0.01,
+                          0.03, 0.0])
+    for Q in (0.0, 1.0, -1.0):
+        th = base.copy()
+        th[15] = Q
+        e = ev if Q == 0.0 else dict(ev, q=np.full(n, Q))
+        f, g = F.nll_grad(m, e, th)
+        assert g[15] == 0.0
 
-    def nll(d, j):
-        tt = th.copy()
-        tt[j] += d
-        return F.nll(m, ev, tt)
+        def nll(d, j):
+            tt = th.copy()
+            tt[j] += d
+            return F.nll(m, e, tt)
 
-    for j in range(14):
-        h = 1e-5 * max(abs(th[j]), 1e-2)
-        fd = (8 * (nll(h, j) - nll(-h, j)) - (nll(2 * h, j) - nll(-2 * h, j))) / (12 * h)
-        assert abs(fd - g[j]) <= 1e-6 * max(abs(g[j]), 1.0), (j, fd, g[j])
+        for j in range(15):
+            h = 1e-5 * max(abs(th[j]), 1e-2)
+            fd = (8 * (nll(h, j) - nll(-h, j)) - (nll(2 * h, j) - nll(-2 * h, j))) / (12 * h)
+            assert abs(fd - g[j]) <= 1e-6 * max(abs(g[j]), 1.0), (Q, j, fd, g[j])
