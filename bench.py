@@ -750,13 +750,13 @@ TH_PHIS = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.08
 
 
 def run_phis(api, synth, torch, dev, flush, steps: int = 30) -> dict:
-    """The time-dependent angular model with tagging (14 parameters) on 1e6
+    """The time-dependent angular model with tagging (16 parameters) on 1e6
     synthetic events (t, angles, tag): NLL+grad per step with L2 flushed, the
     raw and the cached angular basis."""
     m = api.model_phis(0.0, 15.0)
     ev = {k: torch.tensor(v, device=dev) for k, v in synth.events_phis(1_000_000, 11).items()}
     theta = torch.tensor(TH_PHIS, device=dev)
-    out = torch.empty(15, dtype=torch.float64, device=dev)
+    out = torch.empty(1 + m.n_par, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     res = {"workload": "time-dependent angular model with tagging, 1e6 FP64 SoA events (t, 3 angles, q), "
                        "16 params, ipa_nll_grad", "events": 1_000_000}

@@ -41,6 +41,13 @@ def _ptr(x: torch.Tensor | None, dtype=torch.float64, name="tensor") -> int | No
     return x.data_ptr()
 
 
+def _need(x: torch.Tensor | None, n: int, name: str):
+    """Reject a buffer that holds fewer than n elements (the library writes or
+    reads n)."""
+    if x is not None and x.numel() < n:
+        raise IpaError(f"{name} holds {x.numel()} values, the call needs {n}")
+
+
 def _stream(stream) -> int:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
@@ -106,6 +113,8 @@ def ipa_angular_basis(model: C.ipa_model, ev: dict, stream=None) -> torch.Tensor
 def ipa_nll(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor | None = None,
             stream=None) -> torch.Tensor:
     out = torch.empty(1, dtype=torch.float64, device=theta.device) if out is None else out
+    _need(theta, model.n_par, "theta")
+    _need(out, 1, "out")
     e = ipa_events(ev)
     _check(_lib().ipa_nll(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
                           _ptr(out, name="out"), _stream(stream)), "ipa_nll")
@@ -115,6 +124,8 @@ def ipa_nll(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor
 def ipa_nll_grad(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
     out = torch.empty(1 + model.n_par, dtype=torch.float64, device=theta.device) if out is None else out
+    _need(theta, model.n_par, "theta")
+    _need(out, 1 + model.n_par, "out")
     e = ipa_events(ev)
     _check(_lib().ipa_nll_grad(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
                                _ptr(out, name="out"), _stream(stream)), "ipa_nll_grad")
@@ -125,6 +136,8 @@ def ipa_nll_grad_noalloc(model: C.ipa_model, ev: dict, theta: torch.Tensor, out:
                          stream=None) -> torch.Tensor:
     """ipa_nll_grad with the library's fixed scratch array: allocates nothing on the
     device (the caller passes `out`); at most IPA_NOALLOC_MAX_EVENTS events."""
+    _need(theta, model.n_par, "theta")
+    _need(out, 1 + model.n_par, "out")
     e = ipa_events(ev)
     _check(_lib().ipa_nll_grad_noalloc(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
                                        _ptr(out, name="out"), _stream(stream)), "ipa_nll_grad_noalloc")
@@ -136,6 +149,8 @@ def ipa_nll_grad_segmented(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, 
     n_seg = int(seg_off.numel()) - 1
     if out is None:
         out = torch.empty(n_seg, 1 + model.n_par, dtype=torch.float64, device=theta.device)
+    _need(theta, n_seg * model.n_par, "theta")
+    _need(out, n_seg * (1 + model.n_par), "out")
     e = ipa_events(ev)
     _check(_lib().ipa_nll_grad_segmented(ctypes.byref(model), ctypes.byref(e),
                                          _ptr(seg_off, torch.int64, "seg_off"), n_seg,
@@ -231,7 +246,9 @@ def ipa_nll_grad_joint(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, join
     if n_seg % joint.n_cat:
         raise ValueError("the segments are not a whole number of fits")
     n_fits = n_seg // joint.n_cat
-    theta = theta.reshape(n_fits, joint.n_joint)
+    _need(theta, n_fits * joint.n_joint, "theta")
+    if joint.map.shape[1] != model.n_par:
+        raise ValueError("the joint map has a column per model parameter")
     out = torch.empty(n_fits, 1 + joint.n_joint, dtype=torch.float64, device=theta.device)
     e, j = ipa_events(ev), joint.c_struct()
     _check(_lib().ipa_nll_grad_joint(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
@@ -249,6 +266,9 @@ def ipa_fit_joint(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, joint: Jo
     if n_seg % joint.n_cat or len(params) != joint.n_joint:
         raise ValueError("segments or parameters do not match the joint map")
     n_fits = n_seg // joint.n_cat
+    _need(theta, n_fits * joint.n_joint, "theta")
+    if joint.map.shape[1] != model.n_par:
+        raise ValueError("the joint map has a column per model parameter")
     dev = theta.device
     err = torch.zeros(n_fits, joint.n_joint, dtype=torch.float64, device=dev)
     nll = torch.zeros(n_fits, dtype=torch.float64, device=dev)

@@ -164,6 +164,10 @@ ipa_status launch_tag_nll(const ModelDev& m, bool grad, const Cols& cols, int64_
 ipa_status launch_tag_toygen(const ModelDev& m, const Consts* consts, uint64_t seed, int n_toys,
                              const int64_t* n_sig, const int64_t* n_bkg, const int64_t* offsets,
                              const ipa_event_buffers* out, cudaStream_t s);
+// phis.cu: the phi_s model's generator (a PhisConsts record in consts[0])
+ipa_status launch_phis_toygen(const ModelDev& m, const Consts* consts, uint64_t seed, int n_toys,
+                              const int64_t* n_sig, const int64_t* n_bkg, const int64_t* offsets,
+                              const ipa_event_buffers* out, cudaStream_t s);
 // nll.cu: seg_tiles[s] = sum_{r<s} ceil(size_r / kTile), s = 0..n_seg, with the
 // ranges clamped to [0, n]; segments with active[r] == 0 get no tiles (active may
 // be NULL).

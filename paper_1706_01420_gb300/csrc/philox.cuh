@@ -2,10 +2,14 @@
 // easy as 1, 2, 3", SC'11), written out here, and the 53-bit uniform built from
 // two of its words.  Every draw is a pure function of (counter, key), so the
 // generators address their random numbers by (index, toy, call) and the
-// result of a draw does not depend on which thread makes it.
+// result of a draw does not depend on which thread makes it.  Also the block
+// scan with which the accept-reject generators keep accepted candidates in
+// candidate order.
 #pragma once
 
 #include <stdint.h>
+
+#include "ipa_internal.cuh"
 
 namespace ipa {
 
@@ -41,6 +45,34 @@ __device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
 // Counter (idx lo32, idx hi32, toy, call) with key (k0, k1).
 __device__ __forceinline__ U4 draw(uint64_t idx, uint32_t toy, uint32_t call, uint32_t k0, uint32_t k1) {
     return philox(U4{(uint32_t)idx, (uint32_t)(idx >> 32), toy, call}, k0, k1);
+}
+
+// Exclusive scan of one int per thread over the block; returns the prefix and
+// writes the block total to *total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < kBlock / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        if (lane < kBlock / 32) warp_sums[lane] = s;   // inclusive warp prefix
+    }
+    __syncthreads();
+    const int before = wid ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[kBlock / 32 - 1];
+    __syncthreads();
+    return before + x - v;
 }
 
 }  // namespace ipa

@@ -31,6 +31,7 @@
 #include "fp64_math.cuh"
 #include "int_math.cuh"
 #include "ipa_internal.cuh"
+#include "philox.cuh"
 #include "tagged.cuh"
 #include "tile_reduce.cuh"
 
@@ -67,6 +68,8 @@ struct PhisConsts {
     double cw[6], sw[6];            // cos, sin of (dpe - dpa), dpa, dpe, (dpa - dS), (dpe - dS), dS
     double br[10], bi[10];          // Re, Im of b_k
     double csp;                     // C_SP: factor of the S-P interference terms k = 7, 8, 9
+    double qsel;                    // normalisation over both tags (0) or over the tag +1 / -1
+    double pad_;
 };
 
 // Row factor: C_SP for the S-P interference terms, 1 otherwise.
@@ -332,6 +335,8 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     c->cb = fb / V;
     for (int j = 0; j < IPA_NPAR_PHIS; ++j) c->dlnN[j] = dN[j] * inv_N;
     c->csp = th[IPA_PHIS_CSP];
+    c->qsel = qsel > 0.0 ? 1.0 : (qsel < 0.0 ? -1.0 : 0.0);
+    c->pad_ = 0.0;
 }
 
 __global__ void phis_consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg, Consts* __restrict__ out) {
@@ -674,7 +679,156 @@ ipa_status launch_phis_w(const Cols& cols, int64_t n, const int64_t* seg_begin, 
                                               st, cfg);
 }
 
+// ---- generator (Sec. 7, Example 5: accept-reject with counter-based draws) ----
+
+// M >= rate(t, Omega, q) on the range: every observed bilinear is bounded by
+// |b_k| (gL + gH + 2 |gc|) and each convolved exponential by M(x) = min(1,
+// e^{-x (t_lo - mu) + x^2 sigma^2 / 2}), so M = (M(Gamma_L) + M(Gamma_H) +
+// 2 M(Gamma)) sum_k max|f_k| |b_k| r_k (r_k = |C_SP| for the S-P terms).
+__device__ double phis_envelope(const PhisConsts& c, const ModelDev& m) {
+    using namespace cdetail;
+    const double sF = 1.0 - c.F, rFs = c.rF * c.rs;
+    const double mag[10] = {sF * c.x0, sF * c.xa, sF * c.xe, sF * c.ra * c.re, sF * c.r0 * c.ra, sF * c.r0 * c.re,
+                            c.F, rFs * c.ra, rFs * c.re, rFs * c.r0};
+    double ang = 0.0;
+    for (int k = 0; k < 10; ++k) ang += basis_max(k) * mag[k] * (k >= 7 ? fabs(c.csp) : 1.0);
+    const double lo = m.t_lo - c.mu;
+    const double ML = fmin(1.0, exp(-c.GL * lo + 0.5 * c.GL * c.GL * c.s2));
+    const double MH = fmin(1.0, exp(-c.GH * lo + 0.5 * c.GH * c.GH * c.s2));
+    const double MG = fmin(1.0, exp(-c.Gamma * lo + 0.5 * c.Gamma * c.Gamma * c.s2));
+    return (ML + MH + 2.0 * MG) * ang;
+}
+
+// rate(t, Omega, q) = sum_k f_k r_k sum_j C_kj G_j, G = (gL, gH, q Re gc, q Im gc),
+// with the exact convolutions (library exp, erfcx, the Faddeeva function).
+__device__ double phis_rate_exact(const PhisConsts& c, const MathTables* mt, double t, double ck, double cl,
+                                  double phi, double q) {
+    const double tau = t - c.mu;
+    double cr, ci;
+    conv2_complex(c, tau, &cr, &ci);
+    const double G[4] = {0.5 * conv2_real(c, tau, c.GL, c.uL0), 0.5 * conv2_real(c, tau, c.GH, c.uH0),
+                         0.5 * q * cr, 0.5 * q * ci};
+    double f[10];
+    basis_unscaled(ck, cl, phi, mt, f);
+    double r = 0.0;
+    for (int k = 0; k < 10; ++k) {
+        double row[4];
+        c_row(k, c.br[k], c.bi[k], 1.0, c.c, c.s, 1.0, c.D, row);
+        const double e = row[0] * G[0] + row[1] * G[1] + row[2] * G[2] + row[3] * G[3];
+        r += kBasisScale[k] * f[k] * row_scale(c, k) * e;
+    }
+    return r;
+}
+
+constexpr int kGenPerThread = 16;              // candidates per thread per chunk (bits of a mask)
+constexpr int kGenChunk = kBlock * kGenPerThread;
+
+// Signal candidate j of toy k: Philox calls (j, k, 0): t, u_acc; (j, k, 1): ck,
+// cl; (j, k, 2): phi; (j, k, 3): u_q; the tag is the selected one (Q = +-1) or
+// +1 for u_q <= 1/2, else -1; kept iff u_acc M < rate.  The toy takes the first
+// n_sig kept candidates in increasing j.  Background event i: (i, k, 4): t,
+// ck; (i, k, 5): cl, phi; (i, k, 6): u_q.  One block per toy.
+__global__ void __launch_bounds__(kBlock)
+phis_toygen_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, uint32_t k1, int n_toys,
+                   const int64_t* __restrict__ n_sig, const int64_t* __restrict__ n_bkg,
+                   const int64_t* __restrict__ offsets, int64_t capacity, double* __restrict__ ot,
+                   double* __restrict__ ock, double* __restrict__ ocl, double* __restrict__ ophi,
+                   double* __restrict__ oq) {
+    __shared__ __align__(16) PhisConsts c;
+    __shared__ MathTables mt;
+    __shared__ int warp_sums[kBlock / 32];
+    __shared__ double env;
+    {
+        const double* src = reinterpret_cast<const double*>(consts);
+        double* dst = reinterpret_cast<double*>(&c);
+        for (int i = threadIdx.x; i < kPhisDoubles; i += blockDim.x) dst[i] = src[i];
+    }
+    load_math_tables(&mt);
+    __syncthreads();
+    if (threadIdx.x == 0) env = phis_envelope(c, m);
+    __syncthreads();
+    const double M = env;
+    const double span = __dsub_rn(m.t_hi, m.t_lo);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const double Q = c.qsel;
+    auto tag = [&](double u) { return Q != 0.0 ? Q : (u <= 0.5 ? 1.0 : -1.0); };
+    auto angles = [&](const U4& b, const U4& d, double* ck, double* cl, double* ph) {
+        *ck = __dsub_rn(__dmul_rn(2.0, u01(b.x, b.y)), 1.0);
+        *cl = __dsub_rn(__dmul_rn(2.0, u01(b.z, b.w)), 1.0);
+        *ph = __dmul_rn(cdetail::kPi, __dsub_rn(__dmul_rn(2.0, u01(d.x, d.y)), 1.0));
+    };
+    for (int toy = blockIdx.x; toy < n_toys; toy += gridDim.x) {
+        const int64_t ns = n_sig[toy], nb = n_bkg[toy], off = offsets[toy];
+        if (ns < 0 || nb < 0 || off < 0 || off + ns + nb > capacity) continue;   // skipped
+        const bool usable = isfinite(M) && M > 0.0 && isfinite(c.N) && c.N > 0.0;
+        const uint64_t budget = usable ? (uint64_t)ns * 65536ull + (1ull << 22) : 0ull;
+        int64_t got = 0;
+        for (uint64_t j0 = 0; got < ns && j0 < budget; j0 += kGenChunk) {
+            const uint64_t jt = j0 + (uint64_t)threadIdx.x * kGenPerThread;
+            unsigned mask = 0;
+#pragma unroll 1
+            for (int i = 0; i < kGenPerThread; ++i) {
+                const uint64_t j = jt + i;
+                const U4 a = draw(j, (uint32_t)toy, 0u, k0, k1);
+                const U4 b = draw(j, (uint32_t)toy, 1u, k0, k1);
+                const U4 d = draw(j, (uint32_t)toy, 2u, k0, k1);
+                const double uq = Q != 0.0 ? 0.0 : u01(draw(j, (uint32_t)toy, 3u, k0, k1).x,
+                                                       draw(j, (uint32_t)toy, 3u, k0, k1).y);
+                const double t = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+                double ck, cl, ph;
+                angles(b, d, &ck, &cl, &ph);
+                if (__dmul_rn(u01(a.z, a.w), M) < phis_rate_exact(c, &mt, t, ck, cl, ph, tag(uq))) mask |= 1u << i;
+            }
+            int total;
+            const int before = block_exclusive_scan(__popc(mask), warp_sums, &total);
+            int rank = 0;
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int64_t pos = got + before + rank;
+                ++rank;
+                if (pos >= ns) break;
+                const uint64_t j = jt + i;
+                const U4 a = draw(j, (uint32_t)toy, 0u, k0, k1);
+                const U4 b = draw(j, (uint32_t)toy, 1u, k0, k1);
+                const U4 d = draw(j, (uint32_t)toy, 2u, k0, k1);
+                const U4 e = draw(j, (uint32_t)toy, 3u, k0, k1);
+                double ck, cl, ph;
+                angles(b, d, &ck, &cl, &ph);
+                ot[off + pos] = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+                ock[off + pos] = ck;
+                ocl[off + pos] = cl;
+                ophi[off + pos] = ph;
+                oq[off + pos] = tag(u01(e.x, e.y));
+            }
+            got += total;
+        }
+        for (int64_t pos = got + threadIdx.x; pos < ns; pos += blockDim.x)
+            ot[off + pos] = ock[off + pos] = ocl[off + pos] = ophi[off + pos] = oq[off + pos] = nan;
+        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+            const U4 a = draw((uint64_t)i, (uint32_t)toy, 4u, k0, k1);
+            const U4 b = draw((uint64_t)i, (uint32_t)toy, 5u, k0, k1);
+            const U4 e = draw((uint64_t)i, (uint32_t)toy, 6u, k0, k1);
+            const int64_t pos = off + ns + i;
+            ot[pos] = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+            ock[pos] = __dsub_rn(__dmul_rn(2.0, u01(a.z, a.w)), 1.0);
+            ocl[pos] = __dsub_rn(__dmul_rn(2.0, u01(b.x, b.y)), 1.0);
+            ophi[pos] = __dmul_rn(cdetail::kPi, __dsub_rn(__dmul_rn(2.0, u01(b.z, b.w)), 1.0));
+            oq[pos] = tag(u01(e.x, e.y));
+        }
+    }
+}
+
 }  // namespace
+
+ipa_status launch_phis_toygen(const ModelDev& m, const Consts* consts, uint64_t seed, int n_toys,
+                              const int64_t* n_sig, const int64_t* n_bkg, const int64_t* offsets,
+                              const ipa_event_buffers* out, cudaStream_t s) {
+    phis_toygen_kernel<<<n_toys, kBlock, 0, s>>>(m, consts, (uint32_t)seed, (uint32_t)(seed >> 32), n_toys, n_sig,
+                                                 n_bkg, offsets, out->capacity, out->t, out->ck, out->cl, out->phi,
+                                                 out->q);
+    return cuda_fail(cudaGetLastError(), "phi_s toygen kernel launch");
+}
 
 ipa_status launch_phis_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out, cudaStream_t st) {
     if (n_seg <= 0) return IPA_OK;

@@ -188,16 +188,39 @@ __device__ __forceinline__ TagSlow tag_slow(const C& c, double tau, const MathTa
     return s;
 }
 
-// 2 g(tau; x) for real x, exact form (library exp and erfcx).
-__device__ inline double conv2_real(const TagConsts& c, double tau, double x, double u0) {
+// 2 g(tau; x) for real x, exact form (library exp and erfcx).  C: TagConsts or
+// PhisConsts.
+template <class C>
+__device__ inline double conv2_real(const C& c, double tau, double x, double u0) {
     const double u = (u0 - tau) * c.k_z;
     const double Gx = exp(-(tau * tau) * c.k_g);
     if (u >= 0.0) return Gx * erfcx(u);
     return 2.0 * exp(-x * tau + 0.5 * x * x * c.s2) - Gx * erfcx(-u);
 }
 
+// 2 g(tau; Gamma - i Dm) (both parts), exact form.
+template <class C>
+__device__ inline void conv2_complex(const C& c, double tau, double* re, double* im) {
+    const double a = (c.uC0 - tau) * c.k_z;
+    const double Gx = exp(-(tau * tau) * c.k_g);
+    double wr, wi;
+    if (a >= 0.0) {
+        faddeeva_uhp(c.beta, a, &wr, &wi);
+        *re = Gx * wr;
+        *im = Gx * wi;
+        return;
+    }
+    faddeeva_uhp(-c.beta, -a, &wr, &wi);
+    const double m = 2.0 * exp(-c.Gamma * tau + 0.5 * (c.Gamma - c.Dm) * (c.Gamma + c.Dm) * c.s2);
+    double sn, cn;
+    sincos(c.Dm * tau - c.ph0, &sn, &cn);
+    *re = m * cn - Gx * wr;
+    *im = m * sn - Gx * wi;
+}
+
 // 2 Im g(tau; Gamma - i Dm), exact form.
-__device__ inline double conv2_imag(const TagConsts& c, double tau) {
+template <class C>
+__device__ inline double conv2_imag(const C& c, double tau) {
     const double a = (c.uC0 - tau) * c.k_z;
     const double Gx = exp(-(tau * tau) * c.k_g);
     double wr, wi;

@@ -159,33 +159,6 @@ __device__ __forceinline__ int angle_filter(const Filter32& f, const U4& b, cons
     return 0;
 }
 
-// Exclusive scan of one int per thread over the block; returns the prefix and
-// writes the block total to *total.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int s = lane < kBlock / 32 ? warp_sums[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, s, d);
-            if (lane >= d) s += y;
-        }
-        if (lane < kBlock / 32) warp_sums[lane] = s;   // inclusive warp prefix
-    }
-    __syncthreads();
-    const int before = wid ? warp_sums[wid - 1] : 0;
-    *total = warp_sums[kBlock / 32 - 1];
-    __syncthreads();
-    return before + x - v;
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(kBlock)
@@ -395,8 +368,9 @@ extern "C" ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev
         set_error("ipa_toygen: the 4D model needs ck, cl and phi output columns");
         return IPA_ERR_ARG;
     }
-    if (model->kind == IPA_MODEL_PHIS) {
-        set_error("ipa_toygen: no generator for the phi_s model");
+    const bool phis = model->kind == IPA_MODEL_PHIS;
+    if (phis && (!out->ck || !out->cl || !out->phi || !out->q)) {
+        set_error("ipa_toygen: the phi_s model needs ck, cl, phi and q output columns");
         return IPA_ERR_ARG;
     }
     const bool tag = model->kind == IPA_MODEL_TAGGED1D;
@@ -410,6 +384,7 @@ extern "C" ipa_status ipa_toygen(const ipa_model* model, const double* theta_dev
     const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
     if ((st = launch_consts(m, theta_dev, 1, sc->consts, s)) != IPA_OK) return st;
     if (tag) return launch_tag_toygen(m, sc->consts, seed, n_toys, n_sig_dev, n_bkg_dev, offsets_dev, out, s);
+    if (phis) return launch_phis_toygen(m, sc->consts, seed, n_toys, n_sig_dev, n_bkg_dev, offsets_dev, out, s);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int grid = n_toys;
     if (four)

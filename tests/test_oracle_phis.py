@@ -231,3 +231,37 @@ def test_gradient_matches_finite_differences(oracle, F):
             h = 1e-5 * max(abs(th[j]), 1e-2)
             fd = (8 * (nll(h, j) - nll(-h, j)) - (nll(2 * h, j) - nll(-2 * h, j))) / (12 * h)
             assert abs(fd - g[j]) <= 1e-6 * max(abs(g[j]), 1.0), (Q, j, fd, g[j])
+
+
+@pytest.mark.parametrize("Q", [0.0, 1.0])
+def test_envelope_bounds_the_rate(oracle, F, Q):
+    """u M < rate is a valid accept-reject test only if M >= rate everywhere: random
+    parameter points (C_SP up to 1.3) against 2e5 random (t, angles, tag)."""
+    m = oracle.Model("phis", 0.0, 15.0)
+    rng = np.random.default_rng(11)
+    for _ in range(15):
+        th = random_theta(rng)
+        th[1], th[2], th[14], th[15] = rng.uniform(0.02, 0.08), rng.uniform(-0.02, 0.02), rng.uniform(0, 1.3), Q
+        n = 200000
+        ev = {"t": np.concatenate([rng.uniform(0, 0.3, n // 2), rng.uniform(0, 15, n // 2)]),
+              "ck": rng.uniform(-1, 1, n), "cl": rng.uniform(-1, 1, n), "phi": rng.uniform(-math.pi, math.pi, n),
+              "q": np.where(rng.uniform(size=n) < 0.5, 1.0, -1.0)}
+        assert F.rate(m, ev, th).max() <= F.envelope(m, th)
+
+
+def test_toys_recover_the_parameters(oracle, F):
+    """Exact counts, the selected tag, and a fit of Gamma, phi_s and F_S to a
+    one-flavour toy lands within 4.5 sigma of the generating values."""
+    m = oracle.Model("phis", 0.0, 15.0)
+    th = TH.copy()
+    th[13], th[15] = 0.0, -1.0
+    toy = F.toy_one(m, th, 77, 3, 12000, 1000)
+    assert toy["t"].size == 13000 and np.all(toy["q"] == -1.0)
+    assert np.all((toy["t"] >= 0) & (toy["t"] <= 15)) and np.all(np.abs(toy["ck"]) <= 1)
+    free = [0, 8, 12]
+    r = oracle.fit_function(lambda x: F.nll_grad(m, toy, x), F.NPAR, th, free, tol=1e-8, max_iter=60)
+    assert r.status == "CONVERGED"
+    for j in free:
+        assert abs(r.theta[j] - th[j]) < 4.5 * r.err[j], (j, r.theta[j], th[j], r.err[j])
+    toy0 = F.toy_one(m, TH, 78, 0, 500, 20)
+    assert set(np.unique(toy0["q"])) == {-1.0, 1.0} and toy0["t"].size == 520
