@@ -18,7 +18,12 @@ Also reported on the same JSON line:
                 of the 4096-toy batch, batched toy fits vs one-fit-at-a-time;
   large / serve large weighted event sets, the fit server under load;
   tagged        the flavour-tagged model with B_s oscillation (1e6 events):
-                NLL+grad rate and roofline, generator, batched fits, CPU oracle.
+                NLL+grad rate and roofline, generator, batched fits, CPU oracle;
+  errors / cls  HESSE and MINOS of the toy batch; Example 4's CLs toys;
+  phis          the time-dependent angular model with tagging (1e6 events);
+  phis_joint    Example 2's twelve-category simultaneous fit at 1e4 and 1e7
+                events generated from the model: joint NLL+grad rate and the
+                whole fit's wall time.
 
 `--impl reference` times the CPU oracle on the same workload and metric.
 Multi-GPU (torchrun): every rank runs an independent replica (the path is one
@@ -634,6 +639,7 @@ def run_extras(api, synth, torch, dev, m, ev, theta, cal) -> dict:
     out["tagged"] = run_tagged(api, synth, torch, dev, cal, flush)
     out["cls"] = run_cls(api, torch, dev)
     out["phis"] = run_phis(api, synth, torch, dev, flush)
+    out["phis_joint"] = run_phis_joint(api, torch, dev, flush)
     return out
 
 
@@ -776,6 +782,109 @@ def run_phis(api, synth, torch, dev, flush, steps: int = 30) -> dict:
         ms = statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
         res["nll_grad_ms_" + name] = ms
         res["Gevents_per_s_" + name] = 1e6 / (ms * 1e-3) / 1e9
+    return res
+
+
+# Example 2's simultaneous fit: six m(KK) bins times two B flavours, the
+# physics parameters shared, F_S and delta_S per bin, C_SP per bin (synthetic
+# values of the usual size), each flavour normalised over its own tag; events
+# from the model's own generator (no background, perfect tagging, as the
+# paper's generated sample without experimental effects).
+CSP_BINS = (0.96, 0.93, 0.88, 0.90, 0.95, 0.97)
+TRUTH_JOINT = np.array([0.66, 0.52, 0.25, 3.2, 3.1, 0.085, 17.77, 0.8,
+                        0.02, 0.035, 0.05, 0.06, 0.04, 0.03, 1.2, 0.7, 0.2, -0.3, -0.8, -1.3])
+LO_JOINT = np.array([0.3, 0.35, 0.1, 0.0, 0.0, -0.5, 10.0, -3.1] + [1e-3] * 6 + [-3.2] * 6)
+HI_JOINT = np.array([1.5, 0.6, 0.35, 6.3, 6.3, 0.5, 25.0, 3.1] + [0.5] * 6 + [3.2] * 6)
+
+
+def joint_map_phis(n_bins: int = 6):
+    """Category 2 b + (q < 0): joint 0 Gamma, 1 A0sq, 2 Apesq, 3 delta_pa,
+    4 delta_pe, 5 DG, 6 Dm, 7 phi_s, 8.. F_S of each bin, 8 + n_bins.. delta_S;
+    sigma, mu, f_b, omega, C_SP and the tag selector constant."""
+    jmap, value = [], []
+    for b in range(n_bins):
+        for q in (1.0, -1.0):
+            jmap.append([0, -1, -1, -1, 1, 2, 3, 4, 8 + b, 8 + n_bins + b, 5, 6, 7, -1, -1, -1])
+            value.append([0, 0.045, 0.0, 0.0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0.0, CSP_BINS[b], q])
+    return jmap, value
+
+
+def joint_events(api, torch, dev, m, jmap, value, theta_joint, n_total: int, seed: int, sub: int = 8192):
+    """Events of every category (n_total / n_cat each), generated by ipa_toygen
+    in sub-toys of at most `sub` events (one block each), back to back; returns
+    the columns and the category offsets."""
+    n_cat = len(jmap)
+    per = n_total // n_cat
+    cols = {k: [] for k in ("t", "ck", "cl", "phi", "q")}
+    for c in range(n_cat):
+        th = np.array([theta_joint[jmap[c][p]] if jmap[c][p] >= 0 else value[c][p] for p in range(len(jmap[c]))])
+        k = max(1, -(-per // sub))
+        n_sig = np.full(k, per // k, dtype=np.int64)
+        n_sig[: per - int(n_sig.sum())] += 1
+        off = np.concatenate([[0], np.cumsum(n_sig)[:-1]]).astype(np.int64)
+        out = {name: torch.empty(per, dtype=torch.float64, device=dev) for name in cols}
+        d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
+        api.ipa_toygen(m, torch.tensor(th, device=dev), seed + 1000 * c, d64(n_sig), d64(np.zeros(k, np.int64)),
+                       d64(off), out)
+        for name in cols:
+            cols[name].append(out[name])
+    ev = {name: torch.cat(v) for name, v in cols.items()}
+    seg = torch.tensor(np.arange(n_cat + 1, dtype=np.int64) * per, device=dev)
+    return ev, seg
+
+
+def run_phis_joint(api, torch, dev, flush, sizes=(10_000, 10_000_000), steps: int = 20) -> dict:
+    """Example 2 (Table 2: 1e4 and 1e7 events): the twelve-category phi_s fit.
+    Per size: events from the model (ipa_toygen), the joint NLL+grad pass
+    (ipa_nll_grad_joint, L2 flushed, CUDA events) and the whole fit to
+    convergence (ipa_fit_joint, all 20 joint parameters free, started 2 % off
+    the truth), wall time on the host clock around the blocking call."""
+    m = api.model_phis(0.0, 15.0)
+    jmap, value = joint_map_phis()
+    joint = api.Joint(jmap, value)
+    stream = torch.cuda.current_stream()
+    res = {"workload": "phi_s model, 12 categories (6 m(KK) bins x 2 flavours), 20 joint parameters; "
+                       "events from the model (ipa_toygen), FP64"}
+    for n in sizes:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, seg = joint_events(api, torch, dev, m, jmap, value, TRUTH_JOINT, n, seed=31 + n)
+        torch.cuda.synchronize()
+        t_gen = time.perf_counter() - t0
+        n_ev = int(ev["t"].numel())
+        theta = torch.tensor(TRUTH_JOINT[None, :], device=dev)
+        for _ in range(3):
+            api.ipa_nll_grad_joint(m, ev, seg, joint, theta)
+        torch.cuda.synchronize()
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            a[i].record(stream)
+            api.ipa_nll_grad_joint(m, ev, seg, joint, theta)
+            b[i].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
+        start = TRUTH_JOINT * np.where(np.arange(TRUTH_JOINT.size) < 8, 1.02, 1.0)
+        params = [api.Param(float(start[j]), float(LO_JOINT[j]), float(HI_JOINT[j]),
+                            float((HI_JOINT[j] - LO_JOINT[j]) / 100)) for j in range(TRUTH_JOINT.size)]
+        fit_s = []
+        for rep in range(2):        # the first call captures the fit's graph
+            th = torch.tensor(start[None, :], device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = api.ipa_fit_joint(m, ev, seg, joint, params, th, max_iter=500, tol=1e-6)
+            torch.cuda.synchronize()
+            fit_s.append(time.perf_counter() - t0)
+        th_fit = r["theta"].cpu().numpy()[0]
+        err = r["err"].cpu().numpy()[0]
+        pulls = (th_fit - TRUTH_JOINT) / np.where(err > 0, err, np.inf)
+        res[f"events_{n}"] = {
+            "events": n_ev, "generate_s": t_gen, "nll_grad_ms": ms, "Gevents_per_s": n_ev / (ms * 1e-3) / 1e9,
+            "fit_wall_s": fit_s[1], "fit_wall_s_first_call": fit_s[0], "status": int(r["status"].item()),
+            "iterations": int(r["iters"].item()), "passes": int(r["passes"].item()),
+            "fit_Gevents_per_s": n_ev * int(r["passes"].item()) / fit_s[1] / 1e9,
+            "max_abs_pull": float(np.max(np.abs(pulls))), "phi_s": [float(th_fit[7]), float(err[7])]}
     return res
 
 

@@ -336,6 +336,16 @@ ipa_status ipa_hesse(const ipa_model* model, const ipa_events* ev, const int64_t
                      const ipa_param* spec, const double* theta_dev, double* cov_out_dev, double* corr_out_dev,
                      double* err_out_dev, int32_t* status_out_dev, void* stream);
 
+/* HESSE of simultaneous fits (Sec. 4, Example 2: the covariance and
+ * correlation matrix of the twelve-category fit): ipa_hesse over the joint
+ * parameters, each virtual point evaluated as in ipa_nll_grad_joint.
+ * Segments, joint map and spec (n_joint parameters) as in ipa_fit_joint;
+ * theta_dev n_fits x n_joint; outputs as in ipa_hesse with n_par = n_joint. */
+ipa_status ipa_hesse_joint(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                           int32_t n_fits, const ipa_joint* joint, const ipa_param* spec, const double* theta_dev,
+                           double* cov_out_dev, double* corr_out_dev, double* err_out_dev,
+                           int32_t* status_out_dev, void* stream);
+
 /* MINOS status of one side of one parameter's interval. */
 enum {
     IPA_MINOS_OK = 0,            /* |NLL_profile - NLL_min - up| < tol                   */

@@ -73,6 +73,8 @@ PROTOTYPES = {
     "ipa_fit_joint": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_joint),
                                 POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_int32, c_double, c_void_p]),
+    "ipa_hesse_joint": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_joint),
+                                  POINTER(ipa_param), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ipa_hesse": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),
                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ipa_minos": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),

@@ -303,6 +303,29 @@ def ipa_hesse(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[
     return {"cov": cov, "corr": corr, "err": err, "status": status}
 
 
+def ipa_hesse_joint(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, joint: Joint, params: list[Param],
+                    theta: torch.Tensor, stream=None) -> dict:
+    """Covariance, correlation matrix, errors and status of each simultaneous
+    fit at theta (n_fits x n_joint)."""
+    n_seg = int(seg_off.numel()) - 1
+    if n_seg % joint.n_cat or len(params) != joint.n_joint or joint.map.shape[1] != model.n_par:
+        raise ValueError("segments, parameters or map do not match the joint map")
+    n_fits = n_seg // joint.n_cat
+    P = joint.n_joint
+    _need(theta, n_fits * P, "theta")
+    dev = theta.device
+    cov = torch.empty(n_fits, P, P, dtype=torch.float64, device=dev)
+    corr = torch.empty(n_fits, P, P, dtype=torch.float64, device=dev)
+    err = torch.empty(n_fits, P, dtype=torch.float64, device=dev)
+    status = torch.empty(n_fits, dtype=torch.int32, device=dev)
+    e, j = ipa_events(ev), joint.c_struct()
+    _check(_lib().ipa_hesse_joint(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
+                                  n_fits, ctypes.byref(j), _spec(params), _ptr(theta, name="theta"),
+                                  _ptr(cov, name="cov"), _ptr(corr, name="corr"), _ptr(err, name="err"),
+                                  _ptr(status, torch.int32, "status"), _stream(stream)), "ipa_hesse_joint")
+    return {"cov": cov, "corr": corr, "err": err, "status": status}
+
+
 def ipa_minos(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[Param], theta_min: torch.Tensor,
               nll_min: torch.Tensor, cov: torch.Tensor, scan: list[int], up: float = 0.5, tol: float = 1e-7,
               max_rounds: int = 12, max_iter: int = 200, fit_tol: float = 1e-9, stream=None) -> dict:

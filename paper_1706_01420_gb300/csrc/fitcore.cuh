@@ -77,6 +77,8 @@ ipa_status launch_joint_scatter(const JointDev& j, int n_fits, const double* the
                                 cudaStream_t s);
 ipa_status launch_joint_gather(const JointDev& j, int n_fits, const int* active, double* res_joint,
                                cudaStream_t s);
+// joint.cu: host checks of a category map (IPA_ERR_ARG with the reason).
+ipa_status check_joint(const ipa_model* m, const ipa_joint* j, int n_fits);
 
 // fit.cu: run n_fits fits to the end.  Fit i minimises the NLL of events
 // [begin[i], end[i]) with specs[i * spec_stride] (device arrays the caller

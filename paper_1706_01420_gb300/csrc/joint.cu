@@ -133,7 +133,7 @@ ipa_status reserve(JointArgs& a, size_t map_n, size_t n_seg, size_t n_fits) {
 }
 
 // Host checks of the map; IPA_ERR_ARG with the reason.
-ipa_status check_joint(const ipa_model* m, const ipa_joint* j, int n_fits) {
+ipa_status check_joint_map(const ipa_model* m, const ipa_joint* j, int n_fits) {
     if (!j || j->n_cat < 1 || j->n_joint < 1 || j->n_joint > kMaxP || !j->map) {
         set_error("joint: need n_cat >= 1, 1 <= n_joint <= %d and a map", kMaxP);
         return IPA_ERR_ARG;
@@ -195,6 +195,8 @@ JointDev joint_dev(JointArgs& a, const ipa_model* m, const ipa_joint* j, const i
 }
 
 }  // namespace
+
+ipa_status check_joint(const ipa_model* m, const ipa_joint* j, int n_fits) { return check_joint_map(m, j, n_fits); }
 
 ipa_status launch_joint_scatter(const JointDev& j, int n_fits, const double* theta_joint, const int* active,
                                 cudaStream_t s) {

@@ -60,8 +60,10 @@ __global__ void hesse_points_kernel(const Spec* __restrict__ spp, int n_fits, co
         const bool one = hesse_onesided(sp, th, hf, a);
         out[p] = one ? th[p] + (second ? 2.0 : 1.0) * hf[a] : th[p] + (second ? -hf[a] : hf[a]);
     }
-    vbegin[v] = seg_off[f];
-    vend[v] = seg_off[f + 1];
+    if (seg_off) {      // (simultaneous fits take their categories' ranges instead)
+        vbegin[v] = seg_off[f];
+        vend[v] = seg_off[f + 1];
+    }
 }
 
 __global__ void hesse_first_steps_kernel(const Spec* __restrict__ spp, int n_fits, double* __restrict__ h) {
@@ -69,6 +71,17 @@ __global__ void hesse_first_steps_kernel(const Spec* __restrict__ spp, int n_fit
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n_fits) return;
     for (int a = 0; a < sp.n_free; ++a) h[(size_t)f * kMaxP + a] = 1e-3 * sp.step[sp.free_idx[a]];
+}
+
+// Simultaneous fits: category c of virtual point v (of fit v / nv) reads the
+// events of that fit's category c.
+__global__ void hesse_joint_ranges_kernel(const int64_t* __restrict__ seg_off, int n_v, int nv, int n_cat,
+                                          int64_t* __restrict__ jbegin, int64_t* __restrict__ jend) {
+    const int64_t vs = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vs >= (int64_t)n_v * n_cat) return;
+    const int64_t v = vs / n_cat, c = vs - v * n_cat, f = v / nv;
+    jbegin[vs] = seg_off[f * n_cat + c];
+    jend[vs] = seg_off[f * n_cat + c + 1];
 }
 
 // The Hessian of fit f from its virtual segments' gradients; stage 0 sets the
@@ -344,6 +357,13 @@ struct ProfileContext {
     int64_t *vbegin = nullptr, *vend = nullptr;
     double *vtheta = nullptr, *vres = nullptr;
     size_t cap_fit = 0, cap_v = 0;
+    // HESSE of simultaneous fits: the categories of every virtual point
+    int32_t* jmap = nullptr;
+    double* jvalue = nullptr;
+    int64_t *jbegin = nullptr, *jend = nullptr;
+    double *jtheta = nullptr, *jres = nullptr;
+    int* jactive = nullptr;
+    size_t cap_jmap = 0, cap_jseg = 0;
     // MINOS
     Probe* probes = nullptr;
     Spec* pspecs = nullptr;
@@ -397,6 +417,28 @@ ipa_status hesse_reserve(ProfileContext& c, size_t n_fits, size_t n_v, int P) {
     return st;
 }
 
+ipa_status joint_reserve(ProfileContext& c, size_t map_n, size_t n_seg) {
+    ipa_status st = IPA_OK;
+    if (map_n > c.cap_jmap) {
+        cudaDeviceSynchronize();
+        c.cap_jmap = 0;
+        st = grow(&c.jmap, map_n, "hesse joint map");
+        if (st == IPA_OK) st = grow(&c.jvalue, map_n, "hesse joint values");
+        if (st == IPA_OK) c.cap_jmap = map_n;
+    }
+    if (st == IPA_OK && n_seg > c.cap_jseg) {
+        cudaDeviceSynchronize();
+        c.cap_jseg = 0;
+        st = grow(&c.jbegin, n_seg, "hesse joint segments");
+        if (st == IPA_OK) st = grow(&c.jend, n_seg, "hesse joint segments");
+        if (st == IPA_OK) st = grow(&c.jtheta, n_seg * kMaxP, "hesse joint category points");
+        if (st == IPA_OK) st = grow(&c.jres, n_seg * (1 + kMaxP), "hesse joint category results");
+        if (st == IPA_OK) st = grow(&c.jactive, n_seg, "hesse joint category mask");
+        if (st == IPA_OK) c.cap_jseg = n_seg;
+    }
+    return st;
+}
+
 ipa_status minos_reserve(ProfileContext& c, size_t n_p) {
     if (n_p <= c.cap_p) return IPA_OK;
     cudaDeviceSynchronize();
@@ -438,6 +480,103 @@ ipa_status virtual_pass(const ipa_model* model, const ipa_events* ev, int n_v, c
     return launch_nll(m, grad, cols, ev->n, vbegin, vend, sc->seg_tiles, n_v, sc->consts, sc, out, s);
 }
 
+// The same for n_v points of simultaneous fits: every point's categories
+// (theta_J -> theta_c, NLL+gradient per category, fixed-order sums per point).
+ipa_status virtual_pass_joint(const ipa_model* model, const ipa_events* ev, const JointDev& jd, int n_v,
+                              const double* vtheta, int64_t tiles_bound, double* out, cudaStream_t s) {
+    const int n_seg = n_v * jd.n_cat;
+    Scratch* sc = nullptr;
+    ipa_status st = scratch_get(tiles_bound, n_seg + 1, &sc);
+    if (st != IPA_OK) return st;
+    const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
+    if ((st = launch_joint_scatter(jd, n_v, vtheta, nullptr, s)) != IPA_OK) return st;
+    if ((st = launch_seg_tiles(jd.seg_begin, jd.seg_end, nullptr, n_seg, ev->n, sc->seg_tiles, s)) != IPA_OK)
+        return st;
+    if ((st = launch_consts(m, jd.theta_seg, n_seg, sc->consts, s)) != IPA_OK) return st;
+    const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
+    if ((st = launch_nll(m, true, cols, ev->n, jd.seg_begin, jd.seg_end, sc->seg_tiles, n_seg, sc->consts, sc,
+                         jd.res_seg, s)) != IPA_OK)
+        return st;
+    return launch_joint_gather(jd, n_v, nullptr, out, s);
+}
+
+}  // namespace
+}  // namespace ipa
+
+namespace ipa {
+namespace {
+
+// HESSE of n_fits fits (joint: simultaneous fits over categories, P = n_joint).
+ipa_status hesse_run(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev, int32_t n_fits,
+                     const Spec& sp, const double* theta_dev, double* cov_out_dev, double* corr_out_dev,
+                     double* err_out_dev, int32_t* status_out_dev, cudaStream_t s, const ipa_joint* joint,
+                     const char* who) {
+    ProfileContext* cp = profile_context();
+    if (!cp) return IPA_ERR_CUDA;
+    ProfileContext& c = *cp;
+    std::lock_guard<std::mutex> lk(c.mu);
+    const int nv = 1 + 2 * sp.n_free;
+    const size_t n_v = (size_t)n_fits * nv;
+    const int n_cat = joint ? joint->n_cat : 1;
+    ipa_status st;
+    if ((st = profile_basics(c)) != IPA_OK) return st;
+    if ((st = hesse_reserve(c, (size_t)n_fits, n_v, model->n_par)) != IPA_OK) return st;
+    if (joint && (st = joint_reserve(c, (size_t)n_cat * model->n_par, n_v * n_cat)) != IPA_OK) return st;
+    if ((st = cuda_fail(cudaMemcpyAsync(c.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s), "hesse spec copy")) !=
+        IPA_OK)
+        return st;
+    JointDev jd;
+    if (joint) {
+        const size_t mn = (size_t)n_cat * model->n_par;
+        st = cuda_fail(cudaMemcpyAsync(c.jmap, joint->map, mn * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+                       "hesse joint map copy");
+        if (st == IPA_OK)
+            st = joint->value ? cuda_fail(cudaMemcpyAsync(c.jvalue, joint->value, mn * sizeof(double),
+                                                          cudaMemcpyHostToDevice, s), "hesse joint values copy")
+                              : cuda_fail(cudaMemsetAsync(c.jvalue, 0, mn * sizeof(double), s), "hesse joint values");
+        if (st != IPA_OK) return st;
+        const int64_t nj = (int64_t)n_v * n_cat;
+        hesse_joint_ranges_kernel<<<(unsigned)((nj + kHesseBlock - 1) / kHesseBlock), kHesseBlock, 0, s>>>(
+            seg_off_dev, (int)n_v, nv, n_cat, c.jbegin, c.jend);
+        if ((st = cuda_fail(cudaGetLastError(), "hesse joint ranges")) != IPA_OK) return st;
+        jd.n_cat = n_cat;
+        jd.n_model = model->n_par;
+        jd.n_joint = joint->n_joint;
+        jd.map = c.jmap;
+        jd.value = c.jvalue;
+        jd.seg_begin = c.jbegin;
+        jd.seg_end = c.jend;
+        jd.theta_seg = c.jtheta;
+        jd.res_seg = c.jres;
+        jd.seg_active = c.jactive;
+    }
+    const int64_t tiles = (int64_t)nv * ((ev->n + kTile - 1) / kTile + (int64_t)n_fits * n_cat);
+    const int gf = (n_fits + kHesseBlock - 1) / kHesseBlock, gv = (int)((n_v + kHesseBlock - 1) / kHesseBlock);
+    hesse_first_steps_kernel<<<gf, kHesseBlock, 0, s>>>(c.spec, n_fits, c.h);
+    // (joint: the points' event ranges are the categories', set above; the
+    // per-fit ranges the points kernel writes are not used)
+    const int64_t* fit_off = seg_off_dev;
+    for (int stage = 0; stage < 2 && st == IPA_OK; ++stage) {
+        hesse_points_kernel<<<gv, kHesseBlock, 0, s>>>(c.spec, n_fits, joint ? nullptr : fit_off, theta_dev, c.h,
+                                                       c.vbegin, c.vend, c.vtheta);
+        if ((st = cuda_fail(cudaGetLastError(), "hesse points")) != IPA_OK) break;
+        if (joint) {
+            st = virtual_pass_joint(model, ev, jd, (int)n_v, c.vtheta, tiles, c.vres, s);
+        } else {
+            st = virtual_pass(model, ev, (int)n_v, c.vbegin, c.vend, c.vtheta, tiles, true, c.vres, s);
+        }
+        if (st != IPA_OK) break;
+        hesse_assemble_kernel<<<gf, kHesseBlock, 0, s>>>(c.spec, n_fits, theta_dev, c.h, c.vres, stage, c.hwork,
+                                                         cov_out_dev, corr_out_dev, err_out_dev, status_out_dev);
+        st = cuda_fail(cudaGetLastError(), "hesse assemble");
+    }
+    // blocking: the library buffers are reused by the next call
+    ipa_status sy = cuda_fail(cudaStreamSynchronize(s), "hesse sync");
+    trace("{\"call\": \"%s\", \"n_fits\": %d, \"events\": %lld, \"segments\": %lld}", who, n_fits,
+          (long long)ev->n, (long long)(n_v * n_cat));
+    return st != IPA_OK ? st : sy;
+}
+
 }  // namespace
 }  // namespace ipa
 
@@ -453,36 +592,26 @@ extern "C" ipa_status ipa_hesse(const ipa_model* model, const ipa_events* ev, co
     }
     Spec sp{};
     if ((st = build_spec(model, spec, 1, 1.0, &sp)) != IPA_OK) return st;
-    ProfileContext* cp = profile_context();
-    if (!cp) return IPA_ERR_CUDA;
-    ProfileContext& c = *cp;
-    std::lock_guard<std::mutex> lk(c.mu);
-    const int nv = 1 + 2 * sp.n_free;
-    const size_t n_v = (size_t)n_fits * nv;
-    if ((st = profile_basics(c)) != IPA_OK) return st;
-    if ((st = hesse_reserve(c, (size_t)n_fits, n_v, model->n_par)) != IPA_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((st = cuda_fail(cudaMemcpyAsync(c.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s), "hesse spec copy")) !=
-        IPA_OK)
-        return st;
-    const int64_t tiles = (int64_t)nv * ((ev->n + kTile - 1) / kTile + n_fits);
-    const int gf = (n_fits + kHesseBlock - 1) / kHesseBlock, gv = (int)((n_v + kHesseBlock - 1) / kHesseBlock);
-    hesse_first_steps_kernel<<<gf, kHesseBlock, 0, s>>>(c.spec, n_fits, c.h);
-    for (int stage = 0; stage < 2 && st == IPA_OK; ++stage) {
-        hesse_points_kernel<<<gv, kHesseBlock, 0, s>>>(c.spec, n_fits, seg_off_dev, theta_dev, c.h, c.vbegin, c.vend,
-                                                       c.vtheta);
-        if ((st = cuda_fail(cudaGetLastError(), "hesse points")) != IPA_OK) break;
-        if ((st = virtual_pass(model, ev, (int)n_v, c.vbegin, c.vend, c.vtheta, tiles, true, c.vres, s)) != IPA_OK)
-            break;
-        hesse_assemble_kernel<<<gf, kHesseBlock, 0, s>>>(c.spec, n_fits, theta_dev, c.h, c.vres, stage, c.hwork,
-                                                         cov_out_dev, corr_out_dev, err_out_dev, status_out_dev);
-        st = cuda_fail(cudaGetLastError(), "hesse assemble");
+    return hesse_run(model, ev, seg_off_dev, n_fits, sp, theta_dev, cov_out_dev, corr_out_dev, err_out_dev,
+                     status_out_dev, static_cast<cudaStream_t>(stream), nullptr, "ipa_hesse");
+}
+
+extern "C" ipa_status ipa_hesse_joint(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                                      int32_t n_fits, const ipa_joint* joint, const ipa_param* spec,
+                                      const double* theta_dev, double* cov_out_dev, double* corr_out_dev,
+                                      double* err_out_dev, int32_t* status_out_dev, void* stream) {
+    using namespace ipa;
+    ipa_status st = check_common(model, ev, seg_off_dev, n_fits, spec, "ipa_hesse_joint");
+    if (st != IPA_OK) return st;
+    if ((st = check_joint(model, joint, n_fits)) != IPA_OK) return st;
+    if (!theta_dev || !cov_out_dev) {
+        set_error("ipa_hesse_joint: theta and the covariance output are required");
+        return IPA_ERR_ARG;
     }
-    // blocking: the library buffers are reused by the next call
-    ipa_status sy = cuda_fail(cudaStreamSynchronize(s), "hesse sync");
-    trace("{\"call\": \"ipa_hesse\", \"n_fits\": %d, \"events\": %lld, \"segments\": %lld}", n_fits,
-          (long long)ev->n, (long long)n_v);
-    return st != IPA_OK ? st : sy;
+    Spec sp{};
+    if ((st = build_spec(model, spec, 1, 1.0, &sp, joint->n_joint)) != IPA_OK) return st;
+    return hesse_run(model, ev, seg_off_dev, n_fits, sp, theta_dev, cov_out_dev, corr_out_dev, err_out_dev,
+                     status_out_dev, static_cast<cudaStream_t>(stream), joint, "ipa_hesse_joint");
 }
 
 extern "C" ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,

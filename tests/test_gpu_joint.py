@@ -11,7 +11,9 @@ ipa_fit_joint) against the oracle (oracle/joint.py).
   model parameters) of ipa_nll_grad_segmented at the categories' parameters;
 * joint fits within 1e-6 sigma of the oracle's joint fit (4D in four
   categories; the phi_s model in six one-flavour categories), errors within
-  1e-3, and a batch of joint fits bitwise equal to each fit alone.
+  1e-3, and a batch of joint fits bitwise equal to each fit alone;
+* HESSE of joint fits (ipa_hesse_joint): covariance in units of the errors
+  within 2e-3 of the inverse of the oracle's Hessian, errors within 1e-3.
 """
 import math
 
@@ -195,6 +197,21 @@ def test_joint_fit_4d_matches_oracle_and_batch_equals_solo(env):
         assert abs(batch["theta"][0, j] - ref.theta[j]) < 1e-6 * ref.err[j], (j, batch["theta"][0, j], ref.theta[j])
         assert batch["err"][0, j] == pytest.approx(ref.err[j], rel=1e-3)
     assert batch["nll"][0] == pytest.approx(ref.nll, rel=1e-12)
+    # HESSE of both joint fits at their minima: covariance and correlations
+    # against the inverse of the oracle's finite-difference Hessian
+    cols, off = _pack(fits)
+    hs = api.ipa_hesse_joint(m_g, G.to_dev(cols), torch.tensor(off, device="cuda"), api.Joint(jmap, value), params,
+                             torch.tensor(batch["theta"], device="cuda"))
+    hs = {k: v.cpu().numpy() for k, v in hs.items()}
+    assert list(hs["status"]) == [0, 0]
+    cov_ref = np.linalg.inv(ref.hess)
+    got = hs["cov"][0][np.ix_(free, free)]
+    sd = np.sqrt(np.diag(cov_ref))
+    np.testing.assert_allclose(got / np.outer(sd, sd), cov_ref / np.outer(sd, sd), atol=2e-3)
+    np.testing.assert_allclose(hs["err"][0][free], sd, rtol=1e-3)
+    fixed = [j for j in range(nj) if j not in free]
+    assert np.all(hs["cov"][0][fixed] == 0.0) and np.all(hs["err"][0][fixed] == 0.0)
+    np.testing.assert_allclose(np.diag(hs["corr"][0])[free], 1.0, rtol=1e-12)
 
 
 def _sample_one_tag(F, m, th, q, n, seed):

@@ -210,3 +210,26 @@ def test_fit_matches_oracle_and_batch_equals_solo(env):
         assert abs(batch["theta"][0, j] - ref.theta[j]) < 1e-6 * ref.err[j], (j, batch["theta"][0, j], ref.theta[j])
         assert batch["err"][0, j] == pytest.approx(ref.err[j], rel=1e-3)
     assert batch["nll"][0] == pytest.approx(ref.nll, rel=1e-12)
+
+
+@pytest.mark.parametrize("Q", [0.0, 1.0, -1.0])
+def test_toys_bit_exact(env, Q):
+    """The generator's streams equal the oracle's toy_one bit for bit (both tags
+    drawn, or one selected), including an empty toy and one without background."""
+    O, F, G, torch, api = env
+    m_o, m_g = O.Model("phis", 0.0, 15.0), api.model_phis(0.0, 15.0)
+    th = TH.copy()
+    th[15] = Q
+    n_sig = np.array([2000, 0, 700], dtype=np.int64)
+    n_bkg = np.array([200, 30, 0], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(n_sig + n_bkg)[:-1]])
+    cap = int((n_sig + n_bkg).sum())
+    out = {k: torch.empty(cap, dtype=torch.float64, device="cuda") for k in ("t", "ck", "cl", "phi", "q")}
+    dv = lambda a: torch.tensor(a, dtype=torch.int64, device="cuda")
+    api.ipa_toygen(m_g, torch.tensor(th, device="cuda"), 2024, dv(n_sig), dv(n_bkg), dv(off), out)
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    for k in range(3):
+        ref = F.toy_one(m_o, th, 2024, k, int(n_sig[k]), int(n_bkg[k]))
+        sl = slice(int(off[k]), int(off[k] + n_sig[k] + n_bkg[k]))
+        for col in ("t", "ck", "cl", "phi", "q"):
+            assert np.array_equal(got[col][sl], ref[col]), (k, col)
