@@ -377,6 +377,19 @@ ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t
                      int32_t max_iter, double fit_tol, double* lo_out_dev, double* hi_out_dev,
                      int32_t* status_out_dev, void* stream);
 
+/* MINOS of simultaneous fits: ipa_minos over the joint parameters, every
+ * constrained fit a simultaneous fit over the fit's categories (as in
+ * ipa_fit_joint).  Segments, joint map and spec (n_joint parameters) as in
+ * ipa_fit_joint; theta_min_dev n_fits x n_joint, cov_dev n_fits x n_joint x
+ * n_joint (ipa_hesse_joint), scan n_joint flags; outputs as in ipa_minos with
+ * n_par = n_joint. */
+ipa_status ipa_minos_joint(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                           int32_t n_fits, const ipa_joint* joint, const ipa_param* spec,
+                           const double* theta_min_dev, const double* nll_min_dev, const double* cov_dev,
+                           const int32_t* scan, double up, double tol, int32_t max_rounds, int32_t max_iter,
+                           double fit_tol, double* lo_out_dev, double* hi_out_dev, int32_t* status_out_dev,
+                           void* stream);
+
 /* ---- binned workloads (Example 4 "CLs" and the toolkit's generateBinned and
  * Gaussian smearing) ----
  *

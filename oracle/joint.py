@@ -65,3 +65,13 @@ def fit(model: O.Model, cats: list, jmap, value, theta0, free, lo=None, hi=None,
     Newton iteration (``ipa_oracle.fit``) applied to the joint function."""
     return O.fit_function(lambda th: nll_grad(model, cats, jmap, value, th), len(theta0), theta0, free, lo=lo,
                           hi=hi, tol=tol, max_iter=max_iter)
+
+
+def minos(model: O.Model, cats: list, jmap, value, theta_hat, nll_hat: float, free, j: int, sigma0: float,
+          up: float = 0.5, lo=None, hi=None, tol=1e-10):
+    """MINOS errors of joint parameter j (``profile.minos_function`` applied to
+    the joint NLL)."""
+    from . import profile
+    return profile.minos_function(lambda th: nll_grad(model, cats, jmap, value, th), len(theta_hat), theta_hat,
+                                  nll_hat, free, j, sigma0, up, lo, hi, tol)
+

@@ -51,12 +51,17 @@ def hesse(model: O.Model, ev: dict, theta, free):
 
 def profile(model: O.Model, ev: dict, theta_hat, free, j: int, x: float, lo=None, hi=None, tol=1e-10):
     """Profile NLL at theta_j = x and the constrained minimum."""
+    return profile_function(lambda th: O.nll_grad(model, ev, th), model.npar, theta_hat, free, j, x, lo, hi, tol)
+
+
+def profile_function(fn, n, theta_hat, free, j: int, x: float, lo=None, hi=None, tol=1e-10):
+    """The same for any fn(theta) -> (NLL, gradient) of n parameters."""
     th = np.asarray(theta_hat, dtype=np.float64).copy()
     th[j] = x
     others = [p for p in free if p != j]
     if not others:
-        return O.nll(model, ev, th), th
-    r = O.fit(model, ev, th, others, lo=lo, hi=hi, tol=tol, max_iter=100)
+        return fn(th)[0], th
+    r = O.fit_function(fn, n, th, others, lo=lo, hi=hi, tol=tol, max_iter=100)
     return r.nll, r.theta
 
 
@@ -65,14 +70,20 @@ def minos(model: O.Model, ev: dict, theta_hat, nll_hat: float, free, j: int, sig
     """MINOS errors (x_lo - theta_j, x_hi - theta_j) of parameter j and a
     status per side: "OK", or "LIMIT" when the profile stays below the
     threshold up to the parameter's limit (the error then reaches the limit)."""
+    return minos_function(lambda th: O.nll_grad(model, ev, th), model.npar, theta_hat, nll_hat, free, j, sigma0,
+                          up, lo, hi, tol)
+
+
+def minos_function(fn, n, theta_hat, nll_hat: float, free, j: int, sigma0: float, up: float = 0.5, lo=None,
+                   hi=None, tol=1e-10):
+    """The same for any fn(theta) -> (NLL, gradient) of n parameters."""
     theta_hat = np.asarray(theta_hat, dtype=np.float64)
-    n = model.npar
     lo = np.full(n, -np.inf) if lo is None else np.asarray(lo, dtype=np.float64)
     hi = np.full(n, np.inf) if hi is None else np.asarray(hi, dtype=np.float64)
     c = float(theta_hat[j])
 
     def excess(x):
-        return profile(model, ev, theta_hat, free, j, x, lo, hi, tol)[0] - nll_hat - up
+        return profile_function(fn, n, theta_hat, free, j, x, lo, hi, tol)[0] - nll_hat - up
 
     out, status = [0.0, 0.0], ["OK", "OK"]
     for k, side in enumerate((-1.0, 1.0)):

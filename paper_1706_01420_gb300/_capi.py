@@ -80,6 +80,9 @@ PROTOTYPES = {
     "ipa_minos": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_param),
                             c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_double, c_double, c_int32, c_int32,
                             c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ipa_minos_joint": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, POINTER(ipa_joint),
+                                  POINTER(ipa_param), c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_double,
+                                  c_double, c_int32, c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ipa_binned_generate": (c_int32, [c_void_p, c_int64, c_uint64, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
     "ipa_binned_smear": (c_int32, [c_void_p, c_int64, c_double, c_double, c_void_p, c_void_p]),
     "ipa_cls": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_uint64, c_void_p, c_void_p, c_void_p,

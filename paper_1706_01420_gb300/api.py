@@ -346,6 +346,33 @@ def ipa_minos(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[
     return {"lo": lo, "hi": hi, "status": status}
 
 
+def ipa_minos_joint(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, joint: Joint, params: list[Param],
+                    theta_min: torch.Tensor, nll_min: torch.Tensor, cov: torch.Tensor, scan: list[int],
+                    up: float = 0.5, tol: float = 1e-7, max_rounds: int = 12, max_iter: int = 200,
+                    fit_tol: float = 1e-9, stream=None) -> dict:
+    """MINOS intervals of the joint parameters in `scan` of simultaneous fits."""
+    n_seg = int(seg_off.numel()) - 1
+    if n_seg % joint.n_cat or len(params) != joint.n_joint or joint.map.shape[1] != model.n_par:
+        raise ValueError("segments, parameters or map do not match the joint map")
+    n_fits = n_seg // joint.n_cat
+    P = joint.n_joint
+    _need(theta_min, n_fits * P, "theta_min")
+    _need(nll_min, n_fits, "nll_min")
+    _need(cov, n_fits * P * P, "cov")
+    dev = theta_min.device
+    lo = torch.empty(n_fits, P, dtype=torch.float64, device=dev)
+    hi = torch.empty(n_fits, P, dtype=torch.float64, device=dev)
+    status = torch.empty(n_fits, P, 2, dtype=torch.int32, device=dev)
+    flags = (ctypes.c_int32 * P)(*[1 if p in scan else 0 for p in range(P)])
+    e, j = ipa_events(ev), joint.c_struct()
+    _check(_lib().ipa_minos_joint(ctypes.byref(model), ctypes.byref(e), _ptr(seg_off, torch.int64, "seg_off"),
+                                  n_fits, ctypes.byref(j), _spec(params), _ptr(theta_min, name="theta_min"),
+                                  _ptr(nll_min, name="nll_min"), _ptr(cov, name="cov"), flags, up, tol, max_rounds,
+                                  max_iter, fit_tol, _ptr(lo, name="lo"), _ptr(hi, name="hi"),
+                                  _ptr(status, torch.int32, "status"), _stream(stream)), "ipa_minos_joint")
+    return {"lo": lo, "hi": hi, "status": status}
+
+
 def ipa_binned_generate(lam: torch.Tensor, seed: int, n_toys: int, toy0: int = 0, hypothesis: int = 0,
                         stream=None) -> torch.Tensor:
     """(n_toys, n_bins) int32 Poisson counts of the bin means lam (generateBinned)."""

@@ -67,6 +67,7 @@ struct JointDev {
     double* theta_seg = nullptr;        // n_fits * n_cat x n_model
     double* res_seg = nullptr;          // n_fits * n_cat x (1 + n_model)
     int* seg_active = nullptr;          // n_fits * n_cat
+    bool grad = true;                   // false: NLL only (res_seg and the sums one double per entry)
 };
 
 // joint.cu: theta_seg (and seg_active = active[fit], or 1 without a mask) from

@@ -40,6 +40,12 @@ __global__ void joint_gather_kernel(JointDev j, int n_fits, const int* __restric
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_fits) return;
     if (active && !active[i]) return;
+    if (!j.grad) {
+        double f = 0.0;
+        for (int c = 0; c < j.n_cat; ++c) f += j.res_seg[(int64_t)i * j.n_cat + c];
+        res_joint[i] = f;
+        return;
+    }
     double g[kMaxP];
     for (int q = 0; q < j.n_joint; ++q) g[q] = 0.0;
     double f = 0.0;

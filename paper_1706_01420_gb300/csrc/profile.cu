@@ -213,11 +213,12 @@ __global__ void minos_init_kernel(const Spec* __restrict__ spp, const int* __res
 // conditional mean of the Gaussian approximation, clamped into the limits),
 // the fit's event range, or an empty range for a probe that is done.
 __global__ void minos_prepare_kernel(const Spec* __restrict__ spp, const int* __restrict__ scan, int n_scan,
-                                     int n_probes, const int64_t* __restrict__ seg_off,
+                                     int n_probes, const int64_t* __restrict__ seg_off, int n_cat,
                                      const double* __restrict__ theta_min, const double* __restrict__ cov,
                                      const Probe* __restrict__ probes, Spec* __restrict__ pspecs,
                                      int64_t* __restrict__ pbegin, int64_t* __restrict__ pend,
-                                     double* __restrict__ ptheta) {
+                                     double* __restrict__ ptheta, int64_t* __restrict__ jbegin,
+                                     int64_t* __restrict__ jend) {
     const Spec& sp = *spp;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_probes) return;
@@ -242,8 +243,16 @@ __global__ void minos_prepare_kernel(const Spec* __restrict__ spp, const int* __
         th[r] = fmin(fmax(v, sp.lo[r]), sp.hi[r]);
     }
     th[j] = q.x;
-    pbegin[p] = q.done ? 0 : seg_off[f];
-    pend[p] = q.done ? 0 : seg_off[f + 1];
+    // the fit's events (simultaneous fits: all its categories, and each
+    // category's range for the category pass)
+    pbegin[p] = q.done ? 0 : seg_off[(int64_t)f * n_cat];
+    pend[p] = q.done ? 0 : seg_off[(int64_t)(f + 1) * n_cat];
+    if (jbegin) {
+        for (int c = 0; c < n_cat; ++c) {
+            jbegin[(int64_t)p * n_cat + c] = q.done ? 0 : seg_off[(int64_t)f * n_cat + c];
+            jend[(int64_t)p * n_cat + c] = q.done ? 0 : seg_off[(int64_t)f * n_cat + c + 1];
+        }
+    }
 }
 
 // Move every probe that is not done: with d = NLL_profile(x) - NLL_min and
@@ -494,7 +503,7 @@ ipa_status virtual_pass_joint(const ipa_model* model, const ipa_events* ev, cons
         return st;
     if ((st = launch_consts(m, jd.theta_seg, n_seg, sc->consts, s)) != IPA_OK) return st;
     const Cols cols{ev->t, ev->ck, ev->cl, ev->phi, ev->w, ev->fk, ev->fk_stride, ev->q};
-    if ((st = launch_nll(m, true, cols, ev->n, jd.seg_begin, jd.seg_end, sc->seg_tiles, n_seg, sc->consts, sc,
+    if ((st = launch_nll(m, jd.grad, cols, ev->n, jd.seg_begin, jd.seg_end, sc->seg_tiles, n_seg, sc->consts, sc,
                          jd.res_seg, s)) != IPA_OK)
         return st;
     return launch_joint_gather(jd, n_v, nullptr, out, s);
@@ -614,31 +623,24 @@ extern "C" ipa_status ipa_hesse_joint(const ipa_model* model, const ipa_events* 
                      status_out_dev, static_cast<cudaStream_t>(stream), joint, "ipa_hesse_joint");
 }
 
-extern "C" ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
-                                int32_t n_fits, const ipa_param* spec, const double* theta_min_dev,
-                                const double* nll_min_dev, const double* cov_dev, const int32_t* scan, double up,
-                                double tol, int32_t max_rounds, int32_t max_iter, double fit_tol, double* lo_out_dev,
-                                double* hi_out_dev, int32_t* status_out_dev, void* stream) {
-    using namespace ipa;
-    ipa_status st = check_common(model, ev, seg_off_dev, n_fits, spec, "ipa_minos");
-    if (st != IPA_OK) return st;
-    if (!theta_min_dev || !nll_min_dev || !cov_dev || !scan || !lo_out_dev || !hi_out_dev || !(up > 0.0) ||
-        !(tol > 0.0) || max_rounds < 1 || max_iter < 1 || !(fit_tol > 0.0)) {
-        set_error("ipa_minos: bad arguments");
-        return IPA_ERR_ARG;
-    }
-    Spec sp{};
-    if ((st = build_spec(model, spec, max_iter, fit_tol, &sp)) != IPA_OK) return st;
+namespace ipa {
+namespace {
+
+ipa_status minos_run(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev, int32_t n_fits,
+                     const ipa_param* spec, const Spec& sp, int n_par, const double* theta_min_dev,
+                     const double* nll_min_dev, const double* cov_dev, const int32_t* scan, double up, double tol,
+                     int32_t max_rounds, int32_t max_iter, double* lo_out_dev, double* hi_out_dev,
+                     int32_t* status_out_dev, cudaStream_t s, const ipa_joint* joint, const char* who) {
+    ipa_status st = IPA_OK;
     int list[kMaxP], n_scan = 0;
-    for (int p = 0; p < model->n_par; ++p) {
+    for (int p = 0; p < n_par; ++p) {
         if (!scan[p]) continue;
         if (spec[p].fixed) {
-            set_error("ipa_minos: parameter %d is fixed and cannot be scanned", p);
+            set_error("%s: parameter %d is fixed and cannot be scanned", who, p);
             return IPA_ERR_ARG;
         }
         list[n_scan++] = p;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n_scan == 0) {
         // nothing to scan: zero intervals, every status "not scanned"
         ProfileContext* cp0 = profile_context();
@@ -659,29 +661,60 @@ extern "C" ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, co
     ProfileContext& c = *cp;
     std::lock_guard<std::mutex> lk(c.mu);
     const int n_probes = n_fits * n_scan * 2;
+    const int n_cat = joint ? joint->n_cat : 1;
     if ((st = profile_basics(c)) != IPA_OK) return st;
     if ((st = minos_reserve(c, (size_t)n_probes)) != IPA_OK) return st;
+    if (joint && (st = joint_reserve(c, (size_t)n_cat * model->n_par, (size_t)n_probes * n_cat)) != IPA_OK)
+        return st;
     if ((st = cuda_fail(cudaMemcpyAsync(c.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s), "minos spec")) != IPA_OK)
         return st;
     if ((st = cuda_fail(cudaMemcpyAsync(c.scan, list, sizeof(int) * n_scan, cudaMemcpyHostToDevice, s),
                         "minos scan list")) != IPA_OK)
         return st;
+    JointDev jd;
+    if (joint) {
+        const size_t mn = (size_t)n_cat * model->n_par;
+        st = cuda_fail(cudaMemcpyAsync(c.jmap, joint->map, mn * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+                       "minos joint map copy");
+        if (st == IPA_OK)
+            st = joint->value ? cuda_fail(cudaMemcpyAsync(c.jvalue, joint->value, mn * sizeof(double),
+                                                          cudaMemcpyHostToDevice, s), "minos joint values copy")
+                              : cuda_fail(cudaMemsetAsync(c.jvalue, 0, mn * sizeof(double), s), "minos joint values");
+        if (st != IPA_OK) return st;
+        jd.n_cat = n_cat;
+        jd.n_model = model->n_par;
+        jd.n_joint = joint->n_joint;
+        jd.map = c.jmap;
+        jd.value = c.jvalue;
+        jd.seg_begin = c.jbegin;
+        jd.seg_end = c.jend;
+        jd.theta_seg = c.jtheta;
+        jd.res_seg = c.jres;
+        jd.seg_active = c.jactive;
+    }
     const int gp = (n_probes + 127) / 128;
     minos_init_kernel<<<gp, 128, 0, s>>>(c.spec, c.scan, n_scan, n_probes, theta_min_dev, cov_dev, c.probes);
     if ((st = cuda_fail(cudaGetLastError(), "minos init")) != IPA_OK) return st;
-    const int64_t tiles = (int64_t)n_scan * 2 * ((ev->n + kTile - 1) / kTile + n_fits);
+    const int64_t tiles = (int64_t)n_scan * 2 * ((ev->n + kTile - 1) / kTile + (int64_t)n_fits * n_cat);
     const bool only_free = sp.n_free == 1;   // the profile is the NLL itself
     const int max_passes = 6 * max_iter + 4 * sp.n_free + 40;
     int rounds = 0;
     for (; rounds < max_rounds && st == IPA_OK; ++rounds) {
-        minos_prepare_kernel<<<gp, 128, 0, s>>>(c.spec, c.scan, n_scan, n_probes, seg_off_dev, theta_min_dev, cov_dev,
-                                                c.probes, c.pspecs, c.pbegin, c.pend, c.ptheta);
+        minos_prepare_kernel<<<gp, 128, 0, s>>>(c.spec, c.scan, n_scan, n_probes, seg_off_dev, n_cat, theta_min_dev,
+                                                cov_dev, c.probes, c.pspecs, c.pbegin, c.pend, c.ptheta,
+                                                joint ? c.jbegin : nullptr, joint ? c.jend : nullptr);
         if ((st = cuda_fail(cudaGetLastError(), "minos prepare")) != IPA_OK) break;
-        if (only_free) {
+        if (only_free && joint) {
+            jd.grad = false;
+            st = virtual_pass_joint(model, ev, jd, n_probes, c.ptheta, tiles, c.pnll, s);
+        } else if (only_free) {
             st = virtual_pass(model, ev, n_probes, c.pbegin, c.pend, c.ptheta, tiles, false, c.pnll, s);
         } else {
+            jd.grad = true;
             st = fit_run(model, ev, n_probes, c.pbegin, c.pend, c.pspecs, 1, max_passes, tiles, c.ptheta, nullptr,
-                         c.pnll, c.pstatus, nullptr, nullptr, s, "ipa_minos constrained fits");
+                         c.pnll, c.pstatus, nullptr, nullptr, s, joint ? "ipa_minos_joint constrained fits"
+                                                                       : "ipa_minos constrained fits",
+                         joint ? &jd : nullptr);
         }
         if (st != IPA_OK) break;
         if ((st = cuda_fail(cudaMemsetAsync(c.n_open, 0, sizeof(int), s), "minos counter")) != IPA_OK) break;
@@ -704,6 +737,51 @@ extern "C" ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, co
         st = cuda_fail(cudaGetLastError(), "minos final");
     }
     ipa_status sy = cuda_fail(cudaStreamSynchronize(s), "minos sync");
-    trace("{\"call\": \"ipa_minos\", \"n_fits\": %d, \"probes\": %d, \"rounds\": %d}", n_fits, n_probes, rounds);
+    trace("{\"call\": \"%s\", \"n_fits\": %d, \"probes\": %d, \"rounds\": %d}", who, n_fits, n_probes, rounds);
     return st != IPA_OK ? st : sy;
+}
+
+}  // namespace
+}  // namespace ipa
+
+extern "C" ipa_status ipa_minos(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                                int32_t n_fits, const ipa_param* spec, const double* theta_min_dev,
+                                const double* nll_min_dev, const double* cov_dev, const int32_t* scan, double up,
+                                double tol, int32_t max_rounds, int32_t max_iter, double fit_tol, double* lo_out_dev,
+                                double* hi_out_dev, int32_t* status_out_dev, void* stream) {
+    using namespace ipa;
+    ipa_status st = check_common(model, ev, seg_off_dev, n_fits, spec, "ipa_minos");
+    if (st != IPA_OK) return st;
+    if (!theta_min_dev || !nll_min_dev || !cov_dev || !scan || !lo_out_dev || !hi_out_dev || !(up > 0.0) ||
+        !(tol > 0.0) || max_rounds < 1 || max_iter < 1 || !(fit_tol > 0.0)) {
+        set_error("ipa_minos: bad arguments");
+        return IPA_ERR_ARG;
+    }
+    Spec sp{};
+    if ((st = build_spec(model, spec, max_iter, fit_tol, &sp)) != IPA_OK) return st;
+    return minos_run(model, ev, seg_off_dev, n_fits, spec, sp, model->n_par, theta_min_dev, nll_min_dev, cov_dev,
+                     scan, up, tol, max_rounds, max_iter, lo_out_dev, hi_out_dev, status_out_dev,
+                     static_cast<cudaStream_t>(stream), nullptr, "ipa_minos");
+}
+
+extern "C" ipa_status ipa_minos_joint(const ipa_model* model, const ipa_events* ev, const int64_t* seg_off_dev,
+                                      int32_t n_fits, const ipa_joint* joint, const ipa_param* spec,
+                                      const double* theta_min_dev, const double* nll_min_dev, const double* cov_dev,
+                                      const int32_t* scan, double up, double tol, int32_t max_rounds,
+                                      int32_t max_iter, double fit_tol, double* lo_out_dev, double* hi_out_dev,
+                                      int32_t* status_out_dev, void* stream) {
+    using namespace ipa;
+    ipa_status st = check_common(model, ev, seg_off_dev, n_fits, spec, "ipa_minos_joint");
+    if (st != IPA_OK) return st;
+    if ((st = check_joint(model, joint, n_fits)) != IPA_OK) return st;
+    if (!theta_min_dev || !nll_min_dev || !cov_dev || !scan || !lo_out_dev || !hi_out_dev || !(up > 0.0) ||
+        !(tol > 0.0) || max_rounds < 1 || max_iter < 1 || !(fit_tol > 0.0)) {
+        set_error("ipa_minos_joint: bad arguments");
+        return IPA_ERR_ARG;
+    }
+    Spec sp{};
+    if ((st = build_spec(model, spec, max_iter, fit_tol, &sp, joint->n_joint)) != IPA_OK) return st;
+    return minos_run(model, ev, seg_off_dev, n_fits, spec, sp, joint->n_joint, theta_min_dev, nll_min_dev, cov_dev,
+                     scan, up, tol, max_rounds, max_iter, lo_out_dev, hi_out_dev, status_out_dev,
+                     static_cast<cudaStream_t>(stream), joint, "ipa_minos_joint");
 }

@@ -78,3 +78,44 @@ def test_torch_optimiser_reaches_the_fit_minimum(env):
     opt.step(closure)
     got = theta_of(x).detach().cpu().numpy()
     assert np.all(np.abs(got[[0, 1, 3]] - ref[[0, 1, 3]]) < 1e-4 * err[[0, 1, 3]])
+
+
+def test_joint_backward_is_the_joint_gradient(env):
+    """Two simultaneous fits of three 1D categories (Gamma shared, f_b per
+    category): backward of a weighted sum of the fits' NLLs is each fit's joint
+    gradient times its weight, and a torch optimiser on the joint NLL reaches
+    ipa_fit_joint's minimum."""
+    G, torch, api, autograd = env
+    m = api.model_1d(0.3, 15.0)
+    jmap = [[0, -1, -1, 1], [0, -1, -1, 2], [0, -1, -1, 3]]
+    value = [[0.0, 0.045, 0.0, 0.0], [0.0, 0.05, 0.0, 0.0], [0.0, 0.04, 0.0, 0.0]]
+    joint = api.Joint(jmap, value)
+    cats = [synth.events_1d(3000 + 500 * c, 40 + c) for c in range(6)]
+    ev = G.to_dev({"t": np.concatenate(cats)})
+    off = torch.tensor(np.concatenate([[0], np.cumsum([c.size for c in cats])]), dtype=torch.int64, device="cuda")
+    th = torch.tensor([[0.66, 0.1, 0.12, 0.08], [0.6, 0.09, 0.1, 0.11]], dtype=torch.float64, device="cuda",
+                      requires_grad=True)
+    f = autograd.nll_joint(m, ev, off, joint, th)
+    (f * torch.tensor([2.0, -1.0], dtype=torch.float64, device="cuda")).sum().backward()
+    ref = api.ipa_nll_grad_joint(m, ev, off, joint, th.detach())
+    assert torch.equal(f.detach(), ref[:, 0])
+    assert torch.equal(th.grad[0], 2.0 * ref[0, 1:]) and torch.equal(th.grad[1], -1.0 * ref[1, 1:])
+    # an optimiser on fit 0 reaches the joint fit's minimum
+    x = torch.tensor([[0.7, 0.12, 0.12, 0.12]], dtype=torch.float64, device="cuda", requires_grad=True)
+    sub = off[:4].contiguous()
+    opt = torch.optim.LBFGS([x], lr=1.0, max_iter=200, tolerance_grad=1e-10, tolerance_change=1e-14,
+                            line_search_fn="strong_wolfe")
+
+    def closure():
+        opt.zero_grad()
+        v = autograd.nll_joint(m, ev, sub, joint, x).sum()
+        v.backward()
+        return v
+
+    for _ in range(5):
+        opt.step(closure)
+    params = [api.Param(v, 0.0, 2.0, 0.01) for v in (0.7, 0.12, 0.12, 0.12)]
+    r = api.ipa_fit_joint(m, ev, sub, joint, params, torch.tensor([[0.7, 0.12, 0.12, 0.12]], device="cuda"),
+                          max_iter=300, tol=1e-10)
+    err = r["err"][0]
+    assert torch.all((x.detach()[0] - r["theta"][0]).abs() < 1e-4 * err)

@@ -13,7 +13,9 @@ ipa_fit_joint) against the oracle (oracle/joint.py).
   categories; the phi_s model in six one-flavour categories), errors within
   1e-3, and a batch of joint fits bitwise equal to each fit alone;
 * HESSE of joint fits (ipa_hesse_joint): covariance in units of the errors
-  within 2e-3 of the inverse of the oracle's Hessian, errors within 1e-3.
+  within 2e-3 of the inverse of the oracle's Hessian, errors within 1e-3;
+  MINOS of joint fits (ipa_minos_joint) within 1e-5 sigma of the oracle's
+  profile-likelihood roots (a shared and a per-category parameter).
 """
 import math
 
@@ -212,6 +214,43 @@ def test_joint_fit_4d_matches_oracle_and_batch_equals_solo(env):
     fixed = [j for j in range(nj) if j not in free]
     assert np.all(hs["cov"][0][fixed] == 0.0) and np.all(hs["err"][0][fixed] == 0.0)
     np.testing.assert_allclose(np.diag(hs["corr"][0])[free], 1.0, rtol=1e-12)
+
+
+def test_joint_minos_matches_the_oracle_profile(env):
+    """Three 1D categories: Gamma shared, f_b per category, sigma and mu
+    constants.  GPU fit, HESSE and MINOS of Gamma and one f_b against the
+    oracle's profile-likelihood roots of the joint NLL at the GPU minimum."""
+    O, J, F, G, torch, api = env
+    m_o, m_g = O.Model("1d", 0.3, 15.0), api.model_1d(0.3, 15.0)
+    jmap = [[0, -1, -1, 1], [0, -1, -1, 2], [0, -1, -1, 3]]
+    value = [[0.0, 0.045, 0.0, 0.0], [0.0, 0.05, 0.01, 0.0], [0.0, 0.04, -0.01, 0.0]]
+    truth = np.array([0.66, 0.1, 0.2, 0.05])
+    cats = []
+    for c in range(3):
+        thc = J.category_thetas(jmap, value, truth)[c]
+        n_b = int(4000 * thc[3] / (1 - thc[3]))
+        cats.append({"t": O.toygen(m_o, thc, 900 + c, [4000], [n_b])[0]["t"]})
+    lo, hi = np.array([0.2, 0.0, 0.0, 0.0]), np.array([2.0, 0.6, 0.6, 0.6])
+    params = [api.Param(float(truth[j]), float(lo[j]), float(hi[j]), 0.01) for j in range(4)]
+    joint = api.Joint(jmap, value)
+    cols, off = _pack([cats])
+    ev, offd = G.to_dev(cols), torch.tensor(off, device="cuda")
+    r = api.ipa_fit_joint(m_g, ev, offd, joint, params, torch.tensor(truth[None, :], device="cuda"), max_iter=300,
+                          tol=1e-10)
+    assert int(r["status"][0]) == 0
+    hs = api.ipa_hesse_joint(m_g, ev, offd, joint, params, r["theta"])
+    scan = [0, 2]
+    mn = api.ipa_minos_joint(m_g, ev, offd, joint, params, r["theta"], r["nll"], hs["cov"], scan)
+    mn = {k: v.cpu().numpy()[0] for k, v in mn.items()}
+    th_min, nll_min = r["theta"].cpu().numpy()[0], float(r["nll"].cpu()[0])
+    err = hs["err"].cpu().numpy()[0]
+    for j in scan:
+        (elo, ehi), st = J.minos(m_o, cats, jmap, value, th_min, nll_min, [0, 1, 2, 3], j, float(err[j]), lo=lo,
+                                 hi=hi)
+        assert st == ("OK", "OK") and tuple(mn["status"][j]) == (0, 0), (j, mn["status"][j])
+        assert abs(mn["lo"][j] - elo) < 1e-5 * err[j], (j, mn["lo"][j], elo)
+        assert abs(mn["hi"][j] - ehi) < 1e-5 * err[j], (j, mn["hi"][j], ehi)
+    assert tuple(mn["status"][1]) == (5, 5)          # not scanned
 
 
 def _sample_one_tag(F, m, th, q, n, seed):
