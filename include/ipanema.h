@@ -241,14 +241,18 @@ ipa_status ipa_angular_basis(const ipa_model* model, const ipa_events* ev, doubl
  * |(1 - 2 omega) s| M(Gamma) with M(x) = min(1, e^{-x (t_lo - mu) + x^2
  * sigma^2 / 2}); background event i takes t and q from call 4; out->t and
  * out->q are written.
- * phi_s model: candidate j draws (t, u) from call 0, (ck, cl) from call 1,
- * phi from call 2 and u_q from call 3; its tag is the one the normalisation
- * selector names (theta[IPA_PHIS_QNORM] = +-1), else +1 if u_q <= 1/2 and -1
- * otherwise; it is kept iff u M < rate(t, Omega, q) with M = (M(Gamma_L) +
- * M(Gamma_H) + 2 M(Gamma)) sum_k max|f_k| |b_k| r_k (|b_k| the magnitude of the
- * term's amplitude product, r_k = |C_SP| for the S-P terms, else 1).
- * Background event i: t, ck from call 4, cl, phi from call 5, u_q from call 6.
- * All five columns are written.
+ * phi_s model: the proposal is piecewise uniform in t over 64 equal bins
+ * (left edges e_i = t_lo + i w) with weights B_i = (m(Gamma_L) + m(Gamma_H) +
+ * 2 m(Gamma)) sum_k max|f_k| |b_k| r_k, m(x) = min(1, e^{-x (e_i - mu) + x^2
+ * sigma^2 / 2}) (|b_k| the magnitude of the term's amplitude product, r_k =
+ * |C_SP| for the S-P terms, else 1), a bound of the rate on the bin.
+ * Candidate j draws (u_bin, u) from call 0, (ck, cl) from call 1, (phi, u_pos)
+ * from call 2 and u_q from call 3; its bin is the first i with u_bin C_64 <=
+ * C_{i+1} (C the running sums of B), t = min(e_i + u_pos w, t_hi); its tag is
+ * the one the normalisation selector names (theta[IPA_PHIS_QNORM] = +-1),
+ * else +1 if u_q <= 1/2 and -1 otherwise; it is kept iff u B_i < rate(t,
+ * Omega, q).  Background event i: t, ck from call 4, cl, phi from call 5,
+ * u_q from call 6.  All five columns are written.
  * Candidates are built with IEEE-exact operations only, so a stream is
  * reproducible bit for bit.  n_sig, n_bkg, offsets: n_toys int64 each
  * (device).  For 1D only out->t is written.  A toy with a negative count or

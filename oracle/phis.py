@@ -314,42 +314,58 @@ def nll_grad(model: O.Model, ev: dict, theta):
 # Philox draws), with the model's own envelope
 # --------------------------------------------------------------------------
 
-def envelope(model: O.Model, theta) -> float:
-    """M >= rate(t, Omega, q) on the range.  Each observed bilinear is a convex
+GEN_BINS = 64       # decay-time bins of the generator's envelope
+
+
+def envelope_bins(model: O.Model, theta):
+    """The generator's envelope, piecewise constant in t: (w, edges, B, C) with
+    bin width w = (t_hi - t_lo) / 64, left edges e_i = t_lo + i w, bounds
+    B_i >= rate(t, Omega, q) for t in bin i, and C the running sums of B
+    (C_0 = 0, C_{i+1} = C_i + B_i, in order).  Each observed bilinear is a convex
     mix of b (PP +- ...) terms with |PP|, |MM|, |PM|, |MP| <= (gL + gH + 2 |gc|) / 4
-    (|gc| <= g(tau; Gamma)), so |term k| <= |b_k| (gL + gH + 2 |gc|); the
-    convolved exponentials are bounded by M(x) = min(1, e^{-x (t_lo - mu) + x^2
-    sigma^2 / 2}), so M = (M(Gamma_L) + M(Gamma_H) + 2 M(Gamma))
-    sum_k max|f_k| |b_k| r_k, r_k = |C_SP| for the S-P terms, else 1."""
+    (|gc| <= g(tau; Gamma)), so |term k| <= |b_k| (gL + gH + 2 |gc|); a convolved
+    exponential g(tau; x) decreases in tau and is at most min(1, e^{-x tau +
+    x^2 sigma^2 / 2}), taken at the bin's left edge: B_i = (m(Gamma_L) +
+    m(Gamma_H) + 2 m(Gamma)) sum_k max|f_k| |b_k| r_k (r_k = |C_SP| for the S-P
+    terms, else 1)."""
     theta = np.asarray(theta, dtype=np.float64)
     Gamma, sigma, mu = (float(theta[i]) for i in range(3))
     DG = float(theta[10])
     GL, GH = Gamma + 0.5 * DG, Gamma - 0.5 * DG
-
-    def M(x):
-        return min(1.0, math.exp(-x * (model.t_lo - mu) + 0.5 * x * x * sigma * sigma))
-
     A, _ = amplitudes(theta, grad=False)
     ang = 0.0
     for k, (i, j, _) in enumerate(PAIRS):
         r = abs(float(theta[14])) if k in SP_TERMS else 1.0
         ang += O.ANGULAR_MAX[k] * abs(A[i]) * abs(A[j]) * r
-    return (M(GL) + M(GH) + 2.0 * M(Gamma)) * ang
+    w = (model.t_hi - model.t_lo) / GEN_BINS
+    edges = np.array([model.t_lo + i * w for i in range(GEN_BINS)])
+
+    def m(x, e):
+        return min(1.0, math.exp(-x * (e - mu) + 0.5 * x * x * sigma * sigma))
+
+    B = np.array([(m(GL, e) + m(GH, e) + 2.0 * m(Gamma, e)) * ang for e in edges])
+    C = np.zeros(GEN_BINS + 1)
+    for i in range(GEN_BINS):
+        C[i + 1] = C[i] + B[i]
+    return w, edges, B, C
 
 
 def toy_one(model: O.Model, theta, seed: int, toy: int, n_sig: int, n_bkg: int, chunk: int = 1 << 16) -> dict:
-    """One pseudo-experiment of the phi_s model: signal candidate j of toy k draws
-    Philox calls (j_lo, j_hi, k, c):
-      c = 0: t = t_lo + u (t_hi - t_lo), u_acc;   c = 1: ck = 2u - 1, cl = 2u - 1;
-      c = 2: phi = pi (2u - 1), unused;           c = 3: u_q, unused;
-    q = the selected tag when the normalisation selector Q is +-1, else +1 if
-    u_q <= 1/2 and -1 otherwise; kept iff u_acc M < rate(t, Omega, q); the toy
-    takes the first n_sig kept candidates in increasing j.  Background event i
-    uses (i_lo, i_hi, k, 4): t, ck; (.., 5): cl, phi; (.., 6): u_q (the tag as
-    for the signal)."""
+    """One pseudo-experiment of the phi_s model (Sec. 7 accept-reject with
+    counters, the proposal piecewise uniform in t with the envelope's bin
+    bounds as weights).  Signal candidate j of toy k draws Philox calls
+    (j_lo, j_hi, k, c):
+      c = 0: u_bin, u_acc;   c = 1: ck = 2u - 1, cl = 2u - 1;
+      c = 2: phi = pi (2u - 1), u_pos;   c = 3: u_q, unused;
+    its bin is the first i with u_bin C_64 <= C_{i+1}, t = min(e_i + u_pos w,
+    t_hi); q = the selected tag when the normalisation selector Q is +-1, else
+    +1 if u_q <= 1/2 and -1 otherwise; kept iff u_acc B_i < rate(t, Omega, q);
+    the toy takes the first n_sig kept candidates in increasing j.  Background
+    event i uses (i_lo, i_hi, k, 4): t = t_lo + u (t_hi - t_lo), ck; (.., 5): cl,
+    phi; (.., 6): u_q (the tag as for the signal)."""
     theta = np.asarray(theta, dtype=np.float64)
     span = model.t_hi - model.t_lo
-    M = envelope(model, theta)
+    w, edges, B, C = envelope_bins(model, theta)
     Q = _tag_of(theta)
 
     def tag(u):
@@ -362,11 +378,12 @@ def toy_one(model: O.Model, theta, seed: int, toy: int, n_sig: int, n_bkg: int, 
         x = O._philox_call(j, toy, 0, seed)
         y = O._philox_call(j, toy, 1, seed)
         z = O._philox_call(j, toy, 2, seed)
-        w = O._philox_call(j, toy, 3, seed)
-        ev = {"t": model.t_lo + O.u01(x[0], x[1]) * span,
+        v = O._philox_call(j, toy, 3, seed)
+        b = np.searchsorted(C[1:], O.u01(x[0], x[1]) * C[-1], side="left")
+        ev = {"t": np.minimum(edges[b] + O.u01(z[2], z[3]) * w, model.t_hi),
               "ck": 2.0 * O.u01(y[0], y[1]) - 1.0, "cl": 2.0 * O.u01(y[2], y[3]) - 1.0,
-              "phi": math.pi * (2.0 * O.u01(z[0], z[1]) - 1.0), "q": tag(O.u01(w[0], w[1]))}
-        keep = O.u01(x[2], x[3]) * M < rate(model, ev, theta)
+              "phi": math.pi * (2.0 * O.u01(z[0], z[1]) - 1.0), "q": tag(O.u01(v[0], v[1]))}
+        keep = O.u01(x[2], x[3]) * B[b] < rate(model, ev, theta)
         idx = np.nonzero(keep)[0][: n_sig - got]
         for k in cols:
             cols[k].append(ev[k][idx])
@@ -376,11 +393,10 @@ def toy_one(model: O.Model, theta, seed: int, toy: int, n_sig: int, n_bkg: int, 
         i = np.arange(n_bkg, dtype=np.uint64)
         x = O._philox_call(i, toy, 4, seed)
         y = O._philox_call(i, toy, 5, seed)
-        w = O._philox_call(i, toy, 6, seed)
+        v = O._philox_call(i, toy, 6, seed)
         cols["t"].append(model.t_lo + O.u01(x[0], x[1]) * span)
         cols["ck"].append(2.0 * O.u01(x[2], x[3]) - 1.0)
         cols["cl"].append(2.0 * O.u01(y[0], y[1]) - 1.0)
         cols["phi"].append(math.pi * (2.0 * O.u01(y[2], y[3]) - 1.0))
-        cols["q"].append(tag(O.u01(w[0], w[1])))
+        cols["q"].append(tag(O.u01(v[0], v[1])))
     return {k: (np.concatenate(v) if v else np.zeros(0)) for k, v in cols.items()}
-

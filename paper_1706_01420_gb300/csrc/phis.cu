@@ -681,22 +681,31 @@ ipa_status launch_phis_w(const Cols& cols, int64_t n, const int64_t* seg_begin, 
 
 // ---- generator (Sec. 7, Example 5: accept-reject with counter-based draws) ----
 
-// M >= rate(t, Omega, q) on the range: every observed bilinear is bounded by
-// |b_k| (gL + gH + 2 |gc|) and each convolved exponential by M(x) = min(1,
-// e^{-x (t_lo - mu) + x^2 sigma^2 / 2}), so M = (M(Gamma_L) + M(Gamma_H) +
-// 2 M(Gamma)) sum_k max|f_k| |b_k| r_k (r_k = |C_SP| for the S-P terms).
-__device__ double phis_envelope(const PhisConsts& c, const ModelDev& m) {
+constexpr int kGenBins = 64;    // decay-time bins of the generator's envelope
+
+// The envelope, piecewise constant in t: bin i = [e_i, e_i + w), e_i = t_lo +
+// i w, w = (t_hi - t_lo) / 64, bound B_i >= rate there.  Every observed
+// bilinear is at most |b_k| (gL + gH + 2 |gc|) and a convolved exponential
+// g(tau; x) decreases in tau and is at most min(1, e^{-x tau + x^2 sigma^2 /
+// 2}), taken at the left edge: B_i = (m(Gamma_L) + m(Gamma_H) + 2 m(Gamma))
+// sum_k max|f_k| |b_k| r_k (r_k = |C_SP| for the S-P terms).  C: running sums of
+// B in order (C_0 = 0), the proposal's cumulative weights.  One thread.
+__device__ void phis_envelope_bins(const PhisConsts& c, const ModelDev& m, double w, double* B, double* C) {
     using namespace cdetail;
     const double sF = 1.0 - c.F, rFs = c.rF * c.rs;
     const double mag[10] = {sF * c.x0, sF * c.xa, sF * c.xe, sF * c.ra * c.re, sF * c.r0 * c.ra, sF * c.r0 * c.re,
                             c.F, rFs * c.ra, rFs * c.re, rFs * c.r0};
     double ang = 0.0;
     for (int k = 0; k < 10; ++k) ang += basis_max(k) * mag[k] * (k >= 7 ? fabs(c.csp) : 1.0);
-    const double lo = m.t_lo - c.mu;
-    const double ML = fmin(1.0, exp(-c.GL * lo + 0.5 * c.GL * c.GL * c.s2));
-    const double MH = fmin(1.0, exp(-c.GH * lo + 0.5 * c.GH * c.GH * c.s2));
-    const double MG = fmin(1.0, exp(-c.Gamma * lo + 0.5 * c.Gamma * c.Gamma * c.s2));
-    return (ML + MH + 2.0 * MG) * ang;
+    C[0] = 0.0;
+    for (int i = 0; i < kGenBins; ++i) {
+        const double e = __dadd_rn(m.t_lo, __dmul_rn((double)i, w)) - c.mu;
+        const double ML = fmin(1.0, exp(-c.GL * e + 0.5 * c.GL * c.GL * c.s2));
+        const double MH = fmin(1.0, exp(-c.GH * e + 0.5 * c.GH * c.GH * c.s2));
+        const double MG = fmin(1.0, exp(-c.Gamma * e + 0.5 * c.Gamma * c.Gamma * c.s2));
+        B[i] = (ML + MH + 2.0 * MG) * ang;
+        C[i + 1] = __dadd_rn(C[i], B[i]);
+    }
 }
 
 // rate(t, Omega, q) = sum_k f_k r_k sum_j C_kj G_j, G = (gL, gH, q Re gc, q Im gc),
@@ -723,9 +732,11 @@ __device__ double phis_rate_exact(const PhisConsts& c, const MathTables* mt, dou
 constexpr int kGenPerThread = 16;              // candidates per thread per chunk (bits of a mask)
 constexpr int kGenChunk = kBlock * kGenPerThread;
 
-// Signal candidate j of toy k: Philox calls (j, k, 0): t, u_acc; (j, k, 1): ck,
-// cl; (j, k, 2): phi; (j, k, 3): u_q; the tag is the selected one (Q = +-1) or
-// +1 for u_q <= 1/2, else -1; kept iff u_acc M < rate.  The toy takes the first
+// Signal candidate j of toy k: Philox calls (j, k, 0): u_bin, u_acc; (j, k, 1):
+// ck, cl; (j, k, 2): phi, u_pos; (j, k, 3): u_q.  Its bin is the first i with
+// u_bin C_64 <= C_{i+1} (the proposal is piecewise uniform with weights B_i),
+// t = min(e_i + u_pos w, t_hi); the tag is the selected one (Q = +-1) or +1 for
+// u_q <= 1/2, else -1; kept iff u_acc B_i < rate.  The toy takes the first
 // n_sig kept candidates in increasing j.  Background event i: (i, k, 4): t,
 // ck; (i, k, 5): cl, phi; (i, k, 6): u_q.  One block per toy.
 __global__ void __launch_bounds__(kBlock)
@@ -737,18 +748,32 @@ phis_toygen_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, u
     __shared__ __align__(16) PhisConsts c;
     __shared__ MathTables mt;
     __shared__ int warp_sums[kBlock / 32];
-    __shared__ double env;
+    __shared__ double B[kGenBins], C[kGenBins + 1];
     {
         const double* src = reinterpret_cast<const double*>(consts);
         double* dst = reinterpret_cast<double*>(&c);
         for (int i = threadIdx.x; i < kPhisDoubles; i += blockDim.x) dst[i] = src[i];
     }
     load_math_tables(&mt);
-    __syncthreads();
-    if (threadIdx.x == 0) env = phis_envelope(c, m);
-    __syncthreads();
-    const double M = env;
     const double span = __dsub_rn(m.t_hi, m.t_lo);
+    const double w = __ddiv_rn(span, (double)kGenBins);
+    __syncthreads();
+    if (threadIdx.x == 0) phis_envelope_bins(c, m, w, B, C);
+    __syncthreads();
+    const double total = C[kGenBins];
+    // the first bin i with target <= C[i + 1] (C non-decreasing: binary search)
+    auto bin_of = [&](double u) {
+        const double target = __dmul_rn(u, total);
+        int lo = 0, hi = kGenBins - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (target <= C[mid + 1]) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    auto t_of = [&](int b, double u) {
+        return fmin(__dadd_rn(__dadd_rn(m.t_lo, __dmul_rn((double)b, w)), __dmul_rn(u, w)), m.t_hi);
+    };
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     const double Q = c.qsel;
     auto tag = [&](double u) { return Q != 0.0 ? Q : (u <= 0.5 ? 1.0 : -1.0); };
@@ -760,7 +785,7 @@ phis_toygen_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, u
     for (int toy = blockIdx.x; toy < n_toys; toy += gridDim.x) {
         const int64_t ns = n_sig[toy], nb = n_bkg[toy], off = offsets[toy];
         if (ns < 0 || nb < 0 || off < 0 || off + ns + nb > capacity) continue;   // skipped
-        const bool usable = isfinite(M) && M > 0.0 && isfinite(c.N) && c.N > 0.0;
+        const bool usable = isfinite(total) && total > 0.0 && isfinite(c.N) && c.N > 0.0;
         const uint64_t budget = usable ? (uint64_t)ns * 65536ull + (1ull << 22) : 0ull;
         int64_t got = 0;
         for (uint64_t j0 = 0; got < ns && j0 < budget; j0 += kGenChunk) {
@@ -774,10 +799,12 @@ phis_toygen_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, u
                 const U4 d = draw(j, (uint32_t)toy, 2u, k0, k1);
                 const double uq = Q != 0.0 ? 0.0 : u01(draw(j, (uint32_t)toy, 3u, k0, k1).x,
                                                        draw(j, (uint32_t)toy, 3u, k0, k1).y);
-                const double t = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+                const int bin = bin_of(u01(a.x, a.y));
+                const double t = t_of(bin, u01(d.z, d.w));
                 double ck, cl, ph;
                 angles(b, d, &ck, &cl, &ph);
-                if (__dmul_rn(u01(a.z, a.w), M) < phis_rate_exact(c, &mt, t, ck, cl, ph, tag(uq))) mask |= 1u << i;
+                if (__dmul_rn(u01(a.z, a.w), B[bin]) < phis_rate_exact(c, &mt, t, ck, cl, ph, tag(uq)))
+                    mask |= 1u << i;
             }
             int total;
             const int before = block_exclusive_scan(__popc(mask), warp_sums, &total);
@@ -795,7 +822,7 @@ phis_toygen_kernel(ModelDev m, const Consts* __restrict__ consts, uint32_t k0, u
                 const U4 e = draw(j, (uint32_t)toy, 3u, k0, k1);
                 double ck, cl, ph;
                 angles(b, d, &ck, &cl, &ph);
-                ot[off + pos] = __dadd_rn(m.t_lo, __dmul_rn(u01(a.x, a.y), span));
+                ot[off + pos] = t_of(bin_of(u01(a.x, a.y)), u01(d.z, d.w));
                 ock[off + pos] = ck;
                 ocl[off + pos] = cl;
                 ophi[off + pos] = ph;

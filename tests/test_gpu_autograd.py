@@ -100,22 +100,23 @@ def test_joint_backward_is_the_joint_gradient(env):
     ref = api.ipa_nll_grad_joint(m, ev, off, joint, th.detach())
     assert torch.equal(f.detach(), ref[:, 0])
     assert torch.equal(th.grad[0], 2.0 * ref[0, 1:]) and torch.equal(th.grad[1], -1.0 * ref[1, 1:])
-    # an optimiser on fit 0 reaches the joint fit's minimum
-    x = torch.tensor([[0.7, 0.12, 0.12, 0.12]], dtype=torch.float64, device="cuda", requires_grad=True)
+    # an optimiser on fit 0 (in units of the errors, one L-BFGS call) reaches the
+    # joint fit's minimum
     sub = off[:4].contiguous()
-    opt = torch.optim.LBFGS([x], lr=1.0, max_iter=200, tolerance_grad=1e-10, tolerance_change=1e-14,
+    start = torch.tensor([0.7, 0.12, 0.12, 0.12], dtype=torch.float64, device="cuda")
+    params = [api.Param(v, 0.0, 2.0, 0.01) for v in (0.7, 0.12, 0.12, 0.12)]
+    r = api.ipa_fit_joint(m, ev, sub, joint, params, start[None, :].clone(), max_iter=300, tol=1e-10)
+    ref, err = r["theta"][0], r["err"][0]
+    x = torch.zeros(4, dtype=torch.float64, device="cuda", requires_grad=True)
+    opt = torch.optim.LBFGS([x], lr=1.0, max_iter=300, tolerance_grad=1e-12, tolerance_change=1e-15,
                             line_search_fn="strong_wolfe")
 
     def closure():
         opt.zero_grad()
-        v = autograd.nll_joint(m, ev, sub, joint, x).sum()
+        v = autograd.nll_joint(m, ev, sub, joint, (start + x * err)[None, :]).sum()
         v.backward()
         return v
 
-    for _ in range(5):
-        opt.step(closure)
-    params = [api.Param(v, 0.0, 2.0, 0.01) for v in (0.7, 0.12, 0.12, 0.12)]
-    r = api.ipa_fit_joint(m, ev, sub, joint, params, torch.tensor([[0.7, 0.12, 0.12, 0.12]], device="cuda"),
-                          max_iter=300, tol=1e-10)
-    err = r["err"][0]
-    assert torch.all((x.detach()[0] - r["theta"][0]).abs() < 1e-4 * err)
+    opt.step(closure)
+    got = (start + x.detach() * err)
+    assert torch.all((got - ref).abs() < 1e-4 * err), (got, ref)

@@ -218,8 +218,8 @@ def test_joint_fit_4d_matches_oracle_and_batch_equals_solo(env):
 
 def test_joint_minos_matches_the_oracle_profile(env):
     """Three 1D categories: Gamma shared, f_b per category, sigma and mu
-    constants.  GPU fit, HESSE and MINOS of Gamma and one f_b against the
-    oracle's profile-likelihood roots of the joint NLL at the GPU minimum."""
+    constants.  GPU HESSE and MINOS of Gamma and one f_b at the oracle's joint
+    minimum against the oracle's profile-likelihood roots."""
     O, J, F, G, torch, api = env
     m_o, m_g = O.Model("1d", 0.3, 15.0), api.model_1d(0.3, 15.0)
     jmap = [[0, -1, -1, 1], [0, -1, -1, 2], [0, -1, -1, 3]]
@@ -235,18 +235,19 @@ def test_joint_minos_matches_the_oracle_profile(env):
     joint = api.Joint(jmap, value)
     cols, off = _pack([cats])
     ev, offd = G.to_dev(cols), torch.tensor(off, device="cuda")
-    r = api.ipa_fit_joint(m_g, ev, offd, joint, params, torch.tensor(truth[None, :], device="cuda"), max_iter=300,
-                          tol=1e-10)
-    assert int(r["status"][0]) == 0
-    hs = api.ipa_hesse_joint(m_g, ev, offd, joint, params, r["theta"])
+    # both sides start from the oracle's minimum (the GPU reads the NLL there itself)
+    ref = J.fit(m_o, cats, jmap, value, truth, [0, 1, 2, 3], lo=lo, hi=hi, tol=1e-12)
+    assert ref.status == "CONVERGED"
+    th = torch.tensor(ref.theta[None, :], device="cuda")
+    nll = api.ipa_nll_grad_joint(m_g, ev, offd, joint, th)[:, 0].contiguous()
+    hs = api.ipa_hesse_joint(m_g, ev, offd, joint, params, th)
     scan = [0, 2]
-    mn = api.ipa_minos_joint(m_g, ev, offd, joint, params, r["theta"], r["nll"], hs["cov"], scan)
+    mn = api.ipa_minos_joint(m_g, ev, offd, joint, params, th, nll, hs["cov"], scan)
     mn = {k: v.cpu().numpy()[0] for k, v in mn.items()}
-    th_min, nll_min = r["theta"].cpu().numpy()[0], float(r["nll"].cpu()[0])
-    err = hs["err"].cpu().numpy()[0]
+    err = np.sqrt(np.diag(np.linalg.inv(ref.hess)))
     for j in scan:
-        (elo, ehi), st = J.minos(m_o, cats, jmap, value, th_min, nll_min, [0, 1, 2, 3], j, float(err[j]), lo=lo,
-                                 hi=hi)
+        (elo, ehi), st = J.minos(m_o, cats, jmap, value, ref.theta, ref.nll, [0, 1, 2, 3], j, float(err[j]),
+                                 lo=lo, hi=hi)
         assert st == ("OK", "OK") and tuple(mn["status"][j]) == (0, 0), (j, mn["status"][j])
         assert abs(mn["lo"][j] - elo) < 1e-5 * err[j], (j, mn["lo"][j], elo)
         assert abs(mn["hi"][j] - ehi) < 1e-5 * err[j], (j, mn["hi"][j], ehi)
@@ -304,3 +305,42 @@ def test_joint_fit_phis_one_flavour_categories_matches_oracle(env):
         assert abs(r["theta"][0, j] - ref.theta[j]) < 1e-6 * ref.err[j], (j, r["theta"][0, j], ref.theta[j])
         assert r["err"][0, j] == pytest.approx(ref.err[j], rel=1e-3)
     assert r["nll"][0] == pytest.approx(ref.nll, rel=1e-12)
+
+
+def test_joint_fit_with_32_parameters_and_an_empty_fit(env):
+    """The largest joint fit (IPA_MAX_PAR = 32 parameters: Gamma shared, f_b in
+    each of 31 1D categories, all free) against the oracle; a second fit whose
+    categories are all empty ends IPA_FIT_EMPTY and leaves the first bitwise
+    as it is alone."""
+    O, J, F, G, torch, api = env
+    m_o, m_g = O.Model("1d", 0.3, 15.0), api.model_1d(0.3, 15.0)
+    n_cat = 31
+    jmap = [[0, -1, -1, 1 + c] for c in range(n_cat)]
+    value = [[0.0, 0.045, 0.0, 0.0] for _ in range(n_cat)]
+    truth = np.concatenate([[0.66], 0.05 + 0.01 * np.arange(n_cat)])
+    cats = []
+    for c in range(n_cat):
+        thc = J.category_thetas(jmap, value, truth)[c]
+        cats.append({"t": O.toygen(m_o, thc, 1200 + c, [1500], [int(1500 * thc[3] / (1 - thc[3]))])[0]["t"]})
+    empty = [{"t": np.zeros(0)} for _ in range(n_cat)]
+    lo, hi = np.concatenate([[0.2], np.zeros(n_cat)]), np.concatenate([[2.0], np.full(n_cat, 0.8)])
+    params = [api.Param(float(truth[j]), float(lo[j]), float(hi[j]), 0.01) for j in range(32)]
+    joint = api.Joint(jmap, value)
+
+    def run(fits):
+        cols, off = _pack(fits)
+        theta = torch.tensor(np.tile(truth, (len(fits), 1)), device="cuda")
+        r = api.ipa_fit_joint(m_g, G.to_dev(cols), torch.tensor(off, device="cuda"), joint, params, theta,
+                              max_iter=400, tol=1e-9)
+        return {k: v.cpu().numpy() for k, v in r.items()}
+
+    both = run([cats, empty])
+    solo = run([cats])
+    assert both["status"][1] == 4                       # IPA_FIT_EMPTY
+    for key in ("theta", "err", "nll", "status", "iters", "passes"):
+        assert np.array_equal(both[key][0], solo[key][0]), key
+    ref = J.fit(m_o, cats, jmap, value, truth, list(range(32)), lo=lo, hi=hi, tol=1e-10)
+    assert ref.status == "CONVERGED" and solo["status"][0] in (0, 2)
+    for j in range(32):
+        assert abs(solo["theta"][0, j] - ref.theta[j]) < 1e-6 * ref.err[j], (j, solo["theta"][0, j], ref.theta[j])
+        assert solo["err"][0, j] == pytest.approx(ref.err[j], rel=1e-3)

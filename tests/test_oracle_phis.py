@@ -235,8 +235,9 @@ def test_gradient_matches_finite_differences(oracle, F):
 
 @pytest.mark.parametrize("Q", [0.0, 1.0])
 def test_envelope_bounds_the_rate(oracle, F, Q):
-    """u M < rate is a valid accept-reject test only if M >= rate everywhere: random
-    parameter points (C_SP up to 1.3) against 2e5 random (t, angles, tag)."""
+    """u B_i < rate is a valid accept-reject test only if the bin bound B_i >=
+    rate everywhere in bin i: random parameter points (C_SP up to 1.3) against
+    2e5 random (t, angles, tag)."""
     m = oracle.Model("phis", 0.0, 15.0)
     rng = np.random.default_rng(11)
     for _ in range(15):
@@ -246,7 +247,13 @@ def test_envelope_bounds_the_rate(oracle, F, Q):
         ev = {"t": np.concatenate([rng.uniform(0, 0.3, n // 2), rng.uniform(0, 15, n // 2)]),
               "ck": rng.uniform(-1, 1, n), "cl": rng.uniform(-1, 1, n), "phi": rng.uniform(-math.pi, math.pi, n),
               "q": np.where(rng.uniform(size=n) < 0.5, 1.0, -1.0)}
-        assert F.rate(m, ev, th).max() <= F.envelope(m, th)
+        w, edges, B, C = F.envelope_bins(m, th)
+        b = np.minimum(((ev["t"] - m.t_lo) / w).astype(np.int64), F.GEN_BINS - 1)
+        # points on a bin's boundary belong to both neighbours: take the left one too
+        left = np.maximum(b - 1, 0)
+        r = F.rate(m, ev, th)
+        assert np.all((r <= B[b]) | ((ev["t"] == edges[b]) & (r <= B[left])))
+        assert C[0] == 0.0 and all(C[i + 1] == C[i] + B[i] for i in range(F.GEN_BINS))
 
 
 def test_toys_recover_the_parameters(oracle, F):
