@@ -149,15 +149,16 @@ ipa_status check_joint_map(const ipa_model* m, const ipa_joint* j, int n_fits) {
         return IPA_ERR_ARG;
     }
     std::vector<int> used(j->n_joint, 0);
-    for (int k = 0; k < j->n_cat * m->n_par; ++k) {
+    const int64_t n_map = (int64_t)j->n_cat * m->n_par;
+    for (int64_t k = 0; k < n_map; ++k) {
         const int q = j->map[k];
         if (q < -1 || q >= j->n_joint) {
-            set_error("joint: map entry %d (category %d, parameter %d) is %d, outside [-1, %d)", k,
-                      k / m->n_par, k % m->n_par, q, j->n_joint);
+            set_error("joint: map entry %lld (category %lld, parameter %lld) is %d, outside [-1, %d)", (long long)k,
+                      (long long)(k / m->n_par), (long long)(k % m->n_par), q, j->n_joint);
             return IPA_ERR_ARG;
         }
         if (q == -1 && !j->value) {
-            set_error("joint: map entry %d is a constant but no values were given", k);
+            set_error("joint: map entry %lld is a constant but no values were given", (long long)k);
             return IPA_ERR_ARG;
         }
         if (q >= 0) used[q] = 1;

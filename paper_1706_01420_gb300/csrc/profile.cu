@@ -528,6 +528,10 @@ ipa_status hesse_run(const ipa_model* model, const ipa_events* ev, const int64_t
     const size_t n_v = (size_t)n_fits * nv;
     const int n_cat = joint ? joint->n_cat : 1;
     ipa_status st;
+    if (n_v * (size_t)n_cat > (size_t)1 << 30) {
+        set_error("%s: %zu virtual segments, more than 2^30", who, n_v * (size_t)n_cat);
+        return IPA_ERR_ARG;
+    }
     if ((st = profile_basics(c)) != IPA_OK) return st;
     if ((st = hesse_reserve(c, (size_t)n_fits, n_v, model->n_par)) != IPA_OK) return st;
     if (joint && (st = joint_reserve(c, (size_t)n_cat * model->n_par, n_v * n_cat)) != IPA_OK) return st;
@@ -660,8 +664,12 @@ ipa_status minos_run(const ipa_model* model, const ipa_events* ev, const int64_t
     if (!cp) return IPA_ERR_CUDA;
     ProfileContext& c = *cp;
     std::lock_guard<std::mutex> lk(c.mu);
-    const int n_probes = n_fits * n_scan * 2;
     const int n_cat = joint ? joint->n_cat : 1;
+    if ((size_t)n_fits * n_scan * 2 * (size_t)n_cat > (size_t)1 << 30) {
+        set_error("%s: too many profile fits (n_fits x scanned parameters x 2 x categories > 2^30)", who);
+        return IPA_ERR_ARG;
+    }
+    const int n_probes = n_fits * n_scan * 2;
     if ((st = profile_basics(c)) != IPA_OK) return st;
     if ((st = minos_reserve(c, (size_t)n_probes)) != IPA_OK) return st;
     if (joint && (st = joint_reserve(c, (size_t)n_cat * model->n_par, (size_t)n_probes * n_cat)) != IPA_OK)
