@@ -95,6 +95,12 @@ def test_joint_map_host_checks(lib):
     j = C.ipa_joint(n_cat=2, n_joint=6, map=jm.ctypes.data, value=None)
     assert lib.ipa_fit_joint(ctypes.byref(m), ctypes.byref(ev), 16, 1, ctypes.byref(j), spec, 16, None, None,
                              None, None, None, 10, 1e-9, None) == C.IPA_ERR_ARG   # joint parameter 4 unused
+    assert lib.ipa_hesse_joint(ctypes.byref(m), ctypes.byref(ev), 16, 1, ctypes.byref(j), spec, 16, 16, None,
+                               None, None, None) == C.IPA_ERR_ARG
+    flags = (ctypes.c_int32 * 6)(1, 0, 0, 0, 0, 0)
+    assert lib.ipa_minos_joint(ctypes.byref(m), ctypes.byref(ev), 16, 1, ctypes.byref(j), spec, 16, 16, 16, flags,
+                               0.5, 1e-7, 10, 100, 1e-9, 16, 16, None, None) == C.IPA_ERR_ARG
+    assert b"used by no category" in lib.ipa_last_error()
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
