@@ -208,6 +208,21 @@ ipa_status ipa_nll(const ipa_model* model, const ipa_events* ev, const double* t
 ipa_status ipa_nll_grad(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
                         double* out_dev, void* stream);
 
+/* ipa_nll_grad for events in HOST memory (the columns of *host_ev are host
+ * pointers, 16-byte aligned).  Page-locked columns (cudaHostAlloc or
+ * registered) are read by the kernel in place through the device's mapping
+ * of the allocation, so the transfer runs inside the event pass: out_dev is
+ * bitwise ipa_nll_grad of the same events.  Pageable columns are split into
+ * k = clamp(floor(n / 2^20), 1, 16) chunks of ceil(ceil(n / k) / 512) * 512
+ * events (the last one shorter), copied into library staging buffers on four
+ * library copy streams while the likelihood kernel runs, on `stream`, over the
+ * chunks already on the device: out_dev (device, 1 + n_par doubles) = the sum,
+ * in chunk order, of ipa_nll_grad over each chunk (bitwise).  The host columns must stay unchanged until the work on
+ * `stream` completes.  No cached angular basis (IPA_ERR_ARG).  The staging
+ * buffers grow to n events per column (library memory, kept). */
+ipa_status ipa_nll_grad_host(const ipa_model* model, const ipa_events* host_ev, const double* theta_dev,
+                             double* out_dev, void* stream);
+
 /* Same as ipa_nll_grad for n_seg event segments packed back to back in one
  * set of columns: segment s is events [seg_off[s], seg_off[s+1]) and uses
  * theta_dev + s*n_par; out_dev receives (1 + n_par) doubles per segment.

@@ -60,6 +60,7 @@ PROTOTYPES = {
     "ipa_model_init": (c_int32, [POINTER(ipa_model), c_int32, c_double, c_double]),
     "ipa_nll": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
     "ipa_nll_grad": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
+    "ipa_nll_grad_host": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p]),
     "ipa_nll_grad_segmented": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32,
                                          c_void_p, c_void_p, c_void_p]),
     "ipa_angular_basis": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int64, c_void_p]),

@@ -132,6 +132,32 @@ def ipa_nll_grad(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.T
     return out
 
 
+def ipa_nll_grad_host(model: C.ipa_model, ev_host: dict, theta: torch.Tensor, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """ipa_nll_grad for events in host memory (CPU float64 tensors, page-locked for
+    overlap): chunked copies overlapped with the event pass; the host tensors
+    must stay unchanged until the work on the stream completes."""
+    out = torch.empty(1 + model.n_par, dtype=torch.float64, device=theta.device) if out is None else out
+    _need(theta, model.n_par, "theta")
+    _need(out, 1 + model.n_par, "out")
+    e = C.ipa_events()
+    n = None
+    for k in ("t", "ck", "cl", "phi", "w", "q"):
+        v = ev_host.get(k)
+        if v is None:
+            continue
+        if not isinstance(v, torch.Tensor) or v.is_cuda or v.dtype != torch.float64 or not v.is_contiguous():
+            raise IpaError(f"{k} must be a contiguous float64 CPU tensor")
+        n = v.numel() if n is None else n
+        if v.numel() != n:
+            raise IpaError("host columns of different lengths")
+        setattr(e, k, v.data_ptr())
+    e.n = 0 if n is None else n
+    _check(_lib().ipa_nll_grad_host(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
+                                    _ptr(out, name="out"), _stream(stream)), "ipa_nll_grad_host")
+    return out
+
+
 def ipa_nll_grad_noalloc(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor,
                          stream=None) -> torch.Tensor:
     """ipa_nll_grad with the library's fixed scratch array: allocates nothing on the

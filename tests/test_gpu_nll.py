@@ -212,3 +212,62 @@ def test_weight_column_of_ones_equals_no_column(env, kind):
     f_ref, g_ref = O.nll_grad(m_o, wc, th)
     logl, _ = O.nll_grad_terms(m_o, wc, th)
     G.assert_nll_grad_close(got, f_ref, g_ref, G.grad_scale(O, m_o, wc, th), math.fsum(np.abs(logl)))
+
+
+def _chunks(n):
+    """The host entry point's chunking: k = clamp(floor(n / 2^20), 1, 16) pieces of
+    ceil(ceil(n / k) / 512) * 512 events."""
+    k = min(max(n // (1 << 20), 1), 16)
+    per = -(-n // k)
+    chunk = -(-per // 512) * 512
+    return [(o, min(chunk, n - o)) for o in range(0, n, chunk)]
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("kind,n,weighted", [("4d", 1_000_000, False), ("4d", 300_001, True), ("1d", 1000, False),
+                                             ("4d", 3_000_000, True), ("4d", 0, False)])
+def test_host_entry_point(env, kind, n, weighted, pinned):
+    """ipa_nll_grad_host: page-locked columns are read in place, so the result is
+    bitwise ipa_nll_grad of the same events; pageable columns are staged in
+    chunks and the result is the sum, in chunk order, of ipa_nll_grad over each
+    chunk (bitwise).  Both match the oracle (up to 4e5 events)."""
+    O, G, torch, api = env
+    if kind == "1d":
+        m_o, m_g = O.Model("1d", 0.3, 15.0), api.model_1d(0.3, 15.0)
+        cols = {"t": synth.events_1d(n, 5)}
+        th = TH1
+    else:
+        m_o, m_g = O.Model("4d", 0.0, 15.0), api.model_4d(0.0, 15.0)
+        cols = synth.events_4d(n, 6, weighted=weighted)
+        th = TH4 * 1.01
+    host = {k: (torch.tensor(v).pin_memory() if pinned else torch.tensor(v)) for k, v in cols.items()}
+    theta = torch.tensor(th, device="cuda")
+    got = api.ipa_nll_grad_host(m_g, host, theta).cpu().numpy()
+    again = api.ipa_nll_grad_host(m_g, host, theta).cpu().numpy()
+    assert np.array_equal(got, again)
+    if n == 0:
+        assert np.all(got == 0.0)
+        return
+    if pinned:
+        ref = api.ipa_nll_grad(m_g, G.to_dev(cols), theta).cpu().numpy()
+    else:
+        ref = np.zeros(th.size + 1)
+        for o, ln in _chunks(n):
+            part = api.ipa_nll_grad(m_g, G.to_dev({k: v[o:o + ln] for k, v in cols.items()}), theta).cpu().numpy()
+            ref = ref + part
+    assert np.array_equal(got, ref)
+    if n <= 400_000:
+        f_ref, g_ref = O.nll_grad(m_o, cols, th)
+        logl, _ = O.nll_grad_terms(m_o, cols, th)
+        G.assert_nll_grad_close(got, f_ref, g_ref, G.grad_scale(O, m_o, cols, th), math.fsum(np.abs(logl)))
+
+
+def test_host_entry_point_rejects_device_and_mixed_columns(env):
+    O, G, torch, api = env
+    m = api.model_1d(0.3, 15.0)
+    theta = torch.tensor(TH1, device="cuda")
+    with pytest.raises(api.IpaError):
+        api.ipa_nll_grad_host(m, {"t": torch.zeros(10, dtype=torch.float64, device="cuda")}, theta)
+    with pytest.raises(api.IpaError):
+        api.ipa_nll_grad_host(m, {"t": torch.zeros(10, dtype=torch.float64), "w": torch.zeros(9, dtype=torch.float64)},
+                              theta)
