@@ -1,6 +1,6 @@
 """GPU parity of ipa_nll / ipa_nll_grad / ipa_nll_grad_segmented against the oracle.
 
-Tolerances (BASELINE the benchmark spec): NLL to 1e-12 relative (to sum |w log P|);
+Tolerances: NLL to 1e-12 relative (to sum |w log P|);
 gradient to 1e-9 relative to max(|g_j|, condition scale of g_j) -- see
 gpu_common.grad_scale -- and, against central finite differences of the GPU
 NLL itself, to 1e-6.
