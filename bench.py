@@ -309,6 +309,8 @@ def main():
                     help="untimed: 4 ipa_nll_grad calls on 8e6 tagged events (128 MB, > L2), for ncu")
     ap.add_argument("--profile-case-phis", action="store_true",
                     help="untimed: 4 ipa_nll_grad calls on 8e6 phi_s-model events (320 MB, > L2), for ncu")
+    ap.add_argument("--profile-case-joint", action="store_true",
+                    help="untimed: Example 2's twelve-category fit of 1e4 events, twice, for an ncu launch list")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case()
@@ -316,6 +318,8 @@ def main():
         return profile_case_tagged()
     if args.profile_case_phis:
         return profile_case_phis()
+    if args.profile_case_joint:
+        return profile_case_joint()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -544,6 +548,30 @@ def profile_case_phis() -> int:
         out = api.ipa_nll_grad(m, ev, theta)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "ipa_nll_grad phi_s model", "events": n, "nll": float(out[0])}))
+    return 0
+
+
+def profile_case_joint() -> int:
+    """Example 2's fit of 1e4 events (twelve categories), run twice: the launch
+    list of one simultaneous fit at a latency-bound size."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1706_01420_gb300 import api
+    dev = torch.device("cuda")
+    m = api.model_phis(0.0, 15.0)
+    jmap, value = joint_map_phis()
+    joint = api.Joint(jmap, value)
+    ev, seg = joint_events(api, torch, dev, m, jmap, value, TRUTH_JOINT, 10_000, seed=31 + 10_000)
+    start = TRUTH_JOINT * np.where(np.arange(TRUTH_JOINT.size) < 8, 1.02, 1.0)
+    params = [api.Param(float(start[j]), float(LO_JOINT[j]), float(HI_JOINT[j]),
+                        float((HI_JOINT[j] - LO_JOINT[j]) / 100)) for j in range(TRUTH_JOINT.size)]
+    for _ in range(2):
+        r = api.ipa_fit_joint(m, ev, seg, joint, params, torch.tensor(start[None, :], device=dev), max_iter=500,
+                              tol=1e-6)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "ipa_fit_joint, 12 categories, 1e4 events", "passes": int(r["passes"].item()),
+                      "status": int(r["status"].item())}))
     return 0
 
 

@@ -220,10 +220,51 @@ __device__ inline void edge_c(double tau, double zr, double zi, double sigma, do
     out[7] = -gi;
 }
 
-__device__ inline void compute_phis_consts(const ModelDev& md, const double* th, PhisConsts* c) {
+// The transcendental inputs of the constants, independent of one another, so
+// that they can be evaluated side by side: a lane's FP64 instruction holds its
+// sub-partition's FP64 unit for many cycles whether one lane or all 32 are
+// active, so one thread evaluating them in turn takes ~20 times longer than
+// four warps each evaluating one kind in several lanes at once.
+struct PhisPieces {
+    double F[4], dF[4][3];     // edge(): (t_hi, Gamma_L), (t_lo, Gamma_L), (t_hi, Gamma_H), (t_lo, Gamma_H)
+    double ec[2][8];           // edge_c() at t_hi and t_lo (one-tag normalisation only)
+    double sw[6], cw[6];       // sincos of the six strong-phase combinations
+    double sn, cn;             // sincos(phi_s)
+    double r[5];               // sqrt of x0, xa, xe, F, 1 - F
+    double tq;                 // sqrt(39.1 + beta^2)
+};
+constexpr int kPhisPieces = 19;
+
+// Piece k: 0-3 the real edges, 4-5 the complex edges, 6-11 the strong-phase
+// sincos, 12 sincos(phi_s), 13-17 the square roots, 18 the cut's root.
+__device__ inline void phis_piece(const ModelDev& md, const double* th, int k, PhisPieces* p) {
+    using namespace cdetail;
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], DG = th[IPA_PHIS_DG];
+    const double Dm = th[IPA_PHIS_DM];
+    if (k < 4) {
+        const double tau = (k & 1) ? md.t_lo - mu : md.t_hi - mu;
+        edge(tau, k < 2 ? Gamma + 0.5 * DG : Gamma - 0.5 * DG, sigma, &p->F[k], p->dF[k]);
+    } else if (k < 6) {
+        if (th[IPA_PHIS_QNORM] != 0.0) edge_c(k == 4 ? md.t_hi - mu : md.t_lo - mu, Gamma, -Dm, sigma, p->ec[k - 4]);
+    } else if (k < 12) {
+        sincos(ang_arg(k - 6, th[IPA_DPA], th[IPA_DPE], th[IPA_DS]), &p->sw[k - 6], &p->cw[k - 6]);
+    } else if (k == 12) {
+        sincos(th[IPA_PHIS_PHIS], &p->sn, &p->cn);
+    } else if (k < 18) {
+        const double x0 = th[IPA_A0SQ], xe = th[IPA_APESQ], F = th[IPA_FS];
+        const double arg[5] = {x0, 1.0 - x0 - xe, xe, F, 1.0 - F};
+        p->r[k - 13] = sqrt(arg[k - 13]);
+    } else {
+        const double beta = Dm * sigma / kSqrt2;
+        p->tq = sqrt(39.1 + beta * beta);
+    }
+}
+
+__device__ inline void compute_phis_consts(const ModelDev& md, const double* th, const PhisPieces* pc,
+                                           PhisConsts* c) {
     using namespace cdetail;
     const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
-    const double DG = th[IPA_PHIS_DG], Dm = th[IPA_PHIS_DM], phi = th[IPA_PHIS_PHIS], om = th[IPA_PHIS_OMEGA];
+    const double DG = th[IPA_PHIS_DG], Dm = th[IPA_PHIS_DM], om = th[IPA_PHIS_OMEGA];
     const double GH = Gamma - 0.5 * DG, GL = Gamma + 0.5 * DG;
     c->Gamma = Gamma;
     c->sigma = sigma;
@@ -247,7 +288,7 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     c->beta = Dm * sigma / kSqrt2;
     c->ph0 = Gamma * Dm * sigma * sigma;
     const double rmax = fmax(fmax(GH, GL), Gamma);
-    const double tc = mu + (rmax * sigma * sigma + sqrt(39.1 + c->beta * c->beta) * kSqrt2 * sigma);
+    const double tc = mu + (rmax * sigma * sigma + pc->tq * kSqrt2 * sigma);
     c->tcut = tc == tc ? tc : INFINITY;
     // amplitudes
     const double x0 = th[IPA_A0SQ], xe = th[IPA_APESQ], F = th[IPA_FS];
@@ -256,14 +297,16 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     c->xe = xe;
     c->xa = xa;
     c->F = F;
-    c->r0 = sqrt(x0);
-    c->ra = sqrt(xa);
-    c->re = sqrt(xe);
-    c->rF = sqrt(F);
-    c->rs = sqrt(sF);
-    for (int i = 0; i < 6; ++i) sincos(ang_arg(i, th[IPA_DPA], th[IPA_DPE], th[IPA_DS]), &c->sw[i], &c->cw[i]);
-    double sn, cn;
-    sincos(phi, &sn, &cn);
+    c->r0 = pc->r[0];
+    c->ra = pc->r[1];
+    c->re = pc->r[2];
+    c->rF = pc->r[3];
+    c->rs = pc->r[4];
+    for (int i = 0; i < 6; ++i) {
+        c->sw[i] = pc->sw[i];
+        c->cw[i] = pc->cw[i];
+    }
+    const double sn = pc->sn, cn = pc->cn;
     c->c = cn;
     c->s = sn;
     c->D = 1.0 - 2.0 * om;
@@ -278,11 +321,8 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
         c->bi[k] = mag[k] * sps[k];
     }
     // N = (16 pi / 9) (wL I_L + wH I_H): Pe = |A_0|^2 + |A_pa|^2, Po = |A_pe|^2 + |A_S|^2
-    double FhL, FlL, FhH, FlH, dFhL[3], dFlL[3], dFhH[3], dFlH[3];
-    edge(md.t_hi - mu, GL, sigma, &FhL, dFhL);
-    edge(md.t_lo - mu, GL, sigma, &FlL, dFlL);
-    edge(md.t_hi - mu, GH, sigma, &FhH, dFhH);
-    edge(md.t_lo - mu, GH, sigma, &FlH, dFlH);
+    const double FhL = pc->F[0], FlL = pc->F[1], FhH = pc->F[2], FlH = pc->F[3];
+    const double *dFhL = pc->dF[0], *dFlL = pc->dF[1], *dFhH = pc->dF[2], *dFlH = pc->dF[3];
     const double IL = FhL - FlL, IH = FhH - FlH;
     const double Pe = sF * (1.0 - xe), Po = sF * xe + F;
     const double wL = Pe * (1.0 + cn) + Po * (1.0 - cn), wH = Pe * (1.0 - cn) + Po * (1.0 + cn);
@@ -309,9 +349,7 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
         // one tag: N_Q = N / 2 + Q K D sin(phi_s) (Pe - Po) Im I_c, I_c the integral
         // of g(t - mu; Gamma - i Dm) over the range; the background over one tag
         const double Q = qsel > 0.0 ? 1.0 : -1.0;
-        double eh[8], el[8];
-        edge_c(md.t_hi - mu, Gamma, -Dm, sigma, eh);
-        edge_c(md.t_lo - mu, Gamma, -Dm, sigma, el);
+        const double *eh = pc->ec[0], *el = pc->ec[1];
         const double Ii = eh[1] - el[1];
         const double dzr = eh[2] - el[2], dzi = eh[3] - el[3];
         const double W = Pe - Po, D = 1.0 - 2.0 * om;
@@ -339,10 +377,30 @@ __device__ inline void compute_phis_consts(const ModelDev& md, const double* th,
     c->pad_ = 0.0;
 }
 
+// One thread per segment (many segments: the warp's lanes are segments).
 __global__ void phis_consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg, Consts* __restrict__ out) {
     asm volatile("griddepcontrol.launch_dependents;");
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n_seg) compute_phis_consts(m, theta + (size_t)s * m.n_par, reinterpret_cast<PhisConsts*>(out + s));
+    if (s >= n_seg) return;
+    const double* th = theta + (size_t)s * m.n_par;
+    PhisPieces p;
+    for (int k = 0; k < kPhisPieces; ++k) phis_piece(m, th, k, &p);
+    compute_phis_consts(m, th, &p, reinterpret_cast<PhisConsts*>(out + s));
+}
+
+// One four-warp block per segment (few segments): warp 0 evaluates the four
+// real edges in lanes 0-3, warp 1 the two complex edges, warp 2 the seven
+// sincos, warp 3 the six square roots; thread 0 assembles the record.
+__global__ void __launch_bounds__(128) phis_consts_block_kernel(ModelDev m, const double* __restrict__ theta,
+                                                                Consts* __restrict__ out) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    __shared__ PhisPieces p;
+    const double* th = theta + (size_t)blockIdx.x * m.n_par;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int first[4] = {0, 4, 6, 13}, count[4] = {4, 2, 7, 6};
+    if (l < count[w]) phis_piece(m, th, first[w] + l, &p);
+    __syncthreads();
+    if (threadIdx.x == 0) compute_phis_consts(m, th, &p, reinterpret_cast<PhisConsts*>(out + blockIdx.x));
 }
 
 // Per-warp copy: the record and Cq_kj = (cs / 2) C_kj c_k (the basis factor c_k
@@ -859,7 +917,10 @@ ipa_status launch_phis_toygen(const ModelDev& m, const Consts* consts, uint64_t 
 
 ipa_status launch_phis_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out, cudaStream_t st) {
     if (n_seg <= 0) return IPA_OK;
-    phis_consts_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
+    if (n_seg < 64)
+        phis_consts_block_kernel<<<n_seg, 128, 0, st>>>(m, theta, out);
+    else
+        phis_consts_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
     return cuda_fail(cudaGetLastError(), "phi_s consts kernel launch");
 }
 
