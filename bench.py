@@ -569,6 +569,10 @@ def profile_case_joint() -> int:
     for _ in range(2):
         r = api.ipa_fit_joint(m, ev, seg, joint, params, torch.tensor(start[None, :], device=dev), max_iter=500,
                               tol=1e-6)
+    # five joint passes outside a graph: the kernels of one pass, one launch each
+    th = torch.tensor(TRUTH_JOINT[None, :], device=dev)
+    for _ in range(5):
+        api.ipa_nll_grad_joint(m, ev, seg, joint, th)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "ipa_fit_joint, 12 categories, 1e4 events", "passes": int(r["passes"].item()),
                       "status": int(r["status"].item())}))

@@ -35,31 +35,30 @@ __global__ void joint_scatter_kernel(JointDev j, int n_fits, const double* __res
     j.theta_seg[s * j.n_model + p] = q >= 0 ? theta_joint[i * j.n_joint + q] : j.value[c * j.n_model + p];
 }
 
+// One thread per (fit, output): output 0 is the NLL, sum over c of NLL_c;
+// output 1 + q the sum over (c, p) with map[c][p] = q of dNLL_c/dtheta_c[p],
+// both in the order c ascending, then p ascending.  Without the gradient, one
+// thread per fit.
 __global__ void joint_gather_kernel(JointDev j, int n_fits, const int* __restrict__ active,
                                     double* __restrict__ res_joint) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_fits) return;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_out = j.grad ? 1 + j.n_joint : 1;
+    if (idx >= (int64_t)n_fits * n_out) return;
+    const int64_t i = idx / n_out;
+    const int o = (int)(idx - i * n_out);
     if (active && !active[i]) return;
-    if (!j.grad) {
-        double f = 0.0;
-        for (int c = 0; c < j.n_cat; ++c) f += j.res_seg[(int64_t)i * j.n_cat + c];
-        res_joint[i] = f;
-        return;
+    const int stride = j.grad ? 1 + j.n_model : 1;
+    const double* r = j.res_seg + i * j.n_cat * stride;
+    double v = 0.0;
+    if (o == 0) {
+        for (int c = 0; c < j.n_cat; ++c) v += r[c * stride];
+    } else {
+        const int q = o - 1;
+        for (int c = 0; c < j.n_cat; ++c)
+            for (int p = 0; p < j.n_model; ++p)
+                if (j.map[c * j.n_model + p] == q) v += r[c * stride + 1 + p];
     }
-    double g[kMaxP];
-    for (int q = 0; q < j.n_joint; ++q) g[q] = 0.0;
-    double f = 0.0;
-    for (int c = 0; c < j.n_cat; ++c) {
-        const double* r = j.res_seg + ((int64_t)i * j.n_cat + c) * (1 + j.n_model);
-        f += r[0];
-        for (int p = 0; p < j.n_model; ++p) {
-            const int q = j.map[c * j.n_model + p];
-            if (q >= 0) g[q] += r[1 + p];
-        }
-    }
-    double* out = res_joint + (int64_t)i * (1 + j.n_joint);
-    out[0] = f;
-    for (int q = 0; q < j.n_joint; ++q) out[1 + q] = g[q];
+    res_joint[i * n_out + o] = v;
 }
 
 // fit i: the event range of its categories (decides IPA_FIT_EMPTY)
@@ -216,7 +215,8 @@ ipa_status launch_joint_scatter(const JointDev& j, int n_fits, const double* the
 ipa_status launch_joint_gather(const JointDev& j, int n_fits, const int* active, double* res_joint,
                                cudaStream_t s) {
     const int b = 128;
-    joint_gather_kernel<<<(n_fits + b - 1) / b, b, 0, s>>>(j, n_fits, active, res_joint);
+    const int64_t n = (int64_t)n_fits * (j.grad ? 1 + j.n_joint : 1);
+    joint_gather_kernel<<<(unsigned)((n + b - 1) / b), b, 0, s>>>(j, n_fits, active, res_joint);
     return cuda_fail(cudaGetLastError(), "joint gather");
 }
 
