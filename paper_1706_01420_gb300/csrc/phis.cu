@@ -41,6 +41,7 @@ namespace {
 constexpr int kPerLane = kTile / 32;
 constexpr int kSub = 4;
 constexpr int kMaxWarps = 8;
+constexpr int kTeam = kPerLane / kSub;   // warps that share a tile: each takes kSub of a lane's events
 constexpr int kNA = 47;          // accumulators with the gradient (n_acc of the phi_s model)
 static_assert(kNA == n_acc(IPA_MODEL_PHIS, true) && kNA <= kMaxAcc, "the scratch must hold the accumulators");
 constexpr int kS = 2;            // first S_kj
@@ -550,7 +551,7 @@ __device__ __forceinline__ void phis_finalize(const PhisConsts& c, const double*
 }
 
 template <bool GRAD, bool WEIGHTED, bool CACHED>
-__global__ void __launch_bounds__(32 * kMaxWarps, 1)
+__global__ void __launch_bounds__(32 * kTeam, 1)
 phis_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin, const int64_t* __restrict__ seg_end,
             const int64_t* __restrict__ seg_tiles, int n_seg, const Consts* __restrict__ consts,
             double* __restrict__ partials, unsigned* __restrict__ counters, unsigned* __restrict__ gcount,
@@ -558,11 +559,15 @@ phis_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin, const i
     constexpr int NA = GRAD ? kNA : 1;
     const int out_stride = GRAD ? 1 + n_par : 1;
     __shared__ MathTables mt;
+    __shared__ int64_t s_take;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int n_wib = blockDim.x >> 5;
+    const int n_wib = kTeam;
     TagSlow* const sbuf = reinterpret_cast<TagSlow*>(dyn_smem) + wib * (kSub * 32);
     PhisWarp& pw = reinterpret_cast<PhisWarp*>(dyn_smem + (size_t)n_wib * kSub * 32 * sizeof(TagSlow))[wib];
+    double* const xbuf = reinterpret_cast<double*>(dyn_smem + (size_t)n_wib * (kSub * 32 * sizeof(TagSlow) +
+                                                                               sizeof(PhisWarp)));
+    double* const xtot = xbuf + (size_t)kTeam * NA * 32;
 
     load_math_tables(&mt);
     __syncthreads();
@@ -580,9 +585,11 @@ phis_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin, const i
 
     int cur = -1;
     while (true) {
-        unsigned taken = 0;
-        if (lane == 0) taken = atomicAdd(work, 1u);
-        const int64_t first = (int64_t)__shfl_sync(0xffffffffu, taken, 0) * per_take;
+        // the team (the block's four warps) takes tiles together
+        if (threadIdx.x == 0) s_take = (int64_t)atomicAdd(work, 1u) * per_take;
+        __syncthreads();
+        const int64_t first = s_take;
+        __syncthreads();
         if (first >= total) break;
         const int64_t stop = first + per_take < total ? first + per_take : total;
         for (int64_t tile = first; tile < stop; ++tile) {
@@ -619,8 +626,9 @@ phis_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin, const i
             int esum = 0;
             const int64_t tbase = ev0 + (tile - t0) * kTile;
             const unsigned below = (1u << lane) - 1u;
-#pragma unroll 1
-            for (int i0 = 0; i0 < kPerLane; i0 += kSub) {
+            // warp w of the team takes events [4 w, 4 w + 4) of each lane's 16
+            {
+                const int i0 = wib * kSub;
                 unsigned m0, m1, m2, m3;
                 {
                     unsigned mk[kSub];
@@ -668,10 +676,30 @@ phis_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin, const i
                 __syncwarp();
             }
             acc[0] += log_of(prod, esum, &mt);
-            warp_allreduce_wide<NA>(acc);
-            if (!tile_commit_wide<NA>(lane, tile, t0, t1, seg, partials, gcount, counters, acc)) continue;
-            phis_finalize<GRAD, CACHED>(pw.c, acc, n_par, out + (size_t)seg * out_stride, lane);
-            if (lane == 0) counters[seg] = 0u;
+            // every warp's sums to shared memory; warp w then reduces accumulators
+            // w, w + 4, ...: the team's four values lane by lane in warp order, then
+            // the xor butterfly over the lanes (the reduction work spread over the
+            // four sub-partitions); warp 0 commits the tile
+#pragma unroll
+            for (int a = 0; a < NA; ++a) xbuf[(wib * NA + a) * 32 + lane] = acc[a];
+            __syncthreads();
+            for (int a = wib; a < NA; a += kTeam) {
+                double v = xbuf[a * 32 + lane];
+                for (int w = 1; w < kTeam; ++w) v += xbuf[(w * NA + a) * 32 + lane];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) xtot[a] = v;
+            }
+            __syncthreads();
+            if (wib == 0) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) acc[a] = xtot[a];
+                if (tile_commit_wide<NA>(lane, tile, t0, t1, seg, partials, gcount, counters, acc)) {
+                    phis_finalize<GRAD, CACHED>(pw.c, acc, n_par, out + (size_t)seg * out_stride, lane);
+                    if (lane == 0) counters[seg] = 0u;
+                }
+            }
+            __syncthreads();
         }
     }
     work_done(work, lane);
@@ -688,18 +716,20 @@ ipa_status launch_phis_t(const Cols& cols, int64_t n, const int64_t* seg_begin, 
         return IPA_ERR_ARG;
     }
     const LaunchCfg cfg = force ? *force : launch_cfg(IPA_MODEL_PHIS, GRAD, CACHED, n_seg > 1, tiles);
-    const int W = cfg.warps_per_block >= 1 && cfg.warps_per_block <= kMaxWarps ? cfg.warps_per_block : 1;
+    // one block = one team of four warps sharing each tile (the geometry's
+    // warps per block does not apply; its tiles per take and resident blocks do)
+    const int W = kTeam;
     const int K = cfg.tiles_per_take >= 1 ? cfg.tiles_per_take : 1;
     const size_t per_warp = sizeof(PhisWarp) + kSub * 32 * sizeof(TagSlow);
-    const size_t smem = (size_t)W * per_warp;
+    constexpr int NA = GRAD ? kNA : 1;
+    const size_t smem = (size_t)W * per_warp + ((size_t)kTeam * NA * 32 + NA) * sizeof(double);
     auto kern = phis_kernel<GRAD, WEIGHTED, CACHED>;
     static bool attr[64] = {};
     static int occ[64][kMaxWarps + 1] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!attr[dev & 63]) {
-        ipa_status q = cuda_fail(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)(kMaxWarps * per_warp)),
+        ipa_status q = cuda_fail(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                  "phi_s kernel attribute");
         if (q != IPA_OK) return q;
         attr[dev & 63] = true;
