@@ -77,19 +77,42 @@ __device__ inline double env_bound(double x, double t_lo, double mu, double sigm
 }  // namespace tdetail
 
 // theta (8 values) -> the record.
-__device__ inline void compute_tag_consts(const ModelDev& m, const double* th, TagConsts* c) {
+// The transcendental inputs of the record, independent of one another (see
+// tag_piece): evaluated side by side by four warps for a few segments.
+struct TagPieces {
+    double F[4], dF[4][3];     // edge(): (t_hi, Gamma_H), (t_lo, Gamma_H), (t_hi, Gamma_L), (t_lo, Gamma_L)
+    double sn, cn;             // sincos(phi_s)
+    double M[3];               // env_bound of Gamma_H, Gamma_L, Gamma
+    double tq;                 // sqrt(39.1 + beta^2)
+};
+constexpr int kTagPieces = 9;
+
+// Piece k: 0-3 the edges, 4 sincos(phi_s), 5-7 the envelope bounds, 8 the cut's root.
+__device__ inline void tag_piece(const ModelDev& m, const double* th, int k, TagPieces* p) {
+    using namespace cdetail;
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], DG = th[IPA_DG];
+    const double GH = Gamma - 0.5 * DG, GL = Gamma + 0.5 * DG;
+    if (k < 4) {
+        edge((k & 1) ? m.t_lo - mu : m.t_hi - mu, k < 2 ? GH : GL, sigma, &p->F[k], p->dF[k]);
+    } else if (k == 4) {
+        sincos(th[IPA_PHIS], &p->sn, &p->cn);
+    } else if (k < 8) {
+        p->M[k - 5] = tdetail::env_bound(k == 5 ? GH : (k == 6 ? GL : Gamma), m.t_lo, mu, sigma);
+    } else {
+        const double beta = th[IPA_DM] * sigma / kSqrt2;
+        p->tq = sqrt(39.1 + beta * beta);
+    }
+}
+
+__device__ inline void compute_tag_consts(const ModelDev& m, const double* th, const TagPieces* pc, TagConsts* c) {
     using namespace cdetail;
     const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
     const double DG = th[IPA_DG], Dm = th[IPA_DM], phi = th[IPA_PHIS], om = th[IPA_OMEGA];
     const double GH = Gamma - 0.5 * DG, GL = Gamma + 0.5 * DG;
-    double FhH, FlH, FhL, FlL, dFhH[3], dFlH[3], dFhL[3], dFlL[3];
-    edge(m.t_hi - mu, GH, sigma, &FhH, dFhH);
-    edge(m.t_lo - mu, GH, sigma, &FlH, dFlH);
-    edge(m.t_hi - mu, GL, sigma, &FhL, dFhL);
-    edge(m.t_lo - mu, GL, sigma, &FlL, dFlL);
+    const double FhH = pc->F[0], FlH = pc->F[1], FhL = pc->F[2], FlL = pc->F[3];
+    const double *dFhH = pc->dF[0], *dFlH = pc->dF[1], *dFhL = pc->dF[2], *dFlL = pc->dF[3];
     const double IH = FhH - FlH, IL = FhL - FlL;
-    double sn, cn;
-    sincos(phi, &sn, &cn);
+    const double sn = pc->sn, cn = pc->cn;
     const double D = 1.0 - 2.0 * om;
     const double wH = 1.0 - cn, wL = 1.0 + cn;
     const double N = wH * IH + wL * IL;
@@ -144,11 +167,9 @@ __device__ inline void compute_tag_consts(const ModelDev& m, const double* th, T
     // t > tcut: Re u <= -sqrt(39.1 + b^2) for all three rates, so |e^{-u^2} w|
     // <= e^{-39.1} ~ 1e-17 relative to the exponential, and Gx < 1e-17
     const double rmax = fmax(fmax(GH, GL), Gamma);
-    const double tc = mu + (rmax * sigma * sigma + sqrt(39.1 + c->beta * c->beta) * kSqrt2 * sigma);
+    const double tc = mu + (rmax * sigma * sigma + pc->tq * kSqrt2 * sigma);
     c->tcut = tc == tc ? tc : INFINITY;
-    const double MH = tdetail::env_bound(GH, m.t_lo, mu, sigma);
-    const double ML = tdetail::env_bound(GL, m.t_lo, mu, sigma);
-    const double MC = tdetail::env_bound(Gamma, m.t_lo, mu, sigma);
+    const double MH = pc->M[0], ML = pc->M[1], MC = pc->M[2];
     c->MS = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(0.5, __dsub_rn(1.0, cn)), MH),
                                 __dmul_rn(__dmul_rn(0.5, __dadd_rn(1.0, cn)), ML)),
                       __dmul_rn(fabs(__dmul_rn(D, sn)), MC));
