@@ -57,25 +57,27 @@ METRIC = "NLL+grad Gevents/s"
 WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 
 # FP64 operations of the fused 4D NLL+gradient kernel, counted from the formula
-# as nll.cu evaluates it (FMA = 2 flops; each FP64 function call counts its
-# cost in DFMA issue slots measured live by ipa_calibrate_fp64, times 2 flops).
-# exp and the angular basis (sin/cos, the ten products, the square root and
-# the amplitude sum A) run on the integer pipe in fixed point (int_math.cuh)
-# and count no FP64 operation; only their arguments and results do:
-#   every event: tau, the exponent of 2E, T2, A' = A cs/2, P, 1/P (an FP32
-#     seed and one FP64 Newton step: 2 FMA), sum r, r T2, S_k (10), r A', u,
-#     Y1..Y3;
-#     unweighted: one multiply into the lane's log product; weighted: w log P;
-#   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma):
-#     the Gaussian's exponent, the erfcx argument and erfcx, g X;
-#   unweighted, once per lane and 512-event tile (16 events): the log of the
-#     product and its exponent term.
+# as nll.cu evaluates it on whole tiles (FMA = 2 flops; each FP64 function call
+# counts its cost in DFMA issue slots measured live by ipa_calibrate_fp64, times
+# 2 flops).  exp, the angular basis (sin/cos, the ten products, the square root,
+# the amplitude sum A'), the ten angular adjoint sums S_k (64-bit fixed point)
+# and the lane's product of the P mantissas run on the integer pipe and count no
+# FP64 operation; only their arguments and results do:
+#   every event: tau, the exponent of 2E, P, 1/P (an FP32 seed and one FP64
+#     Newton step: 2 FMA), sum r, r T2, r A', u = r A' tau, sum u T2;
+#     weighted: w log P and w / P;
+#   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma,
+#     packed 32 to a warp pass): tau, the Gaussian's exponent, the erfcx
+#     argument and erfcx, g X, the exponent of 2E and T2, and the two sums of the
+#     Gaussian terms;
+#   once per lane and 512-event tile (16 events): the log of the product and
+#     its exponent term.
 # (Angles within 2^-17 of |cos| = 1, about 1.5e-5 of the events, take the FP64
 # basis instead; they are not counted.)
-OPS_EVENT_4D = {"fma": 17, "mul": 4, "add": 3}
-OPS_UNWEIGHTED = {"mul": 1}
+OPS_EVENT_4D = {"fma": 5, "mul": 3, "add": 2}
+OPS_UNWEIGHTED = {}
 OPS_WEIGHTED = {"fma": 1, "mul": 1, "log_fast": 1}
-OPS_NEAR_PEAK = {"mul": 4, "add": 2, "erfcx_poly": 1}
+OPS_NEAR_PEAK = {"fma": 3, "mul": 4, "add": 3, "erfcx_poly": 1}
 OPS_LANE_TILE = {"fma": 2, "log_fast": 1}
 
 
@@ -156,6 +158,25 @@ def kernel_traffic(n_events: int):
         if h.hexdigest() != rec["source_sha256"]:
             return None
         return rec["bytes_per_event"] * n_events
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def kernel_counts(kernel: str):
+    """Per-event counts of a kernel from the committed ncu capture
+    (profiles/kernel_counts.json): warp instructions issued, FP64 lane
+    operations and DRAM bytes per event; None if the record is missing or the
+    kernel's sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "kernel_counts.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, "paper_1706_01420_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["per_event"]
     except (OSError, ValueError, KeyError):
         return None
 
@@ -267,18 +288,152 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline(budget_s: float = 12.0) -> dict:
+# ---- the CPU oracle on the host cores (one worker process per core, spawned) ----
+_W = {}
+
+
+def _w_init(kind: str, n: int, seed: int, chunk: int, n_chunks: int):
+    """A worker's chunk [chunk n / n_chunks, (chunk + 1) n / n_chunks) of a seeded
+    synthetic workload (each chunk drawn with its own seed; generation untimed)."""
     from oracle import ipa_oracle as O
     from paper_1706_01420_gb300 import synth
+    _W.clear()
+    m = (chunk + 1) * n // n_chunks - chunk * n // n_chunks
+    if kind in ("4d", "4dw"):
+        _W.update(model=O.Model("4d", 0.0, 15.0), cols=synth.events_4d(m, seed + chunk, weighted=kind == "4dw"),
+                  th=TH4)
+    else:
+        _W.update(model=O.Model("1d", 0.3, 15.0), cols={"t": synth.events_1d(m, seed + chunk)},
+                  th=np.array([0.66, 0.045, 0.0, 0.1]))
+
+
+def _w_pass():
+    from oracle import ipa_oracle as O
+    f, g = O.nll_grad(_W["model"], _W["cols"], _W["th"])
+    return f, list(g)
+
+
+def _w_toy(k: int):
+    """Toy k of the batched workload (Poisson(2e4) events, seed 0): the oracle's
+    generator, then the oracle's fit with all ten parameters free."""
+    from oracle import ipa_oracle as O
+    from paper_1706_01420_gb300 import synth
+    m = O.Model("4d", 0.0, 15.0)
+    n_sig, n_bkg = synth.toy_sizes(k + 1, 2e4, TH4[3], seed=0)
+    toy = O.toy_one(m, TH4, 0, k, int(n_sig[k]), int(n_bkg[k]))
+    lo = np.array([0.3, 0.01, -0.1, 0.0, 0.2, 0.05, 0.0, 0.0, 0.0, -3.2])
+    hi = np.array([1.5, 0.2, 0.1, 0.5, 0.8, 0.5, 6.3, 6.3, 0.5, 3.2])
+    r = O.fit(m, toy, TH4, list(range(10)), lo, hi, tol=1e-8)
+    return r.status
+
+
+def _w_loop(inq, outq):
+    """A worker: runs the commands of its queue until None."""
+    while True:
+        cmd = inq.get()
+        if cmd is None:
+            return
+        if cmd[0] == "init":
+            _w_init(*cmd[1:])
+            outq.put(("init", None))
+        elif cmd[0] == "pass":
+            outq.put(("pass", _w_pass()))
+        else:
+            outq.put(("toy", _w_toy(cmd[1])))
+
+
+class _Workers:
+    """One spawned process per host core (spawn: safe after CUDA was initialised)."""
+
+    def __init__(self, n: int):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.out = ctx.Queue()
+        self.ins = [ctx.Queue() for _ in range(n)]
+        self.procs = [ctx.Process(target=_w_loop, args=(q, self.out), daemon=True) for q in self.ins]
+        for p in self.procs:
+            p.start()
+
+    def run(self, cmds_per_worker: list) -> list:
+        for q, cmds in zip(self.ins, cmds_per_worker):
+            for c in cmds:
+                q.put(c)
+        return [self.out.get(timeout=600)[1] for _ in range(sum(len(c) for c in cmds_per_worker))]
+
+    def close(self):
+        for q in self.ins:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def cpu_baseline(budget_s: float = 12.0) -> dict:
+    """The oracle (numpy/scipy FP64, untuned) on the host cores, on bounded
+    samples of the workloads: one core and all cores on the 4D workload, the 1D
+    workload (passes and a full fit), a 64-toy subset of the batched toys
+    (generation and fit per toy, all cores), one pass over the 5e7-event
+    weighted workload (all cores), and the tagged model on one core."""
+    from oracle import ipa_oracle as O
+    from paper_1706_01420_gb300 import synth
+    cores = os.cpu_count() or 1
     n = 200_000
     cols = synth.events_4d(n, 0)
     model = O.Model("4d", 0.0, 15.0)
     O.nll_grad(model, cols, TH4)
     reps, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
+    while time.perf_counter() - t0 < budget_s * 0.5:
         O.nll_grad(model, cols, TH4)
         reps += 1
     dt = time.perf_counter() - t0
+    out = {"value": n * reps / dt / 1e9, "unit": "Gevents/s", "cores": 1, "kind": "oracle",
+           "sample": f"{reps} NLL+grad passes over {n} events of the 4D workload "
+                     f"({dt:.1f} s, numpy/scipy FP64, single thread)", "host_cores": cores}
+    # the 1D workload on one core: NLL+grad passes and a full fit (Gamma, f_b free)
+    t1d = synth.events_1d(100_000, 0)
+    m1 = O.Model("1d", 0.3, 15.0)
+    th1 = np.array([0.66, 0.045, 0.0, 0.1])
+    r1, t0 = 0, time.perf_counter()
+    while r1 == 0 or time.perf_counter() - t0 < 1.5:
+        O.nll_grad(m1, {"t": t1d}, th1)
+        r1 += 1
+    d1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    f1 = O.fit(m1, {"t": t1d}, th1 + np.array([0.03, 0, 0, -0.02]), [0, 3], np.array([0.3, 0.01, -0.1, 0.0]),
+               np.array([1.5, 0.2, 0.1, 0.5]), tol=1e-10)
+    out["config1_1d"] = {"events": 100_000, "cores": 1, "nll_grad_Mevents_per_s": 1e5 * r1 / d1 / 1e6,
+                         "fit_wall_s": time.perf_counter() - t0, "fit_status": f1.status}
+    # all cores: the 4D workload split over one worker process per core
+    ncore = max(1, cores)
+    w = _Workers(ncore)
+    try:
+        w.run([[("init", "4d", n * ncore, 100, i, ncore)] for i in range(ncore)])
+        w.run([[("pass",)] for _ in range(ncore)])
+        rm, t0 = 0, time.perf_counter()
+        while rm == 0 or time.perf_counter() - t0 < budget_s * 0.3:
+            w.run([[("pass",)] for _ in range(ncore)])
+            rm += 1
+        dm = time.perf_counter() - t0
+        out["all_cores"] = {"value": n * ncore * rm / dm / 1e9, "unit": "Gevents/s", "cores": ncore,
+                            "sample": f"{rm} NLL+grad passes over {n * ncore} events of the 4D workload, "
+                                      f"{n} per worker process"}
+        # 64 toys of the batched workload, oracle generation + fit, dealt round-robin
+        t0 = time.perf_counter()
+        st = w.run([[("toy", k) for k in range(i, 64, ncore)] for i in range(ncore)])
+        dtoy = time.perf_counter() - t0
+        out["config3_toys"] = {"toys": 64, "cores": ncore, "wall_s": dtoy, "toys_per_s": 64 / dtoy,
+                               "converged": sum(1 for x in st if x == "CONVERGED"),
+                               "sample": "toys 0-63 of Poisson(2e4) events (seed 0): the oracle's generator "
+                                         "and fit of all ten parameters per toy"}
+        # one NLL+grad pass over 5e7 weighted events, split over the workers
+        n5 = 50_000_000
+        w.run([[("init", "4dw", n5, 200, i, ncore)] for i in range(ncore)])
+        t0 = time.perf_counter()
+        w.run([[("pass",)] for _ in range(ncore)])
+        d5 = time.perf_counter() - t0
+        out["config5_pass"] = {"events": n5, "weighted": True, "cores": ncore, "wall_s": d5,
+                               "Gevents_per_s": n5 / d5 / 1e9}
+    finally:
+        w.close()
     # the tagged model's oracle on 2e4 events (about a second)
     from oracle import tagged as T
     cols_t = synth.events_tagged(20_000, 0)
@@ -288,11 +443,9 @@ def cpu_baseline(budget_s: float = 12.0) -> dict:
         T.nll_grad(model_t, cols_t, TH_TAG)
         reps_t += 1
     dt_t = time.perf_counter() - t1
-    return {"value": n * reps / dt / 1e9, "unit": "Gevents/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} NLL+grad passes over {n} events of the 4D workload "
-                      f"({dt:.1f} s, numpy/scipy FP64, single thread)",
-            "tagged": {"value": 20_000 * reps_t / dt_t / 1e9, "unit": "Gevents/s",
-                       "sample": f"{reps_t} NLL+grad passes over 20000 events of the tagged workload"}}
+    out["tagged"] = {"value": 20_000 * reps_t / dt_t / 1e9, "unit": "Gevents/s", "cores": 1,
+                     "sample": f"{reps_t} NLL+grad passes over 20000 events of the tagged workload"}
+    return out
 
 
 def main():
@@ -305,6 +458,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="untimed: 4 ipa_nll_grad calls on 8e6 4D events (256 MB, > L2), for ncu")
+    ap.add_argument("--profile-events", type=int, default=8_000_000,
+                    help="events of --profile-case (1000000: the headline workload's size)")
     ap.add_argument("--profile-case-tagged", action="store_true",
                     help="untimed: 4 ipa_nll_grad calls on 8e6 tagged events (128 MB, > L2), for ncu")
     ap.add_argument("--profile-case-phis", action="store_true",
@@ -313,7 +468,7 @@ def main():
                     help="untimed: Example 2's twelve-category fit of 1e4 events, twice, for an ncu launch list")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_events)
     if args.profile_case_tagged:
         return profile_case_tagged()
     if args.profile_case_phis:
@@ -342,11 +497,31 @@ def main():
     cal = api.ipa_calibrate_fp64()
     m = api.model_4d(0.0, 15.0)
     theta = torch.tensor(TH4, device=dev)
-    # 1e6 events distributed like the 4D PDF at the truth: 50 pseudo-experiments of
-    # 2e4 events (10 % background) from the library's generator, seed = rank
-    ev = gen_sample(api, torch, dev, m, theta, 50, 20000, seed=rank)
+    # 1e6 events per GPU distributed like the 4D PDF at the truth: 50 pseudo-
+    # experiments of 2e4 events (10 % background) from the library's generator.
+    # With N > 1 GPUs the job is ONE likelihood over N x 1e6 events: rank r holds
+    # the events shard_bounds(N x 1e6, r, N) (group-aligned, about 1e6 each) and a
+    # step is the event-sharded pass (ipa_nll_grad_shard, an all-gather of the
+    # group partials, ipa_nll_grad_combine), bitwise the one-GPU result.
+    n_total = N_EVENTS * ws
+    sharded = None
+    if ws > 1:
+        from paper_1706_01420_gb300 import shard
+        lo, hi = shard.shard_bounds(n_total, rank, ws)
+        full = gen_sample(api, torch, dev, m, theta, (hi - lo + 19999) // 20000, 20000, seed=1000 + rank)
+        ev = {k: v[:hi - lo].clone() for k, v in full.items()}
+        del full
+        sharded = shard.ShardedNLL(m, ev, n_total, rank, ws)
+    else:
+        ev = gen_sample(api, torch, dev, m, theta, 50, 20000, seed=rank)
     cols_h = {k: v.cpu().numpy() for k, v in ev.items()}
     out = torch.empty(11, dtype=torch.float64, device=dev)
+
+    def step():
+        if sharded is None:
+            api.ipa_nll_grad(m, ev, theta, out)
+        else:
+            sharded.nll_grad(theta, out)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     api.ipa_reserve(N_EVENTS, 4096)
@@ -367,7 +542,7 @@ def main():
               "tuned_step_ms": mean_ms()}
 
     for _ in range(args.warmup):
-        api.ipa_nll_grad(m, ev, theta, out)
+        step()
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -380,7 +555,7 @@ def main():
         for i in range(args.steps):
             flush.fill_(float(i))                        # evict the 32 MB of inputs from L2
             starts[i].record(stream)
-            api.ipa_nll_grad(m, ev, theta, out)
+            step()
             ends[i].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -389,7 +564,7 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms, dev)
-    value = N_EVENTS * ws / (ms_max * 1e-3) / 1e9
+    value = n_total / (ms_max * 1e-3) / 1e9
 
     # kernel-only time of the dominant kernel, measured with events on its stream:
     # the step is [constants kernel (1 thread per fit), fused NLL+grad kernel]; the
@@ -418,44 +593,74 @@ def main():
     pinned = {k: torch.tensor(v).pin_memory() for k, v in cols_h.items()}
     res_h = torch.empty(11, dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * 8 for v in pinned.values())
-    for _ in range(3):
-        api.ipa_nll_grad_host(m, pinned, theta, out)
+    ev_copy = {k: torch.empty_like(v) for k, v in ev.items()} if sharded is not None else None
+
+    def e2e_step():
+        if sharded is None:
+            api.ipa_nll_grad_host(m, pinned, theta, out)
+        else:
+            for k in ev_copy:
+                ev_copy[k].copy_(pinned[k], non_blocking=True)
+            sharded.ev = ev_copy
+            sharded.nll_grad(theta, out)
         res_h.copy_(out, non_blocking=True)
+    for _ in range(3):
+        e2e_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_e2e = max(20, args.steps // 4)
-    e0.record(stream)
-    for _ in range(n_e2e):
-        api.ipa_nll_grad_host(m, pinned, theta, out)
-        res_h.copy_(out, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
-    e2e_val = N_EVENTS * ws / (e2e_ms * 1e-3) / 1e9
+    e2e_steps = []
+    for i in range(n_e2e):
+        flush.fill_(float(i))                            # no step reads host lines cached in L2
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_steps.append(e0.elapsed_time(e1))
+    e2e_ms = max_over_ranks(sum(e2e_steps) / n_e2e, dev)
+    e2e_val = n_total / (e2e_ms * 1e-3) / 1e9
 
     extras = {}
     if not args.no_extras and rank == 0:
         extras = run_extras(api, synth, torch, dev, m, ev, theta, cal)
 
     clocks = clk.summary()
+    counts = kernel_counts("nll_kernel<4D, grad>")
+    inst_pe = counts["warp_inst"] if counts else None
+    fp64_pe = counts["fp64_lane_ops"] if counts else None
+    if counts and traffic is None:
+        traffic = counts["dram_bytes"] * N_EVENTS
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    issue_peak = 4.0 * 152 * sm_mhz * 1e6 / 1e9
+    issue_achieved = inst_pe * N_EVENTS / (kernel_ms * 1e-3) / 1e9 if inst_pe else None
     line = {
         "metric": METRIC, "value": value, "unit": "Gevents/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events": N_EVENTS, "step": "ipa_nll_grad (a1-a6)",
-                   "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas",
+        "config": {"workload": WORKLOAD, "events": n_total, "events_per_gpu": int(ev["t"].numel()),
+                   "step": "ipa_nll_grad (a1-a6)" if ws == 1 else
+                           "ipa_nll_grad_shard + all-gather of group partials + ipa_nll_grad_combine (a1-a6)",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "one GPU" if ws == 1 else f"events sharded over {ws} GPUs",
                    "launch": launch},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (2 if ws == 1 else 5) * args.steps,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "Gevents/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 88,
-                "ms_per_step": e2e_ms},
-        "roofline": {"bound": "alu", "achieved": ops_achieved, "peak": peak_dfma_derived / 1e9,
-                     "unit": "G FP64 op/s", "frac": ops_achieved * 1e9 / peak_dfma_derived, "traffic": traffic,
-                     "kernel": "nll_kernel<4D, grad>", "kernel_ms": kernel_ms,
-                     "fp64_ops_per_event": spe, "near_peak_fraction": near,
-                     "peak_note": "FP64 pipe: 2 operations/clk/SM x 152 SMs x 2070 MHz (derived); DFMA loop "
-                                  f"measured {cal['dfma_per_s'] * 1e-9:.0f} G/s at {cal['sm_mhz']:.0f} MHz, "
-                                  f"{cal['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM",
+                "ms_per_step": e2e_ms, "l2": "flushed (256 MB write) before every step"},
+        "roofline": {"bound": "alu", "resource": "instruction issue (all pipes)",
+                     "achieved": issue_achieved, "peak": issue_peak, "unit": "G warp instructions/s",
+                     "frac": issue_achieved / issue_peak if issue_achieved is not None else None,
+                     "traffic": traffic, "kernel": "nll_kernel<4D, grad>", "kernel_ms": kernel_ms,
+                     "warp_instructions_per_event": inst_pe,
+                     "peak_note": "4 warp instructions/clk/SM x 152 SMs x the SM clock sampled during the timed "
+                                  "region; instructions per event from the ncu capture of the current source "
+                                  "(profiles/kernel_counts.json)",
+                     "fp64": {"achieved": ops_achieved, "peak": peak_dfma_derived / 1e9, "unit": "G FP64 op/s",
+                              "frac": ops_achieved * 1e9 / peak_dfma_derived, "fp64_ops_per_event": spe,
+                              "fp64_lane_ops_per_event_ncu": fp64_pe, "near_peak_fraction": near,
+                              "peak_note": "FP64 pipe: 2 operations/clk/SM x 152 SMs x 2070 MHz (derived); DFMA loop "
+                                           f"measured {cal['dfma_per_s'] * 1e-9:.0f} G/s at {cal['sm_mhz']:.0f} MHz, "
+                                           f"{cal['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM"},
                      "flops": {"per_event": fpe, "achieved_tflops": achieved, "peak_tflops": peak,
                                "frac": achieved / peak},
                      "library_formula": {"flops_per_event": _flops(OPS_LIBRARY_4D, cal),
@@ -499,14 +704,19 @@ def gen_sample(api, torch, dev, m, theta, n_toys: int, per: int, seed: int) -> d
     return cols
 
 
-def profile_case() -> int:
-    """A small fixed case for Nsight Compute: inputs larger than L2, few launches."""
+def profile_case(n: int = 8_000_000) -> int:
+    """A small fixed case for Nsight Compute: 8e6 events (inputs larger than L2)
+    or the headline workload's 1e6 (drawn from the 4D PDF like the bench's), few
+    launches."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1706_01420_gb300 import api, synth
-    n = 8_000_000
-    ev = {k: torch.tensor(v, device="cuda") for k, v in synth.events_4d(n, 3).items()}
+    if n == N_EVENTS:
+        ev = gen_sample(api, torch, torch.device("cuda"), api.model_4d(0.0, 15.0), torch.tensor(TH4, device="cuda"),
+                        50, 20000, seed=0)
+    else:
+        ev = {k: torch.tensor(v, device="cuda") for k, v in synth.events_4d(n, 3).items()}
     m = api.model_4d(0.0, 15.0)
     theta = torch.tensor(TH4, device="cuda")
     for _ in range(4):
@@ -811,6 +1021,15 @@ def run_phis(api, synth, torch, dev, flush, steps: int = 30) -> dict:
         ms = statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
         res["nll_grad_ms_" + name] = ms
         res["Gevents_per_s_" + name] = 1e6 / (ms * 1e-3) / 1e9
+    counts = kernel_counts("phis_kernel<grad>")
+    if counts:
+        ops = counts["fp64_lane_ops"] * 1e6 / (res["nll_grad_ms_raw"] * 1e-3)
+        peak = 2.0 * 152 * 2070e6
+        res["roofline"] = {"bound": "alu", "resource": "FP64 pipe", "kernel": "phis_kernel<grad>",
+                           "achieved": ops / 1e9, "peak": peak / 1e9, "unit": "G FP64 op/s", "frac": ops / peak,
+                           "fp64_lane_ops_per_event": counts["fp64_lane_ops"],
+                           "note": "FP64 lane operations per event from the ncu capture of the current source "
+                                   "(profiles/kernel_counts.json); step time of the raw-basis call"}
     return res
 
 
@@ -950,37 +1169,46 @@ def run_cls(api, torch, dev, n_bins: int = 10000, n_toys: int = 10000) -> dict:
             "cl_b": float(r["cl_b"]), "cl_sb": float(r["cl_sb"]), "cl_s": float(r["cl_s"])}
 
 
-def run_serve(api, synth, torch, dev, m, theta, params, n_req: int = 60,
-              rates=(25.0, 50.0, 100.0, 200.0)) -> dict:
+SERVE_PLAN = {200.0: (2000, 2000), 100.0: (1000, 500), 50.0: (1000, 500), 25.0: (1000, 500)}
+
+
+def run_serve(api, synth, torch, dev, m, theta, params, plan: dict | None = None) -> dict:
     """Fit requests arriving Poisson at each rate, sizes log-uniform on [1e3, 1e7],
     weights Normal(1, 0.2), events of the 4D PDF: latency (arrival -> result) and
     throughput of the continuous-batching server vs plain sequential fits (one
-    ipa_fit_batch call per request, first come first served)."""
+    ipa_fit_batch call per request, first come first served).  plan: rate ->
+    (requests served, requests of the plain loop, the first of the same stream);
+    2000 requests at the configuration's 200/s, so that p99 is a percentile of
+    2000 latencies."""
+    plan = SERVE_PLAN if plan is None else plan
     pool_n = 20_000_000
     cols = gen_sample(api, torch, dev, m, theta, pool_n // 20000, 20000, seed=9)
     pool = {k: v.cpu().numpy() for k, v in cols.items()}
     del cols
     pool["w"] = synth.weights(pool_n, 13)
     d64 = lambda a: torch.tensor(a, dtype=torch.int64, device=dev)
-    out = {"requests_per_rate": n_req, "sizes": "log-uniform [1e3, 1e7]", "weights": "Normal(1, 0.2)"}
+    out = {"requests": {str(int(r)): {"served": a, "plain": b} for r, (a, b) in plan.items()},
+           "sizes": "log-uniform [1e3, 1e7]", "weights": "Normal(1, 0.2)"}
 
-    def slices(rate):
+    def slices(rate, n_req):
         reqs = synth.request_stream(n_req, rate, seed=int(rate))
         rng = np.random.default_rng(int(rate) + 1)
         return [(r.arrival_s, int(rng.integers(0, pool_n - r.n_events)), r.n_events) for r in reqs]
 
-    for rate in rates:
-        plan = slices(rate)
+    for rate in sorted(plan, reverse=True):
+        n_served, n_plain = plan[rate]
+        full = slices(rate, n_served)
+        plan_r = full
         srv = api.ipa_server_create(m, 16 << 30, max_slots=64, max_iter=200, tol=1e-8)
         lat, done_t = {}, {}
         try:
             pending = {}
             t0 = time.perf_counter()
             i = 0
-            while len(lat) < len(plan):
+            while len(lat) < len(plan_r):
                 now = time.perf_counter() - t0
-                while i < len(plan) and plan[i][0] <= now:
-                    arr, a, n = plan[i]
+                while i < len(plan_r) and plan_r[i][0] <= now:
+                    arr, a, n = plan_r[i]
                     ev = {k: v[a:a + n] for k, v in pool.items()}
                     pending[api.ipa_serve_submit(srv, ev, params)] = (i, arr)
                     i += 1
@@ -994,12 +1222,12 @@ def run_serve(api, synth, torch, dev, m, theta, params, n_req: int = 60,
                 time.sleep(0.0005)
         finally:
             api.ipa_server_destroy(srv)
-        ls = np.array([lat[k] for k in range(len(plan))])
-        span = max(done_t.values()) - plan[0][0]
+        ls = np.array([lat[k] for k in range(len(plan_r))])
+        span = max(done_t.values()) - plan_r[0][0]
         # plain sequential: one fit call per request, first come first served
         plat = []
         t0 = time.perf_counter()
-        for arr, a, n in plan:
+        for arr, a, n in full[:n_plain]:
             now = time.perf_counter() - t0
             if now < arr:
                 time.sleep(arr - now)
@@ -1008,13 +1236,13 @@ def run_serve(api, synth, torch, dev, m, theta, params, n_req: int = 60,
             api.ipa_fit_batch(m, ev, d64([0, n]), params, th, max_iter=200, tol=1e-8)
             torch.cuda.synchronize()
             plat.append(time.perf_counter() - t0 - arr)
-        pspan = time.perf_counter() - t0 - plan[0][0]
+        pspan = time.perf_counter() - t0 - plan_r[0][0]
         pl = np.array(plat)
         out[f"rate_{int(rate)}"] = {
             "served": {"p50_s": float(np.percentile(ls, 50)), "p99_s": float(np.percentile(ls, 99)),
-                       "fits_per_s": len(plan) / span},
+                       "fits_per_s": len(plan_r) / span, "requests": len(plan_r)},
             "plain_sequential": {"p50_s": float(np.percentile(pl, 50)), "p99_s": float(np.percentile(pl, 99)),
-                                 "fits_per_s": len(plan) / pspan}}
+                                 "fits_per_s": n_plain / pspan, "requests": n_plain}}
     return out
 
 

@@ -42,6 +42,11 @@
  *   - Non-physical parameters (sigma <= 0, Gamma <= 0, fractions outside [0,1])
  *     are not rejected on the host (theta lives on the device); they produce
  *     NaN results, which the fitter reports as IPA_FIT_BAD_PDF.
+ *   - The library keeps per-device state between calls (scratch, streams,
+ *     captured graphs, fitter workspace).  It belongs to the device's current
+ *     context: a device reset (cudaDeviceReset) between calls is not supported,
+ *     except by ipa_nll_grad_noalloc, which looks its array up again in a new
+ *     context.
  */
 #ifndef IPANEMA_H
 #define IPANEMA_H
@@ -295,6 +300,75 @@ ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev, const int
                          int32_t* iters_out_dev, int32_t* passes_out_dev, int32_t max_iter, double tol,
                          void* stream);
 
+/* ---- stepwise fits: the minimiser of ipa_fit_batch driven one pass at a time ----
+ * Sec. 3 hands Minuit an FCN that the GPU evaluates; here the caller evaluates
+ * the NLL and gradient (ipa_nll_grad_segmented, or the event-sharded
+ * ipa_nll_grad_shard + ipa_nll_grad_combine over several GPUs) and the library
+ * advances every fit's quasi-Newton state machine on the device (the same
+ * kernels as ipa_fit_batch: BFGS line search, finite-difference Hessian,
+ * Newton steps; given the same evaluations the fits follow the same path).
+ * The state of n_fits fits lives in one device buffer the caller owns
+ * (ipa_fit_state_bytes bytes, 256-byte aligned).  Its first n_fits x n_par
+ * doubles are the points the fits want evaluated next (row i: fit i); the rest
+ * holds the specification and each fit's minimiser state as plain data, so a
+ * copy of the buffer taken between two passes resumes the fits bit for bit
+ * (the analogue of the ParamBox fit summary the paper saves, App. B).  The
+ * calls are asynchronous on `stream` and allocate nothing. */
+uint64_t ipa_fit_state_bytes(int32_t n_fits, int32_t n_par);   /* 0 for bad sizes */
+
+/* Start n_fits fits at theta0_dev (n_fits x n_par, device), with the limits,
+ * steps and fixed flags of spec (host, n_par entries; start values are taken
+ * from theta0_dev) and the tolerance and budget of ipa_fit_batch.  Writes the
+ * state and the first points to evaluate. */
+ipa_status ipa_fit_begin(const ipa_model* model, const ipa_param* spec, int32_t n_fits, const double* theta0_dev,
+                         int32_t max_iter, double tol, void* state_dev, void* stream);
+
+/* One pass: results_dev (n_fits x (1 + n_par), device) holds the NLL and
+ * gradient at each fit's current point (the first rows of the state).  Every
+ * fit still running takes its step and writes its next point; *n_active_dev
+ * (device int32) receives the number of fits still running (0: all done).
+ * Rows of finished fits are not read. */
+ipa_status ipa_fit_advance(const ipa_model* model, int32_t n_fits, const double* results_dev, void* state_dev,
+                           int32_t* n_active_dev, void* stream);
+
+/* The fits' results from their state, as ipa_fit_batch writes them (theta_out
+ * n_fits x n_par; the other outputs may be NULL). */
+ipa_status ipa_fit_end(const ipa_model* model, int32_t n_fits, const void* state_dev, double* theta_out_dev,
+                       double* err_out_dev, double* nll_out_dev, int32_t* fit_status_dev, int32_t* iters_out_dev,
+                       int32_t* passes_out_dev, void* stream);
+
+/* ---- event-sharded likelihood over several GPUs (one process per GPU) ----
+ * The NLL and its gradient are sums over events (Sec. 3: the PDF is evaluated
+ * one thread per event and the log-likelihoods are summed).  Rank r of W holds
+ * the contiguous events [a_r, b_r) of the fit, with every a_r a multiple of
+ * IPA_SHARD_EVENTS (16384 events: one group of 32 tiles of the kernel's fixed
+ * reduction tree).  Each rank calls ipa_nll_grad_shard on its events; the
+ * ranks all-gather the group partials in rank order (ceil((b_r - a_r) /
+ * IPA_SHARD_EVENTS) rows of ipa_shard_width doubles per rank); every rank then
+ * calls ipa_nll_grad_combine on the gathered rows.  The combine runs the last,
+ * fixed-order level of the reduction and the gradient contraction, so every
+ * rank obtains exactly the bits that ipa_nll_grad gives for all events on one
+ * GPU, whatever the number of ranks.  Exchanged per pass: 8 x width bytes per
+ * 16384 events (120 doubles per 1.3e5 events for the 4D model). */
+#define IPA_SHARD_EVENTS 16384
+
+/* Doubles per group partial for this model (15 for 4D, 6 for 1D, 13 tagged,
+ * 47 phi_s). */
+ipa_status ipa_shard_width(const ipa_model* model, int32_t* width);
+
+/* ipa_nll_grad over this rank's events (out_dev: 1 + n_par doubles, this
+ * shard's own NLL and gradient), plus its group partials into groups_dev
+ * (device, ceil(n / IPA_SHARD_EVENTS) x ipa_shard_width doubles; not written
+ * for n = 0). */
+ipa_status ipa_nll_grad_shard(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
+                              double* out_dev, double* groups_dev, void* stream);
+
+/* NLL and gradient (out_dev, 1 + n_par doubles) from n_groups gathered group
+ * partials (groups_dev, device, in event order), at theta_dev; cached: the
+ * shards used a cached angular basis (ev->fk).  n_groups = 0 gives zeros. */
+ipa_status ipa_nll_grad_combine(const ipa_model* model, const double* theta_dev, const double* groups_dev,
+                                int64_t n_groups, int32_t cached, double* out_dev, void* stream);
+
 /* A simultaneous fit over categories (Sec. 4, Example 2: one -2 log L summed
  * over 12 categories, six m(KK) bins times two B flavours, that share most
  * parameters while the S-wave parameters are per bin and C_SP is a constant of
@@ -505,11 +579,38 @@ ipa_status ipa_server_destroy(ipa_server* server);
 ipa_status ipa_nll_grad_noalloc(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
                                 double* out_dev, void* stream);
 
+/* Host-side fault injection for tests of the error paths (the paper has no
+ * counterpart).  Sets the mask and returns the previous one; nothing is ever
+ * injected on the device.
+ *   IPA_FAULT_ALLOC   every device allocation the library makes (scratch,
+ *                     fitter workspace, server memory) fails with IPA_ERR_OOM
+ *                     without calling cudaMalloc; state already allocated is
+ *                     kept, and calls succeed again once the bit is cleared;
+ *   IPA_FAULT_SUBMIT  ipa_serve_submit returns IPA_ERR_OOM before it takes the
+ *                     request (as if its staging allocation failed); the caller
+ *                     still holds the events and may submit them again;
+ *   IPA_FAULT_ADMIT   the fit server admits no queued fit: queued requests
+ *                     keep their place and are admitted once the bit is cleared.
+ * The environment variable IPA_FAULT ("alloc", "submit", "admit", comma
+ * separated) sets the mask when the library is loaded. */
+#define IPA_FAULT_ALLOC 1u
+#define IPA_FAULT_SUBMIT 2u
+#define IPA_FAULT_ADMIT 4u
+uint32_t ipa_fault_inject(uint32_t mask);
+
 /* Grow the library's device scratch on the current device to hold one call
  * over `max_events` events in up to `max_segments` segments, so that later
  * calls allocate nothing (needed before CUDA-graph capture).  Calls allocate
  * on demand otherwise. */
 ipa_status ipa_reserve(int64_t max_events, int32_t max_segments);
+
+/* Bytes of device memory that the library's per-device scratch (the buffers
+ * that ipa_reserve grows and that ipa_nll, ipa_nll_grad, the segmented, joint
+ * and fitting calls use) holds on the current device; 0 before the first such
+ * call.  A diagnostic with no counterpart in the paper: it lets a caller check
+ * that a sequence of calls (for example ipa_nll_grad_noalloc alone) allocated
+ * no scratch.  IPA_ERR_ARG if bytes is NULL. */
+ipa_status ipa_scratch_bytes(uint64_t* bytes);
 
 /* ---- launch geometry and its autotuner (the paper has no counterpart: its
  * kernels use one thread per event and a host-side sum, Sec. 3) ----

@@ -19,6 +19,8 @@ IPA_DG, IPA_DM, IPA_PHIS, IPA_OMEGA = 4, 5, 6, 7
 IPA_PHIS_DG, IPA_PHIS_DM, IPA_PHIS_PHIS, IPA_PHIS_OMEGA, IPA_PHIS_CSP, IPA_PHIS_QNORM = 10, 11, 12, 13, 14, 15
 IPA_NPAR_1D, IPA_NPAR_4D, IPA_NPAR_TAGGED, IPA_NPAR_PHIS, IPA_MAX_PAR = 4, 10, 8, 16, 32
 IPA_NOALLOC_MAX_EVENTS = 8388608
+IPA_SHARD_EVENTS = 16384
+IPA_FAULT_ALLOC, IPA_FAULT_SUBMIT, IPA_FAULT_ADMIT = 1, 2, 4
 IPA_MATH_EXP, IPA_MATH_LOG, IPA_MATH_SIN, IPA_MATH_COS, IPA_MATH_ERFCX, IPA_MATH_RCP = range(6)
 IPA_FIT_CONVERGED, IPA_FIT_MAXITER, IPA_FIT_AT_LIMIT, IPA_FIT_BAD_PDF, IPA_FIT_EMPTY = range(5)
 (IPA_MINOS_OK, IPA_MINOS_MAXROUNDS, IPA_MINOS_AT_LIMIT, IPA_MINOS_FIT_FAILED, IPA_MINOS_NEW_MINIMUM,
@@ -96,6 +98,19 @@ PROTOTYPES = {
                                  POINTER(c_int32)]),
     "ipa_server_destroy": (c_int32, [c_void_p]),
     "ipa_reserve": (c_int32, [c_int64, c_int32]),
+    "ipa_fit_state_bytes": (c_uint64, [c_int32, c_int32]),
+    "ipa_fit_begin": (c_int32, [POINTER(ipa_model), POINTER(ipa_param), c_int32, c_void_p, c_int32, c_double,
+                                c_void_p, c_void_p]),
+    "ipa_fit_advance": (c_int32, [POINTER(ipa_model), c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ipa_fit_end": (c_int32, [POINTER(ipa_model), c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_void_p]),
+    "ipa_shard_width": (c_int32, [POINTER(ipa_model), POINTER(c_int32)]),
+    "ipa_nll_grad_shard": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_void_p, c_void_p,
+                                     c_void_p]),
+    "ipa_nll_grad_combine": (c_int32, [POINTER(ipa_model), c_void_p, c_void_p, c_int64, c_int32, c_void_p,
+                                       c_void_p]),
+    "ipa_scratch_bytes": (c_int32, [POINTER(c_uint64)]),
+    "ipa_fault_inject": (ctypes.c_uint32, [ctypes.c_uint32]),
     "ipa_autotune": (c_int32, [POINTER(ipa_model), POINTER(ipa_events), c_void_p, c_int32, c_void_p, c_int32,
                                POINTER(ipa_launch_config), c_void_p]),
     "ipa_launch_config_get": (c_int32, [POINTER(ipa_model), c_int64, c_int32, c_int32, c_int32,

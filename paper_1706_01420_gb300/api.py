@@ -170,6 +170,49 @@ def ipa_nll_grad_noalloc(model: C.ipa_model, ev: dict, theta: torch.Tensor, out:
     return out
 
 
+def ipa_shard_width(model: C.ipa_model) -> int:
+    """Doubles per group partial of the event-sharded likelihood."""
+    w = ctypes.c_int32(0)
+    _check(_lib().ipa_shard_width(ctypes.byref(model), ctypes.byref(w)), "ipa_shard_width")
+    return int(w.value)
+
+
+def shard_groups(n: int) -> int:
+    """Group partials of a shard of n events: ceil(n / IPA_SHARD_EVENTS)."""
+    return (n + C.IPA_SHARD_EVENTS - 1) // C.IPA_SHARD_EVENTS
+
+
+def ipa_nll_grad_shard(model: C.ipa_model, ev: dict, theta: torch.Tensor, out: torch.Tensor | None = None,
+                       groups: torch.Tensor | None = None, stream=None):
+    """This rank's NLL + gradient and its group partials (shard_groups(n) x width)."""
+    n = int(ev["t"].numel())
+    out = torch.empty(1 + model.n_par, dtype=torch.float64, device=theta.device) if out is None else out
+    if groups is None:
+        groups = torch.empty(shard_groups(n), ipa_shard_width(model), dtype=torch.float64, device=theta.device)
+    _need(theta, model.n_par, "theta")
+    _need(out, 1 + model.n_par, "out")
+    _need(groups, shard_groups(n) * ipa_shard_width(model), "groups")
+    e = ipa_events(ev)
+    _check(_lib().ipa_nll_grad_shard(ctypes.byref(model), ctypes.byref(e), _ptr(theta, name="theta"),
+                                     _ptr(out, name="out"), _ptr(groups, name="groups") if groups.numel() else None,
+                                     _stream(stream)), "ipa_nll_grad_shard")
+    return out, groups
+
+
+def ipa_nll_grad_combine(model: C.ipa_model, theta: torch.Tensor, groups: torch.Tensor, cached: bool = False,
+                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """NLL + gradient from gathered group partials (rows in event order)."""
+    out = torch.empty(1 + model.n_par, dtype=torch.float64, device=theta.device) if out is None else out
+    _need(theta, model.n_par, "theta")
+    _need(out, 1 + model.n_par, "out")
+    width = ipa_shard_width(model)
+    n_groups = int(groups.numel()) // width
+    _check(_lib().ipa_nll_grad_combine(ctypes.byref(model), _ptr(theta, name="theta"),
+                                       _ptr(groups, name="groups") if n_groups else None, n_groups, int(cached),
+                                       _ptr(out, name="out"), _stream(stream)), "ipa_nll_grad_combine")
+    return out
+
+
 def ipa_nll_grad_segmented(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, theta: torch.Tensor,
                            out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     n_seg = int(seg_off.numel()) - 1
@@ -218,6 +261,53 @@ def _spec(params: list[Param]):
             (p.hi - p.lo) / 10 if p.hi < 1e299 and p.lo > -1e299 else 0.0)
         arr[i].fixed = 1 if p.fixed else 0
     return arr
+
+
+def ipa_fit_state_bytes(n_fits: int, n_par: int) -> int:
+    return int(_lib().ipa_fit_state_bytes(n_fits, n_par))
+
+
+def fit_state_new(n_fits: int, n_par: int, device) -> torch.Tensor:
+    """A zeroed uint8 CUDA buffer for the state of n_fits stepwise fits (the
+    caching allocator's blocks are 512-byte aligned)."""
+    return torch.zeros(ipa_fit_state_bytes(n_fits, n_par), dtype=torch.uint8, device=device)
+
+
+def fit_state_points(state: torch.Tensor, n_fits: int, n_par: int) -> torch.Tensor:
+    """View of the points the fits want evaluated next (the state's first rows)."""
+    return state[:8 * n_fits * n_par].view(torch.float64).view(n_fits, n_par)
+
+
+def ipa_fit_begin(model: C.ipa_model, params: list[Param], theta0: torch.Tensor, state: torch.Tensor,
+                  max_iter: int = 100, tol: float = 1e-9, stream=None):
+    n_fits = int(theta0.numel()) // model.n_par
+    _need(state, ipa_fit_state_bytes(n_fits, model.n_par), "state")
+    _check(_lib().ipa_fit_begin(ctypes.byref(model), _spec(params), n_fits, _ptr(theta0, name="theta0"),
+                                max_iter, tol, _ptr(state, torch.uint8, "state"), _stream(stream)), "ipa_fit_begin")
+
+
+def ipa_fit_advance(model: C.ipa_model, n_fits: int, results: torch.Tensor, state: torch.Tensor,
+                    n_active: torch.Tensor, stream=None):
+    _need(results, n_fits * (1 + model.n_par), "results")
+    _check(_lib().ipa_fit_advance(ctypes.byref(model), n_fits, _ptr(results, name="results"),
+                                  _ptr(state, torch.uint8, "state"), _ptr(n_active, torch.int32, "n_active"),
+                                  _stream(stream)), "ipa_fit_advance")
+
+
+def ipa_fit_end(model: C.ipa_model, n_fits: int, state: torch.Tensor, stream=None) -> dict:
+    dev = state.device
+    out = {"theta": torch.empty(n_fits, model.n_par, dtype=torch.float64, device=dev),
+           "err": torch.empty(n_fits, model.n_par, dtype=torch.float64, device=dev),
+           "nll": torch.empty(n_fits, dtype=torch.float64, device=dev),
+           "status": torch.empty(n_fits, dtype=torch.int32, device=dev),
+           "iters": torch.empty(n_fits, dtype=torch.int32, device=dev),
+           "passes": torch.empty(n_fits, dtype=torch.int32, device=dev)}
+    _check(_lib().ipa_fit_end(ctypes.byref(model), n_fits, _ptr(state, torch.uint8, "state"),
+                              _ptr(out["theta"], name="theta"), _ptr(out["err"], name="err"),
+                              _ptr(out["nll"], name="nll"), _ptr(out["status"], torch.int32, "status"),
+                              _ptr(out["iters"], torch.int32, "iters"), _ptr(out["passes"], torch.int32, "passes"),
+                              _stream(stream)), "ipa_fit_end")
+    return out
 
 
 def ipa_fit_batch(model: C.ipa_model, ev: dict, seg_off: torch.Tensor, params: list[Param],
@@ -492,6 +582,18 @@ def ipa_server_destroy(server):
 
 def ipa_reserve(max_events: int, max_segments: int = 1):
     _check(_lib().ipa_reserve(max_events, max_segments), "ipa_reserve")
+
+
+def ipa_fault_inject(mask: int) -> int:
+    """Set the host-side fault-injection mask (IPA_FAULT_*); returns the previous one."""
+    return int(_lib().ipa_fault_inject(mask))
+
+
+def ipa_scratch_bytes() -> int:
+    """Device bytes held by the library's per-device scratch on the current device."""
+    v = ctypes.c_uint64(0)
+    _check(_lib().ipa_scratch_bytes(ctypes.byref(v)), "ipa_scratch_bytes")
+    return int(v.value)
 
 
 def _cfg_dict(c: C.ipa_launch_config) -> dict:

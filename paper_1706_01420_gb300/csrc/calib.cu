@@ -123,12 +123,12 @@ extern "C" ipa_status ipa_calibrate_fp64(double* results, void* stream) {
     double *in = nullptr, *out = nullptr;
     long long* cyc = nullptr;
     ipa_status st;
-    if ((st = cuda_fail(cudaMalloc(&in, sizeof(double) * n), "calibration alloc")) != IPA_OK) return st;
-    if ((st = cuda_fail(cudaMalloc(&out, sizeof(double) * n), "calibration alloc")) != IPA_OK) {
+    if ((st = device_alloc((void**)&in, sizeof(double) * n, "calibration alloc")) != IPA_OK) return st;
+    if ((st = device_alloc((void**)&out, sizeof(double) * n, "calibration alloc")) != IPA_OK) {
         cudaFree(in);
         return st;
     }
-    if ((st = cuda_fail(cudaMalloc(&cyc, sizeof(long long) * blocks), "calibration alloc")) != IPA_OK) {
+    if ((st = device_alloc((void**)&cyc, sizeof(long long) * blocks, "calibration alloc")) != IPA_OK) {
         cudaFree(in);
         cudaFree(out);
         return st;

@@ -198,11 +198,27 @@ __device__ inline void it_quotient(int i, const ModelDev& m, const double* th, d
 }
 constexpr int kItQuotients = 5;
 
+// Whether theta lies in the model's domain: Gamma > 0, sigma > 0, f_b in
+// [0, 1] and (4D) F_S, |A_0|^2, |A_perp|^2 and |A_par|^2 = 1 - |A_0|^2 -
+// |A_perp|^2 in [0, 1] (false for NaN).  Outside, the PDF is not a density.
+__device__ inline bool in_domain(const double* th, bool four) {
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], fb = th[IPA_FB];
+    bool ok = Gamma > 0.0 && sigma > 0.0 && fb >= 0.0 && fb <= 1.0;
+    if (four) {
+        const double x0 = th[IPA_A0SQ], xe = th[IPA_APESQ], F = th[IPA_FS];
+        ok = ok && F >= 0.0 && F <= 1.0 && x0 >= 0.0 && xe >= 0.0 && x0 + xe <= 1.0;
+    }
+    return ok;
+}
+
 // Scalars of the record without a division, and the quotients q[] of
-// scalar_quotient (q[0..5]) and it_quotient (q[6..10]).
+// scalar_quotient (q[0..5]) and it_quotient (q[6..10]).  For theta outside the
+// domain cs and cb are NaN, so that every P, the NLL and the gradient are NaN
+// (the fitter reports such a point as IPA_FIT_BAD_PDF).
 __device__ inline void write_plain_scalars(const double* th, double IT, double MT, double MO, bool four,
                                            const double* q, Consts* c) {
     const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
+    const bool ok = in_domain(th, four);
     c->Gamma = Gamma;
     c->sigma = sigma;
     c->mu = mu;
@@ -220,8 +236,8 @@ __device__ inline void write_plain_scalars(const double* th, double IT, double M
     for (int j = 0; j < 3; ++j) c->dlnIT[j] = q[6 + j];
     c->MT = MT;
     c->MO = four ? MO : 1.0;
-    c->cs = q[9];
-    c->cb = q[4];
+    c->cs = ok ? q[9] : NAN;
+    c->cb = ok ? q[4] : NAN;
     c->inv_ITIO = q[10];
     c->inv_V = q[5];
     c->pad_ = 0.0;

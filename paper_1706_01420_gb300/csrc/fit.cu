@@ -98,7 +98,7 @@ ipa_status ensure_capacity(FitContext& c, int n_fits, int P) {
         if (st != IPA_OK) return st;
     }
     if (!c.nact) {
-        ipa_status st = cuda_fail(cudaMalloc(&c.nact, sizeof(int) * (kGraphSteps + 1)), "fit count");
+        ipa_status st = device_alloc((void**)&c.nact, sizeof(int) * (kGraphSteps + 1), "fit count");
         if (st == IPA_OK) st = cuda_fail(cudaMallocHost(&c.h_nact, sizeof(int) * kGraphSteps), "pinned count");
         if (st != IPA_OK) return st;
     }
@@ -116,10 +116,10 @@ ipa_status ensure_capacity(FitContext& c, int n_fits, int P) {
     c.active = nullptr;
     c.cap = 0;
     const size_t n = (size_t)cap;
-    ipa_status st = cuda_fail(cudaMalloc(&c.states, sizeof(State) * n), "fit state");
-    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.theta_eval, sizeof(double) * n * kMaxP), "fit theta");
-    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.res, sizeof(double) * n * (1 + kMaxP)), "fit results");
-    if (st == IPA_OK) st = cuda_fail(cudaMalloc(&c.active, sizeof(int) * n), "fit mask");
+    ipa_status st = device_alloc((void**)&c.states, sizeof(State) * n, "fit state");
+    if (st == IPA_OK) st = device_alloc((void**)&c.theta_eval, sizeof(double) * n * kMaxP, "fit theta");
+    if (st == IPA_OK) st = device_alloc((void**)&c.res, sizeof(double) * n * (1 + kMaxP), "fit results");
+    if (st == IPA_OK) st = device_alloc((void**)&c.active, sizeof(int) * n, "fit mask");
     if (st == IPA_OK) c.cap = cap;
     (void)P;
     return st;
@@ -143,7 +143,7 @@ BatchArgs* batch_args_of_device() {
 
 // Grow the arguments buffer to n_fits fits (the caller holds a.mu).
 ipa_status batch_args_reserve(BatchArgs& a, int n_fits) {
-    if (!a.spec && cudaMalloc(&a.spec, sizeof(Spec)) != cudaSuccess) {
+    if (!a.spec && device_alloc((void**)&a.spec, sizeof(Spec), "fit spec") != IPA_OK) {
         a.spec = nullptr;
         set_error("fit spec allocation failed");
         return IPA_ERR_OOM;
@@ -155,7 +155,7 @@ ipa_status batch_args_reserve(BatchArgs& a, int n_fits) {
     cudaFree(a.seg_off);
     a.seg_off = nullptr;
     a.cap = 0;
-    ipa_status st = cuda_fail(cudaMalloc(&a.seg_off, sizeof(int64_t) * ((size_t)cap + 1)), "fit offsets");
+    ipa_status st = device_alloc((void**)&a.seg_off, sizeof(int64_t) * ((size_t)cap + 1), "fit offsets");
     if (st == IPA_OK) a.cap = cap;
     return st;
 }
@@ -333,7 +333,108 @@ ipa_status fit_run(const ipa_model* model, const ipa_events* ev, int n_fits, con
     return st;
 }
 
+// ---- stepwise fits: the minimiser's state in memory the caller owns ----
+// Layout of a state buffer of n fits with P parameters (offsets rounded up to
+// 256 bytes): the n x P points to evaluate next, the Spec, n States, n
+// activity flags.  Everything a fit's future depends on is in the buffer, so a
+// copy taken between passes resumes the fits bit for bit.
+namespace {
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+struct StepLayout {
+    size_t spec, states, active, total;
+};
+StepLayout step_layout(int n_fits, int n_par) {
+    StepLayout l;
+    l.spec = round256((size_t)n_fits * n_par * sizeof(double));
+    l.states = l.spec + round256(sizeof(Spec));
+    l.active = l.states + round256((size_t)n_fits * sizeof(State));
+    l.total = l.active + round256((size_t)n_fits * sizeof(int));
+    return l;
+}
+ipa_status step_args(const ipa_model* model, int n_fits, const void* state_dev) {
+    ipa_status st = check_model(model);
+    if (st != IPA_OK) return st;
+    if (n_fits < 1 || !state_dev || (reinterpret_cast<uintptr_t>(state_dev) & 255u)) {
+        set_error("stepwise fit: n_fits >= 1 and a 256-byte aligned state buffer required");
+        return IPA_ERR_ARG;
+    }
+    return IPA_OK;
+}
+}  // namespace
 }  // namespace ipa
+
+extern "C" uint64_t ipa_fit_state_bytes(int32_t n_fits, int32_t n_par) {
+    if (n_fits < 1 || n_par < 1 || n_par > ipa::kMaxP) return 0;
+    return ipa::step_layout(n_fits, n_par).total;
+}
+
+extern "C" ipa_status ipa_fit_begin(const ipa_model* model, const ipa_param* spec, int32_t n_fits,
+                                    const double* theta0_dev, int32_t max_iter, double tol, void* state_dev,
+                                    void* stream) {
+    using namespace ipa;
+    ipa_status st = step_args(model, n_fits, state_dev);
+    if (st != IPA_OK) return st;
+    if (!spec || !theta0_dev || max_iter < 1 || !(tol > 0.0)) {
+        set_error("ipa_fit_begin: bad arguments");
+        return IPA_ERR_ARG;
+    }
+    Spec sp{};
+    if ((st = build_spec(model, spec, max_iter, tol, &sp)) != IPA_OK) return st;
+    const StepLayout l = step_layout(n_fits, model->n_par);
+    unsigned char* base = static_cast<unsigned char*>(state_dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // a pageable source: the copy is staged before cudaMemcpyAsync returns
+    if ((st = cuda_fail(cudaMemcpyAsync(base + l.spec, &sp, sizeof(Spec), cudaMemcpyHostToDevice, s),
+                        "fit spec copy")) != IPA_OK)
+        return st;
+    const int fb = 128, fg = (n_fits + fb - 1) / fb;
+    init_kernel<<<fg, fb, 0, s>>>(reinterpret_cast<const Spec*>(base + l.spec), 0, n_fits, theta0_dev,
+                                  reinterpret_cast<State*>(base + l.states), reinterpret_cast<double*>(base),
+                                  reinterpret_cast<int*>(base + l.active));
+    return cuda_fail(cudaGetLastError(), "fit init");
+}
+
+extern "C" ipa_status ipa_fit_advance(const ipa_model* model, int32_t n_fits, const double* results_dev,
+                                      void* state_dev, int32_t* n_active_dev, void* stream) {
+    using namespace ipa;
+    ipa_status st = step_args(model, n_fits, state_dev);
+    if (st != IPA_OK) return st;
+    if (!results_dev || !n_active_dev) {
+        set_error("ipa_fit_advance: results and n_active are required");
+        return IPA_ERR_ARG;
+    }
+    const StepLayout l = step_layout(n_fits, model->n_par);
+    unsigned char* base = static_cast<unsigned char*>(state_dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = cuda_fail(cudaMemsetAsync(n_active_dev, 0, sizeof(int32_t), s), "fit count reset")) != IPA_OK)
+        return st;
+    const int fb = 128, fg = (n_fits + fb - 1) / fb;
+    qn_kernel<<<fg, fb, 0, s>>>(reinterpret_cast<const Spec*>(base + l.spec), 0, n_fits, nullptr, nullptr,
+                                results_dev, reinterpret_cast<State*>(base + l.states),
+                                reinterpret_cast<double*>(base), reinterpret_cast<int*>(base + l.active),
+                                n_active_dev);
+    return cuda_fail(cudaGetLastError(), "fit step");
+}
+
+extern "C" ipa_status ipa_fit_end(const ipa_model* model, int32_t n_fits, const void* state_dev,
+                                  double* theta_out_dev, double* err_out_dev, double* nll_out_dev,
+                                  int32_t* fit_status_dev, int32_t* iters_out_dev, int32_t* passes_out_dev,
+                                  void* stream) {
+    using namespace ipa;
+    ipa_status st = step_args(model, n_fits, state_dev);
+    if (st != IPA_OK) return st;
+    if (!theta_out_dev) {
+        set_error("ipa_fit_end: theta_out is required");
+        return IPA_ERR_ARG;
+    }
+    const StepLayout l = step_layout(n_fits, model->n_par);
+    const unsigned char* base = static_cast<const unsigned char*>(state_dev);
+    const int fb = 128, fg = (n_fits + fb - 1) / fb;
+    final_kernel<<<fg, fb, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const Spec*>(base + l.spec), 0, n_fits, reinterpret_cast<const State*>(base + l.states),
+        theta_out_dev, err_out_dev, nll_out_dev, fit_status_dev, iters_out_dev, passes_out_dev);
+    return cuda_fail(cudaGetLastError(), "fit final");
+}
 
 extern "C" ipa_status ipa_fit_batch(const ipa_model* model, const ipa_events* ev,
                                     const int64_t* seg_off_dev, int32_t n_fits, const ipa_param* spec,

@@ -277,7 +277,8 @@ __device__ void newton_step(const Spec& sp, State& S, double* theta_eval) {
 }
 
 // Advance fit i by one pass: res holds (NLL, gradient) at theta_eval of fit i.
-// Fit i uses specs[i * spec_stride] and events [seg_begin[i], seg_end[i]).
+// Fit i uses specs[i * spec_stride] and events [seg_begin[i], seg_end[i])
+// (seg_begin NULL: the caller evaluated the points itself, no fit is empty).
 __global__ void qn_kernel(const Spec* __restrict__ specs, int spec_stride, int n_fits,
                           const int64_t* __restrict__ seg_begin, const int64_t* __restrict__ seg_end,
                           const double* __restrict__ res, State* __restrict__ states,
@@ -300,7 +301,7 @@ __global__ void qn_kernel(const Spec* __restrict__ specs, int spec_stride, int n
 
     switch (S.phase) {
     case kInit: {
-        if (seg_end[i] <= seg_begin[i]) {
+        if (seg_begin && seg_end[i] <= seg_begin[i]) {
             S.f = 0.0;
             finish(sp, S, IPA_FIT_EMPTY);
             break;

@@ -48,7 +48,7 @@ ipa_status stage_reserve(HostStage& h, int64_t n) {
             for (int q = 0; q < kCopyStreams && st == IPA_OK; ++q)
                 st = cuda_fail(cudaEventCreateWithFlags(&h.ready[c][q], cudaEventDisableTiming), "host event");
         if (st == IPA_OK)
-            st = cuda_fail(cudaMalloc(&h.part, sizeof(double) * kMaxChunks * (1 + IPA_MAX_PAR)), "chunk results");
+            st = device_alloc((void**)&h.part, sizeof(double) * kMaxChunks * (1 + IPA_MAX_PAR), "chunk results");
         if (st != IPA_OK) return st;
     }
     if (n <= h.cap) return IPA_OK;
@@ -61,7 +61,7 @@ ipa_status stage_reserve(HostStage& h, int64_t n) {
     }
     h.cap = 0;
     for (int k = 0; k < kCols; ++k)
-        if ((st = cuda_fail(cudaMalloc(&h.col[k], sizeof(double) * cap), "host staging")) != IPA_OK) return st;
+        if ((st = device_alloc((void**)&h.col[k], sizeof(double) * cap, "host staging")) != IPA_OK) return st;
     h.cap = cap;
     return IPA_OK;
 }

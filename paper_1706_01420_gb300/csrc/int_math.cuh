@@ -251,4 +251,145 @@ __device__ __forceinline__ void basis_q62(double ck, double cl, double phi, cons
     F[9] = mul_q62(CK, sl2);
 }
 
+// ---- branch-free forms for software-pipelined event loops ----
+// The functions below return the same values as the ones above for inputs in
+// their ranges (exp_int_ok, basis_q62_ok), without a branch, so that a warp can
+// evaluate them for the next event in one basic block together with the FP64
+// work of the current event (the GPU overlaps FP64 and integer instructions of
+// one warp, not of different warps) and fix up the rare lanes outside the
+// ranges afterwards.  Outside the ranges the values are unspecified; every
+// shift stays below 64 and every table index inside its table.
+
+// q62_to_double, also for v = 0 (which gives +0).
+__device__ __forceinline__ double q62_to_double_nb(long long v, int e2) {
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);                   // 64 for a = 0
+    a <<= (lz & 63);
+    unsigned long long m = a >> 11;
+    const unsigned long long rem = a & 0x7FFull;
+    m += (rem > 0x400ull) || (rem == 0x400ull && (m & 1ull));
+    const long long field = (long long)(1 - lz + e2 + 1022);
+    const long long bits = (long long)(sign | (((unsigned long long)field << 52) + m));
+    return __longlong_as_double(v == 0 ? 0ll : bits);
+}
+
+// M 2^sh for a 53-bit M and any sh (0 for sh <= -64; sh >= 64 wraps, for
+// inputs outside the ranges only).
+__device__ __forceinline__ unsigned long long shift_nb(unsigned long long M, int sh) {
+    const unsigned long long up = M << (sh & 63);
+    const unsigned long long dn = M >> ((-sh) & 63);
+    return sh >= 0 ? up : (sh > -64 ? dn : 0ull);
+}
+
+// Range of exp_int's fixed-point path: -705 < a < 709.
+__device__ __forceinline__ bool exp_int_ok(double a) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    return !(E > 9 || ((b >> 63) ? below_neg(a, -705.0) : above(a, 709.0)));
+}
+
+// exp_int without its range test (the caller checks exp_int_ok).
+__device__ __forceinline__ double exp_int_nb(double a, const MathTables* t) {
+    using namespace fp64tab;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    const bool neg = (b >> 63) != 0;
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const unsigned long long A = shift_nb(M, E + 1);       // |a| in Q53
+    const unsigned long long P = __umul64hi(A, kInvLn2x64Q56);
+    const unsigned long long k = (P + (1ull << 44)) >> 45;
+    const unsigned __int128 kl = (unsigned __int128)k * kLn2d64Q128Hi +
+                                 (((unsigned __int128)k * kLn2d64Q128Lo) >> 64);
+    const long long r = (long long)(((__int128)A << 11) - (__int128)kl);
+    const long long rs = neg ? -r : r;
+    const long long ks = neg ? -(long long)k : (long long)k;
+    long long v = kExpC6Q63;
+    v = kExpC5Q63 + __mul64hi(rs, v);
+    v = kExpC4Q63 + __mul64hi(rs, v);
+    v = kExpC3Q63 + __mul64hi(rs, v);
+    v = kExpC2Q63 + __mul64hi(rs, v);
+    const long long pm = rs + (__mul64hi(__mul64hi(rs, v), rs) << 1);
+    const long long T = t->eq[ks & 63];
+    const long long y = T + __mul64hi(T, pm);
+    return q62_to_double_nb(y, (int)(ks >> 6));
+}
+
+// sincos_q62 for any bit pattern (the table index clamped to the table).
+__device__ __forceinline__ void sincos_q62_nb(unsigned long long b, const MathTables* t, long long* sv,
+                                              long long* cv) {
+    using namespace fp64tab;
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const unsigned long long X = shift_nb(M, E + 9);       // |phi| in Q61
+    const unsigned long long U = __umul64hi(X, kTwoOverPiQ64);
+    const unsigned long long k = (U + (1ull << 56)) >> 57;
+    const long long rq = (long long)(U - (k << 57));
+    const bool rneg = rq < 0;
+    const unsigned long long ra = rneg ? (unsigned long long)(-rq) : (unsigned long long)rq;
+    const unsigned long long r = __umul64hi(ra << 7, kPiOver32Q64);
+    sincos_poly_q62(k > 64ull ? 64 : (int)k, r, rneg, t, sv, cv);
+}
+
+// to_q62 for any double (unspecified outside |x| <= 1).
+__device__ __forceinline__ long long to_q62_nb(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const long long v = (long long)shift_nb(M, (int)((b >> 52) & 0x7FFull) - 1023 + 10);
+    return (b >> 63) ? -v : v;
+}
+
+// sqrt_q124 without the branch on zero.
+__device__ __forceinline__ long long sqrt_q124_nb(unsigned __int128 X) {
+    const bool zero = X == 0;
+    const unsigned __int128 Xs = zero ? (unsigned __int128)1 : X;
+    const unsigned long long xh = (unsigned long long)(Xs >> 64), xl = (unsigned long long)Xs;
+    const int lz = xh ? __clzll((long long)xh) : 64 + __clzll((long long)xl);
+    const int d = 124 - (127 - lz);
+    const int s = d & ~1;
+    const unsigned __int128 Xn = Xs << (s & 127);
+    const int top = 127 - lz + s;
+    const unsigned fb = ((unsigned)(top - 124 + 127) << 23) | ((unsigned)(Xn >> ((top - 23) & 127)) & 0x7FFFFFu);
+    const float y0f = rsqrtf(__uint_as_float(fb));
+    const unsigned yb = __float_as_uint(y0f);
+    const int ye = (int)((yb >> 23) & 0xFF) - 127;
+    const long long Y0 = (long long)(((unsigned long long)((yb & 0x7FFFFF) | 0x800000)) << ((39 + ye) & 63));
+    long long Q = mul_q62((long long)(Xn >> 62), Y0);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const __int128 R = (__int128)Xn - (__int128)Q * Q;
+        Q += __mul64hi((long long)(R >> 62), Y0) << 1;
+    }
+    return zero ? 0 : Q >> ((s >> 1) & 63);
+}
+
+// basis_q62 without branches (the caller checks basis_q62_ok).
+__device__ __forceinline__ void basis_q62_nb(double ck, double cl, double phi, const MathTables* t,
+                                             long long F[10]) {
+    const unsigned long long pb = (unsigned long long)__double_as_longlong(phi);
+    long long sp, cp;
+    sincos_q62_nb(pb, t, &sp, &cp);
+    sp = (pb >> 63) ? -sp : sp;
+    const long long CK = to_q62_nb(ck), CL = to_q62_nb(cl);
+    const long long sk2 = one_minus_sq_q62(CK), sl2 = one_minus_sq_q62(CL);
+    const long long ck2 = kOneQ62 - sk2, cl2 = kOneQ62 - sl2;
+    const long long cp2 = mul_q62(cp, cp);
+    const unsigned __int128 sksl2_124 = (unsigned __int128)((__int128)sk2 * sl2);
+    const long long sksl2 = (long long)(sksl2_124 >> 62);
+    const long long q = sqrt_q124_nb(sksl2_124);
+    const long long slcp2 = mul_q62(sl2, cp2);
+    F[0] = mul_q62(ck2, sl2);
+    F[1] = mul_q62(sk2, kOneQ62 - slcp2);
+    F[2] = mul_q62(sk2, slcp2 + cl2);
+    F[3] = mul_q62(sksl2, mul_q62(sp, cp));
+    const long long a = mul_q62(q, mul_q62(CK, CL));
+    F[4] = mul_q62(a, cp);
+    F[5] = mul_q62(a, sp);
+    F[6] = sl2;
+    const long long bq = mul_q62(q, CL);
+    F[7] = mul_q62(bq, cp);
+    F[8] = mul_q62(bq, sp);
+    F[9] = mul_q62(CK, sl2);
+}
+
 }  // namespace ipa

@@ -92,6 +92,10 @@ void set_error(const char* fmt, ...);
 // Append one line to the IPA_TRACE file (if the variable is set).
 void trace(const char* fmt, ...);
 ipa_status cuda_fail(cudaError_t e, const char* what);
+// Host-side fault injection (ipa_fault_inject): whether `bit` is set.
+bool fault(uint32_t bit);
+// cudaMalloc, or IPA_ERR_OOM without calling it while IPA_FAULT_ALLOC is set.
+ipa_status device_alloc(void** p, size_t bytes, const char* what);
 ipa_status check_model(const ipa_model* m);
 ipa_status check_events(const ipa_model* m, const ipa_events* ev);
 
@@ -110,6 +114,8 @@ struct Scratch {
 // (and their group counters) and `segs` segments.  May synchronise the device
 // when it grows.
 ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out);
+// Device bytes that scratch_get has allocated on device `dev`.
+uint64_t scratch_bytes(int dev);
 
 // ---- kernels launched across translation units ----
 // consts.cu: theta (n_seg x n_par) -> Consts[n_seg]
@@ -173,6 +179,13 @@ ipa_status launch_phis_toygen(const ModelDev& m, const Consts* consts, uint64_t 
 // be NULL).
 ipa_status launch_seg_tiles(const int64_t* seg_begin, const int64_t* seg_end, const int* active, int n_seg,
                             int64_t n, int64_t* seg_tiles, cudaStream_t s);
+
+// tagged.cu / phis.cu: the last reduction level and the gradient contraction
+// over gathered group partials (ipa_nll_grad_combine), one warp.
+ipa_status launch_tag_combine(const double* groups, int64_t n_groups, const Consts* consts, int n_par, double* out,
+                              cudaStream_t s);
+ipa_status launch_phis_combine(const double* groups, int64_t n_groups, bool cached, const Consts* consts, int n_par,
+                               double* out, cudaStream_t s);
 
 // Number of SMs of the current device (cached).
 int sm_count();

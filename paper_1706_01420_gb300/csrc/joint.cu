@@ -102,7 +102,7 @@ ipa_status grow(T** p, size_t have, size_t need, const char* what) {
         cudaFree(*p);
         *p = nullptr;
     }
-    return cuda_fail(cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (need ? need : 1)), what);
+    return device_alloc(reinterpret_cast<void**>(p), sizeof(T) * (need ? need : 1), what);
 }
 
 size_t round_up(size_t need, size_t cap) {
@@ -133,7 +133,7 @@ ipa_status reserve(JointArgs& a, size_t map_n, size_t n_seg, size_t n_fits) {
         if ((st = grow(&a.fit_end, 0, cap, "joint fit ranges")) != IPA_OK) return st;
         a.fit_cap = cap;
     }
-    if (!a.spec) st = cuda_fail(cudaMalloc(&a.spec, sizeof(Spec)), "joint fit spec");
+    if (!a.spec) st = device_alloc((void**)&a.spec, sizeof(Spec), "joint fit spec");
     return st;
 }
 

@@ -54,17 +54,34 @@ constexpr int kPerLane = kTile / 32;                 // events per lane per tile
 //   A' = sum_k hq_k f_k = (cs / 2) A, so that P = T2 A' + cb with T2 = 2 T,
 //   hq_k = h_k c_k cs / 2 for the unscaled products f'_k (h_k cs / 2 for a
 //   cached basis), aq = cs / 2 (the 1D model's A' for A = 1),
-//   c2 = Gamma^2 sigma^2 / 2 + ln 2, so that exp(-Gamma tau + c2) = 2 E.
+//   c2 = Gamma^2 sigma^2 / 2 + ln 2, so that exp(-Gamma tau + c2) = 2 E,
+//   hcq_k = h_k c_k (cs / 2) times the power of two 2^s that brings the largest
+//   into [1, 2), in Q62, so that the fixed-point sum gives A' directly.
 struct WarpConsts {
     Consts c;
     double hq[10];
     double aq;
     double c2;
     double tcut;     // t above it: z < -6.25, the Gaussian-erfcx term is below 1e-17 of T
-    long long hcq[10];   // h_k c_k in Q62 (the fixed-point amplitude sum)
-    int fixed;           // every |h_k c_k| < 2 and finite: the fixed-point path may be used
-    int pad_;
+    long long hcq[10];   // h_k c_k (cs / 2) 2^s in Q62 (the fixed-point amplitude sum), with
+    int hexp;            // 2 - s: A' = (sum_k hcq_k F_k in Q60) 2^-s, s making max|hcq| lie in [1, 2)
+    int fixed;           // coefficients finite and s in range: the fixed-point path may be used
 };
+
+// The largest of a non-negative 64-bit value over the warp.
+__device__ __forceinline__ long long max_abs_bits(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// 2^e as a double for -1022 <= e <= 1023 (built from its bit pattern).
+__device__ __forceinline__ double exp2_int(int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
 
 // Decay-time events per compaction round of one lane (see nll_kernel).
 constexpr int kSub = 4;
@@ -145,6 +162,284 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
     }
 }
 
+// ---- the fast tile (4D model, angles on the integer pipe) ----
+// A whole tile of the 4D model's NLL + gradient takes this path; the last,
+// partial tile of a segment and the other variants take the plain loop of
+// nll_kernel.
+//
+// On this GPU an FP64 instruction costs a warp about as much issue time as 64
+// integer instructions, and the two kinds overlap poorly (a warp's FP64 work
+// and other warps' integer work largely serialise).  So the ten angular
+// adjoint sums S_k = sum r T f'_k, which in FP64 cost ten DFMA per event, are
+// accumulated here on the integer pipe: r T is converted once per event to
+// signed 64-bit fixed point with 40 fraction bits (rounded to nearest, for
+// |r T| < 2^19), and each product with the Q62 angular product f'_k is the
+// high 64 bits of the 128-bit product (Q38: the floor, corrected on average
+// by half a unit per product at the end of the tile).  A lane adds its 16
+// events exactly in 64-bit integers (no overflow: |r T f'_k| < 2^19) and
+// converts each sum to a double once per tile, so these sums do not depend on
+// the order of the events within a lane.  Error of a sum: about 2^-39 per
+// event, of random sign (a sum over 1e6 events is off by ~1e-9 absolute,
+// while the sums themselves are ~1e5 and the gradient tolerance is 1e-9 of
+// them).  The remaining
+// accumulators are FP64 as in the plain loop.  The integer work runs with the
+// branch-free functions of int_math.cuh; lanes outside their ranges are fixed
+// up with the FP64 paths of the plain loop.  A tile in which some P lies
+// outside the Newton reciprocal's range (zero, subnormal, negative, huge,
+// infinite or NaN) or some |r T| >= 2^19 is redone by the plain loop.  Either
+// way the tile's sums depend only on its events, never on the launch geometry.
+
+// The integer-pipe results of one event that its FP64 work needs.
+struct RowIn {
+    double tau, w, E2, Ap;
+    long long F[10];   // f'_k in Q62
+};
+
+// tau, E2 = 2 e^{-Gamma tau + Gamma^2 sigma^2 / 2}, the ten f'_k and A' =
+// (cs / 2) A of event e with the branch-free fixed-point functions; false if the
+// lane needs fix_int_phase.
+template <bool WEIGHTED>
+__device__ __forceinline__ bool int_phase(const WarpConsts& wc, const MathTables* mt, const Cols& cols, int64_t e,
+                                          RowIn& v) {
+    const double t = __ldg(cols.t + e);
+    const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
+    v.w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
+    v.tau = t - wc.c.mu;
+    const double a = fma(-wc.c.Gamma, v.tau, wc.c2);
+    v.E2 = exp_int_nb(a, mt);
+    basis_q62_nb(ck, cl, phi, mt, v.F);
+    long long Af = 0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Af += __mul64hi(wc.hcq[k], v.F[k]);
+    v.Ap = q62_to_double_nb(Af, wc.hexp);
+    return wc.fixed && basis_q62_ok(ck, cl, phi) && exp_int_ok(a);
+}
+
+// The FP64 paths of the plain loop for a lane that int_phase could not serve
+// (the FP64 products, in [-1, 1] for valid angles, go to Q62).
+__device__ __forceinline__ void fix_int_phase(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
+                                              int64_t e, RowIn& v) {
+    const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
+    const double a = fma(-wc.c.Gamma, v.tau, wc.c2);
+    if (!(wc.fixed && basis_q62_ok(ck, cl, phi))) {
+        double f[10];
+        basis_unscaled(ck, cl, phi, mt, f);
+        v.Ap = amplitude_sum(wc.hq, f);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) v.F[k] = to_q62_nb(f[k]);
+    }
+    if (!exp_int_ok(a)) v.E2 = exp_fast(a, mt);
+}
+
+// rcp_newton and log_fast without their range branches (P in [2^-125, 2^126)).
+__device__ __forceinline__ double rcp_newton_nb(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned xf = ((unsigned)((unsigned long long)b >> 32) & 0x80000000u) |
+                        ((unsigned)(e - 1023 + 127) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu);
+    const unsigned yf = __float_as_uint(__frcp_rn(__uint_as_float(xf)));
+    const long long yb = ((long long)(yf & 0x80000000u) << 32) |
+                         ((long long)(((yf >> 23) & 0xFFu) - 127 + 1023) << 52) | ((long long)(yf & 0x7FFFFFu) << 29);
+    const double y = __longlong_as_double(yb);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+__device__ __forceinline__ double log_fast_nb(double x, const MathTables* t) {
+    using namespace fp64tab;
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023;
+    const int j = (int)((b >> 45) & 127);
+    const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    const double r = fma(m, t->linv[j], -1.0);
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(q, r, 0.2);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double l = fma(r * r, q, r);
+    const double ed = __longlong_as_double(0x4330000000000000ll + (long long)(e + 2048)) -
+                      (4503599627370496.0 + 2048.0);
+    return fma(ed, kLn2Hi, fma(ed, kLn2Lo, t->ltab[j] + l));
+}
+
+// The lane's product of the mantissas of P in Q62 ([1, 2)) with the exponents
+// summed apart, for positive normal P: the high 64 bits of the 128-bit product
+// (Q61, in [1, 4)) renormalised to [1, 2) (integer pipe; truncation below
+// 2^-61 per step, 2^-57 over a tile's 16 events).
+__device__ __forceinline__ void log_mul_q(double P, unsigned long long* prodq, int* esum) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(P);
+    const unsigned long long mq = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;   // Q63
+    const unsigned long long h = __umul64hi(*prodq, mq);                                      // Q61
+    const int big = (int)(h >> 62);
+    *prodq = big ? h : h << 1;
+    *esum += (int)(b >> 52) - 1023 + big;
+}
+
+// x 2^40 rounded to the nearest signed 64-bit integer (ties away from zero),
+// for |x| < 2^19 (else *bad is set; NaN and infinities included).
+__device__ __forceinline__ long long to_q40(double x, bool* bad) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FFull) - 1023;
+    *bad |= E > 18;
+    const unsigned long long M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = E - 12;
+    const int s = (-sh) & 63;
+    const unsigned long long dn = (M + (s ? 1ull << (s - 1) : 0ull)) >> s;
+    const long long v = (long long)(sh >= 0 ? M << (sh & 63) : (sh > -64 ? dn : 0ull));
+    return (b >> 63) ? -v : v;
+}
+
+// The FP64 work of one event on the fast path.  tg: (T2, Gx) from the near-peak
+// pass for a marked event (slow), else unused.  The adjoint sums: acci (the
+// ten S_k, Q38), acc[1] and acc[12] here; r A' and u = r A' tau of a marked
+// event go to ru[slot] for the packed pass that adds acc[13] and acc[14]
+// (their terms vanish for the other events).  *bad is set when P is outside
+// [2^-125, 2^126) or |r T| >= 2^19.
+template <bool GRAD, bool WEIGHTED>
+__device__ __forceinline__ void event_fast(const WarpConsts& wc, const MathTables* mt, const RowIn& v, bool slow,
+                                           double2 tg, double2* ru, double* acc, long long* acci,
+                                           unsigned long long* prodq, int* esum, bool* bad) {
+    const Consts& c = wc.c;
+    const double T2 = slow ? tg.x : v.E2;
+    const double P = fma(T2, v.Ap, c.cb);
+    const long long pb = __double_as_longlong(P);
+    *bad |= (unsigned long long)(pb - 0x3820000000000000ll) >= 0x0FB0000000000000ull;
+    if (WEIGHTED) {
+        // weight exactly 1: P joins the lane's product (as in event)
+        const bool one = __double_as_longlong(v.w) == 0x3FF0000000000000ll;
+        acc[0] = fma(one ? 0.0 : v.w, log_fast_nb(P, mt), acc[0]);
+        log_mul_q(one ? P : 1.0, prodq, esum);
+    } else {
+        log_mul_q(P, prodq, esum);
+    }
+    if (GRAD) {
+        const double r = WEIGHTED ? v.w * rcp_newton_nb(P) : rcp_newton_nb(P);
+        acc[1] += r;
+        const long long rq = to_q40(r * T2, bad);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acci[k] += __mul64hi(rq, v.F[k]);
+        const double rA = r * v.Ap;
+        const double u = rA * v.tau;
+        acc[12] = fma(u, T2, acc[12]);
+        if (slow) *ru = make_double2(rA, u);
+    }
+}
+
+// Near-peak marks of rows i0 .. i0 + kSub - 1 of a tile (lane l: event tbase +
+// l + 32 i): the warp's ballots of t <= tcut, and the packed Gaussian/erfcx
+// values of the marked events (in row order, lanes in order within a row) in
+// sbuf.  m[q] is row i0 + q's ballot, p[q] the number of marked events in the
+// rows before it.
+template <bool FULL>
+__device__ __forceinline__ void near_peak_rows(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
+                                               int64_t tbase, int64_t ev1, int i0, int lane, double2* sbuf,
+                                               unsigned m[kSub], int p[kSub]) {
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+        const int64_t e = tbase + lane + 32 * (i0 + q);
+        const bool slow = (FULL || e < ev1) && !greater(__ldg(cols.t + e), wc.tcut);
+        m[q] = __ballot_sync(0xffffffffu, slow);
+    }
+    p[0] = 0;
+    p[1] = __popc(m[0]);
+    p[2] = p[1] + __popc(m[1]);
+    p[3] = p[2] + __popc(m[2]);
+    const int n_slow = p[3] + __popc(m[3]);
+    for (int j = lane; j < n_slow; j += 32) {
+        const int q = (j >= p[1]) + (j >= p[2]) + (j >= p[3]);
+        const unsigned mq = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+        const int before = q == 0 ? 0 : (q == 1 ? p[1] : (q == 2 ? p[2] : p[3]));
+        const int64_t e = tbase + nth_set(mq, j - before) + 32 * (i0 + q);
+        sbuf[j] = gauss_erfcx(wc.c, __ldg(cols.t + e) - wc.c.mu, mt);
+    }
+    __syncwarp();
+}
+
+// The near-peak values of the fast path for the marked events of rows i0 ..
+// i0 + kSub - 1 (packed as in near_peak_rows): T2 = 2 g(tau) itself (E2 minus
+// the erfcx term, or the erfcx term) and the Gaussian Gx.
+__device__ __forceinline__ void near_peak_fast(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
+                                               int64_t tbase, int i0, int lane, double2* sbuf, const unsigned m[kSub],
+                                               const int p[kSub], int n_slow) {
+    for (int j = lane; j < n_slow; j += 32) {
+        const int q = (j >= p[1]) + (j >= p[2]) + (j >= p[3]);
+        const unsigned mq = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+        const int before = q == 0 ? 0 : (q == 1 ? p[1] : (q == 2 ? p[2] : p[3]));
+        const int64_t e = tbase + nth_set(mq, j - before) + 32 * (i0 + q);
+        const double tau = __ldg(cols.t + e) - wc.c.mu;
+        const double2 ge = gauss_erfcx(wc.c, tau, mt);
+        const double E2 = exp_int(fma(-wc.c.Gamma, tau, wc.c2), mt);
+        const long long gb = __double_as_longlong(ge.y);
+        sbuf[j] = make_double2(gb >= 0 ? E2 - ge.x : ge.x, __longlong_as_double(gb & 0x7FFFFFFFFFFFFFFFll));
+    }
+    __syncwarp();
+}
+
+// One whole tile (kTile events from tbase) of the 4D model on the fast path.
+// Returns false if the tile must be redone by the plain loop (acc, prod and
+// esum are then meaningless).  ru: the warp's kSub x 32 slots for the marked
+// events' r A' and u.
+template <bool GRAD, bool WEIGHTED>
+__device__ __forceinline__ bool tile_fast(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
+                                          int64_t tbase, double2* sbuf, double2* ru, int lane, double* acc,
+                                          double* prod, int* esum) {
+    const unsigned below = (1u << lane) - 1u;
+    bool bad = false;
+    long long acci[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acci[k] = 0;
+    unsigned long long prodq = 1ull << 62;
+#pragma unroll 1
+    for (int i0 = 0; i0 < kPerLane; i0 += kSub) {
+        unsigned m[kSub];
+        int p[kSub];
+#pragma unroll
+        for (int q = 0; q < kSub; ++q) {
+            const int64_t e = tbase + lane + 32 * (i0 + q);
+            m[q] = __ballot_sync(0xffffffffu, !greater(__ldg(cols.t + e), wc.tcut));
+        }
+        p[0] = 0;
+        p[1] = __popc(m[0]);
+        p[2] = p[1] + __popc(m[1]);
+        p[3] = p[2] + __popc(m[2]);
+        const int n_slow = p[3] + __popc(m[3]);
+        near_peak_fast(wc, mt, cols, tbase, i0, lane, sbuf, m, p, n_slow);
+#pragma unroll 1
+        for (int q = 0; q < kSub; ++q) {
+            const unsigned mq = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
+            const int before = q == 0 ? 0 : (q == 1 ? p[1] : (q == 2 ? p[2] : p[3]));
+            const int slot = (before + __popc(mq & below)) & (kSub * 32 - 1);
+            const bool slow = (mq >> lane) & 1u;
+            const double2 tg = sbuf[slot];
+            const int64_t e = tbase + lane + 32 * (i0 + q);
+            RowIn v;
+            const bool ok = int_phase<WEIGHTED>(wc, mt, cols, e, v);
+            if (__any_sync(0xffffffffu, !ok)) fix_int_phase(wc, mt, cols, e, v);
+            event_fast<GRAD, WEIGHTED>(wc, mt, v, slow, tg, ru + slot, acc, acci, &prodq, esum, &bad);
+        }
+        __syncwarp();
+        if (GRAD) {
+            // the Gaussian terms of the marked events, packed: r A' Gx and u Gx
+            for (int j = lane; j < n_slow; j += 32) {
+                const double2 x = ru[j];
+                const double Gx = sbuf[j].y;
+                acc[13] = fma(x.x, Gx, acc[13]);
+                acc[14] = fma(x.y, Gx, acc[14]);
+            }
+        }
+        __syncwarp();
+    }
+    *prod = q62_to_double_nb((long long)prodq, 0);
+    if (GRAD) {
+        // the lane's fixed-point sums (Q38) as doubles; each high product is
+        // the floor of the exact one, half a unit low on average, so the lane's
+        // kPerLane products get kPerLane / 2 units back
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[2 + k] = q62_to_double_nb(acci[k] + kPerLane / 2, 24);
+    }
+    return !__any_sync(0xffffffffu, bad);
+}
+
 // Write NLL (and gradient) of one segment from its reduced accumulators.
 // With S_k = sum r T f_k and SH = sum_k h_k S_k = sum r T A (A = 1 in 1D), and
 // D_j = sum r A dT/dtheta_j where
@@ -211,8 +506,11 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int n_wib = blockDim.x >> 5;
+    // per warp: the near-peak values (sbuf), the marked events' r A' and u (ru)
+    // and the segment's constants
     double2* const sbuf = reinterpret_cast<double2*>(dyn_smem) + wib * (kSub * 32);
-    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem + (size_t)n_wib * kSub * 32 * sizeof(double2))[wib];
+    double2* const ru = reinterpret_cast<double2*>(dyn_smem) + (n_wib + wib) * (kSub * 32);
+    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem + (size_t)2 * n_wib * kSub * 32 * sizeof(double2))[wib];
 
     load_math_tables(&mt);
     __syncthreads();
@@ -269,14 +567,21 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                     const double tc = wc.c.mu + (wc.c.Gs2 + 6.25 / wc.c.k_z);
                     wc.tcut = tc == tc ? tc : INFINITY;    // NaN constants: every event takes the full path
                 }
-                // h_k c_k in Q62 for the fixed-point amplitude sum; non-finite or
-                // |h_k c_k| >= 2 (non-physical theta) keeps the FP64 path, which
-                // propagates NaN
-                const double hc = lane < 10 ? wc.c.h[lane] * kBasisScale[lane] : 0.0;
-                const bool hc_ok = abs_below(hc, 2.0);
-                if (lane < 10) wc.hcq[lane] = hc_ok ? to_q62(hc) : 0;
-                const bool all_ok = __all_sync(0xffffffffu, hc_ok) && abs_below(wc.c.cs, 1e300);
-                if (lane == 0) wc.fixed = all_ok ? 1 : 0;
+                // h_k c_k (cs / 2) scaled by 2^s into Q62 for the fixed-point
+                // amplitude sum (multiplying by a power of two is exact);
+                // non-finite coefficients (non-physical theta) or a scale outside
+                // [-64, 900] keep the FP64 path, which propagates NaN
+                const double hca = lane < 10 ? (wc.c.h[lane] * kBasisScale[lane]) * half_cs : 0.0;
+                const long long amag = __double_as_longlong(hca) & 0x7FFFFFFFFFFFFFFFll;
+                const long long amax = max_abs_bits(amag);
+                const int eb = (int)(amax >> 52);                 // biased exponent of max |hca|
+                const int sc = amax == 0 ? 0 : 1023 - eb;         // max |hca| 2^sc in [1, 2)
+                const bool sc_ok = amax < 0x7FF0000000000000ll && sc >= -64 && sc <= 900;
+                if (lane < 10) wc.hcq[lane] = sc_ok ? to_q62(hca * exp2_int(sc)) : 0;
+                if (lane == 0) {
+                    wc.hexp = 2 - sc;
+                    wc.fixed = sc_ok && abs_below(wc.c.cs, 1e300) ? 1 : 0;
+                }
                 __syncwarp();
                 cur = seg;
             }
@@ -294,8 +599,18 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             // instruction on lanes that would discard the result.
             const int64_t tbase = ev0 + (tile - t0) * kTile;
             const unsigned below = (1u << lane) - 1u;
+            bool done = false;
+            if (KIND == IPA_MODEL_ANGTIME4D && GRAD && !CACHED && tbase + kTile <= ev1) {
+                done = tile_fast<GRAD, WEIGHTED>(wc, &mt, cols, tbase, sbuf, ru, lane, acc, &prod, &esum);
+                if (!done) {
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) acc[a] = 0.0;
+                    prod = 1.0;
+                    esum = 0;
+                }
+            }
 #pragma unroll 1
-            for (int i0 = 0; i0 < kPerLane; i0 += kSub) {
+            for (int i0 = 0; !done && i0 < kPerLane; i0 += kSub) {
                 unsigned m0, m1, m2, m3;
                 {
                     unsigned mk[kSub];
@@ -348,7 +663,7 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                                         f[k] = q62_to_double(F[k], 0);
                                         Af += __mul64hi(wc.hcq[k], F[k]);
                                     }
-                                    Ap = q62_to_double(Af, 2) * wc.aq;      // Af is Q60
+                                    Ap = q62_to_double(Af, wc.hexp);        // Af is Q60, times 2^-s
                                 } else {
                                     basis_unscaled(ck, cl, phi, &mt, f);
                                     Ap = amplitude_sum(wc.hq, f);
@@ -418,7 +733,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
     const LaunchCfg cfg = force ? *force : launch_cfg(KIND, GRAD, CACHED, n_seg > 1, tiles);
     const int W = cfg.warps_per_block >= 1 && cfg.warps_per_block <= kMaxWarps ? cfg.warps_per_block : 1;
     const int K = cfg.tiles_per_take >= 1 ? cfg.tiles_per_take : 1;
-    const size_t smem = (size_t)W * (sizeof(WarpConsts) + kSub * 32 * sizeof(double2));
+    const size_t smem = (size_t)W * (sizeof(WarpConsts) + 2 * kSub * 32 * sizeof(double2));
     // resident blocks per SM for each block size (cached per device and variant)
     static int occ[64][kMaxWarps + 1] = {};
     int dev = 0;
@@ -564,6 +879,36 @@ ipa_status run(const ipa_model* model, const ipa_events* ev, const int64_t* seg_
                       seg_off ? sc->seg_tiles : nullptr, n_seg, sc->consts, sc, out, s);
 }
 
+// ---- event-sharded likelihood ----
+// After a single-segment launch, group g's reduced partial (the sums of its 32
+// tiles) sits in the slot of its first tile, g * kGroupTiles.  Copy them out,
+// n_groups x na doubles, in group order.
+__global__ void group_partials_kernel(const double* __restrict__ partials, int na, int64_t n_groups,
+                                      double* __restrict__ out) {
+    const int64_t total = n_groups * na;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = i / na;
+        out[i] = __ldcg(partials + (g * kGroupTiles) * na + (i - g * na));
+    }
+}
+
+// The last level of the kernel's reduction (lane l adds groups l, l + 32, ...
+// in order, then the butterfly) and the gradient contraction, over group
+// partials gathered from several launches: one warp.
+template <int KIND, bool CACHED>
+__global__ void combine_kernel(const double* __restrict__ groups, int64_t n_groups, const Consts* __restrict__ consts,
+                               int n_par, double* __restrict__ out) {
+    constexpr int NA = n_acc(KIND, true);
+    const int lane = threadIdx.x & 31;
+    if (n_groups == 0) {
+        for (int j = lane; j < 1 + n_par; j += 32) out[j] = 0.0;
+        return;
+    }
+    double acc[NA];
+    gather_butterfly<NA>(reduce_partials<NA>(groups, 0, n_groups, 1, lane), acc);
+    finalize<KIND, true, CACHED>(consts[0], acc, n_par, out, lane);
+}
+
 }  // namespace
 }  // namespace ipa
 
@@ -586,4 +931,78 @@ extern "C" ipa_status ipa_nll_grad_segmented(const ipa_model* model, const ipa_e
         return IPA_ERR_ARG;
     }
     return ipa::run(model, ev, seg_off_dev, n_seg, theta_dev, out_dev, true, stream);
+}
+
+
+// Group partials of a single-segment call over n events: ceil(n / 16384).
+static int64_t shard_groups(int64_t n) {
+    const int64_t tiles = (n + ipa::kTile - 1) / ipa::kTile;
+    return (tiles + ipa::kGroupTiles - 1) / ipa::kGroupTiles;
+}
+
+extern "C" ipa_status ipa_shard_width(const ipa_model* model, int32_t* width) {
+    ipa_status st = ipa::check_model(model);
+    if (st != IPA_OK) return st;
+    if (!width) {
+        ipa::set_error("ipa_shard_width: width is NULL");
+        return IPA_ERR_ARG;
+    }
+    *width = ipa::n_acc(model->kind, true);
+    return IPA_OK;
+}
+
+extern "C" ipa_status ipa_nll_grad_shard(const ipa_model* model, const ipa_events* ev, const double* theta_dev,
+                                         double* out_dev, double* groups_dev, void* stream) {
+    using namespace ipa;
+    if (!groups_dev && ev && ev->n > 0) {
+        set_error("ipa_nll_grad_shard: groups_dev is NULL");
+        return IPA_ERR_ARG;
+    }
+    ipa_status st = run(model, ev, nullptr, 1, theta_dev, out_dev, true, stream);
+    if (st != IPA_OK || ev->n == 0) return st;
+    Scratch* sc = nullptr;
+    if ((st = scratch_get((ev->n + kTile - 1) / kTile + 1, 2, &sc)) != IPA_OK) return st;
+    const int na = n_acc(model->kind, true);
+    const int64_t ng = shard_groups(ev->n);
+    const int64_t blocks = (ng * na + 255) / 256;
+    group_partials_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        sc->partials, na, ng, groups_dev);
+    return cuda_fail(cudaGetLastError(), "group partials copy");
+}
+
+extern "C" ipa_status ipa_nll_grad_combine(const ipa_model* model, const double* theta_dev, const double* groups_dev,
+                                           int64_t n_groups, int32_t cached, double* out_dev, void* stream) {
+    using namespace ipa;
+    ipa_status st = check_model(model);
+    if (st != IPA_OK) return st;
+    if (!theta_dev || !out_dev || n_groups < 0 || (n_groups > 0 && !groups_dev)) {
+        set_error("ipa_nll_grad_combine: bad arguments");
+        return IPA_ERR_ARG;
+    }
+    if (cached && model->kind != IPA_MODEL_ANGTIME4D && model->kind != IPA_MODEL_PHIS) {
+        set_error("ipa_nll_grad_combine: only models with angles have a cached basis");
+        return IPA_ERR_ARG;
+    }
+    Scratch* sc = nullptr;
+    if ((st = scratch_get(1, 2, &sc)) != IPA_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const ModelDev m{model->kind, model->n_par, model->t_lo, model->t_hi};
+    if ((st = launch_consts(m, theta_dev, 1, sc->consts, s)) != IPA_OK) return st;
+    const int P = model->n_par;
+    switch (model->kind) {
+    case IPA_MODEL_TIME1D:
+        combine_kernel<IPA_MODEL_TIME1D, false><<<1, 32, 0, s>>>(groups_dev, n_groups, sc->consts, P, out_dev);
+        break;
+    case IPA_MODEL_ANGTIME4D:
+        if (cached)
+            combine_kernel<IPA_MODEL_ANGTIME4D, true><<<1, 32, 0, s>>>(groups_dev, n_groups, sc->consts, P, out_dev);
+        else
+            combine_kernel<IPA_MODEL_ANGTIME4D, false><<<1, 32, 0, s>>>(groups_dev, n_groups, sc->consts, P, out_dev);
+        break;
+    case IPA_MODEL_TAGGED1D:
+        return launch_tag_combine(groups_dev, n_groups, sc->consts, P, out_dev, s);
+    default:
+        return launch_phis_combine(groups_dev, n_groups, cached != 0, sc->consts, P, out_dev, s);
+    }
+    return cuda_fail(cudaGetLastError(), "combine kernel launch");
 }

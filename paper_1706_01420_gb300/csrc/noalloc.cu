@@ -12,10 +12,15 @@
 // use its name as a device address, so the first call on each device looks
 // the address up with cudaGetSymbolAddress while that device is current, and
 // later calls reuse it.  That first call should therefore come before any
-// stream capture.  All calls share the one array and it keeps the previous
+// stream capture.  The address belongs to the device's current CUDA context:
+// each call compares the context's unique id with the one the address was
+// looked up in and looks it up again after a device reset (a new primary
+// context reloads the library's device code, and the array with it).  All calls share the one array and it keeps the previous
 // call's contents: the completion, group and work counters are cleared on the stream
 // before every launch, and calls that overlap on the GPU (different streams, or
 // different host threads without ordering) race on the array.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ipa_internal.cuh"
@@ -36,8 +41,38 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kConstsBytes + 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_addr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
 
-// Device address of the array on the current device (looked up once per device).
+// Unique id of the calling thread's current CUDA context (cuCtxGetId, reached
+// through the runtime's driver entry points, so that the library needs no
+// link-time dependency on the driver library); 0 when it cannot be read.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the array on the current device: looked up once per
+// device and context.  A thread whose context is not yet current reads id 0
+// and looks the address up (which makes the context current); the id read
+// after the lookup is the one kept.
 ipa_status noalloc_base(unsigned char** base) {
     int dev = 0;
     ipa_status st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
@@ -46,12 +81,14 @@ ipa_status noalloc_base(unsigned char** base) {
         set_error("ipa_nll_grad_noalloc: device ordinal %d not supported", dev);
         return IPA_ERR_ARG;
     }
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_noalloc_addr[dev] || ctx == 0 || g_noalloc_ctx[dev] != ctx) {
         void* p = nullptr;
         if ((st = cuda_fail(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress")) != IPA_OK)
             return st;
         g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+        g_noalloc_ctx[dev] = current_context_id();
     }
     *base = g_noalloc_addr[dev];
     return IPA_OK;

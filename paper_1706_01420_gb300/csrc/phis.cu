@@ -954,6 +954,33 @@ ipa_status launch_phis_consts(const ModelDev& m, const double* theta, int n_seg,
     return cuda_fail(cudaGetLastError(), "phi_s consts kernel launch");
 }
 
+namespace {
+// ipa_nll_grad_combine for the phi_s model: the kernel's last reduction level
+// (the wide form) over gathered group partials, then phis_finalize (one warp).
+template <bool CACHED>
+__global__ void phis_combine_kernel(const double* __restrict__ groups, int64_t n_groups,
+                                    const Consts* __restrict__ consts, int n_par, double* __restrict__ out) {
+    constexpr int NA = n_acc(IPA_MODEL_PHIS, true);
+    const int lane = threadIdx.x & 31;
+    if (n_groups == 0) {
+        for (int j = lane; j < 1 + n_par; j += 32) out[j] = 0.0;
+        return;
+    }
+    double acc[NA];
+    reduce_partials_wide<NA>(groups, 0, n_groups, 1, acc);
+    phis_finalize<true, CACHED>(*reinterpret_cast<const PhisConsts*>(consts), acc, n_par, out, lane);
+}
+}  // namespace
+
+ipa_status launch_phis_combine(const double* groups, int64_t n_groups, bool cached, const Consts* consts, int n_par,
+                               double* out, cudaStream_t s) {
+    if (cached)
+        phis_combine_kernel<true><<<1, 32, 0, s>>>(groups, n_groups, consts, n_par, out);
+    else
+        phis_combine_kernel<false><<<1, 32, 0, s>>>(groups, n_groups, consts, n_par, out);
+    return cuda_fail(cudaGetLastError(), "phi_s combine kernel launch");
+}
+
 ipa_status launch_phis_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                            const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                            const Consts* consts, Scratch* sc, double* out, cudaStream_t st, const LaunchCfg* cfg) {

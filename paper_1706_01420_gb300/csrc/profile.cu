@@ -393,14 +393,14 @@ template <typename T>
 ipa_status grow(T** p, size_t n, const char* what) {
     cudaFree(*p);
     *p = nullptr;
-    return cuda_fail(cudaMalloc(p, sizeof(T) * (n ? n : 1)), what);
+    return device_alloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1), what);
 }
 
 ipa_status profile_basics(ProfileContext& c) {
     ipa_status st = IPA_OK;
-    if (!c.spec) st = cuda_fail(cudaMalloc(&c.spec, sizeof(Spec)), "profile spec");
-    if (st == IPA_OK && !c.scan) st = cuda_fail(cudaMalloc(&c.scan, sizeof(int) * kMaxP), "profile scan list");
-    if (st == IPA_OK && !c.n_open) st = cuda_fail(cudaMalloc(&c.n_open, sizeof(int)), "profile counter");
+    if (!c.spec) st = device_alloc((void**)&c.spec, sizeof(Spec), "profile spec");
+    if (st == IPA_OK && !c.scan) st = device_alloc((void**)&c.scan, sizeof(int) * kMaxP, "profile scan list");
+    if (st == IPA_OK && !c.n_open) st = device_alloc((void**)&c.n_open, sizeof(int), "profile counter");
     if (st == IPA_OK && !c.h_open) st = cuda_fail(cudaMallocHost(&c.h_open, sizeof(int)), "profile counter");
     return st;
 }

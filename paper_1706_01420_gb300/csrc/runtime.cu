@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -12,6 +13,17 @@
 namespace ipa {
 
 namespace {
+// Host-side fault injection mask (ipa_fault_inject; IPA_FAULT at load).
+uint32_t fault_from_env() {
+    const char* v = getenv("IPA_FAULT");
+    if (!v) return 0;
+    uint32_t m = 0;
+    if (strstr(v, "alloc")) m |= IPA_FAULT_ALLOC;
+    if (strstr(v, "submit")) m |= IPA_FAULT_SUBMIT;
+    if (strstr(v, "admit")) m |= IPA_FAULT_ADMIT;
+    return m;
+}
+std::atomic<uint32_t> g_fault{fault_from_env()};
 thread_local char g_err[512] = "";
 std::mutex g_mu;
 std::vector<Scratch> g_scratch;   // indexed by device ordinal
@@ -39,6 +51,16 @@ void trace(const char* fmt, ...) {
     va_end(ap);
     fputc('\n', f);
     fflush(f);
+}
+
+bool fault(uint32_t bit) { return (g_fault.load(std::memory_order_relaxed) & bit) != 0; }
+
+ipa_status device_alloc(void** p, size_t bytes, const char* what) {
+    if (fault(IPA_FAULT_ALLOC)) {
+        set_error("%s: allocation of %zu bytes failed (injected, IPA_FAULT_ALLOC)", what, bytes);
+        return IPA_ERR_OOM;
+    }
+    return cuda_fail(cudaMalloc(p, bytes), what);
 }
 
 void set_error(const char* fmt, ...) {
@@ -154,19 +176,22 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
             s.gcount = nullptr;
             s.partials_cap = 0;
         }
-        if ((st = cuda_fail(cudaMalloc(&s.partials, cap * sizeof(double)), "scratch partials")) != IPA_OK)
+        if ((st = device_alloc((void**)&s.partials, cap * sizeof(double), "scratch partials")) != IPA_OK)
             return st;
         // one group counter per tile; zero between calls (kernels reset what they use)
         const size_t n_tiles = cap / kMaxAcc + 1;
-        if ((st = cuda_fail(cudaMalloc(&s.gcount, n_tiles * sizeof(unsigned)), "scratch group counters")) != IPA_OK)
+        if ((st = device_alloc((void**)&s.gcount, n_tiles * sizeof(unsigned), "scratch group counters")) != IPA_OK) {
+            cudaFree(s.partials);
+            s.partials = nullptr;
             return st;
+        }
         if ((st = cuda_fail(cudaMemset(s.gcount, 0, n_tiles * sizeof(unsigned)), "scratch memset")) != IPA_OK)
             return st;
         if ((st = cuda_fail(cudaDeviceSynchronize(), "scratch init")) != IPA_OK) return st;
         s.partials_cap = cap;
     }
     if (!s.work) {
-        if ((st = cuda_fail(cudaMalloc(&s.work, 2 * sizeof(unsigned)), "scratch work counters")) != IPA_OK) return st;
+        if ((st = device_alloc((void**)&s.work, 2 * sizeof(unsigned), "scratch work counters")) != IPA_OK) return st;
         if ((st = cuda_fail(cudaMemset(s.work, 0, 2 * sizeof(unsigned)), "scratch memset")) != IPA_OK) return st;
         if ((st = cuda_fail(cudaDeviceSynchronize(), "scratch init")) != IPA_OK) return st;
     }
@@ -183,12 +208,16 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
             s.consts = nullptr;
             s.seg_cap = 0;
         }
-        if ((st = cuda_fail(cudaMalloc(&s.counters, cap * sizeof(unsigned)), "scratch counters")) != IPA_OK)
+        if ((st = device_alloc((void**)&s.counters, cap * sizeof(unsigned), "scratch counters")) != IPA_OK)
             return st;
-        if ((st = cuda_fail(cudaMalloc(&s.seg_tiles, (cap + 1) * sizeof(int64_t)), "scratch tiles")) != IPA_OK)
+        if ((st = device_alloc((void**)&s.seg_tiles, (cap + 1) * sizeof(int64_t), "scratch tiles")) != IPA_OK ||
+            (st = device_alloc((void**)&s.consts, cap * sizeof(Consts), "scratch consts")) != IPA_OK) {
+            cudaFree(s.counters);
+            cudaFree(s.seg_tiles);
+            s.counters = nullptr;
+            s.seg_tiles = nullptr;
             return st;
-        if ((st = cuda_fail(cudaMalloc(&s.consts, cap * sizeof(Consts)), "scratch consts")) != IPA_OK)
-            return st;
+        }
         // counters must be zero between calls; kernels reset what they use
         if ((st = cuda_fail(cudaMemset(s.counters, 0, cap * sizeof(unsigned)), "scratch memset")) != IPA_OK)
             return st;
@@ -197,6 +226,18 @@ ipa_status scratch_get(int64_t tiles, int64_t segs, Scratch** out) {
     }
     *out = &s;
     return IPA_OK;
+}
+
+// Device bytes of the scratch held on device `dev` (the buffers scratch_get allocates).
+uint64_t scratch_bytes(int dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= (int)g_scratch.size()) return 0;
+    const Scratch& s = g_scratch[dev];
+    uint64_t b = 0;
+    if (s.partials) b += s.partials_cap * sizeof(double) + (s.partials_cap / kMaxAcc + 1) * sizeof(unsigned);
+    if (s.work) b += 2 * sizeof(unsigned);
+    if (s.counters) b += s.seg_cap * (sizeof(unsigned) + sizeof(Consts)) + (s.seg_cap + 1) * sizeof(int64_t);
+    return b;
 }
 
 }  // namespace ipa
@@ -230,6 +271,22 @@ extern "C" ipa_status ipa_reserve(int64_t max_events, int32_t max_segments) {
     ipa::Scratch* sc = nullptr;
     return ipa::scratch_get((max_events + ipa::kTile - 1) / ipa::kTile + max_segments,
                             (int64_t)max_segments + 1, &sc);
+}
+
+extern "C" ipa_status ipa_scratch_bytes(uint64_t* bytes) {
+    if (!bytes) {
+        ipa::set_error("ipa_scratch_bytes: bytes is NULL");
+        return IPA_ERR_ARG;
+    }
+    int dev = 0;
+    ipa_status st = ipa::cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != IPA_OK) return st;
+    *bytes = ipa::scratch_bytes(dev);
+    return IPA_OK;
+}
+
+extern "C" uint32_t ipa_fault_inject(uint32_t mask) {
+    return ipa::g_fault.exchange(mask & (IPA_FAULT_ALLOC | IPA_FAULT_SUBMIT | IPA_FAULT_ADMIT));
 }
 
 extern "C" const char* ipa_last_error(void) { return ipa::g_err; }

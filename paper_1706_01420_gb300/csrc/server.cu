@@ -181,7 +181,9 @@ void worker_main(ipa_server* s) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (s->stop || s->fatal != IPA_OK) break;
-            while (!s->queue.empty()) {
+            // an injected admission failure (IPA_FAULT_ADMIT) leaves every queued
+            // request waiting, in order, for a later tick
+            while (!s->queue.empty() && !fault(IPA_FAULT_ADMIT)) {
                 Request* r = s->queue.front();
                 int slot = -1;
                 for (int i = 0; i < s->max_slots; ++i)
@@ -305,7 +307,7 @@ void worker_main(ipa_server* s) {
 
 template <class T>
 ipa_status dalloc(T** p, size_t count, const char* what) {
-    return cuda_fail(cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1)), what);
+    return device_alloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1), what);
 }
 
 template <class T>
@@ -455,6 +457,11 @@ extern "C" ipa_status ipa_serve_submit(ipa_server* s, const ipa_events* ev, cons
         set_error("ipa_serve_submit: %lld events exceed the server's HBM budget of %lld events",
                   (long long)ev->n, (long long)s->arena_cap);
         return IPA_ERR_ARG;
+    }
+    if (fault(IPA_FAULT_SUBMIT)) {
+        set_error("ipa_serve_submit: staging allocation failed (injected, IPA_FAULT_SUBMIT); the request was "
+                  "not taken and may be submitted again");
+        return IPA_ERR_OOM;
     }
     Request* r = new Request();
     if ((st = build_spec(&s->model, spec, s->max_iter, s->tol, &r->spec)) != IPA_OK) {

@@ -332,6 +332,29 @@ ipa_status launch_tag_consts(const ModelDev& m, const double* theta, int n_seg, 
     return cuda_fail(cudaGetLastError(), "tagged consts kernel launch");
 }
 
+namespace {
+// ipa_nll_grad_combine for the tagged model: the kernel's last reduction level
+// over gathered group partials, then tag_finalize (one warp).
+__global__ void tag_combine_kernel(const double* __restrict__ groups, int64_t n_groups,
+                                   const Consts* __restrict__ consts, int n_par, double* __restrict__ out) {
+    constexpr int NA = n_acc(IPA_MODEL_TAGGED1D, true);
+    const int lane = threadIdx.x & 31;
+    if (n_groups == 0) {
+        for (int j = lane; j < 1 + n_par; j += 32) out[j] = 0.0;
+        return;
+    }
+    double acc[NA];
+    gather_butterfly<NA>(reduce_partials<NA>(groups, 0, n_groups, 1, lane), acc);
+    tag_finalize<true>(*reinterpret_cast<const TagConsts*>(consts), acc, n_par, out, lane);
+}
+}  // namespace
+
+ipa_status launch_tag_combine(const double* groups, int64_t n_groups, const Consts* consts, int n_par, double* out,
+                              cudaStream_t s) {
+    tag_combine_kernel<<<1, 32, 0, s>>>(groups, n_groups, consts, n_par, out);
+    return cuda_fail(cudaGetLastError(), "tagged combine kernel launch");
+}
+
 ipa_status launch_tag_nll(const ModelDev& m, bool grad, const Cols& cols, int64_t n,
                           const int64_t* seg_begin, const int64_t* seg_end, const int64_t* seg_tiles, int n_seg,
                           const Consts* consts, Scratch* sc, double* out, cudaStream_t st, const LaunchCfg* cfg) {

@@ -159,7 +159,7 @@ extern "C" ipa_status ipa_autotune(const ipa_model* model, const ipa_events* ev,
     const bool g = grad != 0;
     const int stride = g ? 1 + model->n_par : 1;
     double* out = nullptr;
-    if ((st = cuda_fail(cudaMalloc(&out, sizeof(double) * (size_t)n_seg * stride), "tuner output")) != IPA_OK)
+    if ((st = device_alloc((void**)&out, sizeof(double) * (size_t)n_seg * stride, "tuner output")) != IPA_OK)
         return st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);

@@ -47,9 +47,71 @@ def grad_scale(O, m, ev, th):
     return out
 
 
+def grad_scale_tagged(O, T, m, ev, th):
+    """Condition scale of each gradient component: sum over events of |w| / P
+    times the absolute values of the pieces the kernel adds for it (each
+    derivative of g is a sum of terms in g, tau g and the Gaussian)."""
+    Gamma, sigma, mu, f_b, DG, Dm, phi, om = (float(v) for v in th)
+    GH, GL = Gamma - DG / 2, Gamma + DG / 2
+    c, s, D = math.cos(phi), math.sin(phi), 1 - 2 * om
+    aH, aL, Ds = (1 - c) / 2, (1 + c) / 2, D * s
+    t = np.asarray(ev["t"])
+    w = np.abs(np.asarray(ev["w"])) if ev.get("w") is not None else np.ones_like(t)
+    tau = t - mu
+    G = O.gauss(tau, sigma)
+    gH = np.abs(T.conv_c(tau, GH, sigma))
+    gL = np.abs(T.conv_c(tau, GL, sigma))
+    z = complex(Gamma, -Dm)
+    gc = np.abs(T.conv_c(tau, z, sigma))
+    at = np.abs(tau)
+
+    def pieces(x, g):
+        ax = abs(x)
+        return (ax * sigma ** 2 * g + at * g + sigma ** 2 * G,
+                ax * ax * sigma * g + ax * sigma * G + at / sigma * G,
+                ax * g + G)
+
+    pH, pL, pC = pieces(GH, gH), pieces(GL, gL), pieces(z, gc)
+    N, dN = T.norm_grad(m, th)
+    S, _ = T.signal(m, ev, th)
+    P = T.pdf(m, ev, th)
+    cs = (1 - f_b) / N
+    r = w / P
+    rows = [aH * pH[0] + aL * pL[0] + abs(Ds) * pC[0],
+            aH * pH[1] + aL * pL[1] + abs(Ds) * pC[1],
+            aH * pH[2] + aL * pL[2] + abs(Ds) * pC[2],
+            None,
+            0.5 * aH * pH[0] + 0.5 * aL * pL[0],
+            abs(Ds) * pC[0],
+            0.5 * abs(s) * (gH + gL) + abs(D * c) * gc,
+            2 * abs(s) * gc]
+    out = np.zeros(8)
+    for j, row in enumerate(rows):
+        if row is None:
+            out[j] = math.fsum(r * (np.abs(S) / N + 1 / (2 * (m.t_hi - m.t_lo))))
+        else:
+            out[j] = cs * math.fsum(r * (row + np.abs(S) * abs(dN[j] / N)))
+    return out
+
+
 def assert_nll_grad_close(got, f_ref, g_ref, scale, logl_abs, rtol_f=1e-12, rtol_g=1e-9):
     f_got, g_got = float(got[0]), np.asarray(got[1:])
     assert abs(f_got - f_ref) <= rtol_f * logl_abs, (f_got, f_ref, (f_got - f_ref) / logl_abs)
     bound = rtol_g * np.maximum(np.abs(g_ref), scale)
     bad = np.abs(g_got - g_ref) > bound
     assert not bad.any(), {"got": g_got[bad], "ref": g_ref[bad], "bound": bound[bad]}
+
+
+def report_margin(name, got, f_ref, g_ref, scale):
+    """Print (pytest -s, or -rP) how far inside the tolerances a result is: the
+    NLL's relative error, and per gradient component the error relative to |g_j|
+    and to the condition scale B_j that the 1e-9 bound uses."""
+    got = np.asarray(got)
+    g_ref, scale = np.asarray(g_ref), np.asarray(scale)
+    d = np.abs(got[1:] - g_ref)
+    nz = np.abs(g_ref) > 0
+    rel_g = float((d[nz] / np.abs(g_ref[nz])).max()) if nz.any() else 0.0
+    rel_b = float((d / np.maximum(np.maximum(np.abs(g_ref), scale), 1e-300)).max())
+    print(f"MARGIN {name}: nll rel {abs(float(got[0]) - f_ref) / abs(f_ref):.2e}, "
+          f"max |dg|/|g| {rel_g:.2e}, max |dg|/max(|g|,B) {rel_b:.2e}, "
+          f"max B/|g| {float((scale[nz] / np.abs(g_ref[nz])).max()) if nz.any() else 0.0:.2e}")

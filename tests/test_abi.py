@@ -58,6 +58,7 @@ def test_model_init_and_host_argument_checks(lib):
     bad = C.ipa_model(kind=2, n_par=4, t_lo=0.0, t_hi=1.0)
     assert lib.ipa_nll(ctypes.byref(bad), ctypes.byref(ev), 16, 16, None) == C.IPA_ERR_ARG
     assert lib.ipa_reserve(-1, 1) == C.IPA_ERR_ARG
+    assert lib.ipa_scratch_bytes(None) == C.IPA_ERR_ARG
     assert lib.ipa_version().startswith(b"ipanema")
 
 
@@ -151,3 +152,21 @@ def test_launch_config_table_host_logic(lib):
     assert lib.ipa_launch_config_get(ctypes.byref(m), -1, 1, 1, 0, ctypes.byref(cfg)) == C.IPA_ERR_ARG
     assert lib.ipa_launch_config_get(ctypes.byref(m), 10, 0, 1, 0, ctypes.byref(cfg)) == C.IPA_ERR_ARG
     lib.ipa_launch_config_set(ctypes.byref(m), 3_000_000, 1, 1, 0, ctypes.byref(default))   # leave the default
+
+
+def test_fault_mask_set_and_read_back(lib):
+    """ipa_fault_inject returns the previous mask and keeps only the known bits;
+    IPA_FAULT in the environment sets the mask when the library loads (checked in
+    a fresh process).  No GPU is needed: nothing is injected on a device."""
+    import subprocess
+    import sys
+    from paper_1706_01420_gb300 import _capi as C
+    old = lib.ipa_fault_inject(C.IPA_FAULT_SUBMIT | 64)
+    assert lib.ipa_fault_inject(0) == C.IPA_FAULT_SUBMIT
+    lib.ipa_fault_inject(old)
+    code = ("import sys; sys.path.insert(0, %r); from paper_1706_01420_gb300 import _capi as C; "
+            "print(C.load().ipa_fault_inject(0))" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120,
+                       env=dict(os.environ, IPA_FAULT="admit,alloc"))
+    assert r.returncode == 0, r.stderr
+    assert int(r.stdout.strip()) == C.IPA_FAULT_ALLOC | C.IPA_FAULT_ADMIT

@@ -111,24 +111,19 @@ def test_fit_runs_as_one_device_loop_and_reuses_its_graph(env, tmp_path, monkeyp
     assert len(lines) == 4 and all(x["loop"] == "device" for x in lines)
 
 
-@pytest.mark.slow
-def test_gpu_toy_pulls(env):
-    """256 GPU-generated toys of Poisson(2e4) events fitted in one batch: pulls of
-    the eight well-measured parameters have mean 0 and width 1 within 3.5
-    standard errors.  sigma and mu are measured only by the ~1e3 events of the
-    turn-on at t ~ 0; at this size their pulls are visibly non-Gaussian (a
-    small-sample property of the likelihood that fades at 2e5 events), so they
-    get a looser bound."""
+def _toy_pulls(env, n_toys, mean_size, seed, gen_seed):
+    """Pulls (theta - truth) / error of n_toys GPU-generated toys of
+    Poisson(mean_size) events fitted in one batch, all ten parameters free,
+    over the converged fits."""
     O, G, torch, api = env
-    n_toys = 256
-    n_sig, n_bkg = synth.toy_sizes(n_toys, 2e4, TH4[3], seed=2)
+    n_sig, n_bkg = synth.toy_sizes(n_toys, mean_size, TH4[3], seed=seed)
     sizes = n_sig + n_bkg
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     total = int(off[-1])
     dev = lambda a: torch.tensor(a, dtype=torch.int64, device="cuda")
     cols = {k: torch.empty(total, dtype=torch.float64, device="cuda") for k in ("t", "ck", "cl", "phi")}
     m = api.model_4d(0.0, 15.0)
-    api.ipa_toygen(m, torch.tensor(TH4, device="cuda"), 77, dev(n_sig), dev(n_bkg), dev(off[:-1]), cols)
+    api.ipa_toygen(m, torch.tensor(TH4, device="cuda"), gen_seed, dev(n_sig), dev(n_bkg), dev(off[:-1]), cols)
     free = list(range(10))
     theta = torch.tensor(np.tile(TH4, (n_toys, 1)), device="cuda")
     r = api.ipa_fit_batch(m, cols, dev(off), _params(api, TH4, LO4, HI4, STEP4, free), theta,
@@ -138,11 +133,44 @@ def test_gpu_toy_pulls(env):
     er = r["err"].cpu().numpy()
     ok = st == 0
     assert ok.mean() > 0.95, np.bincount(st)
-    se = 1 / math.sqrt(ok.sum())
+    del cols
+    torch.cuda.empty_cache()
+    pulls = (th[ok] - TH4) / er[ok]
+    print(f"PULLS {n_toys} toys of Poisson({mean_size:g}): mean", np.round(pulls.mean(axis=0), 4).tolist(),
+          "width", np.round(pulls.std(axis=0, ddof=1), 4).tolist())
+    return pulls
+
+
+@pytest.mark.slow
+def test_gpu_toy_pulls_all_parameters_2e5(env):
+    """256 toys of Poisson(2e5) events: the pulls of all ten parameters have
+    mean 0 and width 1, |mean| < 3.5/sqrt(n) and |width - 1| < 3.5/sqrt(2n) +
+    0.03 (the HESSE errors at NLL_min + 1/2 of Sec. 3 are the standard
+    deviations of the estimates)."""
+    pulls = _toy_pulls(env, 256, 2e5, seed=3, gen_seed=79)
+    n = pulls.shape[0]
+    for j in range(10):
+        p = pulls[:, j]
+        assert abs(p.mean()) < 3.5 / math.sqrt(n), (j, p.mean())
+        assert abs(p.std(ddof=1) - 1) < 3.5 / math.sqrt(2 * n) + 0.03, (j, p.std(ddof=1))
+
+
+@pytest.mark.slow
+def test_gpu_toy_pulls(env):
+    """256 GPU-generated toys of Poisson(2e4) events fitted in one batch: pulls of
+    the eight parameters other than sigma and mu have mean 0 and width 1 within
+    3.5 standard errors.  sigma and mu are measured only by the ~1e3 events of
+    the turn-on at t ~ 0; at this size their pulls are biased (the maximum-
+    likelihood bias of order 1/sqrt(N) in pull units: mu's mean pull is about
+    +0.25 at 2e4 events and falls to about a third of that at 2e5, where
+    test_gpu_toy_pulls_all_parameters_2e5 checks all ten with the strict
+    bound), so here they get a looser one."""
+    pulls = _toy_pulls(env, 256, 2e4, seed=2, gen_seed=77)
+    se = 1 / math.sqrt(pulls.shape[0])
     for j in (0, 3, 4, 5, 6, 7, 8, 9):
-        p = (th[ok, j] - TH4[j]) / er[ok, j]
+        p = pulls[:, j]
         assert abs(p.mean()) < 3.5 * se, (j, p.mean())
         assert abs(p.std(ddof=1) - 1) < 3.5 * se / math.sqrt(2) + 0.03, (j, p.std(ddof=1))
     for j in (1, 2):
-        p = (th[ok, j] - TH4[j]) / er[ok, j]
+        p = pulls[:, j]
         assert abs(p.mean()) < 0.5 and 0.8 < p.std(ddof=1) < 1.35, (j, p.mean(), p.std(ddof=1))

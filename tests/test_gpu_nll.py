@@ -49,6 +49,8 @@ def _parity(env, kind, n, seed, weighted, th, t_lo=None):
     scale = G.grad_scale(O, m_o, cols, th) if n else np.zeros(th.size)
     G.assert_nll_grad_close(got, f_ref, g_ref, scale, labs)
     assert abs(nll_only - f_ref) <= 1e-12 * labs
+    if n >= 100_000:
+        G.report_margin(f"{kind} {n}", got, f_ref, g_ref, scale)
     return got
 
 

@@ -233,3 +233,23 @@ def test_toys_bit_exact(env, Q):
         sl = slice(int(off[k]), int(off[k] + n_sig[k] + n_bkg[k]))
         for col in ("t", "ck", "cl", "phi", "q"):
             assert np.array_equal(got[col][sl], ref[col]), (k, col)
+
+
+def test_parity_full_size_bench_workload(env):
+    """The phi_s workload of the benchmark at its full size: 1e6 synthetic
+    events (seed 11) at the benchmark's parameters, NLL and gradient against the
+    oracle, raw and with the cached angular basis."""
+    O, F, G, torch, api = env
+    th = np.array([0.66, 0.045, 0.0, 0.1, 0.52, 0.25, 3.2, 3.1, 0.04, 0.3, 0.085, 17.77, 0.8, 0.3, 0.8, 0.0])
+    m_o, m_g = O.Model("phis", 0.0, 15.0), api.model_phis(0.0, 15.0)
+    cols = synth.events_phis(1_000_000, 11)
+    ev = G.to_dev(cols)
+    theta = torch.tensor(th, device="cuda")
+    got = api.ipa_nll_grad(m_g, ev, theta).cpu().numpy()
+    cached = api.ipa_nll_grad(m_g, dict(ev, fk=api.ipa_angular_basis(m_g, ev)), theta).cpu().numpy()
+    f_ref, g_ref = F.nll_grad(m_o, cols, th)
+    logl, _ = F.nll_grad_terms(m_o, cols, th)
+    scale = grad_scale(F, m_o, cols, th)
+    for out in (got, cached):
+        G.assert_nll_grad_close(out, f_ref, g_ref, scale, math.fsum(np.abs(logl)))
+    G.report_margin("phis 1e6", got, f_ref, g_ref, scale)

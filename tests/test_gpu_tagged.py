@@ -41,53 +41,6 @@ def env(oracle):
     return oracle, tagged, G, torch, api
 
 
-def grad_scale(O, T, m, ev, th):
-    """Condition scale of each gradient component: sum over events of |w| / P
-    times the absolute values of the pieces the kernel adds for it (each
-    derivative of g is a sum of terms in g, tau g and the Gaussian)."""
-    Gamma, sigma, mu, f_b, DG, Dm, phi, om = (float(v) for v in th)
-    GH, GL = Gamma - DG / 2, Gamma + DG / 2
-    c, s, D = math.cos(phi), math.sin(phi), 1 - 2 * om
-    aH, aL, Ds = (1 - c) / 2, (1 + c) / 2, D * s
-    t = np.asarray(ev["t"])
-    w = np.abs(np.asarray(ev["w"])) if ev.get("w") is not None else np.ones_like(t)
-    tau = t - mu
-    G = O.gauss(tau, sigma)
-    gH = np.abs(T.conv_c(tau, GH, sigma))
-    gL = np.abs(T.conv_c(tau, GL, sigma))
-    z = complex(Gamma, -Dm)
-    gc = np.abs(T.conv_c(tau, z, sigma))
-    at = np.abs(tau)
-
-    def pieces(x, g):
-        ax = abs(x)
-        return (ax * sigma ** 2 * g + at * g + sigma ** 2 * G,
-                ax * ax * sigma * g + ax * sigma * G + at / sigma * G,
-                ax * g + G)
-
-    pH, pL, pC = pieces(GH, gH), pieces(GL, gL), pieces(z, gc)
-    N, dN = T.norm_grad(m, th)
-    S, _ = T.signal(m, ev, th)
-    P = T.pdf(m, ev, th)
-    cs = (1 - f_b) / N
-    r = w / P
-    rows = [aH * pH[0] + aL * pL[0] + abs(Ds) * pC[0],
-            aH * pH[1] + aL * pL[1] + abs(Ds) * pC[1],
-            aH * pH[2] + aL * pL[2] + abs(Ds) * pC[2],
-            None,
-            0.5 * aH * pH[0] + 0.5 * aL * pL[0],
-            abs(Ds) * pC[0],
-            0.5 * abs(s) * (gH + gL) + abs(D * c) * gc,
-            2 * abs(s) * gc]
-    out = np.zeros(8)
-    for j, row in enumerate(rows):
-        if row is None:
-            out[j] = math.fsum(r * (np.abs(S) / N + 1 / (2 * (m.t_hi - m.t_lo))))
-        else:
-            out[j] = cs * math.fsum(r * (row + np.abs(S) * abs(dN[j] / N)))
-    return out
-
-
 def _parity(env, n, seed, th, weighted=False, t_lo=0.0):
     O, T, G, torch, api = env
     m_o, m_g = O.Model("tag", t_lo, 15.0), api.model_tagged(t_lo, 15.0)
@@ -99,7 +52,7 @@ def _parity(env, n, seed, th, weighted=False, t_lo=0.0):
     f_ref, g_ref = T.nll_grad(m_o, cols, th)
     logl, _ = T.nll_grad_terms(m_o, cols, th)
     labs = math.fsum(np.abs(logl)) if n else 1.0
-    scale = grad_scale(O, T, m_o, cols, th) if n else np.zeros(8)
+    scale = G.grad_scale_tagged(O, T, m_o, cols, th) if n else np.zeros(8)
     G.assert_nll_grad_close(got, f_ref, g_ref, scale, labs)
     assert abs(nll_only - f_ref) <= 1e-12 * labs
     return got
@@ -250,3 +203,21 @@ def test_fit_matches_oracle_and_batch_equals_solo(env):
         assert batch["err"][0, j] == pytest.approx(ref.err[j], rel=1e-3)
     assert batch["nll"][0] == pytest.approx(ref.nll, rel=1e-12)
     del cols
+
+
+def test_parity_full_size_bench_workload(env):
+    """The tagged workload of the benchmark at its full size: 50 toys of 2e4
+    events (1.8e4 signal, 2e3 background, seed 7) drawn by the oracle's
+    generator (bit for bit the events ipa_toygen writes), NLL and gradient
+    against the oracle at the truth."""
+    O, T, G, torch, api = env
+    m_o, m_g = O.Model("tag", 0.0, 15.0), api.model_tagged(0.0, 15.0)
+    toys = [T.toy_one(m_o, TRUTH, 7, k, 18000, 2000) for k in range(50)]
+    cols = {k: np.concatenate([t[k] for t in toys]) for k in toys[0]}
+    ev = G.to_dev(cols)
+    got = api.ipa_nll_grad(m_g, ev, torch.tensor(TRUTH, device="cuda")).cpu().numpy()
+    f_ref, g_ref = T.nll_grad(m_o, cols, TRUTH)
+    logl, _ = T.nll_grad_terms(m_o, cols, TRUTH)
+    scale = G.grad_scale_tagged(O, T, m_o, cols, TRUTH)
+    G.assert_nll_grad_close(got, f_ref, g_ref, scale, math.fsum(np.abs(logl)))
+    G.report_margin("tagged 1e6", got, f_ref, g_ref, scale)
