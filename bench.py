@@ -33,6 +33,8 @@ GPU; there is no data-path collective); value = total events / max time.
 from __future__ import annotations
 
 import argparse
+import csv
+import hashlib
 import json
 import math
 import os
@@ -63,21 +65,23 @@ WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 # the amplitude sum A'), the ten angular adjoint sums S_k (64-bit fixed point)
 # and the lane's product of the P mantissas run on the integer pipe and count no
 # FP64 operation; only their arguments and results do:
-#   every event: tau, the exponent of 2E, P, 1/P (an FP32 seed and one FP64
-#     Newton step: 2 FMA), sum r, r T2, r A', u = r A' tau, sum u T2;
-#     weighted: w log P and w / P;
+#   every event: tau, the exponent of 2E, T2 = 2E - X (computed for every
+#     event, selected for the near-peak ones), P, 1/P (an FP32 seed and one
+#     FP64 Newton step: 2 FMA), sum r, r T2 (then fixed point), r A', u = r A'
+#     tau and the three sums u T2, r A' Gx, u Gx (Gx = 0 away from the peak);
+#   unweighted: the lane's product of the P mantissas (one multiply);
+#     weighted: w log P, w / P and the product (by 1 or P);
 #   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma,
-#     packed 32 to a warp pass): tau, the Gaussian's exponent, the erfcx
-#     argument and erfcx, g X, the exponent of 2E and T2, and the two sums of the
-#     Gaussian terms;
+#     packed 32 to a warp pass): tau, the Gaussian's exponent (tau^2 k_g), the
+#     erfcx argument ((Gs2 - tau) k_z), erfcx and g X;
 #   once per lane and 512-event tile (16 events): the log of the product and
 #     its exponent term.
 # (Angles within 2^-17 of |cos| = 1, about 1.5e-5 of the events, take the FP64
 # basis instead; they are not counted.)
-OPS_EVENT_4D = {"fma": 5, "mul": 3, "add": 2}
-OPS_UNWEIGHTED = {}
-OPS_WEIGHTED = {"fma": 1, "mul": 1, "log_fast": 1}
-OPS_NEAR_PEAK = {"fma": 3, "mul": 4, "add": 3, "erfcx_poly": 1}
+OPS_EVENT_4D = {"fma": 7, "mul": 3, "add": 3}
+OPS_UNWEIGHTED = {"mul": 1}
+OPS_WEIGHTED = {"fma": 1, "mul": 2, "log_fast": 1}
+OPS_NEAR_PEAK = {"mul": 4, "add": 2, "erfcx_poly": 1}
 OPS_LANE_TILE = {"fma": 2, "log_fast": 1}
 
 
@@ -144,22 +148,12 @@ def flops_per_event(cal: dict, near: float, weighted: bool = False) -> float:
     return f + _flops(OPS_UNWEIGHTED, cal) + _flops(OPS_LANE_TILE, cal) / 16.0
 
 
-def kernel_traffic(n_events: int):
-    """DRAM bytes per launch of the fused kernel from the committed ncu capture
-    (profiles/traffic.json), scaled by events; None if the kernel sources changed
-    since the capture."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        rec = json.load(open(path))
-        h = hashlib.sha256()
-        for f in rec["source_files"]:
-            h.update(open(os.path.join(ROOT, "paper_1706_01420_gb300", "csrc", f), "rb").read())
-        if h.hexdigest() != rec["source_sha256"]:
-            return None
-        return rec["bytes_per_event"] * n_events
-    except (OSError, ValueError, KeyError):
-        return None
+def kernel_traffic(n_events: int, kernel: str = "nll_kernel<4D, grad>"):
+    """DRAM bytes per launch of a kernel (read + write, from the committed ncu
+    capture in profiles/kernel_counts.json) scaled by events; None if the
+    kernel's sources changed since the capture."""
+    counts = kernel_counts(kernel)
+    return None if counts is None else counts["dram_bytes"] * n_events
 
 
 def kernel_counts(kernel: str):
@@ -167,7 +161,6 @@ def kernel_counts(kernel: str):
     (profiles/kernel_counts.json): warp instructions issued, FP64 lane
     operations and DRAM bytes per event; None if the record is missing or the
     kernel's sources changed since the capture."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "kernel_counts.json")
     try:
         rec = json.load(open(path))[kernel]
@@ -179,6 +172,71 @@ def kernel_counts(kernel: str):
         return rec["per_event"]
     except (OSError, ValueError, KeyError):
         return None
+
+
+# ---- profiles/kernel_counts.json: per-event counts of the likelihood kernels ----
+# From the CSV logs of these ncu captures (each after the same command exited
+# 0 without ncu):
+#   ncu --metrics <COUNT_METRICS> --clock-control none -k regex:<kernel> -s 2 -c 1 --csv \
+#       --log-file <dir>/counts_<name>.csv python bench.py --profile-case[-phis|-tagged]
+# `python bench.py --write-kernel-counts <dir>` writes the record with a SHA-256
+# of the sources each count belongs to; kernel_counts() uses a record only while
+# that hash matches.
+COUNT_METRICS = ("smsp__inst_executed.sum,smsp__inst_executed_pipe_fp64.sum,"
+                 "sm__sass_thread_inst_executed_op_dfma_pred_on.sum,sm__sass_thread_inst_executed_op_dmul_pred_on.sum,"
+                 "sm__sass_thread_inst_executed_op_dadd_pred_on.sum,dram__bytes_read.sum,dram__bytes_write.sum,"
+                 "gpu__time_duration.sum,smsp__cycles_active.sum,smsp__issue_active.sum")
+COUNT_COMMON = ["tile_reduce.cuh", "fp64_math.cuh", "fp64_tables.cuh", "int_math.cuh", "ipa_internal.cuh"]
+COUNT_CAPTURES = {
+    "nll_kernel<4D, grad>": ("counts_4d.csv", "bench.py --profile-case", 8_000_000,
+                             ["nll.cu", "angular.cuh", "consts.cuh"] + COUNT_COMMON),
+    "phis_kernel<grad>": ("counts_phis.csv", "bench.py --profile-case-phis", 8_000_000,
+                          ["phis.cu", "angular.cuh", "tagged.cuh", "faddeeva.cuh", "consts.cuh", "philox.cuh"] + COUNT_COMMON),
+    "tag_kernel<grad>": ("counts_tag.csv", "bench.py --profile-case-tagged", 8_000_000,
+                         ["tagged.cu", "tagged.cuh", "faddeeva.cuh", "consts.cuh"] + COUNT_COMMON),
+}
+
+
+def _csv_metrics(path):
+    rows = list(csv.reader(open(path)))
+    hdr, out = None, {}
+    for r in rows:
+        if r and r[0] == "ID":
+            hdr = r
+            continue
+        if hdr and len(r) == len(hdr):
+            d = dict(zip(hdr, r))
+            out[d["Metric Name"]] = float(d["Metric Value"].replace(",", ""))
+    return out
+
+
+def write_kernel_counts(src_dir: str) -> int:
+    rec = {}
+    for kernel, (fname, cmd, n, files) in COUNT_CAPTURES.items():
+        m = _csv_metrics(os.path.join(src_dir, fname))
+        h = hashlib.sha256()
+        for f in files:
+            h.update(open(os.path.join(ROOT, "paper_1706_01420_gb300", "csrc", f), "rb").read())
+        fp64 = (m["sm__sass_thread_inst_executed_op_dfma_pred_on.sum"] +
+                m["sm__sass_thread_inst_executed_op_dmul_pred_on.sum"] +
+                m["sm__sass_thread_inst_executed_op_dadd_pred_on.sum"])
+        rec[kernel] = {
+            "capture": f"ncu --metrics {COUNT_METRICS} --clock-control none -k regex:{kernel.split('<')[0]} -s 2 -c 1 "
+                       f"--csv --log-file {fname} python {cmd}",
+            "events": n,
+            "duration_us": m["gpu__time_duration.sum"] / 1e3,
+            "issue_active_frac": m["smsp__issue_active.sum"] / m["smsp__cycles_active.sum"],
+            "per_event": {"warp_inst": m["smsp__inst_executed.sum"] / n,
+                          "fp64_warp_inst": m["smsp__inst_executed_pipe_fp64.sum"] / n,
+                          "fp64_lane_ops": fp64 / n,
+                          "dram_bytes": (m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]) / n},
+            "source_files": files,
+            "source_sha256": h.hexdigest(),
+        }
+    json.dump(rec, open(os.path.join(ROOT, "profiles", "kernel_counts.json"), "w"), indent=1)
+    print(json.dumps({k: v["per_event"] for k, v in rec.items()}, indent=1))
+    return 0
+
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -455,9 +513,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip fit/toygen/batch sub-benchmarks")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of single-core oracle timing (0: no CPU baseline, for profiling runs)")
     ap.add_argument("--profile-case", action="store_true",
                     help="untimed: 4 ipa_nll_grad calls on 8e6 4D events (256 MB, > L2), for ncu")
+    ap.add_argument("--write-kernel-counts", metavar="DIR",
+                    help="write profiles/kernel_counts.json from the ncu CSV logs in DIR and exit")
     ap.add_argument("--profile-events", type=int, default=8_000_000,
                     help="events of --profile-case (1000000: the headline workload's size)")
     ap.add_argument("--profile-case-tagged", action="store_true",
@@ -467,6 +528,8 @@ def main():
     ap.add_argument("--profile-case-joint", action="store_true",
                     help="untimed: Example 2's twelve-category fit of 1e4 events, twice, for an ncu launch list")
     args = ap.parse_args()
+    if args.write_kernel_counts:
+        return write_kernel_counts(args.write_kernel_counts)
     if args.profile_case:
         return profile_case(args.profile_events)
     if args.profile_case_tagged:
@@ -685,7 +748,8 @@ def main():
         lg["flops_frac"] = flops_per_event(cal, near_l, weighted=True) * lg["events"] / (
             lg["nll_grad_ms"] * 1e-3) / 1e12 / peak
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+        if args.cpu_budget > 0:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

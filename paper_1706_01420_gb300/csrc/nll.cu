@@ -167,11 +167,13 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
 // partial tile of a segment and the other variants take the plain loop of
 // nll_kernel.
 //
-// On this GPU an FP64 instruction costs a warp about as much issue time as 64
-// integer instructions, and the two kinds overlap poorly (a warp's FP64 work
-// and other warps' integer work largely serialise).  So the ten angular
-// adjoint sums S_k = sum r T f'_k, which in FP64 cost ten DFMA per event, are
-// accumulated here on the integer pipe: r T is converted once per event to
+// On this GPU a warp FP64 instruction occupies the sub-partition's FP64 unit
+// for about 64 cycles (2 FP64 operations per clock per SM).  A few FP64
+// instructions spread among a warp's integer work overlap with it, but a burst
+// of them does not (measured: removing the ten back-to-back DFMA of the
+// angular adjoint sums saved far more time than removing isolated DMUL or DADD
+// instructions, which cost about nothing).  So the ten sums S_k = sum r T f'_k
+// are accumulated here on the integer pipe: r T is converted once per event to
 // signed 64-bit fixed point with 40 fraction bits (rounded to nearest, for
 // |r T| < 2^19), and each product with the Q62 angular product f'_k is the
 // high 64 bits of the 128-bit product (Q38: the floor, corrected on average
@@ -181,13 +183,13 @@ __device__ __forceinline__ void event(const WarpConsts& wc, const MathTables* mt
 // the order of the events within a lane.  Error of a sum: about 2^-39 per
 // event, of random sign (a sum over 1e6 events is off by ~1e-9 absolute,
 // while the sums themselves are ~1e5 and the gradient tolerance is 1e-9 of
-// them).  The remaining
-// accumulators are FP64 as in the plain loop.  The integer work runs with the
-// branch-free functions of int_math.cuh; lanes outside their ranges are fixed
-// up with the FP64 paths of the plain loop.  A tile in which some P lies
-// outside the Newton reciprocal's range (zero, subnormal, negative, huge,
-// infinite or NaN) or some |r T| >= 2^19 is redone by the plain loop.  Either
-// way the tile's sums depend only on its events, never on the launch geometry.
+// them).  The remaining accumulators are FP64 as in the plain loop.  The
+// integer work runs with the branch-free functions of int_math.cuh; lanes
+// outside their ranges are fixed up with the FP64 paths of the plain loop.  A
+// tile in which some P lies outside the Newton reciprocal's range (zero,
+// subnormal, negative, huge, infinite or NaN) or some |r T| >= 2^19 is redone
+// by the plain loop.  Either way the tile's sums depend only on its events,
+// never on the launch geometry.
 
 // The integer-pipe results of one event that its FP64 work needs.
 struct RowIn {
@@ -262,17 +264,11 @@ __device__ __forceinline__ double log_fast_nb(double x, const MathTables* t) {
     return fma(ed, kLn2Hi, fma(ed, kLn2Lo, t->ltab[j] + l));
 }
 
-// The lane's product of the mantissas of P in Q62 ([1, 2)) with the exponents
-// summed apart, for positive normal P: the high 64 bits of the 128-bit product
-// (Q61, in [1, 4)) renormalised to [1, 2) (integer pipe; truncation below
-// 2^-61 per step, 2^-57 over a tile's 16 events).
-__device__ __forceinline__ void log_mul_q(double P, unsigned long long* prodq, int* esum) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(P);
-    const unsigned long long mq = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 11;   // Q63
-    const unsigned long long h = __umul64hi(*prodq, mq);                                      // Q61
-    const int big = (int)(h >> 62);
-    *prodq = big ? h : h << 1;
-    *esum += (int)(b >> 52) - 1023 + big;
+// log_mul for positive normal P (no branch for zero, subnormal or special P).
+__device__ __forceinline__ void log_mul_nb(double P, double* prod, int* esum) {
+    const long long b = __double_as_longlong(P);
+    *prod *= __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    *esum += (int)(b >> 52) - 1023;
 }
 
 // x 2^40 rounded to the nearest signed 64-bit integer (ties away from zero),
@@ -289,18 +285,17 @@ __device__ __forceinline__ long long to_q40(double x, bool* bad) {
     return (b >> 63) ? -v : v;
 }
 
-// The FP64 work of one event on the fast path.  tg: (T2, Gx) from the near-peak
-// pass for a marked event (slow), else unused.  The adjoint sums: acci (the
-// ten S_k, Q38), acc[1] and acc[12] here; r A' and u = r A' tau of a marked
-// event go to ru[slot] for the packed pass that adds acc[13] and acc[14]
-// (their terms vanish for the other events).  *bad is set when P is outside
-// [2^-125, 2^126) or |r T| >= 2^19.
+// The FP64 work of one event on the fast path: event() with the exponential
+// and the angular products from int_phase and the ten angular adjoint sums in
+// fixed point (acci, Q38).  ge: the event's gauss_erfcx value or (0, +0).
+// *bad is set when P is outside [2^-125, 2^126) or |r T| >= 2^19.
 template <bool GRAD, bool WEIGHTED>
-__device__ __forceinline__ void event_fast(const WarpConsts& wc, const MathTables* mt, const RowIn& v, bool slow,
-                                           double2 tg, double2* ru, double* acc, long long* acci,
-                                           unsigned long long* prodq, int* esum, bool* bad) {
+__device__ __forceinline__ void event_fast(const WarpConsts& wc, const MathTables* mt, const RowIn& v, double2 ge,
+                                           double* acc, long long* acci, double* prod, int* esum, bool* bad) {
     const Consts& c = wc.c;
-    const double T2 = slow ? tg.x : v.E2;
+    const long long gb = __double_as_longlong(ge.y);
+    const double T2 = gb >= 0 ? v.E2 - ge.x : ge.x;
+    const double Gx = __longlong_as_double(gb & 0x7FFFFFFFFFFFFFFFll);
     const double P = fma(T2, v.Ap, c.cb);
     const long long pb = __double_as_longlong(P);
     *bad |= (unsigned long long)(pb - 0x3820000000000000ll) >= 0x0FB0000000000000ull;
@@ -308,9 +303,9 @@ __device__ __forceinline__ void event_fast(const WarpConsts& wc, const MathTable
         // weight exactly 1: P joins the lane's product (as in event)
         const bool one = __double_as_longlong(v.w) == 0x3FF0000000000000ll;
         acc[0] = fma(one ? 0.0 : v.w, log_fast_nb(P, mt), acc[0]);
-        log_mul_q(one ? P : 1.0, prodq, esum);
+        log_mul_nb(one ? P : 1.0, prod, esum);
     } else {
-        log_mul_q(P, prodq, esum);
+        log_mul_nb(P, prod, esum);
     }
     if (GRAD) {
         const double r = WEIGHTED ? v.w * rcp_newton_nb(P) : rcp_newton_nb(P);
@@ -321,24 +316,27 @@ __device__ __forceinline__ void event_fast(const WarpConsts& wc, const MathTable
         const double rA = r * v.Ap;
         const double u = rA * v.tau;
         acc[12] = fma(u, T2, acc[12]);
-        if (slow) *ru = make_double2(rA, u);
+        acc[13] = fma(rA, Gx, acc[13]);
+        acc[14] = fma(u, Gx, acc[14]);
     }
 }
 
-// Near-peak marks of rows i0 .. i0 + kSub - 1 of a tile (lane l: event tbase +
-// l + 32 i): the warp's ballots of t <= tcut, and the packed Gaussian/erfcx
-// values of the marked events (in row order, lanes in order within a row) in
-// sbuf.  m[q] is row i0 + q's ballot, p[q] the number of marked events in the
-// rows before it.
-template <bool FULL>
-__device__ __forceinline__ void near_peak_rows(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
-                                               int64_t tbase, int64_t ev1, int i0, int lane, double2* sbuf,
-                                               unsigned m[kSub], int p[kSub]) {
+// Rows i0 .. i0 + kSub - 1 of a whole tile (lane l: events tbase + l + 32 i) of
+// the 4D model on the fast path: the near-peak events of the kSub rows marked
+// by ballot and their Gaussian/erfcx values evaluated packed into sbuf, then
+// the events row by row into acc (FP64 sums), acci (the fixed-point S_k), the
+// log product and *bad.
+template <bool WEIGHTED>
+__device__ __forceinline__ void block_fast(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
+                                           int64_t tbase, int i0, double2* sbuf, int lane, double* acc,
+                                           long long* acci, double* prod, int* esum, bool* bad) {
+    const unsigned below = (1u << lane) - 1u;
+    unsigned m[kSub];
+    int p[kSub];
 #pragma unroll
     for (int q = 0; q < kSub; ++q) {
         const int64_t e = tbase + lane + 32 * (i0 + q);
-        const bool slow = (FULL || e < ev1) && !greater(__ldg(cols.t + e), wc.tcut);
-        m[q] = __ballot_sync(0xffffffffu, slow);
+        m[q] = __ballot_sync(0xffffffffu, !greater(__ldg(cols.t + e), wc.tcut));
     }
     p[0] = 0;
     p[1] = __popc(m[0]);
@@ -353,90 +351,40 @@ __device__ __forceinline__ void near_peak_rows(const WarpConsts& wc, const MathT
         sbuf[j] = gauss_erfcx(wc.c, __ldg(cols.t + e) - wc.c.mu, mt);
     }
     __syncwarp();
-}
-
-// The near-peak values of the fast path for the marked events of rows i0 ..
-// i0 + kSub - 1 (packed as in near_peak_rows): T2 = 2 g(tau) itself (E2 minus
-// the erfcx term, or the erfcx term) and the Gaussian Gx.
-__device__ __forceinline__ void near_peak_fast(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
-                                               int64_t tbase, int i0, int lane, double2* sbuf, const unsigned m[kSub],
-                                               const int p[kSub], int n_slow) {
-    for (int j = lane; j < n_slow; j += 32) {
-        const int q = (j >= p[1]) + (j >= p[2]) + (j >= p[3]);
+#pragma unroll 1
+    for (int q = 0; q < kSub; ++q) {
         const unsigned mq = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
         const int before = q == 0 ? 0 : (q == 1 ? p[1] : (q == 2 ? p[2] : p[3]));
-        const int64_t e = tbase + nth_set(mq, j - before) + 32 * (i0 + q);
-        const double tau = __ldg(cols.t + e) - wc.c.mu;
-        const double2 ge = gauss_erfcx(wc.c, tau, mt);
-        const double E2 = exp_int(fma(-wc.c.Gamma, tau, wc.c2), mt);
-        const long long gb = __double_as_longlong(ge.y);
-        sbuf[j] = make_double2(gb >= 0 ? E2 - ge.x : ge.x, __longlong_as_double(gb & 0x7FFFFFFFFFFFFFFFll));
+        const double2 gv = sbuf[(before + __popc(mq & below)) & (kSub * 32 - 1)];
+        const double2 ge = (mq >> lane) & 1u ? gv : make_double2(0.0, 0.0);
+        const int64_t e = tbase + lane + 32 * (i0 + q);
+        RowIn v;
+        const bool ok = int_phase<WEIGHTED>(wc, mt, cols, e, v);
+        if (__any_sync(0xffffffffu, !ok)) fix_int_phase(wc, mt, cols, e, v);
+        event_fast<true, WEIGHTED>(wc, mt, v, ge, acc, acci, prod, esum, bad);
     }
     __syncwarp();
 }
 
-// One whole tile (kTile events from tbase) of the 4D model on the fast path.
-// Returns false if the tile must be redone by the plain loop (acc, prod and
-// esum are then meaningless).  ru: the warp's kSub x 32 slots for the marked
-// events' r A' and u.
-template <bool GRAD, bool WEIGHTED>
+// One whole tile (kTile events from tbase) of the 4D model's NLL + gradient on
+// the fast path, kSub rows at a time.  Returns false if the tile must be redone
+// by the plain loop (acc, prod and esum are then meaningless).
+template <bool WEIGHTED>
 __device__ __forceinline__ bool tile_fast(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
-                                          int64_t tbase, double2* sbuf, double2* ru, int lane, double* acc,
-                                          double* prod, int* esum) {
-    const unsigned below = (1u << lane) - 1u;
+                                          int64_t tbase, double2* sbuf, int lane, double* acc, double* prod,
+                                          int* esum) {
     bool bad = false;
     long long acci[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acci[k] = 0;
-    unsigned long long prodq = 1ull << 62;
 #pragma unroll 1
-    for (int i0 = 0; i0 < kPerLane; i0 += kSub) {
-        unsigned m[kSub];
-        int p[kSub];
+    for (int i0 = 0; i0 < kPerLane; i0 += kSub)
+        block_fast<WEIGHTED>(wc, mt, cols, tbase, i0, sbuf, lane, acc, acci, prod, esum, &bad);
+    // the lane's fixed-point sums (Q38) as doubles; each high product is the
+    // floor of the exact one, half a unit low on average, so the lane's
+    // kPerLane products get kPerLane / 2 units back
 #pragma unroll
-        for (int q = 0; q < kSub; ++q) {
-            const int64_t e = tbase + lane + 32 * (i0 + q);
-            m[q] = __ballot_sync(0xffffffffu, !greater(__ldg(cols.t + e), wc.tcut));
-        }
-        p[0] = 0;
-        p[1] = __popc(m[0]);
-        p[2] = p[1] + __popc(m[1]);
-        p[3] = p[2] + __popc(m[2]);
-        const int n_slow = p[3] + __popc(m[3]);
-        near_peak_fast(wc, mt, cols, tbase, i0, lane, sbuf, m, p, n_slow);
-#pragma unroll 1
-        for (int q = 0; q < kSub; ++q) {
-            const unsigned mq = q == 0 ? m[0] : (q == 1 ? m[1] : (q == 2 ? m[2] : m[3]));
-            const int before = q == 0 ? 0 : (q == 1 ? p[1] : (q == 2 ? p[2] : p[3]));
-            const int slot = (before + __popc(mq & below)) & (kSub * 32 - 1);
-            const bool slow = (mq >> lane) & 1u;
-            const double2 tg = sbuf[slot];
-            const int64_t e = tbase + lane + 32 * (i0 + q);
-            RowIn v;
-            const bool ok = int_phase<WEIGHTED>(wc, mt, cols, e, v);
-            if (__any_sync(0xffffffffu, !ok)) fix_int_phase(wc, mt, cols, e, v);
-            event_fast<GRAD, WEIGHTED>(wc, mt, v, slow, tg, ru + slot, acc, acci, &prodq, esum, &bad);
-        }
-        __syncwarp();
-        if (GRAD) {
-            // the Gaussian terms of the marked events, packed: r A' Gx and u Gx
-            for (int j = lane; j < n_slow; j += 32) {
-                const double2 x = ru[j];
-                const double Gx = sbuf[j].y;
-                acc[13] = fma(x.x, Gx, acc[13]);
-                acc[14] = fma(x.y, Gx, acc[14]);
-            }
-        }
-        __syncwarp();
-    }
-    *prod = q62_to_double_nb((long long)prodq, 0);
-    if (GRAD) {
-        // the lane's fixed-point sums (Q38) as doubles; each high product is
-        // the floor of the exact one, half a unit low on average, so the lane's
-        // kPerLane products get kPerLane / 2 units back
-#pragma unroll
-        for (int k = 0; k < 10; ++k) acc[2 + k] = q62_to_double_nb(acci[k] + kPerLane / 2, 24);
-    }
+    for (int k = 0; k < 10; ++k) acc[2 + k] = q62_to_double_nb(acci[k] + kPerLane / 2, 24);
     return !__any_sync(0xffffffffu, bad);
 }
 
@@ -489,6 +437,119 @@ __device__ void finalize(const Consts& c, const double* acc, int n_par, double* 
         out[1 + j] = 0.0;
 }
 
+// The plain loop over one tile's events [tbase, min(tbase + kTile, ev1)): lane
+// l adds events l, l + 32, ... in order into acc (and the log product).  Those
+// near the resolution peak are marked by ballot kSub rows at a time and their
+// Gaussian/erfcx values evaluated packed, 32 per pass, into the warp's buffer.
+template <int KIND, bool GRAD, bool CACHED, bool WEIGHTED>
+__device__ __forceinline__ void tile_plain(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
+                                           int64_t tbase, int64_t ev1, double2* sbuf, int lane, double* acc,
+                                           double* prod, int* esum) {
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll 1
+    for (int i0 = 0; i0 < kPerLane; i0 += kSub) {
+        unsigned m0, m1, m2, m3;
+        {
+            unsigned mk[kSub];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) {
+                const int64_t e = tbase + lane + 32 * (i0 + q);
+                const bool slow = e < ev1 && !greater(__ldg(cols.t + e), wc.tcut);
+                mk[q] = __ballot_sync(0xffffffffu, slow);
+            }
+            m0 = mk[0];
+            m1 = mk[1];
+            m2 = mk[2];
+            m3 = mk[3];
+        }
+        const int p1 = __popc(m0), p2 = p1 + __popc(m1), p3 = p2 + __popc(m2);
+        const int n_slow = p3 + __popc(m3);
+        for (int j = lane; j < n_slow; j += 32) {
+            const int q = (j >= p1) + (j >= p2) + (j >= p3);
+            const unsigned m = q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
+            const int before = q == 0 ? 0 : (q == 1 ? p1 : (q == 2 ? p2 : p3));
+            const int64_t e = tbase + nth_set(m, j - before) + 32 * (i0 + q);
+            sbuf[j] = gauss_erfcx(wc.c, __ldg(cols.t + e) - wc.c.mu, mt);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int q = 0; q < kSub; ++q) {
+            const int64_t e = tbase + lane + 32 * (i0 + q);
+            if (e < ev1) {
+                const unsigned m = q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
+                const int before = q == 0 ? 0 : (q == 1 ? p1 : (q == 2 ? p2 : p3));
+                const double2 ge = (m >> lane) & 1u ? sbuf[before + __popc(m & below)]
+                                                    : make_double2(0.0, 0.0);
+                const double w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
+                double f[10];
+                double Ap = wc.aq;
+                if (KIND == IPA_MODEL_ANGTIME4D) {
+                    if (CACHED) {
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
+                        Ap = amplitude_sum(wc.hq, f);
+                    } else {
+                        const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
+                        if (wc.fixed && basis_q62_ok(ck, cl, phi)) {
+                            // the angular products and A on the integer pipe
+                            long long F[10];
+                            basis_q62(ck, cl, phi, mt, F);
+                            long long Af = 0;
+#pragma unroll
+                            for (int k = 0; k < 10; ++k) {
+                                f[k] = q62_to_double(F[k], 0);
+                                Af += __mul64hi(wc.hcq[k], F[k]);
+                            }
+                            Ap = q62_to_double(Af, wc.hexp);        // Af is Q60, times 2^-s
+                        } else {
+                            basis_unscaled(ck, cl, phi, mt, f);
+                            Ap = amplitude_sum(wc.hq, f);
+                        }
+                    }
+                }
+                event<KIND, GRAD, CACHED, WEIGHTED>(wc, mt, __ldg(cols.t + e), f, Ap, w, ge, acc, prod,
+                                                    esum);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// A segment's constants into the warp's copy in shared memory, with the
+// factors the event loop uses (warp-collective).
+template <bool CACHED>
+__device__ __forceinline__ void load_warp_consts(WarpConsts& wc, const Consts* src_consts, int lane) {
+    __syncwarp();
+    const double* src = reinterpret_cast<const double*>(src_consts);
+    double* dst = reinterpret_cast<double*>(&wc.c);
+    for (int i = lane; i < kConstsDoubles; i += 32) dst[i] = __ldg(src + i);
+    __syncwarp();
+    const double half_cs = 0.5 * wc.c.cs;
+    if (lane < 10) wc.hq[lane] = (CACHED ? wc.c.h[lane] : wc.c.h[lane] * kBasisScale[lane]) * half_cs;
+    if (lane == 10) wc.aq = half_cs;
+    if (lane == 11) wc.c2 = wc.c.c_exp + fp64tab::kLn2Hi;
+    if (lane == 12) {
+        const double tc = wc.c.mu + (wc.c.Gs2 + 6.25 / wc.c.k_z);
+        wc.tcut = tc == tc ? tc : INFINITY;    // NaN constants: every event takes the full path
+    }
+    // h_k c_k (cs / 2) scaled by 2^s into Q62 for the fixed-point
+    // amplitude sum (multiplying by a power of two is exact);
+    // non-finite coefficients (non-physical theta) or a scale outside
+    // [-64, 900] keep the FP64 path, which propagates NaN
+    const double hca = lane < 10 ? (wc.c.h[lane] * kBasisScale[lane]) * half_cs : 0.0;
+    const long long amag = __double_as_longlong(hca) & 0x7FFFFFFFFFFFFFFFll;
+    const long long amax = max_abs_bits(amag);
+    const int eb = (int)(amax >> 52);                 // biased exponent of max |hca|
+    const int sc = amax == 0 ? 0 : 1023 - eb;         // max |hca| 2^sc in [1, 2)
+    const bool sc_ok = amax < 0x7FF0000000000000ll && sc >= -64 && sc <= 900;
+    if (lane < 10) wc.hcq[lane] = sc_ok ? to_q62(hca * exp2_int(sc)) : 0;
+    if (lane == 0) {
+        wc.hexp = 2 - sc;
+        wc.fixed = sc_ok && abs_below(wc.c.cs, 1e300) ? 1 : 0;
+    }
+    __syncwarp();
+}
+
 // Blocks of any whole number of warps (1..kMaxWarps); each warp keeps a copy of
 // its current segment's constants in dynamic shared memory.
 constexpr int kMaxWarps = 8;
@@ -506,11 +567,8 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int n_wib = blockDim.x >> 5;
-    // per warp: the near-peak values (sbuf), the marked events' r A' and u (ru)
-    // and the segment's constants
     double2* const sbuf = reinterpret_cast<double2*>(dyn_smem) + wib * (kSub * 32);
-    double2* const ru = reinterpret_cast<double2*>(dyn_smem) + (n_wib + wib) * (kSub * 32);
-    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem + (size_t)2 * n_wib * kSub * 32 * sizeof(double2))[wib];
+    WarpConsts& wc = reinterpret_cast<WarpConsts*>(dyn_smem + (size_t)n_wib * kSub * 32 * sizeof(double2))[wib];
 
     load_math_tables(&mt);
     __syncthreads();
@@ -554,35 +612,7 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                 if (ev1 < ev0) ev1 = ev0;
             }
             if (seg != cur) {
-                __syncwarp();
-                const double* src = reinterpret_cast<const double*>(consts + seg);
-                double* dst = reinterpret_cast<double*>(&wc.c);
-                for (int i = lane; i < kConstsDoubles; i += 32) dst[i] = __ldg(src + i);
-                __syncwarp();
-                const double half_cs = 0.5 * wc.c.cs;
-                if (lane < 10) wc.hq[lane] = (CACHED ? wc.c.h[lane] : wc.c.h[lane] * kBasisScale[lane]) * half_cs;
-                if (lane == 10) wc.aq = half_cs;
-                if (lane == 11) wc.c2 = wc.c.c_exp + fp64tab::kLn2Hi;
-                if (lane == 12) {
-                    const double tc = wc.c.mu + (wc.c.Gs2 + 6.25 / wc.c.k_z);
-                    wc.tcut = tc == tc ? tc : INFINITY;    // NaN constants: every event takes the full path
-                }
-                // h_k c_k (cs / 2) scaled by 2^s into Q62 for the fixed-point
-                // amplitude sum (multiplying by a power of two is exact);
-                // non-finite coefficients (non-physical theta) or a scale outside
-                // [-64, 900] keep the FP64 path, which propagates NaN
-                const double hca = lane < 10 ? (wc.c.h[lane] * kBasisScale[lane]) * half_cs : 0.0;
-                const long long amag = __double_as_longlong(hca) & 0x7FFFFFFFFFFFFFFFll;
-                const long long amax = max_abs_bits(amag);
-                const int eb = (int)(amax >> 52);                 // biased exponent of max |hca|
-                const int sc = amax == 0 ? 0 : 1023 - eb;         // max |hca| 2^sc in [1, 2)
-                const bool sc_ok = amax < 0x7FF0000000000000ll && sc >= -64 && sc <= 900;
-                if (lane < 10) wc.hcq[lane] = sc_ok ? to_q62(hca * exp2_int(sc)) : 0;
-                if (lane == 0) {
-                    wc.hexp = 2 - sc;
-                    wc.fixed = sc_ok && abs_below(wc.c.cs, 1e300) ? 1 : 0;
-                }
-                __syncwarp();
+                load_warp_consts<CACHED>(wc, consts + seg, lane);
                 cur = seg;
             }
 
@@ -598,10 +628,9 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
             // into the warp's buffer, so the FP64 pipe does not spend a full warp
             // instruction on lanes that would discard the result.
             const int64_t tbase = ev0 + (tile - t0) * kTile;
-            const unsigned below = (1u << lane) - 1u;
             bool done = false;
             if (KIND == IPA_MODEL_ANGTIME4D && GRAD && !CACHED && tbase + kTile <= ev1) {
-                done = tile_fast<GRAD, WEIGHTED>(wc, &mt, cols, tbase, sbuf, ru, lane, acc, &prod, &esum);
+                done = tile_fast<WEIGHTED>(wc, &mt, cols, tbase, sbuf, lane, acc, &prod, &esum);
                 if (!done) {
 #pragma unroll
                     for (int a = 0; a < NA; ++a) acc[a] = 0.0;
@@ -609,73 +638,8 @@ nll_kernel(Cols cols, int64_t n, const int64_t* __restrict__ seg_begin,
                     esum = 0;
                 }
             }
-#pragma unroll 1
-            for (int i0 = 0; !done && i0 < kPerLane; i0 += kSub) {
-                unsigned m0, m1, m2, m3;
-                {
-                    unsigned mk[kSub];
-#pragma unroll
-                    for (int q = 0; q < kSub; ++q) {
-                        const int64_t e = tbase + lane + 32 * (i0 + q);
-                        const bool slow = e < ev1 && !greater(__ldg(cols.t + e), wc.tcut);
-                        mk[q] = __ballot_sync(0xffffffffu, slow);
-                    }
-                    m0 = mk[0];
-                    m1 = mk[1];
-                    m2 = mk[2];
-                    m3 = mk[3];
-                }
-                const int p1 = __popc(m0), p2 = p1 + __popc(m1), p3 = p2 + __popc(m2);
-                const int n_slow = p3 + __popc(m3);
-                for (int j = lane; j < n_slow; j += 32) {
-                    const int q = (j >= p1) + (j >= p2) + (j >= p3);
-                    const unsigned m = q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
-                    const int before = q == 0 ? 0 : (q == 1 ? p1 : (q == 2 ? p2 : p3));
-                    const int64_t e = tbase + nth_set(m, j - before) + 32 * (i0 + q);
-                    sbuf[j] = gauss_erfcx(wc.c, __ldg(cols.t + e) - wc.c.mu, &mt);
-                }
-                __syncwarp();
-#pragma unroll 1
-                for (int q = 0; q < kSub; ++q) {
-                    const int64_t e = tbase + lane + 32 * (i0 + q);
-                    if (e < ev1) {
-                        const unsigned m = q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
-                        const int before = q == 0 ? 0 : (q == 1 ? p1 : (q == 2 ? p2 : p3));
-                        const double2 ge = (m >> lane) & 1u ? sbuf[before + __popc(m & below)]
-                                                            : make_double2(0.0, 0.0);
-                        const double w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
-                        double f[10];
-                        double Ap = wc.aq;
-                        if (KIND == IPA_MODEL_ANGTIME4D) {
-                            if (CACHED) {
-#pragma unroll
-                                for (int k = 0; k < 10; ++k) f[k] = __ldg(cols.fk + k * cols.fk_stride + e);
-                                Ap = amplitude_sum(wc.hq, f);
-                            } else {
-                                const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
-                                if (wc.fixed && basis_q62_ok(ck, cl, phi)) {
-                                    // the angular products and A on the integer pipe
-                                    long long F[10];
-                                    basis_q62(ck, cl, phi, &mt, F);
-                                    long long Af = 0;
-#pragma unroll
-                                    for (int k = 0; k < 10; ++k) {
-                                        f[k] = q62_to_double(F[k], 0);
-                                        Af += __mul64hi(wc.hcq[k], F[k]);
-                                    }
-                                    Ap = q62_to_double(Af, wc.hexp);        // Af is Q60, times 2^-s
-                                } else {
-                                    basis_unscaled(ck, cl, phi, &mt, f);
-                                    Ap = amplitude_sum(wc.hq, f);
-                                }
-                            }
-                        }
-                        event<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, __ldg(cols.t + e), f, Ap, w, ge, acc, &prod,
-                                                            &esum);
-                    }
-                }
-                __syncwarp();
-            }
+            if (!done)
+                tile_plain<KIND, GRAD, CACHED, WEIGHTED>(wc, &mt, cols, tbase, ev1, sbuf, lane, acc, &prod, &esum);
             acc[0] += log_of(prod, esum, &mt);
             const double share = warp_butterfly<NA>(acc, lane);
             // the group and segment levels; the warp that completes the
@@ -733,7 +697,7 @@ ipa_status launch_t(const Cols& cols, int64_t n, const int64_t* seg_begin, const
     const LaunchCfg cfg = force ? *force : launch_cfg(KIND, GRAD, CACHED, n_seg > 1, tiles);
     const int W = cfg.warps_per_block >= 1 && cfg.warps_per_block <= kMaxWarps ? cfg.warps_per_block : 1;
     const int K = cfg.tiles_per_take >= 1 ? cfg.tiles_per_take : 1;
-    const size_t smem = (size_t)W * (sizeof(WarpConsts) + 2 * kSub * 32 * sizeof(double2));
+    const size_t smem = (size_t)W * (sizeof(WarpConsts) + kSub * 32 * sizeof(double2));
     // resident blocks per SM for each block size (cached per device and variant)
     static int occ[64][kMaxWarps + 1] = {};
     int dev = 0;

@@ -162,7 +162,7 @@ def test_gpu_toy_pulls(env):
     3.5 standard errors.  sigma and mu are measured only by the ~1e3 events of
     the turn-on at t ~ 0; at this size their pulls are biased (the maximum-
     likelihood bias of order 1/sqrt(N) in pull units: mu's mean pull is about
-    +0.25 at 2e4 events and falls to about a third of that at 2e5, where
+    +0.25 at 2e4 events (4096 toys) and 0.15 +- 0.06 at 2e5, where
     test_gpu_toy_pulls_all_parameters_2e5 checks all ten with the strict
     bound), so here they get a looser one."""
     pulls = _toy_pulls(env, 256, 2e4, seed=2, gen_seed=77)
