@@ -73,7 +73,7 @@ WORKLOAD = "4D angular+time unbinned NLL+grad, 1e6 FP64 SoA events, 10 params"
 #     weighted: w log P, w / P and the product (by 1 or P);
 #   events near the resolution peak (t <= mu + Gamma sigma^2 + 6.25 sqrt2 sigma,
 #     packed 32 to a warp pass): tau, the Gaussian's exponent (tau^2 k_g), the
-#     erfcx argument ((Gs2 - tau) k_z), erfcx and g X;
+#     erfcx argument ((Gs2 - tau) k_z), erfcx (FP64 polynomial) and g X;
 #   once per lane and 512-event tile (16 events): the log of the product and
 #     its exponent term.
 # (Angles within 2^-17 of |cos| = 1, about 1.5e-5 of the events, take the FP64
@@ -98,10 +98,11 @@ OPS_LIBRARY_4D = {"fma": 32, "mul": 30, "add": 6, "exp": 2, "erfc": 1, "log": 1,
 #     q qD and P, 1/P, and the 12 adjoint sums;
 #   events with t <= tcut (mu + max(Gamma_H, Gamma_L, Gamma) sigma^2 +
 #     sqrt(39.1 + (Dm sigma)^2 / 2) sqrt2 sigma): the Gaussian's exponent, three
-#     erfc arguments, two erfcx and the Faddeeva function (39 complex Horner
-#     steps, one division), and the five products stored for the event.
+#     erfc arguments, the Faddeeva function's division, Z and final
+#     combination, and the five products stored for the event (two erfcx and
+#     the Faddeeva function's 39 complex Horner steps run on the integer pipe).
 OPS_TAG_EVENT = {"fma": 17, "mul": 8, "add": 9}
-OPS_TAG_SLOW = {"fma": 125, "mul": 58, "add": 5, "erfcx_poly": 2, "rcp": 1}
+OPS_TAG_SLOW = {"fma": 8, "mul": 19, "add": 5, "rcp": 1}
 TH_TAG = np.array([0.66, 0.045, 0.0, 0.1, 0.085, 17.77, 0.8, 0.3])
 
 

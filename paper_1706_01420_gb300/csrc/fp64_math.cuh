@@ -19,6 +19,8 @@
 //   erfcx_poly(x)    exp(x^2) erfc(x) for 0 <= x <= 6.25: 13 pieces of width 1/2
 //                    centred at k/2, degree-13 Chebyshev interpolants (relative
 //                    error ~2e-16); erfcx_fast falls back to erfcx() above 6.25.
+//                    (erfcx_poly_q in int_math.cuh evaluates the same pieces in
+//                    fixed point on the integer pipe.)
 #pragma once
 
 #include <math.h>
@@ -35,6 +37,7 @@ struct MathTables {
     double sn[64];
     double cs[64];
     double ex[fp64tab::kErfcxPieces * fp64tab::kErfcxCoeffs];
+    long long exq[fp64tab::kErfcxPieces * fp64tab::kErfcxCoeffs];   // the same pieces in Q62 (int_math.cuh)
     long long sq[65], cq[65];   // sin, cos (j pi/32) in Q62 (int_math.cuh)
     long long eq[64];           // 2^(j/64) in Q62 (int_math.cuh)
 };
@@ -51,7 +54,10 @@ __device__ __forceinline__ void load_math_tables(MathTables* t) {
         t->linv[i] = kLogInv[i];
         t->ltab[i] = kLogTab[i];
     }
-    for (int i = threadIdx.x; i < kErfcxPieces * kErfcxCoeffs; i += blockDim.x) t->ex[i] = kErfcxTab[i];
+    for (int i = threadIdx.x; i < kErfcxPieces * kErfcxCoeffs; i += blockDim.x) {
+        t->ex[i] = kErfcxTab[i];
+        t->exq[i] = kErfcxQ62[i];
+    }
     for (int i = threadIdx.x; i < 65; i += blockDim.x) {
         t->sq[i] = kSinQ62[i];
         t->cq[i] = kCosQ62[i];
@@ -75,6 +81,14 @@ __device__ __forceinline__ bool abs_below(double x, double c) {      // |x| < c,
     return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) < __double_as_longlong(c);
 }
 __device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
+// |x| and -x by the sign bit alone (integer pipe), so that they never take an
+// FP64 instruction.
+__device__ __forceinline__ double abs_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double neg_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
 
 __device__ __forceinline__ double exp_fast(double x, const MathTables* t) {
     using namespace fp64tab;

@@ -9,7 +9,10 @@ with mpmath and rounded once to double.
   sincos: S_j = sin(j pi/32), C_j = cos(j pi/32), j = 0..63; 32/pi; pi/32 as hi + lo
   erfcx:  erfcx(x) = exp(x^2) erfc(x) on x in [0, 6.25] as 13 pieces centred at
           k/2 (k = 0..12), each the degree-13 Chebyshev interpolant on
-          [k/2 - 0.26, k/2 + 0.26] written as monomials in u = x - k/2.
+          [k/2 - 0.26, k/2 + 0.26] written as monomials in u = x - k/2, each
+          coefficient rounded once to double and once to signed Q62 (for the
+          fixed-point evaluation: every coefficient and every partial Horner
+          sum over |u| <= 1/4 is below 1.5 in magnitude, checked here);
 
 the coefficients of the Faddeeva function (faddeeva.cuh), Weideman's rational
 approximation (SIAM J. Numer. Anal. 31 (1994) 1497) with N = 40 and
@@ -19,7 +22,9 @@ L = 2^(-1/4) sqrt(N):
   psi = exp(-t^2) (L^2 + t^2) at t = L tan(theta / 2),
 
 by the midpoint rule with 1024 nodes (psi is smooth and periodic, so the rule
-converges geometrically; 512 nodes give the same doubles), and
+converges geometrically; 512 nodes give the same doubles), each rounded once
+to signed Q59 (the Horner sum in Z, |Z| <= 1, is evaluated in fixed point and
+never exceeds sum |a_n| = 12.64 < 16, checked here), and
 the fixed-point tables and constants of the integer-pipe functions
 (int_math.cuh), each the exact value rounded once to an integer:
 
@@ -131,14 +136,27 @@ def main():
     exp2_q62 = [q(mp.power(2, mp.mpf(j) / 64), 62) for j in range(64)]
     ln2_64_q128 = q(ln2 / 64, 128)
     fact = [mp.factorial(n) for n in range(10)]
-    erfcx_tab = []
+    erfcx_tab, erfcx_q62 = [], []
     for k in range(ERFCX_PIECES):
         c = mp.mpf(k) / 2
         coef = cheb_monomial(erfcx, c - ERFCX_HALF, c + ERFCX_HALF, ERFCX_DEG)
+        # partial Horner sums on a grid of |u| <= 1/4 (the sums are polynomials
+        # of low degree in u with decaying coefficients: the grid maximum is the
+        # maximum to well within the margin to 2)
+        worst = max(abs(v) for v in coef)
+        for i in range(201):
+            u = mp.mpf(i) / 400 - mp.mpf(1) / 4
+            v = coef[-1]
+            for j in range(len(coef) - 2, -1, -1):
+                v = coef[j] + v * u
+                worst = max(worst, abs(v))
+        assert worst < 1.5, (k, worst)
         erfcx_tab.extend(d(v) for v in coef)
+        erfcx_q62.extend(q(v, 62) for v in coef)
 
     weid_L, weid_a = weideman(WEID_N, WEID_NODES)
-    weid_a = [d(v) for v in weid_a]
+    assert mp.fsum(abs(v) for v in weid_a) < 13
+    weid_q59 = [q(v, 59) for v in weid_a]
 
     text = f"""// Generated by gen_fp64_tables.py (mpmath, 60 digits, rounded once to double
 // or to an integer).
@@ -215,17 +233,22 @@ __device__ const long long kExp2Q62[64] = {{
 {fmt_int(exp2_q62)}
 }};
 
-// erfcx piece k (centre k/2): coefficients of u^0 .. u^{ERFCX_DEG}
+// erfcx piece k (centre k/2): coefficients of u^0 .. u^{ERFCX_DEG}, as doubles
+// and in Q62
 __device__ const double kErfcxTab[{ERFCX_PIECES * (ERFCX_DEG + 1)}] = {{
 {fmt(erfcx_tab, 2)}
 }};
+__device__ const long long kErfcxQ62[{ERFCX_PIECES * (ERFCX_DEG + 1)}] = {{
+{fmt_int(erfcx_q62, 2)}
+}};
 
-// Faddeeva function (faddeeva.cuh): Weideman's N = {WEID_N} coefficients a_1..a_N and L
+// Faddeeva function (faddeeva.cuh): L and Weideman's N = {WEID_N} coefficients
+// a_1..a_N in Q59
 constexpr int kWeidN = {WEID_N};
 constexpr double kWeidL = {d(weid_L)!r};
 constexpr double kInvSqrtPi = {d(1 / mp.sqrt(mp.pi))!r};
-static __constant__ double kWeidA[{WEID_N}] = {{
-{fmt(weid_a)}
+static __constant__ long long kWeidAQ59[{WEID_N}] = {{
+{fmt_int(weid_q59)}
 }};
 
 }}  // namespace fp64tab

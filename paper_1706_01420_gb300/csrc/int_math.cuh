@@ -21,8 +21,16 @@
 //               2^(j/64) (Q62, j = k mod 64) and 2^floor(k/64).  Relative error
 //               before the final rounding: about 2^-53 from the input
 //               quantisation for |a| < 1/2, a few 2^-62 otherwise.
+//   erfcx_poly_q  0 <= x <= 6.25: x in Q60, k = nearest multiple of 1/2 (piece
+//               centre), u = x - k/2 in Q63 (|u| <= 1/4), the degree-13
+//               Chebyshev interpolant of the piece (monomials in u, Q62) by
+//               Horner's rule with 64 x 64 -> 128-bit products.  Absolute error
+//               before the final rounding below 2^-61 (the values are above
+//               0.088, so below 2e-17 relative, plus the interpolant's own
+//               ~1e-16).
 //
-// Outside these ranges both fall back to the table-driven FP64 functions.
+// Outside these ranges sincos_int and exp_int fall back to the table-driven
+// FP64 functions; erfcx_fast_q falls back to the library erfcx.
 #pragma once
 
 #include "fp64_math.cuh"
@@ -390,6 +398,33 @@ __device__ __forceinline__ void basis_q62_nb(double ck, double cl, double phi, c
     F[7] = mul_q62(bq, cp);
     F[8] = mul_q62(bq, sp);
     F[9] = mul_q62(CK, sl2);
+}
+
+// erfcx(x) = exp(x^2) erfc(x) for 0 <= x <= 6.25 from the piecewise
+// polynomial of fp64_tables.cuh (erfcx_poly's pieces), on the integer pipe.  x
+// above 6.25, infinite or NaN is evaluated as 6.25 and a negative x as |x|: the
+// value is then meaningless and callers select it away (erfcx_fast_q).  The
+// Horner loop is not unrolled: unrolled, the 64-bit products of the kernels
+// that call this twice per event overflowed the instruction cache.
+__device__ __forceinline__ double erfcx_poly_q(double x, const MathTables* t) {
+    using namespace fp64tab;
+    long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll;
+    b = b > 0x4019000000000000ll ? 0x4019000000000000ll : b;      // 6.25
+    const unsigned long long M = ((unsigned long long)b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const unsigned long long X = shift_nb(M, (int)(b >> 52) - 1023 + 8);   // x in Q60, < 2^63
+    int k = (int)((X + (1ull << 58)) >> 59);                      // nearest piece centre k/2
+    k = k > kErfcxPieces - 1 ? kErfcxPieces - 1 : k;
+    const long long u = (long long)((X - ((unsigned long long)k << 59)) << 3);   // Q63, |u| <= 2^61
+    const long long* c = t->exq + k * kErfcxCoeffs;
+    long long v = c[kErfcxCoeffs - 1];
+#pragma unroll 1
+    for (int i = kErfcxCoeffs - 2; i >= 0; --i)
+        v = c[i] + (long long)((unsigned long long)__mul64hi(v, u) << 1);   // |v| < 1.5 in Q62
+    return q62_to_double_nb(v, 0);
+}
+
+__device__ __forceinline__ double erfcx_fast_q(double x, const MathTables* t) {
+    return above(x, 6.25) ? erfcx(x) : erfcx_poly_q(x, t);
 }
 
 }  // namespace ipa

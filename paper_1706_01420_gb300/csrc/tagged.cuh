@@ -196,10 +196,10 @@ template <class C>
 __device__ __forceinline__ TagSlow tag_slow(const C& c, double tau, const MathTables* mt) {
     const double gx = exp_int(-(tau * tau) * c.k_g, mt);
     const double uH = (c.uH0 - tau) * c.k_z, uL = (c.uL0 - tau) * c.k_z, a = (c.uC0 - tau) * c.k_z;
-    const double XH = erfcx_fast(fabs(uH), mt), XL = erfcx_fast(fabs(uL), mt);
+    const double XH = erfcx_fast_q(abs_bits(uH), mt), XL = erfcx_fast_q(abs_bits(uL), mt);
     const bool ap = !negative(a);
     double wr, wi;
-    faddeeva_uhp(ap ? c.beta : -c.beta, fabs(a), &wr, &wi);
+    faddeeva_uhp(ap ? c.beta : neg_bits(c.beta), abs_bits(a), &wr, &wi);
     TagSlow s;
     s.xH = with_sign(gx * XH, !negative(uH));
     s.xL = with_sign(gx * XL, !negative(uL));
