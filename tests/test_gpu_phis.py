@@ -107,6 +107,30 @@ def test_parity_one_tag_normalisation(env, name, tag):
     _parity(env, 4097, seed=10, th=THETAS[name], tag=tag, cached=True)
 
 
+def test_parity_pole_angles_and_a_huge_weight(env):
+    """Angles within 2^-17 of the poles (|cos| = 1 - 1e-7, 1 - 2^-18) and phi =
+    +-pi, where the angular functions lose relative precision, and one event of
+    weight 1e7 that dominates the weighted sums: against the oracle, weighted
+    and not, with the tolerances of the other parity tests."""
+    O, F, G, torch, api = env
+    m_o, m_g = O.Model("phis", 0.0, 15.0), api.model_phis(0.0, 15.0)
+    for weighted in (False, True):
+        cols = synth.events_phis(4096, 31, weighted=weighted)
+        cols["ck"][::97] = 1.0 - 1e-7
+        cols["ck"][5::97] = -(1.0 - 1e-7)
+        cols["cl"][11::89] = 1.0 - 2.0 ** -18
+        cols["phi"][3::53] = np.pi
+        cols["phi"][7::53] = -np.pi
+        if weighted:
+            cols["w"][1234] = 1.0e7
+        ev = G.to_dev(cols)
+        theta = torch.tensor(TH, device="cuda")
+        got = api.ipa_nll_grad(m_g, ev, theta).cpu().numpy()
+        f_ref, g_ref = F.nll_grad(m_o, cols, TH)
+        logl, _ = F.nll_grad_terms(m_o, cols, TH)
+        G.assert_nll_grad_close(got, f_ref, g_ref, grad_scale(F, m_o, cols, TH), math.fsum(np.abs(logl)))
+
+
 def test_parity_cached_basis_and_early_range(env):
     _parity(env, 12000, seed=4, th=TH, cached=True)
     _parity(env, 12000, seed=6, th=THETAS["large_s_wave"], weighted=True, t_lo=-0.3, cached=True)
