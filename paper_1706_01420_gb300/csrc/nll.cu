@@ -20,9 +20,11 @@
 //     erfc(z) = exp(-z^2) erfcx(z) for z >= 0, with exp(-Gamma tau + Gamma^2
 //     sigma^2/2) exp(-z^2) = exp(-tau^2/(2 sigma^2)): the Gaussian factor that
 //     the gradient needs anyway replaces the exponential inside erfc;
-//   * sin/cos and exp run on the integer pipe in 64-bit fixed point and are
-//     rounded once to double (int_math.cuh); log and erfcx are table-driven
-//     FP64 (fp64_math.cuh);
+//   * sin/cos, the whole angular basis and the Gaussian's exp run on the
+//     integer pipe in 64-bit fixed point and are rounded once to double
+//     (int_math.cuh); the decay exponential, log and erfcx are table-driven
+//     FP64 (fp64_math.cuh): the split between the FP64 and the integer pipes
+//     is the measured fastest one;
 //   * sin(theta_K) sin(theta_mu) is one square root; the constant factors of
 //     the ten angular functions are folded into the amplitude coefficients.
 //
@@ -95,7 +97,11 @@ static_assert((IPA_TILE_EVENTS / 32) % kSub == 0, "events per lane must be a mul
 // (z < 0) or gX (z >= 0).  Events with t > tcut have 2 g(tau) = 2E to 1e-17
 // relative and a Gaussian below 1e-17; they are given (0, +0).
 __device__ __forceinline__ double2 gauss_erfcx(const Consts& c, double tau, const MathTables* mt) {
-    const double g = exp_int(-(tau * tau) * c.k_g, mt);
+    // branch-free integer exp; the argument is clamped at -705 (events more
+    // than 37 sigma before mu), where the Gaussian, below 1e-306, is nothing
+    // against the exponential term of 2 g(tau)
+    const double gr = -(tau * tau) * c.k_g;
+    const double g = exp_int_nb(below_neg(gr, -705.0) ? -705.0 : gr, mt);
     const double z = (c.Gs2 - tau) * c.k_z;
     const double x = fabs(z);
     const bool zneg = negative(z);
@@ -198,8 +204,11 @@ struct RowIn {
 };
 
 // tau, E2 = 2 e^{-Gamma tau + Gamma^2 sigma^2 / 2}, the ten f'_k and A' =
-// (cs / 2) A of event e with the branch-free fixed-point functions; false if the
-// lane needs fix_int_phase.
+// (cs / 2) A of event e: the angular basis and A' with the branch-free
+// fixed-point functions, E2 with the table-driven FP64 exp (measured 7 % faster
+// here than the integer-pipe exp, whose long dependent chain sat in front of
+// the event's FP64 work; the FP64 pipe has room since the adjoint sums moved to
+// fixed point); false if the lane needs fix_int_phase.
 template <bool WEIGHTED>
 __device__ __forceinline__ bool int_phase(const WarpConsts& wc, const MathTables* mt, const Cols& cols, int64_t e,
                                           RowIn& v) {
@@ -207,22 +216,20 @@ __device__ __forceinline__ bool int_phase(const WarpConsts& wc, const MathTables
     const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
     v.w = WEIGHTED ? __ldg(cols.w + e) : 1.0;
     v.tau = t - wc.c.mu;
-    const double a = fma(-wc.c.Gamma, v.tau, wc.c2);
-    v.E2 = exp_int_nb(a, mt);
+    v.E2 = exp_fast(fma(-wc.c.Gamma, v.tau, wc.c2), mt);
     basis_q62_nb(ck, cl, phi, mt, v.F);
     long long Af = 0;
 #pragma unroll
     for (int k = 0; k < 10; ++k) Af += __mul64hi(wc.hcq[k], v.F[k]);
     v.Ap = q62_to_double_nb(Af, wc.hexp);
-    return wc.fixed && basis_q62_ok(ck, cl, phi) && exp_int_ok(a);
+    return wc.fixed && basis_q62_ok(ck, cl, phi);
 }
 
-// The FP64 paths of the plain loop for a lane that int_phase could not serve
+// The FP64 basis of the plain loop for a lane that int_phase could not serve
 // (the FP64 products, in [-1, 1] for valid angles, go to Q62).
 __device__ __forceinline__ void fix_int_phase(const WarpConsts& wc, const MathTables* mt, const Cols& cols,
                                               int64_t e, RowIn& v) {
     const double ck = __ldg(cols.ck + e), cl = __ldg(cols.cl + e), phi = __ldg(cols.phi + e);
-    const double a = fma(-wc.c.Gamma, v.tau, wc.c2);
     if (!(wc.fixed && basis_q62_ok(ck, cl, phi))) {
         double f[10];
         basis_unscaled(ck, cl, phi, mt, f);
@@ -230,7 +237,6 @@ __device__ __forceinline__ void fix_int_phase(const WarpConsts& wc, const MathTa
 #pragma unroll
         for (int k = 0; k < 10; ++k) v.F[k] = to_q62_nb(f[k]);
     }
-    if (!exp_int_ok(a)) v.E2 = exp_fast(a, mt);
 }
 
 // rcp_newton and log_fast without their range branches (P in [2^-125, 2^126)).

@@ -194,7 +194,10 @@ __device__ __forceinline__ double with_sign(double v, bool set) {
 
 template <class C>
 __device__ __forceinline__ TagSlow tag_slow(const C& c, double tau, const MathTables* mt) {
-    const double gx = exp_int(-(tau * tau) * c.k_g, mt);
+    // branch-free integer exp, the argument clamped at -705 (the Gaussian is then
+    // below 1e-306, nothing against the exponential terms)
+    const double gr = -(tau * tau) * c.k_g;
+    const double gx = exp_int_nb(below_neg(gr, -705.0) ? -705.0 : gr, mt);
     const double uH = (c.uH0 - tau) * c.k_z, uL = (c.uL0 - tau) * c.k_z, a = (c.uC0 - tau) * c.k_z;
     const double XH = erfcx_fast_q(abs_bits(uH), mt), XL = erfcx_fast_q(abs_bits(uL), mt);
     const bool ap = !negative(a);
