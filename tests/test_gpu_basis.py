@@ -51,6 +51,28 @@ def test_nll_grad_with_basis_matches_oracle(env, n):
     G.assert_nll_grad_close(got, f_ref, g_ref, G.grad_scale(O, mo, cols, TH4), math.fsum(np.abs(logl)))
 
 
+def test_unweighted_full_size_and_a_nan_in_the_basis(env):
+    """Whole tiles read the cached basis on the fixed-point path (the f_k in
+    Q62): unweighted, 1e6 events, against the oracle; and one event whose
+    cached f_k is NaN makes the NLL and the gradient NaN, as the FP64 loop
+    does (the tile falls back to it)."""
+    O, G, torch, api = env
+    cols = synth.events_4d(1_000_000, 8)
+    ev = G.to_dev(cols)
+    m = api.model_4d()
+    ev["fk"] = api.ipa_angular_basis(m, ev)
+    theta = torch.tensor(TH4, device="cuda")
+    got = api.ipa_nll_grad(m, ev, theta).cpu().numpy()
+    mo = O.Model("4d", 0.0, 15.0)
+    f_ref, g_ref = O.nll_grad(mo, cols, TH4)
+    logl, _ = O.nll_grad_terms(mo, cols, TH4)
+    G.assert_nll_grad_close(got, f_ref, g_ref, G.grad_scale(O, mo, cols, TH4), math.fsum(np.abs(logl)))
+    fk = ev["fk"].clone()
+    fk[3, 4321] = float("nan")
+    bad = api.ipa_nll_grad(m, dict(ev, fk=fk), theta).cpu().numpy()
+    assert np.isnan(bad[0]) and np.isnan(bad[1:]).any()
+
+
 def test_fit_with_basis_matches_oracle(env):
     O, G, torch, api = env
     mo = O.Model("4d", 0.0, 15.0)
