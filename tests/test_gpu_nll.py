@@ -69,6 +69,17 @@ def test_parity_weighted_and_off_truth(env, kind):
     _parity(env, kind, 20000, seed=5, weighted=True, th=th, t_lo=0.0)
 
 
+@pytest.mark.parametrize("kind", ["1d", "4d"])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_parity_range_far_before_the_peak(env, kind, weighted):
+    """A range starting 3 ps (67 sigma) before mu: the early events' Gaussian
+    exponent -tau^2/(2 sigma^2) reaches -2200, below the integer exp's range,
+    where the kernels clamp it at -705 (the Gaussian is then nothing against
+    the exponential term); whole tiles, a ragged tail, against the oracle."""
+    _parity(env, kind, 20_001, seed=41, weighted=weighted and kind == "4d", th=TH4 if kind == "4d" else TH1,
+            t_lo=-3.0)
+
+
 def test_parity_config2_full_size(env):
     """4D, 1e6 events (the headline workload), unweighted."""
     _parity(env, "4d", 1_000_000, seed=0, weighted=False, th=TH4)

@@ -110,6 +110,14 @@ def test_parity_range_before_the_peak(env):
     _parity(env, 20000, seed=9, th=TRUTH, t_lo=-0.3, weighted=True)
 
 
+def test_parity_range_far_before_the_peak(env):
+    """t_lo - mu = -3 ps (67 sigma): the Gaussian exponent of the earliest events
+    is below the integer exp's range and clamped at -705 (the Gaussian is then
+    nothing against the exponential terms)."""
+    _parity(env, 20001, seed=12, th=TRUTH, t_lo=-3.0)
+    _parity(env, 20001, seed=13, th=TRUTH, t_lo=-3.0, weighted=True)
+
+
 def test_gradient_matches_finite_differences(env):
     O, T, G, torch, api = env
     m = api.model_tagged(0.0, 15.0)
