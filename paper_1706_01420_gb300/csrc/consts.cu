@@ -1,14 +1,14 @@
 // Step a1 of the hot path: theta -> the Consts record read by every event
-// tile (see consts.cuh for the formulas): one four-warp block per fit for a
+// tile (see consts.cuh for the formulas): one six-warp block per fit for a
 // few fits, one thread per fit for many.
 #include "consts.cuh"
 
 namespace ipa {
 
 namespace {
-// One block of four warps per fit (few fits: latency).
-__global__ void __launch_bounds__(128) consts_block_kernel(ModelDev m, const double* __restrict__ theta,
-                                                           Consts* __restrict__ out) {
+// One block of six warps per fit (few fits: latency).
+__global__ void __launch_bounds__(kConstsBlock) consts_block_kernel(ModelDev m, const double* __restrict__ theta,
+                                                                    Consts* __restrict__ out) {
     __shared__ ConstsBlockScratch S;
     // the likelihood kernel that follows may start now (it waits for this
     // kernel's results before reading them)
@@ -20,9 +20,12 @@ __global__ void __launch_bounds__(128) consts_block_kernel(ModelDev m, const dou
 // One thread per fit (many fits: throughput).
 __global__ void consts_thread_kernel(ModelDev m, const double* __restrict__ theta, int n_seg,
                                      Consts* __restrict__ out) {
+    __shared__ MathTables mt;
     asm volatile("griddepcontrol.launch_dependents;");
+    cdetail::load_consts_tables(&mt);
+    __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n_seg) compute_consts_thread(m, theta + (size_t)s * m.n_par, out + s);
+    if (s < n_seg) compute_consts_thread(m, theta + (size_t)s * m.n_par, &mt, out + s);
 }
 }  // namespace
 
@@ -35,7 +38,7 @@ ipa_status launch_consts(const ModelDev& m, const double* theta, int n_seg, Cons
         consts_thread_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
         return cuda_fail(cudaGetLastError(), "consts kernel launch");
     }
-    consts_block_kernel<<<n_seg, 128, 0, st>>>(m, theta, out);
+    consts_block_kernel<<<n_seg, kConstsBlock, 0, st>>>(m, theta, out);
     return cuda_fail(cudaGetLastError(), "consts kernel launch");
 }
 

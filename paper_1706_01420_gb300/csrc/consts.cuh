@@ -2,7 +2,7 @@
 // from theta once per call, so that theta can stay in device memory and calls
 // can be captured in CUDA graphs.  Two layouts share every arithmetic step
 // (so they give bit-identical records): one thread per fit when many fits are
-// evaluated at once, one four-warp block per fit when latency matters.
+// evaluated at once, one block per fit when latency matters.
 //
 // Time part (Sec. 3, analytic normalisation): with F(tau) = [Phi(tau/sigma) -
 // g(tau)] / Gamma, dF/dtau = g, the normalisation is I_T = F(t_hi - mu) -
@@ -15,10 +15,21 @@
 // |A_0|^2 = (1-F_S) A0sq, |A_perp|^2 = (1-F_S) Apesq,
 // |A_par|^2 = (1-F_S)(1 - A0sq - Apesq), |A_S|^2 = F_S, delta_0 = 0, and the
 // ten coefficients h_k of the helicity-basis angular functions.
+//
+// Latency.  For a single fit the record sits in front of every likelihood
+// pass, and on this GPU a dependent FP64 operation costs of the order of a
+// hundred cycles, so the 4D and 1D records are computed along short chains:
+// the edges' erfc and Gaussian through exp(-x^2/2) and the table-driven erfcx
+// and exp of fp64_math.cuh (as the event kernel does), every division by a
+// parameter as a product with a reciprocal (recip: three FP64 operations), and
+// the 70 entries of h and dh/dtheta as products of at most four factors from a
+// table, one entry per lane.  The tagged and phi_s models keep the library
+// functions of edge().
 #pragma once
 
 #include <math.h>
 
+#include "fp64_math.cuh"
 #include "ipa_internal.cuh"
 
 namespace ipa {
@@ -26,8 +37,11 @@ namespace ipa {
 namespace cdetail {
 
 constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kInvSqrt2 = 0.70710678118654752440;
 constexpr double kInvSqrt2Pi = 0.39894228040143267794;
 constexpr double kPi = 3.14159265358979323846;
+
+// ---- edge terms with library functions (tagged and phi_s models) ----
 
 __device__ inline double conv_g(double tau, double Gamma, double sigma) {
     const double z = (Gamma * sigma * sigma - tau) / (kSqrt2 * sigma);
@@ -61,13 +75,8 @@ __device__ inline void edge(double tau, double Gamma, double sigma, double* F, d
     edge_combine(tau, Gamma, sigma, conv_g(tau, Gamma, sigma), gauss(tau, sigma), edge_phi(tau, sigma), F, dF);
 }
 
-
-// The transcendental inputs of the angular coefficients.
-struct AngPieces {
-    double sn[6], cs[6];   // sin/cos of (dpe - dpa), dpa, dpe, (dpa - dS), (dpe - dS), dS
-    double rt[5];          // sqrt of x0, xa, xe, F, s
-};
-
+// The six strong-phase combinations whose sine and cosine enter h_k:
+// (dpe - dpa), dpa, dpe, (dpa - dS), (dpe - dS), dS.
 __device__ inline double ang_arg(int i, double dpa, double dpe, double dS) {
     switch (i) {
     case 0: return dpe - dpa;
@@ -76,76 +85,6 @@ __device__ inline double ang_arg(int i, double dpa, double dpe, double dS) {
     case 3: return dpa - dS;
     case 4: return dpe - dS;
     default: return dS;
-    }
-}
-
-__device__ inline double sqrt_arg(int i, double x0, double xa, double xe, double F, double s) {
-    switch (i) {
-    case 0: return x0;
-    case 1: return xa;
-    case 2: return xe;
-    case 3: return F;
-    default: return s;
-    }
-}
-
-// h_k and dh_k / d(A0sq, Apesq, delta_pa, delta_pe, F_S, delta_S) for row k.
-__device__ inline void h_row(int k, const AngPieces& a, double x0, double xe, double xa, double s, double F,
-                             double* h, double* d) {
-    const double s4 = a.sn[0], c4 = a.cs[0], s5 = a.sn[1], c5 = a.cs[1], s6 = a.sn[2], c6 = a.cs[2];
-    const double s8 = a.sn[3], c8 = a.cs[3], s9 = a.sn[4], c9 = a.cs[4], s10 = a.sn[5], c10 = a.cs[5];
-    const double r0 = a.rt[0], ra = a.rt[1], re = a.rt[2], rF = a.rt[3], rs = a.rt[4];
-    const double rFs = rF * rs;
-    const double dFs = (1.0 - 2.0 * F) / (2.0 * rFs);
-    for (int j = 0; j < 6; ++j) d[j] = 0.0;
-    switch (k) {
-    case 0: *h = s * x0; d[0] = s; d[4] = -x0; break;
-    case 1: *h = s * xa; d[0] = -s; d[1] = -s; d[4] = -xa; break;
-    case 2: *h = s * xe; d[1] = s; d[4] = -xe; break;
-    case 3:
-        *h = s * ra * re * s4;
-        d[0] = s * (-xe) / (2.0 * ra * re) * s4;
-        d[1] = s * (xa - xe) / (2.0 * ra * re) * s4;
-        d[2] = -s * ra * re * c4;
-        d[3] = s * ra * re * c4;
-        d[4] = -ra * re * s4;
-        break;
-    case 4:
-        *h = s * r0 * ra * c5;
-        d[0] = s * (xa - x0) / (2.0 * r0 * ra) * c5;
-        d[1] = s * (-x0) / (2.0 * r0 * ra) * c5;
-        d[2] = -s * r0 * ra * s5;
-        d[4] = -r0 * ra * c5;
-        break;
-    case 5:
-        *h = s * r0 * re * s6;
-        d[0] = s * xe / (2.0 * r0 * re) * s6;
-        d[1] = s * x0 / (2.0 * r0 * re) * s6;
-        d[3] = s * r0 * re * c6;
-        d[4] = -r0 * re * s6;
-        break;
-    case 6: *h = F; d[4] = 1.0; break;
-    case 7:
-        *h = rFs * ra * c8;
-        d[0] = -rFs / (2.0 * ra) * c8;
-        d[1] = -rFs / (2.0 * ra) * c8;
-        d[2] = -rFs * ra * s8;
-        d[4] = dFs * ra * c8;
-        d[5] = rFs * ra * s8;
-        break;
-    case 8:
-        *h = rFs * re * s9;
-        d[1] = rFs / (2.0 * re) * s9;
-        d[3] = rFs * re * c9;
-        d[4] = dFs * re * s9;
-        d[5] = -rFs * re * c9;
-        break;
-    default:
-        *h = rFs * r0 * c10;
-        d[0] = rFs / (2.0 * r0) * c10;
-        d[4] = dFs * r0 * c10;
-        d[5] = -rFs * r0 * s10;
-        break;
     }
 }
 
@@ -161,43 +100,6 @@ __device__ inline double basis_max(int k) {
     }
 }
 
-__device__ inline double time_envelope(const ModelDev& m, double Gamma, double sigma, double mu) {
-    return fmin(1.0, exp(-Gamma * (m.t_lo - mu) + 0.5 * Gamma * Gamma * sigma * sigma));
-}
-
-// The divisions of the record that need only theta and the model:
-// k_z, k_g, cG, inv_s, cb, inv_V (numerator and denominator of item i).
-__device__ inline void scalar_quotient(int i, const ModelDev& m, const double* th, double* num, double* den) {
-    const double sigma = th[IPA_SIGMA], fb = th[IPA_FB];
-    const bool four = m.kind == IPA_MODEL_ANGTIME4D;
-    const double span = m.t_hi - m.t_lo;
-    const double V = four ? span * 8.0 * kPi : span;
-    switch (i) {
-    case 0: *num = 1.0; *den = kSqrt2 * sigma; break;
-    case 1: *num = 1.0; *den = 2.0 * sigma * sigma; break;
-    case 2: *num = kInvSqrt2Pi; *den = sigma; break;
-    case 3: *num = 1.0; *den = sigma; break;
-    case 4: *num = fb; *den = V; break;
-    default: *num = 1.0; *den = V; break;
-    }
-}
-constexpr int kScalarQuotients = 6;
-
-// The divisions by I_T: dlnIT[0..2], cs, inv_ITIO (numerator, denominator).
-__device__ inline void it_quotient(int i, const ModelDev& m, const double* th, double IT, const double* dIT,
-                                   double* num, double* den) {
-    const double fb = th[IPA_FB];
-    const double IO = m.kind == IPA_MODEL_ANGTIME4D ? 16.0 * kPi / 9.0 : 1.0;
-    if (i < 3) {
-        *num = dIT[i];
-        *den = IT;
-    } else {
-        *num = i == 3 ? 1.0 - fb : 1.0;
-        *den = IT * IO;
-    }
-}
-constexpr int kItQuotients = 5;
-
 // Whether theta lies in the model's domain: Gamma > 0, sigma > 0, f_b in
 // [0, 1] and (4D) F_S, |A_0|^2, |A_perp|^2 and |A_par|^2 = 1 - |A_0|^2 -
 // |A_perp|^2 in [0, 1] (false for NaN).  Outside, the PDF is not a density.
@@ -209,56 +111,6 @@ __device__ inline bool in_domain(const double* th, bool four) {
         ok = ok && F >= 0.0 && F <= 1.0 && x0 >= 0.0 && xe >= 0.0 && x0 + xe <= 1.0;
     }
     return ok;
-}
-
-// Scalars of the record without a division, and the quotients q[] of
-// scalar_quotient (q[0..5]) and it_quotient (q[6..10]).  For theta outside the
-// domain cs and cb are NaN, so that every P, the NLL and the gradient are NaN
-// (the fitter reports such a point as IPA_FIT_BAD_PDF).
-__device__ inline void write_plain_scalars(const double* th, double IT, double MT, double MO, bool four,
-                                           const double* q, Consts* c) {
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
-    const bool ok = in_domain(th, four);
-    c->Gamma = Gamma;
-    c->sigma = sigma;
-    c->mu = mu;
-    c->fb = fb;
-    c->c_exp = 0.5 * Gamma * Gamma * sigma * sigma;
-    c->Gs2 = Gamma * sigma * sigma;
-    c->k_z = q[0];
-    c->k_g = q[1];
-    c->cG = q[2];
-    c->s2 = sigma * sigma;
-    c->G2s = Gamma * Gamma * sigma;
-    c->Gsig = Gamma * sigma;
-    c->inv_s = q[3];
-    c->IT = IT;
-    for (int j = 0; j < 3; ++j) c->dlnIT[j] = q[6 + j];
-    c->MT = MT;
-    c->MO = four ? MO : 1.0;
-    c->cs = ok ? q[9] : NAN;
-    c->cb = ok ? q[4] : NAN;
-    c->inv_ITIO = q[10];
-    c->inv_V = q[5];
-    c->pad_ = 0.0;
-}
-
-// Scalars of the record from I_T pieces and the envelopes.
-__device__ inline void write_scalars(const ModelDev& m, const double* th, double Fh, double Fl,
-                                     const double* dIT, double MT, double MO, Consts* c) {
-    const double IT = Fh - Fl;
-    double q[kScalarQuotients + kItQuotients];
-    for (int i = 0; i < kScalarQuotients; ++i) {
-        double a, b;
-        scalar_quotient(i, m, th, &a, &b);
-        q[i] = a / b;
-    }
-    for (int i = 0; i < kItQuotients; ++i) {
-        double a, b;
-        it_quotient(i, m, th, IT, dIT, &a, &b);
-        q[kScalarQuotients + i] = a / b;
-    }
-    write_plain_scalars(th, IT, MT, MO, m.kind == IPA_MODEL_ANGTIME4D, q, c);
 }
 
 struct AmpParams {
@@ -280,129 +132,424 @@ __device__ inline AmpParams amp_params(const ModelDev& m, const double* th) {
     return p;
 }
 
+// ---- the 4D and 1D record along short chains ----
+
+// 1/d: the FP32 reciprocal (rcp.approx, within 1 ulp) of d's leading 24 bits,
+// converted by integer operations, is a seed y with e = 1 - d y below 2^-21;
+// 1/d = y (1 + e + e^2 + ...) = y + y (e + e^2) up to y e^3 < 2^-63 relative,
+// so the result is within about half an ulp, from three dependent FP64
+// operations instead of the seven or so of a division.  Outside 2^-125 <= |d|
+// < 2^126 (0, infinities and NaN included) the division itself.
+__device__ inline double recip(double d) {
+    const long long b = __double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e < 1023 - 125 || e > 1023 + 125) return 1.0 / d;
+    const unsigned xf = ((unsigned)((unsigned long long)b >> 32) & 0x80000000u) |
+                        ((unsigned)(e - 1023 + 127) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(xf)));
+    const unsigned yu = __float_as_uint(yf);
+    const long long yb = ((long long)(yu & 0x80000000u) << 32) |
+                         ((long long)(((yu >> 23) & 0xFFu) - 127 + 1023) << 52) | ((long long)(yu & 0x7FFFFFu) << 29);
+    const double y = __longlong_as_double(yb);
+    const double r = fma(-d, y, 1.0);
+    return fma(y, fma(r, r, r), y);
+}
+
+// Products of theta used by the record and by the edges.
+struct TimeScalars {
+    double Gamma, sigma, mu, fb;
+    double c_exp;            // Gamma^2 sigma^2 / 2
+    double Gs2, s2, G2s, Gsig;
+};
+
+__device__ inline TimeScalars time_scalars(const double* th) {
+    TimeScalars s;
+    s.Gamma = th[IPA_GAMMA];
+    s.sigma = th[IPA_SIGMA];
+    s.mu = th[IPA_MU];
+    s.fb = th[IPA_FB];
+    s.c_exp = 0.5 * s.Gamma * s.Gamma * s.sigma * s.sigma;
+    s.Gs2 = s.Gamma * s.sigma * s.sigma;
+    s.s2 = s.sigma * s.sigma;
+    s.G2s = s.Gamma * s.Gamma * s.sigma;
+    s.Gsig = s.Gamma * s.sigma;
+    return s;
+}
+
+// Edge e of the range (0: t_hi, 1: t_lo) as tau = t_e - mu.
+__device__ inline double edge_tau(const ModelDev& m, double mu, int e) { return (e == 0 ? m.t_hi : m.t_lo) - mu; }
+
+// With x = tau / sigma: the argument z = (Gamma sigma^2 - tau) / (sqrt2 sigma)
+// = (Gamma sigma - x) / sqrt2 of the erfc in g(tau), the argument w =
+// -x / sqrt2 of the erfc in Phi(x) = erfc(w) / 2, and the exponents of the
+// Gaussian factor gq = exp(-x^2 / 2) and of E = exp(-Gamma tau + Gamma^2
+// sigma^2 / 2).
+__device__ inline double edge_z(const TimeScalars& s, double x) { return (s.Gsig - x) * kInvSqrt2; }
+__device__ inline double edge_w(double x) { return neg_bits(x) * kInvSqrt2; }
+__device__ inline double gauss_exponent(double x) { return (-0.5 * x) * x; }
+__device__ inline double decay_exponent(const TimeScalars& s, double tau) { return fma(-s.Gamma, tau, s.c_exp); }
+
+// erfcx at the argument w of one of an edge's erfc terms: erfc(w) = e^{-w^2}
+// erfcx(w) for w >= 0 and 2 - e^{-w^2} erfcx(-w) for w < 0.  For w < -6.25
+// the erfcx term is below 1e-18 of the term beside it (E for g, 1 for Phi)
+// and leaves the sum unchanged in double precision: 0 without evaluating it.
+__device__ inline double edge_erfcx(double w, const MathTables* t) {
+    return below_neg(w, -6.25) ? 0.0 : erfcx_fast(abs_bits(w), t);
+}
+
+// g(tau) = E erfc(z) / 2, Phi(x) = erfc(w) / 2 and the Gaussian G(tau) = cG gq
+// at one edge from gq = exp(-x^2/2) = E e^{-z^2} = e^{-w^2} and the erfcx
+// values X1 (at z) and X2 (at w).
+__device__ inline void edge_values(double z, double w, double gq, double E, double X1, double X2, double cG,
+                                   double* g, double* Phi, double* G) {
+    const double a = 0.5 * (gq * X1);
+    *g = negative(z) ? E - a : a;
+    const double b = 0.5 * (gq * X2);
+    *Phi = negative(w) ? 1.0 - b : b;
+    *G = cG * gq;
+}
+
+// F(tau) and its derivatives (Gamma, sigma, mu) at one edge (see the top of
+// this file), with x = tau / sigma and rG = 1 / Gamma as factors.
+__device__ inline void edge_combine_r(const TimeScalars& s, double tau, double x, double rG, double g, double G,
+                                      double Phi, double* F, double* dF) {
+    const double dg_dG = (s.Gs2 - tau) * g - s.s2 * G;
+    const double dg_ds = s.G2s * g - (s.Gsig + x) * G;
+    *F = (Phi - g) * rG;
+    dF[0] = -(*F + dg_dG) * rG;
+    dF[1] = (-(x * G) - dg_ds) * rG;
+    dF[2] = -g;
+}
+
+// The scalars of the record that need theta only (rs = 1 / sigma, rV = 1 / V).
+// For theta outside the domain cb is NaN (and cs, written with the divisions
+// by I_T), so that every P, the NLL and the gradient are NaN (the fitter
+// reports such a point as IPA_FIT_BAD_PDF).
+__device__ inline void write_time_scalars(const TimeScalars& s, double rs, double rV, bool ok, Consts* c) {
+    c->Gamma = s.Gamma;
+    c->sigma = s.sigma;
+    c->mu = s.mu;
+    c->fb = s.fb;
+    c->c_exp = s.c_exp;
+    c->Gs2 = s.Gs2;
+    c->k_z = rs * kInvSqrt2;
+    c->k_g = 0.5 * (rs * rs);
+    c->cG = kInvSqrt2Pi * rs;
+    c->s2 = s.s2;
+    c->G2s = s.G2s;
+    c->Gsig = s.Gsig;
+    c->inv_s = rs;
+    c->cb = ok ? s.fb * rV : NAN;
+    c->inv_V = rV;
+    c->pad_ = 0.0;
+}
+
+// The range's volume V (t_hi - t_lo, times 8 pi for the angles) and the
+// angular integral I_Omega of the 4D model.
+__device__ inline double volume(const ModelDev& m) {
+    const double span = m.t_hi - m.t_lo;
+    return m.kind == IPA_MODEL_ANGTIME4D ? span * 8.0 * kPi : span;
+}
+__device__ inline double omega_integral(const ModelDev& m) {
+    return m.kind == IPA_MODEL_ANGTIME4D ? 16.0 * kPi / 9.0 : 1.0;
+}
+
+// Item j of the divisions by I_T: (dI_T/dtheta_j) / I_T for j < 3 (dIT_j
+// given), cs = (1 - f_b) / (I_T I_Omega) for j = 3, 1 / (I_T I_Omega) for j = 4.
+__device__ inline double it_item(int j, double IT, double IO, double dIT_j, double fb) {
+    const double den = j < 3 ? IT : IT * IO;
+    const double num = j < 3 ? dIT_j : (j == 3 ? 1.0 - fb : 1.0);
+    return num * recip(den);
+}
+
+// The factors of h_k and dh_k/dtheta_j (index: value):
+//   0: 1, 1: s = 1 - F, 2: x0, 3: xa, 4: xe, 5: F, 6: sqrt xa, 7: sqrt xe,
+//   8: sqrt x0, 9: sqrt F sqrt s, 10: 1/(2 sqrt xa sqrt xe), 11: 1/(2 sqrt x0
+//   sqrt xa), 12: 1/(2 sqrt x0 sqrt xe), 13: 1/(2 sqrt xa), 14: 1/(2 sqrt xe),
+//   15: 1/(2 sqrt x0), 16: (1 - 2F)/(2 sqrt F sqrt s), 17: xa - xe,
+//   18: xa - x0, 19-24: sine and 25-30: cosine of ang_arg 0-5,
+// with x0 = A0sq, xe = Apesq, xa = 1 - x0 - xe and F = F_S.
+constexpr int kAngFactors = 31;
+
+// Factors 0-5, 17 and 18 (no transcendental function).
+__device__ inline double plain_factor(int i, const AmpParams& p) {
+    switch (i) {
+    case 0: return 1.0;
+    case 1: return p.s;
+    case 2: return p.x0;
+    case 3: return p.xa;
+    case 4: return p.xe;
+    case 5: return p.F;
+    case 17: return p.xa - p.xe;
+    default: return p.xa - p.x0;
+    }
+}
+__device__ inline int plain_factor_index(int i) { return i < 6 ? i : 11 + i; }   // i = 0..7
+constexpr int kPlainFactors = 8;
+
+// Square root i (0..4) is taken of x0, xa, xe, F, s.
+__device__ inline double sqrt_in(int i, const AmpParams& p) {
+    return i == 0 ? p.x0 : (i == 1 ? p.xa : (i == 2 ? p.xe : (i == 3 ? p.F : p.s)));
+}
+
+// Factors 9-16 as m (k (a b)): the sources of a and b (0-4: square root i,
+// 5-9: its reciprocal, 10: one), k = 1 for factor 9 and 1/2 otherwise, m =
+// 1 - 2F for factor 16 and 1 otherwise.
+__device__ inline int combo_a(int i) {
+    return i == 0 ? 3 : (i == 1 ? 6 : (i == 2 ? 5 : (i == 3 ? 5 : (i == 4 ? 6 : (i == 5 ? 7 : (i == 6 ? 5 : 8))))));
+}
+__device__ inline int combo_b(int i) {
+    return i == 0 ? 4 : (i == 1 ? 7 : (i == 2 ? 6 : (i == 3 ? 7 : (i == 7 ? 9 : 10))));
+}
+__device__ inline double combo(int i, double a, double b, double omtF) {
+    return (i == 7 ? omtF : 1.0) * ((i == 0 ? 1.0 : 0.5) * (a * b));
+}
+constexpr int kComboFactors = 8;
+
+// Entry e of the record's h (e < 10) and dh (10 + 6k + j, j over A0sq,
+// Apesq, delta_pa, delta_pe, F_S, delta_S): the product of the factors of
+// its four 5-bit fields (0 in an unused field is the factor 1), negated if
+// bit 30 is set, 0 if bit 31 is set.
+constexpr unsigned kNeg = 1u << 30, kZero = 1u << 31;
+constexpr unsigned fac(unsigned a, unsigned b = 0, unsigned c = 0, unsigned d = 0) {
+    return a | b << 5 | c << 10 | d << 15;
+}
+constexpr int kRowEntries = 70;
+__device__ const unsigned kRowSpec[kRowEntries] = {
+    // h_0 .. h_9: s x0, s xa, s xe, s ra re s4, s r0 ra c5, s r0 re s6, F,
+    // rFs ra c8, rFs re s9, rFs r0 c10
+    fac(1, 2), fac(1, 3), fac(1, 4), fac(1, 6, 7, 19), fac(1, 8, 6, 26), fac(1, 8, 7, 21), fac(5),
+    fac(9, 6, 28), fac(9, 7, 23), fac(9, 8, 30),
+    // dh_0 .. dh_2
+    fac(1), kZero, kZero, kZero, kNeg | fac(2), kZero,
+    kNeg | fac(1), kNeg | fac(1), kZero, kZero, kNeg | fac(3), kZero,
+    kZero, fac(1), kZero, kZero, kNeg | fac(4), kZero,
+    // dh_3
+    kNeg | fac(1, 4, 10, 19), fac(1, 17, 10, 19), kNeg | fac(1, 6, 7, 25), fac(1, 6, 7, 25),
+    kNeg | fac(6, 7, 19), kZero,
+    // dh_4
+    fac(1, 18, 11, 26), kNeg | fac(1, 2, 11, 26), kNeg | fac(1, 8, 6, 20), kZero, kNeg | fac(8, 6, 26), kZero,
+    // dh_5
+    fac(1, 4, 12, 21), fac(1, 2, 12, 21), kZero, fac(1, 8, 7, 27), kNeg | fac(8, 7, 21), kZero,
+    // dh_6
+    kZero, kZero, kZero, kZero, fac(0), kZero,
+    // dh_7
+    kNeg | fac(9, 13, 28), kNeg | fac(9, 13, 28), kNeg | fac(9, 6, 22), kZero, fac(16, 6, 28), fac(9, 6, 22),
+    // dh_8
+    kZero, fac(9, 14, 23), kZero, fac(9, 7, 29), fac(16, 7, 23), kNeg | fac(9, 7, 29),
+    // dh_9
+    fac(9, 15, 30), kZero, kZero, kZero, fac(16, 8, 30), kNeg | fac(9, 8, 24),
+};
+
+__device__ inline double row_entry(unsigned spec, const double* f) {
+    const double v = ((f[spec & 31u] * f[(spec >> 5) & 31u]) * f[(spec >> 10) & 31u]) * f[(spec >> 15) & 31u];
+    return (spec & kZero) ? 0.0 : ((spec & kNeg) ? neg_bits(v) : v);
+}
+
+// M_Omega = sum_k |h_k| max|f_k| added pairwise in a fixed order:
+// ((a_0 + a_1) + (a_2 + a_3)) + a_4 with a_i = p_2i + p_2i+1.
+__device__ inline double mo_sum(const double* h) {
+    double a[5];
+    for (int i = 0; i < 5; ++i)
+        a[i] = fabs(h[2 * i]) * basis_max(2 * i) + fabs(h[2 * i + 1]) * basis_max(2 * i + 1);
+    return ((a[0] + a[1]) + (a[2] + a[3])) + a[4];
+}
+
+// The tables of exp_fast, sincos_fast and erfcx_fast into shared memory
+// (block-cooperative; the caller syncs).
+__device__ inline void load_consts_tables(MathTables* t) {
+    using namespace fp64tab;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        t->exp2[i] = kExp2Tab[i];
+        t->sn[i] = kSinTab[i];
+        t->cs[i] = kCosTab[i];
+    }
+    for (int i = threadIdx.x; i < kErfcxPieces * kErfcxCoeffs; i += blockDim.x) t->ex[i] = kErfcxTab[i];
+}
+
 }  // namespace cdetail
 
 // One thread computes one Consts record: used when many fits are evaluated at
 // once (batched fits, the server), where lanes of a warp hold different fits
-// and every FP64 instruction does useful work in all of them.
-__device__ inline void compute_consts_thread(const ModelDev& m, const double* th, Consts* c) {
+// and every FP64 instruction does useful work in all of them.  mt holds the
+// tables of load_consts_tables.
+__device__ inline void compute_consts_thread(const ModelDev& m, const double* th, const MathTables* mt, Consts* c) {
     using namespace cdetail;
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU];
-    double Fh, Fl, dFh[3], dFl[3];
-    edge(m.t_hi - mu, Gamma, sigma, &Fh, dFh);
-    edge(m.t_lo - mu, Gamma, sigma, &Fl, dFl);
-    double dIT[3];
-    for (int j = 0; j < 3; ++j) dIT[j] = dFh[j] - dFl[j];
-    const double MT = time_envelope(m, Gamma, sigma, mu);
-    const AmpParams p = amp_params(m, th);
-    double MO = 0.0;
-    if (m.kind == IPA_MODEL_ANGTIME4D) {
-        AngPieces a;
-        for (int i = 0; i < 6; ++i) sincos(ang_arg(i, p.dpa, p.dpe, p.dS), &a.sn[i], &a.cs[i]);
-        for (int i = 0; i < 5; ++i) a.rt[i] = sqrt(sqrt_arg(i, p.x0, p.xa, p.xe, p.F, p.s));
-        for (int k = 0; k < 10; ++k) {
-            double h, d[6];
-            h_row(k, a, p.x0, p.xe, p.xa, p.s, p.F, &h, d);
-            c->h[k] = h;
-            for (int j = 0; j < 6; ++j) c->dh[k][j] = d[j];
-            MO = k ? MO + fabs(h) * basis_max(k) : fabs(h) * basis_max(k);
-        }
-    } else {
-        for (int k = 0; k < 10; ++k) {
-            c->h[k] = k == 0 ? 1.0 : 0.0;
-            for (int j = 0; j < 6; ++j) c->dh[k][j] = 0.0;
-        }
+    const bool four = m.kind == IPA_MODEL_ANGTIME4D;
+    const bool ok = in_domain(th, four);
+    const TimeScalars s = time_scalars(th);
+    const double rs = recip(s.sigma), rG = recip(s.Gamma), rV = recip(volume(m));
+    double F[2], dF[2][3];
+    for (int e = 0; e < 2; ++e) {
+        const double tau = edge_tau(m, s.mu, e);
+        const double x = tau * rs;
+        const double z = edge_z(s, x), w = edge_w(x);
+        const double X1 = edge_erfcx(z, mt), X2 = edge_erfcx(w, mt);
+        const double gq = exp_fast(gauss_exponent(x), mt), E = exp_fast(decay_exponent(s, tau), mt);
+        double g, Phi, G;
+        edge_values(z, w, gq, E, X1, X2, kInvSqrt2Pi * rs, &g, &Phi, &G);
+        edge_combine_r(s, tau, x, rG, g, G, Phi, &F[e], dF[e]);
+        if (e == 1) c->MT = fmin(1.0, E);
     }
-    write_scalars(m, th, Fh, Fl, dIT, MT, MO, c);
+    write_time_scalars(s, rs, rV, ok, c);
+    const double IT = F[0] - F[1], IO = omega_integral(m);
+    c->IT = IT;
+    for (int j = 0; j < 3; ++j) c->dlnIT[j] = it_item(j, IT, IO, dF[0][j] - dF[1][j], s.fb);
+    c->cs = ok ? it_item(3, IT, IO, 0.0, s.fb) : NAN;
+    c->inv_ITIO = it_item(4, IT, IO, 0.0, s.fb);
+    double* hd = &c->h[0];      // h[10] and dh[10][6], contiguous
+    if (four) {
+        const AmpParams p = amp_params(m, th);
+        double f[kAngFactors];
+        for (int i = 0; i < kPlainFactors; ++i) f[plain_factor_index(i)] = plain_factor(plain_factor_index(i), p);
+        for (int i = 0; i < 6; ++i) sincos_fast(ang_arg(i, p.dpa, p.dpe, p.dS), mt, &f[19 + i], &f[25 + i]);
+        double r[11];            // square roots, their reciprocals, one (the sources of combo)
+        for (int i = 0; i < 5; ++i) {
+            r[i] = sqrt(sqrt_in(i, p));
+            r[5 + i] = recip(r[i]);
+        }
+        r[10] = 1.0;
+        f[8] = r[0];
+        f[6] = r[1];
+        f[7] = r[2];
+        const double omtF = 1.0 - 2.0 * p.F;
+        for (int i = 0; i < kComboFactors; ++i) f[9 + i] = combo(i, r[combo_a(i)], r[combo_b(i)], omtF);
+        for (int i = 0; i < kRowEntries; ++i) hd[i] = row_entry(kRowSpec[i], f);
+        c->MO = mo_sum(c->h);
+    } else {
+        for (int i = 0; i < kRowEntries; ++i) hd[i] = i == 0 ? 1.0 : 0.0;
+        c->MO = 1.0;
+    }
 }
 
 // Exchange buffer of compute_consts_block.
 struct ConstsBlockScratch {
-    double g[2], G[2], Phi[2];     // edge 0: t_hi, edge 1: t_lo
+    MathTables mt;
+    double f[32];                  // angular factors
+    double X1[2], X2[2], gq[2], E[2];   // edge 0: t_hi, edge 1: t_lo
+    double rG;
     double F[2], dF[2][3];
-    double MT, MO;
-    cdetail::AngPieces a;
-    double q[cdetail::kScalarQuotients + cdetail::kItQuotients];
-    double h[10], d[10][6];
+    Consts c;                      // the record, copied out at the end
 };
+constexpr int kConstsBlock = 192;
 
-// One block of 128 threads (four warps, one per SM sub-partition) computes one
-// Consts record: a single fit, where latency matters.  On this GPU a warp's
-// FP64 instruction occupies its sub-partition's FP64 unit for tens of cycles
-// whatever the active lanes, so the record's independent pieces go to
-// different warps and, within a warp, to lanes running the same code:
-//   phase 1  warp 0: g at both edges (exp, erfc); warp 1: Phi at both edges
-//            (erfc); warp 2: the Gaussian at both edges and the envelope M_T;
-//            warp 3: six sine/cosine pairs, five square roots and the six
-//            divisions that need theta only;
-//   phase 2  warp 0: F and its derivatives at both edges; warps 1-3: the ten
-//            rows of h and dh (at most two rows with divisions per warp);
-//   phase 3  warp 0: the five divisions by I_T; warp 1: M_Omega.
-// Every value comes from the same expression as in compute_consts_thread, so
-// both give the same bits (this file is compiled without FMA contraction).
-__device__ inline void compute_consts_block(const ModelDev& m, const double* th, Consts* c,
-                                            ConstsBlockScratch* S) {
+// One block of six warps computes one Consts record: a single fit, where
+// latency matters.  A warp's FP64 instruction occupies its sub-partition's
+// FP64 unit for tens of cycles whatever the active lanes, and a dependent one
+// waits for the one before, so independent chains go to different warps and,
+// within a warp, to lanes running the same code:
+//   phase 1  warp 0: erfcx at z (both edges); warp 1: erfcx at w; warp 2: the
+//            Gaussian factor and E (both edges); warp 3: six sine/cosine pairs;
+//            warp 4: five square roots, their reciprocals and the products
+//            among them (shuffles), the plain factors; warp 5: 1/Gamma and the
+//            scalars that need theta only;
+//   phase 2  warp 0: g, Phi, G, F and its derivatives at both edges, M_T;
+//            warps 1-3: the 70 entries of h and dh, one per lane;
+//   phase 3  warp 0: I_T and the five divisions by it; warp 1: M_Omega
+//            (shuffle tree);
+// then every thread copies part of the record out.  Every value comes from the
+// same expression as in compute_consts_thread, so both give the same bits
+// (this file is compiled without FMA contraction).
+__device__ inline void compute_consts_block(const ModelDev& m, const double* th, Consts* c, ConstsBlockScratch* S) {
     using namespace cdetail;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU];
     const bool four = m.kind == IPA_MODEL_ANGTIME4D;
-    const AmpParams p = amp_params(m, th);
-    const double tau_e = (lane == 0 ? m.t_hi : m.t_lo) - mu;
+    const int row = (int)threadIdx.x - 32;             // warps 1-3: entry of h / dh
+    const unsigned spec = four && row >= 0 && row < kRowEntries ? kRowSpec[row] : 0u;
+    load_consts_tables(&S->mt);
+    __syncthreads();
+
+    const TimeScalars s = time_scalars(th);
+    const int e = lane & 1;
+    double tau = 0.0, x = 0.0, z = 0.0, rs = 0.0, X1 = 0.0;
+    if (w <= 2 && lane < 4) {
+        rs = recip(s.sigma);
+        tau = edge_tau(m, s.mu, e);
+        x = tau * rs;
+    }
     if (w == 0) {
-        if (lane < 2) S->g[lane] = conv_g(tau_e, Gamma, sigma);
+        if (lane < 2) {
+            z = edge_z(s, x);
+            X1 = edge_erfcx(z, &S->mt);
+        }
     } else if (w == 1) {
-        if (lane < 2) S->Phi[lane] = edge_phi(tau_e, sigma);
+        if (lane < 2) S->X2[e] = edge_erfcx(edge_w(x), &S->mt);
     } else if (w == 2) {
-        if (lane < 2) S->G[lane] = gauss(tau_e, sigma);
-        else if (lane == 2) S->MT = time_envelope(m, Gamma, sigma, mu);
+        if (lane < 4) {
+            const double v = exp_fast(lane < 2 ? gauss_exponent(x) : decay_exponent(s, tau), &S->mt);
+            if (lane < 2) S->gq[e] = v;
+            else S->E[e] = v;
+        }
     } else if (w == 3) {
-        if (lane < 6) {
-            if (four) sincos(ang_arg(lane, p.dpa, p.dpe, p.dS), &S->a.sn[lane], &S->a.cs[lane]);
-        } else if (lane < 11) {
-            if (four) S->a.rt[lane - 6] = sqrt(sqrt_arg(lane - 6, p.x0, p.xa, p.xe, p.F, p.s));
-        } else if (lane < 11 + kScalarQuotients) {
-            double num, den;
-            scalar_quotient(lane - 11, m, th, &num, &den);
-            S->q[lane - 11] = num / den;
+        if (four && lane < 6) {
+            const AmpParams p = amp_params(m, th);
+            sincos_fast(ang_arg(lane, p.dpa, p.dpe, p.dS), &S->mt, &S->f[19 + lane], &S->f[25 + lane]);
+        }
+    } else if (w == 4) {
+        if (four) {
+            const AmpParams p = amp_params(m, th);
+            double r = 0.0, ir = 0.0;
+            if (lane < 5) {
+                r = sqrt(sqrt_in(lane, p));
+                ir = recip(r);
+            }
+            const int ia = combo_a(lane & 7), ib = combo_b(lane & 7);
+            const double ra = __shfl_sync(0xffffffffu, r, ia % 5), ira = __shfl_sync(0xffffffffu, ir, ia % 5);
+            const double rb = __shfl_sync(0xffffffffu, r, ib % 5), irb = __shfl_sync(0xffffffffu, ir, ib % 5);
+            const double a = ia < 5 ? ra : ira;
+            const double b = ib == 10 ? 1.0 : (ib < 5 ? rb : irb);
+            if (lane < kComboFactors) S->f[9 + lane] = combo(lane, a, b, 1.0 - 2.0 * p.F);
+            if (lane < 3) S->f[lane == 0 ? 8 : 5 + lane] = r;
+            if (lane >= 16 && lane < 16 + kPlainFactors) {
+                const int i = plain_factor_index(lane - 16);
+                S->f[i] = plain_factor(i, p);
+            }
+        }
+    } else if (w == 5) {
+        if (lane == 0) {
+            S->rG = recip(s.Gamma);
+            write_time_scalars(s, recip(s.sigma), recip(volume(m)), in_domain(th, four), &S->c);
         }
     }
     __syncthreads();
-    // rows of h: warp 1 -> 0, 3, 4; warp 2 -> 1, 5, 7; warp 3 -> 2, 6, 8, 9
-    int k = -1;
+
+    double* hd = &S->c.h[0];   // h[10] and dh[10][6], contiguous
     if (w == 0) {
-        if (lane < 2) edge_combine(tau_e, Gamma, sigma, S->g[lane], S->G[lane], S->Phi[lane], &S->F[lane], S->dF[lane]);
+        if (lane < 2) {
+            double g, Phi, G;
+            edge_values(z, edge_w(x), S->gq[e], S->E[e], X1, S->X2[e], kInvSqrt2Pi * rs, &g, &Phi, &G);
+            edge_combine_r(s, tau, x, S->rG, g, G, Phi, &S->F[e], S->dF[e]);
+            if (e == 1) S->c.MT = fmin(1.0, S->E[1]);
+        }
+    } else if (row >= 0 && row < kRowEntries) {
+        hd[row] = four ? row_entry(spec, S->f) : (row == 0 ? 1.0 : 0.0);
+    }
+    __syncthreads();
+
+    if (w == 0) {
+        if (lane < 5) {
+            const double IT = S->F[0] - S->F[1];
+            const double dIT = lane < 3 ? S->dF[0][lane] - S->dF[1][lane] : 0.0;
+            const double v = it_item(lane, IT, omega_integral(m), dIT, s.fb);
+            if (lane < 3) S->c.dlnIT[lane] = v;
+            else if (lane == 3) S->c.cs = in_domain(th, four) ? v : NAN;
+            else S->c.inv_ITIO = v;
+            if (lane == 0) S->c.IT = IT;
+        }
     } else if (w == 1) {
-        k = lane == 0 ? 0 : (lane == 1 ? 3 : (lane == 2 ? 4 : -1));
-    } else if (w == 2) {
-        k = lane == 0 ? 1 : (lane == 1 ? 5 : (lane == 2 ? 7 : -1));
-    } else if (w == 3) {
-        k = lane == 0 ? 2 : (lane == 1 ? 6 : (lane == 2 ? 8 : (lane == 3 ? 9 : -1)));
-    }
-    if (k >= 0) {
-        double h = k == 0 ? 1.0 : 0.0, d[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        if (four) h_row(k, S->a, p.x0, p.xe, p.xa, p.s, p.F, &h, d);
-        S->h[k] = h;
-        for (int j = 0; j < 6; ++j) S->d[k][j] = d[j];
+        // a_i = p_2i + p_2i+1 in lane 2i, then ((a_0 + a_1) + (a_2 + a_3)) + a_4 as in mo_sum
+        const double p = four && lane < 10 ? fabs(hd[lane]) * basis_max(lane) : 0.0;
+        const double a = p + __shfl_down_sync(0xffffffffu, p, 1);
+        const double b = a + __shfl_down_sync(0xffffffffu, a, 2);
+        const double q = b + __shfl_down_sync(0xffffffffu, b, 4);
+        const double a4 = __shfl_sync(0xffffffffu, a, 8);
+        if (lane == 0) S->c.MO = four ? q + a4 : 1.0;
     }
     __syncthreads();
-    const double IT = S->F[0] - S->F[1];
-    if (w == 0 && lane < kItQuotients) {
-        double dIT[3];
-        for (int j = 0; j < 3; ++j) dIT[j] = S->dF[0][j] - S->dF[1][j];
-        double num, den;
-        it_quotient(lane, m, th, IT, dIT, &num, &den);
-        S->q[kScalarQuotients + lane] = num / den;
-    } else if (w == 1 && lane == 0) {
-        double MO = 0.0;
-        if (four)
-            for (int r = 0; r < 10; ++r)
-                MO = r ? MO + fabs(S->h[r]) * basis_max(r) : fabs(S->h[r]) * basis_max(r);
-        S->MO = MO;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) write_plain_scalars(th, IT, S->MT, S->MO, four, S->q, c);
-    if (threadIdx.x < 60) c->dh[threadIdx.x / 6][threadIdx.x % 6] = S->d[threadIdx.x / 6][threadIdx.x % 6];
-    if (threadIdx.x >= 64 && threadIdx.x < 74) c->h[threadIdx.x - 64] = S->h[threadIdx.x - 64];
+    const double* src = reinterpret_cast<const double*>(&S->c);
+    double* dst = reinterpret_cast<double*>(c);
+    for (int i = threadIdx.x; i < kConstsDoubles; i += blockDim.x) dst[i] = src[i];
 }
 
 }  // namespace ipa
