@@ -255,6 +255,9 @@ __device__ inline double omega_integral(const ModelDev& m) {
     return m.kind == IPA_MODEL_ANGTIME4D ? 16.0 * kPi / 9.0 : 1.0;
 }
 
+// M_T = min(1, E) at t_lo (1 for NaN E), by a bit comparison.
+__device__ inline double time_envelope(double E_lo) { return above(E_lo, 1.0) ? 1.0 : E_lo; }
+
 // Item j of the divisions by I_T: (dI_T/dtheta_j) / I_T for j < 3 (dIT_j
 // given), cs = (1 - f_b) / (I_T I_Omega) for j = 3, 1 / (I_T I_Omega) for j = 4.
 __device__ inline double it_item(int j, double IT, double IO, double dIT_j, double fb) {
@@ -352,7 +355,7 @@ __device__ inline double row_entry(unsigned spec, const double* f) {
 __device__ inline double mo_sum(const double* h) {
     double a[5];
     for (int i = 0; i < 5; ++i)
-        a[i] = fabs(h[2 * i]) * basis_max(2 * i) + fabs(h[2 * i + 1]) * basis_max(2 * i + 1);
+        a[i] = abs_bits(h[2 * i]) * basis_max(2 * i) + abs_bits(h[2 * i + 1]) * basis_max(2 * i + 1);
     return ((a[0] + a[1]) + (a[2] + a[3])) + a[4];
 }
 
@@ -390,7 +393,7 @@ __device__ inline void compute_consts_thread(const ModelDev& m, const double* th
         double g, Phi, G;
         edge_values(z, w, gq, E, X1, X2, kInvSqrt2Pi * rs, &g, &Phi, &G);
         edge_combine_r(s, tau, x, rG, g, G, Phi, &F[e], dF[e]);
-        if (e == 1) c->MT = fmin(1.0, E);
+        if (e == 1) c->MT = time_envelope(E);
     }
     write_time_scalars(s, rs, rV, ok, c);
     const double IT = F[0] - F[1], IO = omega_integral(m);
@@ -426,10 +429,12 @@ __device__ inline void compute_consts_thread(const ModelDev& m, const double* th
 // Exchange buffer of compute_consts_block.
 struct ConstsBlockScratch {
     MathTables mt;
+    double th[IPA_NPAR_4D];        // theta
     double f[32];                  // angular factors
     double X1[2], X2[2], gq[2], E[2];   // edge 0: t_hi, edge 1: t_lo
     double rG;
     double F[2], dF[2][3];
+    int ok;                        // theta in the domain
     Consts c;                      // the record, copied out at the end
 };
 constexpr int kConstsBlock = 192;
@@ -457,8 +462,12 @@ __device__ inline void compute_consts_block(const ModelDev& m, const double* th,
     const bool four = m.kind == IPA_MODEL_ANGTIME4D;
     const int row = (int)threadIdx.x - 32;             // warps 1-3: entry of h / dh
     const unsigned spec = four && row >= 0 && row < kRowEntries ? kRowSpec[row] : 0u;
+    // theta and the tables come from memory together; everything after the
+    // barrier reads them from shared memory
+    if (threadIdx.x < (four ? IPA_NPAR_4D : IPA_NPAR_1D)) S->th[threadIdx.x] = th[threadIdx.x];
     load_consts_tables(&S->mt);
     __syncthreads();
+    th = S->th;
 
     const TimeScalars s = time_scalars(th);
     const int e = lane & 1;
@@ -508,8 +517,10 @@ __device__ inline void compute_consts_block(const ModelDev& m, const double* th,
         }
     } else if (w == 5) {
         if (lane == 0) {
+            const bool ok = in_domain(th, four);
+            S->ok = ok;
             S->rG = recip(s.Gamma);
-            write_time_scalars(s, recip(s.sigma), recip(volume(m)), in_domain(th, four), &S->c);
+            write_time_scalars(s, recip(s.sigma), recip(volume(m)), ok, &S->c);
         }
     }
     __syncthreads();
@@ -520,7 +531,7 @@ __device__ inline void compute_consts_block(const ModelDev& m, const double* th,
             double g, Phi, G;
             edge_values(z, edge_w(x), S->gq[e], S->E[e], X1, S->X2[e], kInvSqrt2Pi * rs, &g, &Phi, &G);
             edge_combine_r(s, tau, x, S->rG, g, G, Phi, &S->F[e], S->dF[e]);
-            if (e == 1) S->c.MT = fmin(1.0, S->E[1]);
+            if (e == 1) S->c.MT = time_envelope(S->E[1]);
         }
     } else if (row >= 0 && row < kRowEntries) {
         hd[row] = four ? row_entry(spec, S->f) : (row == 0 ? 1.0 : 0.0);
@@ -533,13 +544,13 @@ __device__ inline void compute_consts_block(const ModelDev& m, const double* th,
             const double dIT = lane < 3 ? S->dF[0][lane] - S->dF[1][lane] : 0.0;
             const double v = it_item(lane, IT, omega_integral(m), dIT, s.fb);
             if (lane < 3) S->c.dlnIT[lane] = v;
-            else if (lane == 3) S->c.cs = in_domain(th, four) ? v : NAN;
+            else if (lane == 3) S->c.cs = S->ok ? v : NAN;
             else S->c.inv_ITIO = v;
             if (lane == 0) S->c.IT = IT;
         }
     } else if (w == 1) {
         // a_i = p_2i + p_2i+1 in lane 2i, then ((a_0 + a_1) + (a_2 + a_3)) + a_4 as in mo_sum
-        const double p = four && lane < 10 ? fabs(hd[lane]) * basis_max(lane) : 0.0;
+        const double p = four && lane < 10 ? abs_bits(hd[lane]) * basis_max(lane) : 0.0;
         const double a = p + __shfl_down_sync(0xffffffffu, p, 1);
         const double b = a + __shfl_down_sync(0xffffffffu, a, 2);
         const double q = b + __shfl_down_sync(0xffffffffu, b, 4);
