@@ -191,7 +191,7 @@ COUNT_METRICS = ("smsp__inst_executed.sum,smsp__inst_executed_pipe_fp64.sum,"
 COUNT_COMMON = ["tile_reduce.cuh", "fp64_math.cuh", "fp64_tables.cuh", "int_math.cuh", "ipa_internal.cuh"]
 COUNT_CAPTURES = {
     "nll_kernel<4D, grad>": ("counts_4d.csv", "bench.py --profile-case", 8_000_000,
-                             ["nll.cu", "angular.cuh", "consts.cuh"] + COUNT_COMMON),
+                             ["nll.cu", "angular.cuh"] + COUNT_COMMON),
     "phis_kernel<grad>": ("counts_phis.csv", "bench.py --profile-case-phis", 8_000_000,
                           ["phis.cu", "angular.cuh", "tagged.cuh", "faddeeva.cuh", "consts.cuh", "philox.cuh"] + COUNT_COMMON),
     "tag_kernel<grad>": ("counts_tag.csv", "bench.py --profile-case-tagged", 8_000_000,

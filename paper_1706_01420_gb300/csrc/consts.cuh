@@ -163,18 +163,22 @@ struct TimeScalars {
     double Gs2, s2, G2s, Gsig;
 };
 
-__device__ inline TimeScalars time_scalars(const double* th) {
+__device__ inline TimeScalars time_scalars_of(double Gamma, double sigma, double mu, double fb) {
     TimeScalars s;
-    s.Gamma = th[IPA_GAMMA];
-    s.sigma = th[IPA_SIGMA];
-    s.mu = th[IPA_MU];
-    s.fb = th[IPA_FB];
+    s.Gamma = Gamma;
+    s.sigma = sigma;
+    s.mu = mu;
+    s.fb = fb;
     s.c_exp = 0.5 * s.Gamma * s.Gamma * s.sigma * s.sigma;
     s.Gs2 = s.Gamma * s.sigma * s.sigma;
     s.s2 = s.sigma * s.sigma;
     s.G2s = s.Gamma * s.Gamma * s.sigma;
     s.Gsig = s.Gamma * s.sigma;
     return s;
+}
+
+__device__ inline TimeScalars time_scalars(const double* th) {
+    return time_scalars_of(th[IPA_GAMMA], th[IPA_SIGMA], th[IPA_MU], th[IPA_FB]);
 }
 
 // Edge e of the range (0: t_hi, 1: t_lo) as tau = t_e - mu.

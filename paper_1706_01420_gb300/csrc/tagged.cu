@@ -284,34 +284,6 @@ ipa_status launch_tag_t(const Cols& cols, int64_t n, const int64_t* seg_begin, c
                      "tagged likelihood kernel launch");
 }
 
-// One thread per fit.
-// One thread per segment (many segments: the warp's lanes are segments).
-__global__ void tag_consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg, Consts* __restrict__ out) {
-    asm volatile("griddepcontrol.launch_dependents;");
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_seg) return;
-    const double* th = theta + (size_t)s * m.n_par;
-    TagPieces p;
-    for (int k = 0; k < kTagPieces; ++k) tag_piece(m, th, k, &p);
-    compute_tag_consts(m, th, &p, reinterpret_cast<TagConsts*>(out + s));
-}
-
-// One four-warp block per segment (few segments): a lane's FP64 instruction
-// holds its sub-partition's FP64 unit as long as a full warp's, so the pieces
-// go side by side: warp 0 the four edges (lanes 0-3), warp 1 sincos, warp 2
-// the three envelope bounds, warp 3 the root; thread 0 assembles the record.
-__global__ void __launch_bounds__(128) tag_consts_block_kernel(ModelDev m, const double* __restrict__ theta,
-                                                               Consts* __restrict__ out) {
-    asm volatile("griddepcontrol.launch_dependents;");
-    __shared__ TagPieces p;
-    const double* th = theta + (size_t)blockIdx.x * m.n_par;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int first[4] = {0, 4, 5, 8}, count[4] = {4, 1, 3, 1};
-    if (l < count[w]) tag_piece(m, th, first[w] + l, &p);
-    __syncthreads();
-    if (threadIdx.x == 0) compute_tag_consts(m, th, &p, reinterpret_cast<TagConsts*>(out + blockIdx.x));
-}
-
 __global__ void faddeeva_kernel(const double* __restrict__ z, double* __restrict__ w, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double wr, wi;
@@ -322,15 +294,6 @@ __global__ void faddeeva_kernel(const double* __restrict__ z, double* __restrict
 }
 
 }  // namespace
-
-ipa_status launch_tag_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out, cudaStream_t st) {
-    if (n_seg <= 0) return IPA_OK;
-    if (n_seg < 64)
-        tag_consts_block_kernel<<<n_seg, 128, 0, st>>>(m, theta, out);
-    else
-        tag_consts_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
-    return cuda_fail(cudaGetLastError(), "tagged consts kernel launch");
-}
 
 namespace {
 // ipa_nll_grad_combine for the tagged model: the kernel's last reduction level

@@ -76,103 +76,253 @@ __device__ inline double env_bound(double x, double t_lo, double mu, double sigm
 
 }  // namespace tdetail
 
-// theta (8 values) -> the record.
-// The transcendental inputs of the record, independent of one another (see
-// tag_piece): evaluated side by side by four warps for a few segments.
-struct TagPieces {
-    double F[4], dF[4][3];     // edge(): (t_hi, Gamma_H), (t_lo, Gamma_H), (t_hi, Gamma_L), (t_lo, Gamma_L)
-    double sn, cn;             // sincos(phi_s)
-    double M[3];               // env_bound of Gamma_H, Gamma_L, Gamma
-    double tq;                 // sqrt(39.1 + beta^2)
-};
-constexpr int kTagPieces = 9;
+// theta (8 values) -> the record, along short chains as for the 4D record
+// (consts.cuh: erfc and the Gaussian through exp(-x^2/2) and the table-driven
+// erfcx and exp, products with reciprocals instead of divisions).  Edge k =
+// 2r + e of the normalisation: rate r (0: Gamma_H, 1: Gamma_L) at edge e (0:
+// t_hi, 1: t_lo).  One thread per segment (tag_consts_thread) and one block per
+// segment (tag_consts_block) call the same functions, so both give the same bits
+// (tagged.cu is compiled without FMA contraction).
+namespace tdetail {
 
-// Piece k: 0-3 the edges, 4 sincos(phi_s), 5-7 the envelope bounds, 8 the cut's root.
-__device__ inline void tag_piece(const ModelDev& m, const double* th, int k, TagPieces* p) {
-    using namespace cdetail;
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], DG = th[IPA_DG];
-    const double GH = Gamma - 0.5 * DG, GL = Gamma + 0.5 * DG;
-    if (k < 4) {
-        edge((k & 1) ? m.t_lo - mu : m.t_hi - mu, k < 2 ? GH : GL, sigma, &p->F[k], p->dF[k]);
-    } else if (k == 4) {
-        sincos(th[IPA_PHIS], &p->sn, &p->cn);
-    } else if (k < 8) {
-        p->M[k - 5] = tdetail::env_bound(k == 5 ? GH : (k == 6 ? GL : Gamma), m.t_lo, mu, sigma);
-    } else {
-        const double beta = th[IPA_DM] * sigma / kSqrt2;
-        p->tq = sqrt(39.1 + beta * beta);
-    }
+__device__ inline double rate_H(const double* th) { return th[IPA_GAMMA] - 0.5 * th[IPA_DG]; }
+__device__ inline double rate_L(const double* th) { return th[IPA_GAMMA] + 0.5 * th[IPA_DG]; }
+
+__device__ inline cdetail::TimeScalars rate_scalars(const double* th, int r) {
+    return cdetail::time_scalars_of(r == 0 ? rate_H(th) : rate_L(th), th[IPA_SIGMA], th[IPA_MU], th[IPA_FB]);
 }
 
-__device__ inline void compute_tag_consts(const ModelDev& m, const double* th, const TagPieces* pc, TagConsts* c) {
+// Piece k of the edges: erfcx at the argument of g at edge k (k < 4) or of
+// Phi at edge k - 4 (k = 4, 5); rs = 1 / sigma.
+__device__ inline double edge_X(const ModelDev& m, const double* th, int k, double rs, const MathTables* mt) {
     using namespace cdetail;
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
-    const double DG = th[IPA_DG], Dm = th[IPA_DM], phi = th[IPA_PHIS], om = th[IPA_OMEGA];
-    const double GH = Gamma - 0.5 * DG, GL = Gamma + 0.5 * DG;
-    const double FhH = pc->F[0], FlH = pc->F[1], FhL = pc->F[2], FlL = pc->F[3];
-    const double *dFhH = pc->dF[0], *dFlH = pc->dF[1], *dFhL = pc->dF[2], *dFlL = pc->dF[3];
-    const double IH = FhH - FlH, IL = FhL - FlL;
-    const double sn = pc->sn, cn = pc->cn;
-    const double D = 1.0 - 2.0 * om;
-    const double wH = 1.0 - cn, wL = 1.0 + cn;
-    const double N = wH * IH + wL * IL;
-    double dN[8];
-    for (int j = 0; j < 3; ++j) dN[j] = wH * (dFhH[j] - dFlH[j]) + wL * (dFhL[j] - dFlL[j]);
-    dN[3] = 0.0;
-    dN[4] = -0.5 * wH * (dFhH[0] - dFlH[0]) + 0.5 * wL * (dFhL[0] - dFlL[0]);
-    dN[5] = 0.0;
-    dN[6] = sn * IH - sn * IL;
-    dN[7] = 0.0;
-    const double inv_N = 1.0 / N;
-    const double V2 = 2.0 * (m.t_hi - m.t_lo);
+    const double x = edge_tau(m, th[IPA_MU], k & 1) * rs;
+    const double z = edge_z(rate_scalars(th, (k >> 1) & 1), x);
+    return edge_erfcx(k < 4 ? z : edge_w(x), mt);
+}
+
+// Piece k of the edges: E = exp(-Gamma_r tau + Gamma_r^2 sigma^2 / 2) at edge
+// k (k < 4) or the Gaussian factor exp(-x^2/2) at edge k - 4 (k = 4, 5).
+__device__ inline double edge_exp(const ModelDev& m, const double* th, int k, double rs, const MathTables* mt) {
+    using namespace cdetail;
+    const double tau = edge_tau(m, th[IPA_MU], k & 1);
+    const double x = tau * rs;
+    return exp_fast(k < 4 ? decay_exponent(rate_scalars(th, (k >> 1) & 1), tau) : gauss_exponent(x), mt);
+}
+
+// F and its derivatives (rate, sigma, mu) at edge k < 4 from its pieces:
+// X1 = edge_X(k), X2 = edge_X(4 + e), E = edge_exp(k), gq = edge_exp(4 + e),
+// rs = 1 / sigma, rG = 1 / Gamma_r.
+__device__ inline void edge_F(const ModelDev& m, const double* th, int k, double rs, double rG, double X1,
+                              double X2, double E, double gq, double* F, double* dF) {
+    using namespace cdetail;
+    const double tau = edge_tau(m, th[IPA_MU], k & 1);
+    const double x = tau * rs;
+    const TimeScalars s = rate_scalars(th, k >> 1);
+    double g, Phi, G;
+    edge_values(edge_z(s, x), edge_w(x), gq, E, X1, X2, kInvSqrt2Pi * rs, &g, &Phi, &G);
+    edge_combine_r(s, tau, x, rG, g, G, Phi, F, dF);
+}
+
+// The denominators that get a reciprocal: sigma, Gamma_H, Gamma_L and 2 (t_hi - t_lo).
+__device__ inline double recip_arg(const ModelDev& m, const double* th, int i) {
+    return i == 0 ? th[IPA_SIGMA] : (i == 1 ? rate_H(th) : (i == 2 ? rate_L(th) : 2.0 * (m.t_hi - m.t_lo)));
+}
+
+// sqrt(39.1 + beta^2), beta = Dm sigma / sqrt2 (the near-peak cut's root).
+__device__ inline double cut_root(const double* th) {
+    const double beta = th[IPA_DM] * th[IPA_SIGMA] * cdetail::kInvSqrt2;
+    return sqrt(39.1 + beta * beta);
+}
+
+// M_x for x = Gamma_H, Gamma_L, Gamma (i = 0, 1, 2).
+__device__ inline double env_piece(const ModelDev& m, const double* th, int i) {
+    return env_bound(i == 0 ? rate_H(th) : (i == 1 ? rate_L(th) : th[IPA_GAMMA]), m.t_lo, th[IPA_MU], th[IPA_SIGMA]);
+}
+
+// Record fields from theta alone.
+__device__ inline void theta_fields(const double* th, TagConsts* c) {
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], Dm = th[IPA_DM];
+    const double GH = rate_H(th), GL = rate_L(th);
     c->Gamma = Gamma;
     c->sigma = sigma;
-    c->mu = mu;
-    c->fb = fb;
-    c->DG = DG;
+    c->mu = th[IPA_MU];
+    c->fb = th[IPA_FB];
+    c->DG = th[IPA_DG];
     c->Dm = Dm;
-    c->phi = phi;
-    c->om = om;
+    c->phi = th[IPA_PHIS];
+    c->om = th[IPA_OMEGA];
     c->GH = GH;
     c->GL = GL;
-    c->k_z = 1.0 / (kSqrt2 * sigma);
-    c->k_g = 1.0 / (2.0 * sigma * sigma);
-    c->cG = kInvSqrt2Pi / sigma;
+    c->cH2 = 0.5 * GH * GH * sigma * sigma + kLn2;
+    c->cL2 = 0.5 * GL * GL * sigma * sigma + kLn2;
+    c->cC2 = 0.5 * (Gamma - Dm) * (Gamma + Dm) * sigma * sigma + kLn2;
+}
+
+// Record fields from theta, rs = 1 / sigma and rV2 = 1 / (2 (t_hi - t_lo)).
+__device__ inline void scale_fields(const double* th, double rs, double rV2, TagConsts* c) {
+    using namespace cdetail;
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], Dm = th[IPA_DM];
+    c->k_z = rs * kInvSqrt2;
+    c->k_g = 0.5 * (rs * rs);
+    c->cG = kInvSqrt2Pi * rs;
     c->s2 = sigma * sigma;
-    c->inv_s = 1.0 / sigma;
-    c->cH2 = 0.5 * GH * GH * sigma * sigma + tdetail::kLn2;
-    c->cL2 = 0.5 * GL * GL * sigma * sigma + tdetail::kLn2;
-    c->cC2 = 0.5 * (Gamma - Dm) * (Gamma + Dm) * sigma * sigma + tdetail::kLn2;
-    c->uH0 = GH * sigma * sigma;
-    c->uL0 = GL * sigma * sigma;
+    c->inv_s = rs;
+    c->uH0 = rate_H(th) * sigma * sigma;
+    c->uL0 = rate_L(th) * sigma * sigma;
     c->uC0 = Gamma * sigma * sigma;
-    c->beta = Dm * sigma / kSqrt2;
+    c->beta = Dm * sigma * kInvSqrt2;
     c->ph0 = Gamma * Dm * sigma * sigma;
-    c->aH = 0.5 * wH;
-    c->aL = 0.5 * wL;
+    c->D = 1.0 - 2.0 * th[IPA_OMEGA];
+    c->cb = th[IPA_FB] * rV2;
+    c->inv_V2 = rV2;
+    c->pad_ = 0.0;
+}
+
+// Record fields from sin/cos phi_s (sn, cn), the cut's root tq and the envelope bounds M.
+__device__ inline void phase_fields(const double* th, double sn, double cn, double tq, const double* M, TagConsts* c) {
+    using namespace cdetail;
+    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU];
+    const double D = 1.0 - 2.0 * th[IPA_OMEGA];
+    c->aH = 0.5 * (1.0 - cn);
+    c->aL = 0.5 * (1.0 + cn);
     c->Ds = D * sn;
-    c->D = D;
     c->c = cn;
     c->s = sn;
-    const double cs = (1.0 - fb) * inv_N;
-    c->cs = cs;
-    c->qH = 0.5 * cs * c->aH;
-    c->qL = 0.5 * cs * c->aL;
-    c->qD = 0.5 * cs * c->Ds;
-    c->cb = fb / V2;
-    c->inv_N = inv_N;
-    c->inv_V2 = 1.0 / V2;
-    c->N = N;
-    for (int j = 0; j < 8; ++j) c->dlnN[j] = dN[j] * inv_N;
     // t > tcut: Re u <= -sqrt(39.1 + b^2) for all three rates, so |e^{-u^2} w|
     // <= e^{-39.1} ~ 1e-17 relative to the exponential, and Gx < 1e-17
-    const double rmax = fmax(fmax(GH, GL), Gamma);
-    const double tc = mu + (rmax * sigma * sigma + pc->tq * kSqrt2 * sigma);
+    const double rmax = fmax(fmax(rate_H(th), rate_L(th)), Gamma);
+    const double tc = mu + (rmax * sigma * sigma + tq * kSqrt2 * sigma);
     c->tcut = tc == tc ? tc : INFINITY;
-    const double MH = pc->M[0], ML = pc->M[1], MC = pc->M[2];
-    c->MS = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(0.5, __dsub_rn(1.0, cn)), MH),
-                                __dmul_rn(__dmul_rn(0.5, __dadd_rn(1.0, cn)), ML)),
-                      __dmul_rn(fabs(__dmul_rn(D, sn)), MC));
+    c->MS = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(0.5, __dsub_rn(1.0, cn)), M[0]),
+                                __dmul_rn(__dmul_rn(0.5, __dadd_rn(1.0, cn)), M[1])),
+                      __dmul_rn(fabs(__dmul_rn(D, sn)), M[2]));
+}
+
+// N = (1 - cos phi_s) I(Gamma_H) + (1 + cos phi_s) I(Gamma_L), I = F(t_hi) - F(t_lo).
+__device__ inline double norm_N(const double* F, double cn) {
+    return (1.0 - cn) * (F[0] - F[1]) + (1.0 + cn) * (F[2] - F[3]);
+}
+
+// dN/dtheta_j as a (P - Q) + b (R - S): j < 3 (Gamma, sigma, mu) the edges'
+// derivatives weighted by 1 -+ cos phi_s, j = 4 (DG) their rate derivatives
+// weighted by -+(1 -+ cos phi_s)/2, j = 6 (phi_s) the integrals weighted by
+// +-sin phi_s; 0 for mu's neighbours f_b, Dm and omega.
+__device__ inline double norm_dN(int j, const double* F, const double (*dF)[3], double sn, double cn) {
+    const double wH = 1.0 - cn, wL = 1.0 + cn;
+    const int jj = j < 3 ? j : 0;
+    const double a = j < 3 ? wH : (j == 4 ? -0.5 * wH : sn);
+    const double b = j < 3 ? wL : (j == 4 ? 0.5 * wL : neg_bits(sn));
+    const bool val = j == 6;
+    const double P = val ? F[0] : dF[0][jj], Q = val ? F[1] : dF[1][jj];
+    const double R = val ? F[2] : dF[2][jj], S = val ? F[3] : dF[3][jj];
+    const double v = a * (P - Q) + b * (R - S);
+    return (j == 3 || j == 5 || j == 7) ? 0.0 : v;
+}
+
+// cs, qH, qL, qD, N and 1/N from N and the phase fields.
+__device__ inline void norm_fields(const double* th, double N, double inv_N, double sn, double cn, TagConsts* c) {
+    const double cs = (1.0 - th[IPA_FB]) * inv_N;
+    const double D = 1.0 - 2.0 * th[IPA_OMEGA];
+    c->cs = cs;
+    c->qH = 0.5 * cs * (0.5 * (1.0 - cn));
+    c->qL = 0.5 * cs * (0.5 * (1.0 + cn));
+    c->qD = 0.5 * cs * (D * sn);
+    c->inv_N = inv_N;
+    c->N = N;
+}
+
+}  // namespace tdetail
+
+// One thread computes the record (many segments: lanes hold different fits).
+__device__ inline void tag_consts_thread(const ModelDev& m, const double* th, const MathTables* mt, TagConsts* c) {
+    using namespace tdetail;
+    double r[4], X[6], Ex[6], M[3], F[4], dF[4][3];
+    for (int i = 0; i < 4; ++i) r[i] = cdetail::recip(recip_arg(m, th, i));
+    for (int k = 0; k < 6; ++k) {
+        X[k] = edge_X(m, th, k, r[0], mt);
+        Ex[k] = edge_exp(m, th, k, r[0], mt);
+    }
+    for (int i = 0; i < 3; ++i) M[i] = env_piece(m, th, i);
+    double sn, cn;
+    sincos_fast(th[IPA_PHIS], mt, &sn, &cn);
+    theta_fields(th, c);
+    scale_fields(th, r[0], r[3], c);
+    phase_fields(th, sn, cn, cut_root(th), M, c);
+    for (int k = 0; k < 4; ++k)
+        edge_F(m, th, k, r[0], r[1 + (k >> 1)], X[k], X[4 + (k & 1)], Ex[k], Ex[4 + (k & 1)], &F[k], dF[k]);
+    const double N = norm_N(F, cn), inv_N = cdetail::recip(N);
+    for (int j = 0; j < 8; ++j) c->dlnN[j] = norm_dN(j, F, dF, sn, cn) * inv_N;
+    norm_fields(th, N, inv_N, sn, cn, c);
+}
+
+// Exchange buffer of tag_consts_block.
+struct TagBlockScratch {
+    MathTables mt;
+    double th[IPA_NPAR_TAGGED];
+    double r[4];                  // 1/sigma, 1/Gamma_H, 1/Gamma_L, 1/(2 (t_hi - t_lo))
+    double X[6], Ex[6];           // edge pieces (edge_X, edge_exp)
+    double M[3], sn, cn, tq;
+    double F[4], dF[4][3];
+    TagConsts c;
+};
+constexpr int kTagConstsBlock = 256;
+
+// One block of eight warps computes the record (few segments: latency).  A
+// warp's FP64 instructions do not overlap one another, different warps' do,
+// so independent pieces go to different warps and, within a warp, to lanes
+// running the same code:
+//   phase 1  warp 0: the six erfcx; warp 1: the six exponentials; warp 2: the
+//            three envelope bounds; warp 3: sin/cos phi_s; warp 4: the four
+//            reciprocals and the cut's root; warp 5: the fields of theta alone;
+//   phase 2  warp 0: F and its derivatives at the four edges; warp 1: the
+//            phase fields; warp 2: the fields that need 1/sigma;
+//   phase 3  warp 0: N, 1/N, dN/dtheta_j / N (lane j) and the fields of 1/N;
+// then every thread copies part of the record out.
+__device__ inline void tag_consts_block(const ModelDev& m, const double* th, TagConsts* c, TagBlockScratch* S) {
+    using namespace tdetail;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < IPA_NPAR_TAGGED) S->th[threadIdx.x] = th[threadIdx.x];
+    cdetail::load_consts_tables(&S->mt);
+    __syncthreads();
+    th = S->th;
+
+    if (w == 0) {
+        if (lane < 6) S->X[lane] = edge_X(m, th, lane, cdetail::recip(th[IPA_SIGMA]), &S->mt);
+    } else if (w == 1) {
+        if (lane < 6) S->Ex[lane] = edge_exp(m, th, lane, cdetail::recip(th[IPA_SIGMA]), &S->mt);
+    } else if (w == 2) {
+        if (lane < 3) S->M[lane] = env_piece(m, th, lane);
+    } else if (w == 3) {
+        if (lane == 0) sincos_fast(th[IPA_PHIS], &S->mt, &S->sn, &S->cn);
+    } else if (w == 4) {
+        if (lane < 4) S->r[lane] = cdetail::recip(recip_arg(m, th, lane));
+        else if (lane == 4) S->tq = cut_root(th);
+    } else if (w == 5) {
+        if (lane == 0) theta_fields(th, &S->c);
+    }
+    __syncthreads();
+
+    if (w == 0) {
+        if (lane < 4)
+            edge_F(m, th, lane, S->r[0], S->r[1 + (lane >> 1)], S->X[lane], S->X[4 + (lane & 1)], S->Ex[lane],
+                   S->Ex[4 + (lane & 1)], &S->F[lane], S->dF[lane]);
+    } else if (w == 1) {
+        if (lane == 0) phase_fields(th, S->sn, S->cn, S->tq, S->M, &S->c);
+    } else if (w == 2) {
+        if (lane == 0) scale_fields(th, S->r[0], S->r[3], &S->c);
+    }
+    __syncthreads();
+
+    if (w == 0 && lane < 9) {
+        const double N = norm_N(S->F, S->cn), inv_N = cdetail::recip(N);
+        if (lane < 8) S->c.dlnN[lane] = norm_dN(lane, S->F, S->dF, S->sn, S->cn) * inv_N;
+        else norm_fields(th, N, inv_N, S->sn, S->cn, &S->c);
+    }
+    __syncthreads();
+    const double* src = reinterpret_cast<const double*>(&S->c);
+    double* dst = reinterpret_cast<double*>(c);
+    for (int i = threadIdx.x; i < kTagConstsDoubles; i += blockDim.x) dst[i] = src[i];
 }
 
 // The slow-branch values of one event (t <= tcut), with Gx = exp(-tau^2 /
