@@ -32,6 +32,7 @@
 #include "int_math.cuh"
 #include "ipa_internal.cuh"
 #include "philox.cuh"
+#include "phis_consts.cuh"
 #include "tagged.cuh"
 #include "tile_reduce.cuh"
 
@@ -53,31 +54,8 @@ __device__ const int kPairI[10] = {0, 1, 2, 1, 0, 0, 3, 3, 3, 3};
 __device__ const int kPairJ[10] = {0, 1, 2, 2, 1, 2, 3, 1, 2, 0};
 __device__ const int kPairIm[10] = {0, 0, 0, 1, 0, 1, 0, 0, 1, 0};
 
-// Constants of one fit (a Consts slot).
-struct PhisConsts {
-    // time part: the fields tag_slow reads, named as in TagConsts
-    double Gamma, sigma, mu, fb, DG, Dm;
-    double GH, GL, k_z, k_g, cG, s2, inv_s;
-    double cH2, cL2, cC2, uH0, uL0, uC0, beta, ph0, tcut;
-    // normalisation
-    double cs, cb, inv_N, inv_V, N;
-    double dlnN[IPA_NPAR_PHIS];
-    // phase, mistag dilution, amplitudes
-    double c, s, D;
-    double x0, xe, xa, F;           // A0sq, Apesq, 1 - A0sq - Apesq, F_S
-    double r0, ra, re, rF, rs;      // sqrt of x0, xa, xe, F, 1 - F
-    double cw[6], sw[6];            // cos, sin of (dpe - dpa), dpa, dpe, (dpa - dS), (dpe - dS), dS
-    double br[10], bi[10];          // Re, Im of b_k
-    double csp;                     // C_SP: factor of the S-P interference terms k = 7, 8, 9
-    double qsel;                    // normalisation over both tags (0) or over the tag +1 / -1
-    double pad_;
-};
-
 // Row factor: C_SP for the S-P interference terms, 1 otherwise.
 __device__ __forceinline__ double row_scale(const PhisConsts& c, int k) { return k >= 7 ? c.csp : 1.0; }
-static_assert(sizeof(PhisConsts) <= sizeof(Consts), "PhisConsts must fit a Consts slot");
-static_assert(sizeof(PhisConsts) % 16 == 0, "PhisConsts must be a multiple of 16 bytes");
-constexpr int kPhisDoubles = sizeof(PhisConsts) / sizeof(double);
 
 // Row k of C from part(b) pieces: pr = Re b, pi = Im b.  Every entry is a
 // product of part(b), one of (one, c, s) and of wu (untagged entries) or wt
@@ -164,244 +142,6 @@ __device__ inline void b_deriv(const PhisConsts& c, int k, int a, double* dr, do
     }
     *dr = dm * cp - m * dpsi * sp;
     *di = dm * sp + m * dpsi * cp;
-}
-
-// Complex antiderivative of the oscillating time function: F(tau) with
-// dF/dtau = g(tau; z), z = zr + i zi, F = (Phi(tau / sigma) - g) / z (from
-// g' = G - z g), and dF/dz, dF/dsigma, dF/dmu = -(F + dg/dz) / z,
-// (-(tau / sigma) G - dg/dsigma) / z, -g with dg/dz = (z s^2 - tau) g - s^2 G and
-// dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G.  g through the Faddeeva
-// function: 1/2 e^{-tau^2 / 2 s^2} w(x + i y) for y >= 0, else
-// e^{-z tau + z^2 s^2 / 2} - 1/2 e^{-tau^2 / 2 s^2} w(-x - i y), with
-// x + i y = i (z s^2 - tau) / (sqrt2 s).  Out: F, dF/dz, dF/dsigma, dF/dmu as
-// (re, im) pairs.
-__device__ inline void edge_c(double tau, double zr, double zi, double sigma, double* out) {
-    using namespace cdetail;
-    const double s2 = sigma * sigma;
-    const double y = (zr * s2 - tau) / (kSqrt2 * sigma), x = -zi * sigma / kSqrt2;
-    const double gx = exp(-tau * tau / (2.0 * s2));
-    double wr, wi, gr, gi;
-    if (y >= 0.0) {
-        faddeeva_uhp(x, y, &wr, &wi);
-        gr = 0.5 * gx * wr;
-        gi = 0.5 * gx * wi;
-    } else {
-        faddeeva_uhp(-x, -y, &wr, &wi);
-        const double a = -zr * tau + 0.5 * s2 * (zr * zr - zi * zi), b = -zi * tau + zr * zi * s2;
-        double sb, cb;
-        sincos(b, &sb, &cb);
-        const double ea = exp(a);
-        gr = ea * cb - 0.5 * gx * wr;
-        gi = ea * sb - 0.5 * gx * wi;
-    }
-    const double G = gx * kInvSqrt2Pi / sigma;
-    const double Phi = edge_phi(tau, sigma);
-    const double n2 = zr * zr + zi * zi, ir = zr / n2, ii = -zi / n2;     // 1/z
-    // F = (Phi - g) / z
-    const double nr = Phi - gr, ni = -gi;
-    const double Fr = nr * ir - ni * ii, Fi = nr * ii + ni * ir;
-    // dg/dz = (z s^2 - tau) g - s^2 G
-    const double pr = zr * s2 - tau, pi = zi * s2;
-    const double dzr = pr * gr - pi * gi - s2 * G, dzi = pr * gi + pi * gr;
-    // dF/dz = -(F + dg/dz) / z
-    const double ar = -(Fr + dzr), ai = -(Fi + dzi);
-    out[2] = ar * ir - ai * ii;
-    out[3] = ar * ii + ai * ir;
-    // dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G
-    const double z2r = (zr * zr - zi * zi) * sigma, z2i = 2.0 * zr * zi * sigma;
-    const double dsr = z2r * gr - z2i * gi - (zr * sigma + tau / sigma) * G;
-    const double dsi = z2r * gi + z2i * gr - zi * sigma * G;
-    // dF/dsigma = (-(tau / sigma) G - dg/dsigma) / z
-    const double br = -(tau / sigma) * G - dsr, bi = -dsi;
-    out[4] = br * ir - bi * ii;
-    out[5] = br * ii + bi * ir;
-    out[0] = Fr;
-    out[1] = Fi;
-    out[6] = -gr;
-    out[7] = -gi;
-}
-
-// The transcendental inputs of the constants, independent of one another, so
-// that they can be evaluated side by side: a lane's FP64 instruction holds its
-// sub-partition's FP64 unit for many cycles whether one lane or all 32 are
-// active, so one thread evaluating them in turn takes ~20 times longer than
-// four warps each evaluating one kind in several lanes at once.
-struct PhisPieces {
-    double F[4], dF[4][3];     // edge(): (t_hi, Gamma_L), (t_lo, Gamma_L), (t_hi, Gamma_H), (t_lo, Gamma_H)
-    double ec[2][8];           // edge_c() at t_hi and t_lo (one-tag normalisation only)
-    double sw[6], cw[6];       // sincos of the six strong-phase combinations
-    double sn, cn;             // sincos(phi_s)
-    double r[5];               // sqrt of x0, xa, xe, F, 1 - F
-    double tq;                 // sqrt(39.1 + beta^2)
-};
-constexpr int kPhisPieces = 19;
-
-// Piece k: 0-3 the real edges, 4-5 the complex edges, 6-11 the strong-phase
-// sincos, 12 sincos(phi_s), 13-17 the square roots, 18 the cut's root.
-__device__ inline void phis_piece(const ModelDev& md, const double* th, int k, PhisPieces* p) {
-    using namespace cdetail;
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], DG = th[IPA_PHIS_DG];
-    const double Dm = th[IPA_PHIS_DM];
-    if (k < 4) {
-        const double tau = (k & 1) ? md.t_lo - mu : md.t_hi - mu;
-        edge(tau, k < 2 ? Gamma + 0.5 * DG : Gamma - 0.5 * DG, sigma, &p->F[k], p->dF[k]);
-    } else if (k < 6) {
-        if (th[IPA_PHIS_QNORM] != 0.0) edge_c(k == 4 ? md.t_hi - mu : md.t_lo - mu, Gamma, -Dm, sigma, p->ec[k - 4]);
-    } else if (k < 12) {
-        sincos(ang_arg(k - 6, th[IPA_DPA], th[IPA_DPE], th[IPA_DS]), &p->sw[k - 6], &p->cw[k - 6]);
-    } else if (k == 12) {
-        sincos(th[IPA_PHIS_PHIS], &p->sn, &p->cn);
-    } else if (k < 18) {
-        const double x0 = th[IPA_A0SQ], xe = th[IPA_APESQ], F = th[IPA_FS];
-        const double arg[5] = {x0, 1.0 - x0 - xe, xe, F, 1.0 - F};
-        p->r[k - 13] = sqrt(arg[k - 13]);
-    } else {
-        const double beta = Dm * sigma / kSqrt2;
-        p->tq = sqrt(39.1 + beta * beta);
-    }
-}
-
-__device__ inline void compute_phis_consts(const ModelDev& md, const double* th, const PhisPieces* pc,
-                                           PhisConsts* c) {
-    using namespace cdetail;
-    const double Gamma = th[IPA_GAMMA], sigma = th[IPA_SIGMA], mu = th[IPA_MU], fb = th[IPA_FB];
-    const double DG = th[IPA_PHIS_DG], Dm = th[IPA_PHIS_DM], om = th[IPA_PHIS_OMEGA];
-    const double GH = Gamma - 0.5 * DG, GL = Gamma + 0.5 * DG;
-    c->Gamma = Gamma;
-    c->sigma = sigma;
-    c->mu = mu;
-    c->fb = fb;
-    c->DG = DG;
-    c->Dm = Dm;
-    c->GH = GH;
-    c->GL = GL;
-    c->k_z = 1.0 / (kSqrt2 * sigma);
-    c->k_g = 1.0 / (2.0 * sigma * sigma);
-    c->cG = kInvSqrt2Pi / sigma;
-    c->s2 = sigma * sigma;
-    c->inv_s = 1.0 / sigma;
-    c->cH2 = 0.5 * GH * GH * sigma * sigma + tdetail::kLn2;
-    c->cL2 = 0.5 * GL * GL * sigma * sigma + tdetail::kLn2;
-    c->cC2 = 0.5 * (Gamma - Dm) * (Gamma + Dm) * sigma * sigma + tdetail::kLn2;
-    c->uH0 = GH * sigma * sigma;
-    c->uL0 = GL * sigma * sigma;
-    c->uC0 = Gamma * sigma * sigma;
-    c->beta = Dm * sigma / kSqrt2;
-    c->ph0 = Gamma * Dm * sigma * sigma;
-    const double rmax = fmax(fmax(GH, GL), Gamma);
-    const double tc = mu + (rmax * sigma * sigma + pc->tq * kSqrt2 * sigma);
-    c->tcut = tc == tc ? tc : INFINITY;
-    // amplitudes
-    const double x0 = th[IPA_A0SQ], xe = th[IPA_APESQ], F = th[IPA_FS];
-    const double xa = 1.0 - x0 - xe, sF = 1.0 - F;
-    c->x0 = x0;
-    c->xe = xe;
-    c->xa = xa;
-    c->F = F;
-    c->r0 = pc->r[0];
-    c->ra = pc->r[1];
-    c->re = pc->r[2];
-    c->rF = pc->r[3];
-    c->rs = pc->r[4];
-    for (int i = 0; i < 6; ++i) {
-        c->sw[i] = pc->sw[i];
-        c->cw[i] = pc->cw[i];
-    }
-    const double sn = pc->sn, cn = pc->cn;
-    c->c = cn;
-    c->s = sn;
-    c->D = 1.0 - 2.0 * om;
-    // b_k = m_k e^{i psi_k} (P-wave magnitudes carry 1 - F_S)
-    const double rFs = c->rF * c->rs;
-    const double mag[10] = {sF * x0, sF * xa, sF * xe, sF * c->ra * c->re, sF * c->r0 * c->ra, sF * c->r0 * c->re, F,
-                            rFs * c->ra, rFs * c->re, rFs * c->r0};
-    const double cps[10] = {1.0, 1.0, 1.0, c->cw[0], c->cw[1], c->cw[2], 1.0, c->cw[3], c->cw[4], c->cw[5]};
-    const double sps[10] = {0.0, 0.0, 0.0, c->sw[0], c->sw[1], c->sw[2], 0.0, c->sw[3], c->sw[4], -c->sw[5]};
-    for (int k = 0; k < 10; ++k) {
-        c->br[k] = mag[k] * cps[k];
-        c->bi[k] = mag[k] * sps[k];
-    }
-    // N = (16 pi / 9) (wL I_L + wH I_H): Pe = |A_0|^2 + |A_pa|^2, Po = |A_pe|^2 + |A_S|^2
-    const double FhL = pc->F[0], FlL = pc->F[1], FhH = pc->F[2], FlH = pc->F[3];
-    const double *dFhL = pc->dF[0], *dFlL = pc->dF[1], *dFhH = pc->dF[2], *dFlH = pc->dF[3];
-    const double IL = FhL - FlL, IH = FhH - FlH;
-    const double Pe = sF * (1.0 - xe), Po = sF * xe + F;
-    const double wL = Pe * (1.0 + cn) + Po * (1.0 - cn), wH = Pe * (1.0 - cn) + Po * (1.0 + cn);
-    const double K = 16.0 * kPi / 9.0;
-    double N = K * (wL * IL + wH * IH);
-    double dN[IPA_NPAR_PHIS];
-    for (int j = 0; j < 3; ++j) dN[j] = K * (wL * (dFhL[j] - dFlL[j]) + wH * (dFhH[j] - dFlH[j]));
-    dN[IPA_FB] = 0.0;
-    // dPe, dPo in A0sq, Apesq, F_S (the phases do not enter N)
-    const double dPe[6] = {0.0, -sF, 0.0, 0.0, -(1.0 - xe), 0.0};
-    const double dPo[6] = {0.0, sF, 0.0, 0.0, 1.0 - xe, 0.0};
-    for (int a = 0; a < 6; ++a)
-        dN[IPA_A0SQ + a] = K * ((dPe[a] * (1.0 + cn) + dPo[a] * (1.0 - cn)) * IL +
-                                (dPe[a] * (1.0 - cn) + dPo[a] * (1.0 + cn)) * IH);
-    dN[IPA_PHIS_DG] = K * (0.5 * wL * (dFhL[0] - dFlL[0]) - 0.5 * wH * (dFhH[0] - dFlH[0]));
-    dN[IPA_PHIS_DM] = 0.0;
-    dN[IPA_PHIS_PHIS] = K * ((-Pe * sn + Po * sn) * IL + (Pe * sn - Po * sn) * IH);
-    dN[IPA_PHIS_OMEGA] = 0.0;
-    dN[IPA_PHIS_CSP] = 0.0;     // the interference terms integrate to zero over the angles
-    dN[IPA_PHIS_QNORM] = 0.0;
-    double V = 2.0 * (md.t_hi - md.t_lo) * 8.0 * kPi;
-    const double qsel = th[IPA_PHIS_QNORM];
-    if (qsel != 0.0) {
-        // one tag: N_Q = N / 2 + Q K D sin(phi_s) (Pe - Po) Im I_c, I_c the integral
-        // of g(t - mu; Gamma - i Dm) over the range; the background over one tag
-        const double Q = qsel > 0.0 ? 1.0 : -1.0;
-        const double *eh = pc->ec[0], *el = pc->ec[1];
-        const double Ii = eh[1] - el[1];
-        const double dzr = eh[2] - el[2], dzi = eh[3] - el[3];
-        const double W = Pe - Po, D = 1.0 - 2.0 * om;
-        const double odd = Q * K * D * sn * W;
-        N = 0.5 * N + odd * Ii;
-        for (int j = 0; j < IPA_NPAR_PHIS; ++j) dN[j] *= 0.5;
-        dN[IPA_GAMMA] += odd * dzi;                      // d/dGamma = d/dz
-        dN[IPA_SIGMA] += odd * (eh[5] - el[5]);
-        dN[IPA_MU] += odd * (eh[7] - el[7]);
-        dN[IPA_PHIS_DM] += odd * (-dzr);                 // d/dDm = -i d/dz: Im(-i u) = -Re u
-        dN[IPA_PHIS_PHIS] += Q * K * D * cn * W * Ii;
-        dN[IPA_PHIS_OMEGA] += Q * K * (-2.0) * sn * W * Ii;
-        for (int a = 0; a < 6; ++a) dN[IPA_A0SQ + a] += Q * K * D * sn * (dPe[a] - dPo[a]) * Ii;
-        V *= 0.5;
-    }
-    const double inv_N = 1.0 / N;
-    c->N = N;
-    c->inv_N = inv_N;
-    c->inv_V = 1.0 / V;
-    c->cs = (1.0 - fb) * inv_N;
-    c->cb = fb / V;
-    for (int j = 0; j < IPA_NPAR_PHIS; ++j) c->dlnN[j] = dN[j] * inv_N;
-    c->csp = th[IPA_PHIS_CSP];
-    c->qsel = qsel > 0.0 ? 1.0 : (qsel < 0.0 ? -1.0 : 0.0);
-    c->pad_ = 0.0;
-}
-
-// One thread per segment (many segments: the warp's lanes are segments).
-__global__ void phis_consts_kernel(ModelDev m, const double* __restrict__ theta, int n_seg, Consts* __restrict__ out) {
-    asm volatile("griddepcontrol.launch_dependents;");
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_seg) return;
-    const double* th = theta + (size_t)s * m.n_par;
-    PhisPieces p;
-    for (int k = 0; k < kPhisPieces; ++k) phis_piece(m, th, k, &p);
-    compute_phis_consts(m, th, &p, reinterpret_cast<PhisConsts*>(out + s));
-}
-
-// One four-warp block per segment (few segments): warp 0 evaluates the four
-// real edges in lanes 0-3, warp 1 the two complex edges, warp 2 the seven
-// sincos, warp 3 the six square roots; thread 0 assembles the record.
-__global__ void __launch_bounds__(128) phis_consts_block_kernel(ModelDev m, const double* __restrict__ theta,
-                                                                Consts* __restrict__ out) {
-    asm volatile("griddepcontrol.launch_dependents;");
-    __shared__ PhisPieces p;
-    const double* th = theta + (size_t)blockIdx.x * m.n_par;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int first[4] = {0, 4, 6, 13}, count[4] = {4, 2, 7, 6};
-    if (l < count[w]) phis_piece(m, th, first[w] + l, &p);
-    __syncthreads();
-    if (threadIdx.x == 0) compute_phis_consts(m, th, &p, reinterpret_cast<PhisConsts*>(out + blockIdx.x));
 }
 
 // Per-warp copy: the record and Cq_kj = (cs / 2) C_kj c_k (the basis factor c_k
@@ -945,14 +685,6 @@ ipa_status launch_phis_toygen(const ModelDev& m, const Consts* consts, uint64_t 
     return cuda_fail(cudaGetLastError(), "phi_s toygen kernel launch");
 }
 
-ipa_status launch_phis_consts(const ModelDev& m, const double* theta, int n_seg, Consts* out, cudaStream_t st) {
-    if (n_seg <= 0) return IPA_OK;
-    if (n_seg < 64)
-        phis_consts_block_kernel<<<n_seg, 128, 0, st>>>(m, theta, out);
-    else
-        phis_consts_kernel<<<(n_seg + 63) / 64, 64, 0, st>>>(m, theta, n_seg, out);
-    return cuda_fail(cudaGetLastError(), "phi_s consts kernel launch");
-}
 
 namespace {
 // ipa_nll_grad_combine for the phi_s model: the kernel's last reduction level
