@@ -193,7 +193,8 @@ COUNT_CAPTURES = {
     "nll_kernel<4D, grad>": ("counts_4d.csv", "bench.py --profile-case", 8_000_000,
                              ["nll.cu", "angular.cuh"] + COUNT_COMMON),
     "phis_kernel<grad>": ("counts_phis.csv", "bench.py --profile-case-phis", 8_000_000,
-                          ["phis.cu", "angular.cuh", "tagged.cuh", "faddeeva.cuh", "consts.cuh", "philox.cuh"] + COUNT_COMMON),
+                          ["phis.cu", "phis_consts.cuh", "angular.cuh", "tagged.cuh", "faddeeva.cuh", "consts.cuh",
+                           "philox.cuh"] + COUNT_COMMON),
     "tag_kernel<grad>": ("counts_tag.csv", "bench.py --profile-case-tagged", 8_000_000,
                          ["tagged.cu", "tagged.cuh", "faddeeva.cuh", "consts.cuh"] + COUNT_COMMON),
 }
