@@ -137,7 +137,7 @@ def test_deterministic_and_segment_equals_solo(env):
 
 def test_many_segments_equal_solo(env):
     """80 segments (the constants are then computed one thread per fit) against
-    solo calls (one four-warp block per fit): bitwise equal, with every
+    solo calls (one six-warp block per fit): bitwise equal, with every
     parameter moved so that every row of the constants is exercised."""
     O, G, torch, api = env
     m = api.model_4d()

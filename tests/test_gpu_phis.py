@@ -178,6 +178,40 @@ def test_segments_equal_solo(env):
         assert np.array_equal(seg[i], solo), i
 
 
+def test_many_segments_equal_solo(env):
+    """72 segments (the record then computed one thread per segment) against
+    solo calls (one block per segment): bitwise equal, every parameter moved and
+    the normalisation over both tags, the tag +1 and the tag -1 in turn (the
+    complex edges of the one-tag record in both layouts)."""
+    O, F, G, torch, api = env
+    m = api.model_phis(0.0, 15.0)
+    rng = np.random.default_rng(32)
+    n_seg = 72
+    sizes = rng.integers(0, 1200, n_seg)
+    parts = [synth.events_phis(int(k), 200 + i, weighted=True) for i, k in enumerate(sizes)]
+    cols = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    ev = G.to_dev(cols)
+    names = sorted(THETAS)
+    ths = np.stack([THETAS[names[i % len(names)]] for i in range(n_seg)])
+    ths[:, 0] += rng.normal(0, 0.02, n_seg)
+    ths[:, 1] += rng.normal(0, 0.003, n_seg)
+    ths[:, 2] += rng.normal(0, 0.005, n_seg)
+    ths[:, 4:6] += rng.normal(0, 0.01, (n_seg, 2))
+    ths[:, 6:8] += rng.normal(0, 0.3, (n_seg, 2))
+    ths[:, 8] = np.clip(ths[:, 8] + rng.normal(0, 0.01, n_seg), 0.0, 1.0)
+    ths[:, 9] += rng.normal(0, 0.3, n_seg)
+    ths[:, 10] += rng.normal(0, 0.01, n_seg)
+    ths[:, 11] += rng.normal(0, 0.2, n_seg)
+    ths[:, 12] += rng.normal(0, 0.3, n_seg)
+    ths[:, 13] = np.clip(ths[:, 13] + rng.normal(0, 0.02, n_seg), 0.0, 0.5)
+    ths[:, 15] = np.array([0.0, 1.0, -1.0])[np.arange(n_seg) % 3]
+    off = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int64, device="cuda")
+    seg = api.ipa_nll_grad_segmented(m, ev, off, torch.tensor(ths, device="cuda")).cpu().numpy()
+    for i in (0, 1, 2, 31, 64, 70, 71):
+        solo = api.ipa_nll_grad(m, G.to_dev(parts[i]), torch.tensor(ths[i], device="cuda")).cpu().numpy()
+        assert np.array_equal(seg[i], solo), i
+
+
 def _sample(F, m, th, n, seed):
     """Events of the model by accept-reject (uniform t, angles, tag; the bound is
     1.5 x the largest density of 2e5 candidates, checked against every candidate)."""

@@ -155,6 +155,35 @@ def test_segments_equal_solo(env):
         assert np.array_equal(seg[i], solo), i
 
 
+def test_many_segments_equal_solo(env):
+    """80 segments (the record then computed one thread per segment) against
+    solo calls (one block per segment): bitwise equal, every parameter moved so
+    that every field of the record is exercised."""
+    O, T, G, torch, api = env
+    m = api.model_tagged(0.0, 15.0)
+    rng = np.random.default_rng(31)
+    n_seg = 80
+    sizes = rng.integers(0, 1500, n_seg)
+    parts = [synth.events_tagged(int(k), 100 + i, weighted=True) for i, k in enumerate(sizes)]
+    cols = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    ev = G.to_dev(cols)
+    names = sorted(THETAS)
+    ths = np.stack([THETAS[names[i % len(names)]] for i in range(n_seg)])
+    ths[:, 0] += rng.normal(0, 0.02, n_seg)
+    ths[:, 1] += rng.normal(0, 0.003, n_seg)
+    ths[:, 2] += rng.normal(0, 0.005, n_seg)
+    ths[:, 3] = np.clip(ths[:, 3] + rng.normal(0, 0.01, n_seg), 0.0, 1.0)
+    ths[:, 4] += rng.normal(0, 0.01, n_seg)
+    ths[:, 5] += rng.normal(0, 0.2, n_seg)
+    ths[:, 6] += rng.normal(0, 0.3, n_seg)
+    ths[:, 7] = np.clip(ths[:, 7] + rng.normal(0, 0.02, n_seg), 0.0, 0.5)
+    off = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int64, device="cuda")
+    seg = api.ipa_nll_grad_segmented(m, ev, off, torch.tensor(ths, device="cuda")).cpu().numpy()
+    for i in (0, 1, 23, 47, 64, 79):
+        solo = api.ipa_nll_grad(m, G.to_dev(parts[i]), torch.tensor(ths[i], device="cuda")).cpu().numpy()
+        assert np.array_equal(seg[i], solo), i
+
+
 @pytest.mark.parametrize("th", [TRUTH, THETAS["fast_mixing"]], ids=["truth", "fast_mixing"])
 def test_toys_bit_exact(env, th):
     O, T, G, torch, api = env
