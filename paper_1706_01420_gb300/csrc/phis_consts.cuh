@@ -5,7 +5,8 @@
 // the table-driven erfcx and exp, products with reciprocals instead of
 // divisions, independent pieces in different warps).  The normalisation
 // over one tag (qsel != 0) adds the two complex edges of the oscillating
-// time function (edge_c, library functions and the Faddeeva function).
+// time function (cedge_F: the Faddeeva function, the table erfcx, exp and
+// sin/cos).
 //
 // Normalisation (both tags, the interference terms integrate to zero over
 // the angles): N = (16 pi / 9) (wL I_L + wH I_H), I_x = F(t_hi) - F(t_lo)
@@ -46,61 +47,6 @@ struct PhisConsts {
 static_assert(sizeof(PhisConsts) <= sizeof(Consts), "PhisConsts must fit a Consts slot");
 static_assert(sizeof(PhisConsts) % 16 == 0, "PhisConsts must be a multiple of 16 bytes");
 constexpr int kPhisDoubles = sizeof(PhisConsts) / sizeof(double);
-
-// Complex antiderivative of the oscillating time function: F(tau) with
-// dF/dtau = g(tau; z), z = zr + i zi, F = (Phi(tau / sigma) - g) / z (from
-// g' = G - z g), and dF/dz, dF/dsigma, dF/dmu = -(F + dg/dz) / z,
-// (-(tau / sigma) G - dg/dsigma) / z, -g with dg/dz = (z s^2 - tau) g - s^2 G and
-// dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G.  g through the Faddeeva
-// function: 1/2 e^{-tau^2 / 2 s^2} w(x + i y) for y >= 0, else
-// e^{-z tau + z^2 s^2 / 2} - 1/2 e^{-tau^2 / 2 s^2} w(-x - i y), with
-// x + i y = i (z s^2 - tau) / (sqrt2 s).  Out: F, dF/dz, dF/dsigma, dF/dmu as
-// (re, im) pairs.
-__device__ inline void edge_c(double tau, double zr, double zi, double sigma, double* out) {
-    using namespace cdetail;
-    const double s2 = sigma * sigma;
-    const double y = (zr * s2 - tau) / (kSqrt2 * sigma), x = -zi * sigma / kSqrt2;
-    const double gx = exp(-tau * tau / (2.0 * s2));
-    double wr, wi, gr, gi;
-    if (y >= 0.0) {
-        faddeeva_uhp(x, y, &wr, &wi);
-        gr = 0.5 * gx * wr;
-        gi = 0.5 * gx * wi;
-    } else {
-        faddeeva_uhp(-x, -y, &wr, &wi);
-        const double a = -zr * tau + 0.5 * s2 * (zr * zr - zi * zi), b = -zi * tau + zr * zi * s2;
-        double sb, cb;
-        sincos(b, &sb, &cb);
-        const double ea = exp(a);
-        gr = ea * cb - 0.5 * gx * wr;
-        gi = ea * sb - 0.5 * gx * wi;
-    }
-    const double G = gx * kInvSqrt2Pi / sigma;
-    const double Phi = edge_phi(tau, sigma);
-    const double n2 = zr * zr + zi * zi, ir = zr / n2, ii = -zi / n2;     // 1/z
-    // F = (Phi - g) / z
-    const double nr = Phi - gr, ni = -gi;
-    const double Fr = nr * ir - ni * ii, Fi = nr * ii + ni * ir;
-    // dg/dz = (z s^2 - tau) g - s^2 G
-    const double pr = zr * s2 - tau, pi = zi * s2;
-    const double dzr = pr * gr - pi * gi - s2 * G, dzi = pr * gi + pi * gr;
-    // dF/dz = -(F + dg/dz) / z
-    const double ar = -(Fr + dzr), ai = -(Fi + dzi);
-    out[2] = ar * ir - ai * ii;
-    out[3] = ar * ii + ai * ir;
-    // dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G
-    const double z2r = (zr * zr - zi * zi) * sigma, z2i = 2.0 * zr * zi * sigma;
-    const double dsr = z2r * gr - z2i * gi - (zr * sigma + tau / sigma) * G;
-    const double dsi = z2r * gi + z2i * gr - zi * sigma * G;
-    // dF/dsigma = (-(tau / sigma) G - dg/dsigma) / z
-    const double br = -(tau / sigma) * G - dsr, bi = -dsi;
-    out[4] = br * ir - bi * ii;
-    out[5] = br * ii + bi * ir;
-    out[0] = Fr;
-    out[1] = Fi;
-    out[6] = -gr;
-    out[7] = -gi;
-}
 
 namespace pdetail {
 
@@ -276,6 +222,96 @@ __device__ inline void b_entry(int k, const double* th, const double* r, const d
     *bi = mag * sp;
 }
 
+// The complex antiderivative of the oscillating time function (the
+// normalisation over one tag): F(tau) with dF/dtau = g(tau; z), z = zr + i zi
+// = Gamma - i Dm, F = (Phi(tau / sigma) - g) / z (from g' = G - z g), and
+// dF/dz, dF/dsigma, dF/dmu = -(F + dg/dz) / z, (-(tau / sigma) G - dg/dsigma)
+// / z, -g with dg/dz = (z s^2 - tau) g - s^2 G and dg/dsigma = z^2 sigma g -
+// (z sigma + tau / sigma) G.  g through the Faddeeva function: 1/2 gx w(x + i
+// y) for y >= 0, else e^{-z tau + z^2 s^2 / 2} - 1/2 gx w(-x - i y), with gx =
+// exp(-tau^2 / 2 s^2) and x + i y = i (z s^2 - tau) / (sqrt2 s).  Two halves
+// of independent pieces (cedge_fad, cedge_exp) and their combination
+// (cedge_F); rs = 1 / sigma, edge e = 0 (t_hi) or 1 (t_lo).
+struct CEdgeArg {
+    double tau, xt, y, x;        // tau, tau / sigma, and x + i y above
+};
+__device__ inline CEdgeArg cedge_arg(const ModelDev& m, const double* th, int e, double rs) {
+    using namespace cdetail;
+    const double sigma = th[IPA_SIGMA], zr = th[IPA_GAMMA], zi = -th[IPA_PHIS_DM];
+    CEdgeArg a;
+    a.tau = edge_tau(m, th[IPA_MU], e);
+    a.xt = a.tau * rs;
+    a.y = (zr * sigma - a.xt) * kInvSqrt2;
+    a.x = -zi * sigma * kInvSqrt2;
+    return a;
+}
+
+// (Re w, Im w, gx): w at x + i y (y >= 0) or at -x - i y (y < 0).
+__device__ inline void cedge_fad(const ModelDev& m, const double* th, int e, double rs, const MathTables* mt,
+                                 double* out) {
+    const CEdgeArg a = cedge_arg(m, th, e, rs);
+    const bool up = a.y >= 0.0;
+    faddeeva_uhp(up ? a.x : neg_bits(a.x), up ? a.y : neg_bits(a.y), &out[0], &out[1]);
+    out[2] = exp_fast(cdetail::gauss_exponent(a.xt), mt);
+}
+
+// (erfcx for Phi, e^{Re(-z tau + z^2 s^2 / 2)}, sin and cos of its imaginary part).
+__device__ inline void cedge_exp(const ModelDev& m, const double* th, int e, double rs, const MathTables* mt,
+                                 double* out) {
+    using namespace cdetail;
+    const CEdgeArg a = cedge_arg(m, th, e, rs);
+    const double sigma = th[IPA_SIGMA], zr = th[IPA_GAMMA], zi = -th[IPA_PHIS_DM];
+    const double s2 = sigma * sigma;
+    out[0] = edge_erfcx(edge_w(a.xt), mt);
+    const double er = -zr * a.tau + 0.5 * s2 * (zr * zr - zi * zi), ei = -zi * a.tau + zr * zi * s2;
+    out[1] = exp_fast(er, mt);
+    sincos_fast(ei, mt, &out[2], &out[3]);
+}
+
+// F, dF/dz, dF/dsigma, dF/dmu as (re, im) pairs at edge e from fa = cedge_fad
+// and ex = cedge_exp.
+__device__ inline void cedge_F(const ModelDev& m, const double* th, int e, double rs, const double* fa,
+                               const double* ex, double* out) {
+    using namespace cdetail;
+    const CEdgeArg a = cedge_arg(m, th, e, rs);
+    const double sigma = th[IPA_SIGMA], zr = th[IPA_GAMMA], zi = -th[IPA_PHIS_DM];
+    const double s2 = sigma * sigma, tau = a.tau, xt = a.xt, gx = fa[2];
+    double gr, gi;
+    if (a.y >= 0.0) {
+        gr = 0.5 * gx * fa[0];
+        gi = 0.5 * gx * fa[1];
+    } else {
+        gr = ex[1] * ex[3] - 0.5 * gx * fa[0];
+        gi = ex[1] * ex[2] - 0.5 * gx * fa[1];
+    }
+    const double G = gx * (kInvSqrt2Pi * rs);
+    const double b2 = 0.5 * (gx * ex[0]);
+    const double Phi = negative(edge_w(xt)) ? 1.0 - b2 : b2;
+    const double rn = recip(zr * zr + zi * zi), ir = zr * rn, ii = -zi * rn;    // 1/z
+    // F = (Phi - g) / z
+    const double nr = Phi - gr, ni = -gi;
+    const double Fr = nr * ir - ni * ii, Fi = nr * ii + ni * ir;
+    // dg/dz = (z s^2 - tau) g - s^2 G
+    const double pr = zr * s2 - tau, pi = zi * s2;
+    const double dzr = pr * gr - pi * gi - s2 * G, dzi = pr * gi + pi * gr;
+    // dF/dz = -(F + dg/dz) / z
+    const double ar = -(Fr + dzr), ai = -(Fi + dzi);
+    out[2] = ar * ir - ai * ii;
+    out[3] = ar * ii + ai * ir;
+    // dg/dsigma = z^2 sigma g - (z sigma + tau / sigma) G
+    const double z2r = (zr * zr - zi * zi) * sigma, z2i = 2.0 * zr * zi * sigma;
+    const double dsr = z2r * gr - z2i * gi - (zr * sigma + xt) * G;
+    const double dsi = z2r * gi + z2i * gr - zi * sigma * G;
+    // dF/dsigma = (-(tau / sigma) G - dg/dsigma) / z
+    const double br = -xt * G - dsr, bi = -dsi;
+    out[4] = br * ir - bi * ii;
+    out[5] = br * ii + bi * ir;
+    out[0] = Fr;
+    out[1] = Fi;
+    out[6] = -gr;
+    out[7] = -gi;
+}
+
 // N over both tags, or over the tag qsel (ec: the complex edges at t_hi, t_lo).
 __device__ inline double norm_N(const double* th, const double* F, const double* ec, double sn, double cn) {
     const Amp a = amp(th);
@@ -352,10 +388,14 @@ __device__ inline void phis_consts_thread(const ModelDev& m, const double* th, c
     }
     for (int i = 0; i < 7; ++i) sincos_fast(phase_arg(th, i), mt, &sw[i], &cw[i]);
     for (int e = 0; e < 2; ++e) {
-        if (th[IPA_PHIS_QNORM] != 0.0)
-            edge_c(cdetail::edge_tau(m, th[IPA_MU], e), th[IPA_GAMMA], -th[IPA_PHIS_DM], th[IPA_SIGMA], ec + 8 * e);
-        else
+        if (th[IPA_PHIS_QNORM] != 0.0) {
+            double fa[3], ex[4];
+            cedge_fad(m, th, e, rc[0], mt, fa);
+            cedge_exp(m, th, e, rc[0], mt, ex);
+            cedge_F(m, th, e, rc[0], fa, ex, ec + 8 * e);
+        } else {
             for (int i = 0; i < 8; ++i) ec[8 * e + i] = 0.0;
+        }
     }
     theta_fields(th, c);
     scale_fields(th, rc[0], r[5], c);
@@ -380,6 +420,7 @@ struct PhisBlockScratch {
     double X[6], Ex[6];           // real-edge pieces (edge_X, edge_exp)
     double r[6];                  // sqrt of x0, xa, xe, F, 1 - F; the cut's root
     double sw[7], cw[7];          // sin, cos of the strong phases and of phi_s
+    double cf[2][3], cx[2][4];    // complex-edge pieces (cedge_fad, cedge_exp) at t_hi, t_lo
     double ec[16];                // complex edges at t_hi and t_lo (one-tag normalisation)
     double F[4], dF[4][3];
     PhisConsts c;
@@ -391,10 +432,12 @@ constexpr int kPhisConstsBlock = 256;
 // the same code:
 //   phase 1  warp 0: the six erfcx of the real edges; warp 1: their six
 //            exponentials; warp 2: seven sine/cosine pairs; warp 3: six square
-//            roots; warp 4: four reciprocals; warp 5: the complex edges (one
-//            tag only); warp 6: the fields of theta alone;
+//            roots; warp 4: four reciprocals; warps 5 and 7: the two halves of
+//            the complex edges' pieces (one tag only); warp 6: the fields of
+//            theta alone;
 //   phase 2  warp 0: F and its derivatives at the four real edges; warp 1: the
 //            fields of 1/sigma; warp 2: b_k (lane k) and the amplitude fields;
+//            warp 5: the complex edges;
 //   phase 3  warps 0-2: dN/dtheta_j / N (a parameter per lane) and the fields of 1/N;
 // then every thread copies part of the record out.
 __device__ inline void phis_consts_block(const ModelDev& m, const double* th, PhisConsts* c, PhisBlockScratch* S) {
@@ -416,15 +459,13 @@ __device__ inline void phis_consts_block(const ModelDev& m, const double* th, Ph
     } else if (w == 4) {
         if (lane < 4) S->rc[lane] = cdetail::recip(recip_arg(m, th, lane));
     } else if (w == 5) {
-        if (lane < 2) {
-            if (th[IPA_PHIS_QNORM] != 0.0)
-                edge_c(cdetail::edge_tau(m, th[IPA_MU], lane), th[IPA_GAMMA], -th[IPA_PHIS_DM], th[IPA_SIGMA],
-                       S->ec + 8 * lane);
-            else
-                for (int i = 0; i < 8; ++i) S->ec[8 * lane + i] = 0.0;
-        }
+        if (lane < 2 && th[IPA_PHIS_QNORM] != 0.0)
+            cedge_fad(m, th, lane, cdetail::recip(th[IPA_SIGMA]), &S->mt, S->cf[lane]);
     } else if (w == 6) {
         if (lane == 0) theta_fields(th, &S->c);
+    } else if (w == 7) {
+        if (lane < 2 && th[IPA_PHIS_QNORM] != 0.0)
+            cedge_exp(m, th, lane, cdetail::recip(th[IPA_SIGMA]), &S->mt, S->cx[lane]);
     }
     __syncthreads();
 
@@ -437,6 +478,13 @@ __device__ inline void phis_consts_block(const ModelDev& m, const double* th, Ph
     } else if (w == 2) {
         if (lane < 10) b_entry(lane, th, S->r, S->sw, S->cw, &S->c.br[lane], &S->c.bi[lane]);
         else if (lane == 10) amp_fields(th, S->r, S->sw, S->cw, S->sw[6], S->cw[6], &S->c);
+    } else if (w == 5) {
+        if (lane < 2) {
+            if (th[IPA_PHIS_QNORM] != 0.0)
+                cedge_F(m, th, lane, S->rc[0], S->cf[lane], S->cx[lane], S->ec + 8 * lane);
+            else
+                for (int i = 0; i < 8; ++i) S->ec[8 * lane + i] = 0.0;
+        }
     }
     __syncthreads();
 
