@@ -633,8 +633,8 @@ def main():
     value = n_total / (ms_max * 1e-3) / 1e9
 
     # kernel-only time of the dominant kernel, measured with events on its stream:
-    # the step is [constants kernel (1 thread per fit), fused NLL+grad kernel]; the
-    # constants kernel is timed alone and subtracted.
+    # the step is [constants kernel (one block for the fit), fused NLL+grad kernel];
+    # a constants-only call (n = 0) is timed alone and subtracted.
     k_ev0, k_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cons = []
     for i in range(20):
