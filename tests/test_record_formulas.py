@@ -19,7 +19,6 @@ import math
 import os
 import re
 
-import mpmath as mp
 import numpy as np
 import pytest
 from scipy.special import erfcx
@@ -53,7 +52,7 @@ def _edge(tau, Gamma, sigma):
     return np.array([F, -(F + dg_dG) * rG, (-(x * G) - dg_ds) * rG, -g])
 
 
-def _edge_mp(tau, Gamma, sigma):
+def _edge_mp(mp, tau, Gamma, sigma):
     """The same quantities from the closed form in 50-digit arithmetic."""
     mp.mp.dps = 50
     tau, Gamma, sigma = mp.mpf(tau), mp.mpf(Gamma), mp.mpf(sigma)
@@ -77,9 +76,11 @@ CASES = [(0.66, 0.045, 0.0, 0.0, 15.0), (0.66, 0.045, 0.01, 0.3, 15.0), (0.66, 0
 
 @pytest.mark.parametrize("case", CASES)
 def test_edges_through_the_gaussian_factor(case):
+    mp = pytest.importorskip("mpmath")
     Gamma, sigma, mu, lo, hi = case
     got = _edge(hi - mu, Gamma, sigma) - _edge(lo - mu, Gamma, sigma)
-    ref = np.array([float(a - b) for a, b in zip(_edge_mp(hi - mu, Gamma, sigma), _edge_mp(lo - mu, Gamma, sigma))])
+    ref = np.array([float(a - b)
+                    for a, b in zip(_edge_mp(mp, hi - mu, Gamma, sigma), _edge_mp(mp, lo - mu, Gamma, sigma))])
     lib = O.time_norm_grad(Gamma, sigma, mu, lo, hi)
     # every component as close to the 50-digit value as the library evaluation
     # of the same formulas, or within 1e-13: F = (Phi - g) / Gamma itself
@@ -92,6 +93,7 @@ def test_edges_through_the_gaussian_factor(case):
 
 
 def test_dropped_erfcx_term_is_below_half_an_ulp():
+    mp = pytest.importorskip("mpmath")
     # at the cut the dropped term erfc(6.25) / 2 is below half an ulp of 1 (Phi)
     # and of E (g, relative), so the sum is unchanged in double precision
     dropped = float(mp.erfc(6.25)) / 2
